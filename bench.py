@@ -1,0 +1,346 @@
+"""FAMST build throughput on GB300.
+
+Default workload: 1,000,000 unit vectors in 128-D drawn from a 1,000-cluster
+mixture (k = 32, lambda = 10). A step is one full FAMST build (kNN graph,
+components, connect, refine, MST, FP64 weight) of one cloud that is already
+resident in HBM. Timing: W warm-up builds, then K builds between CUDA events
+on the library's stream, bracketed by barrier + synchronize; max over ranks.
+The cloud (512 MB) is larger than L2, so no flush is needed between steps.
+
+Under torchrun each rank builds its own cloud (seed + rank): independent
+problems, weak scaling, no data-path collective.
+
+``--impl reference`` times the CPU oracle (the only implementation of the
+method besides this one) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "points/sec for full FAMST build"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}
+SMS = 152
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        p["_source"] = "measured"
+        return p
+    except Exception:
+        p = dict(FALLBACK)
+        p["_source"] = "fallback"
+        return p
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clocks, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def kernel_source_hash(prec: str) -> str:
+    f = "knn_fp32.cu" if prec == "fp32" else "knn_tc.cu"
+    p = os.path.join(ROOT, "paper_2507_14261_gb300", "csrc", f)
+    try:
+        with open(p, "rb") as fh:
+            return hashlib.sha256(fh.read()).hexdigest()[:16]
+    except OSError:
+        return ""
+
+
+def traffic_from_profile(workload: str, prec: str):
+    """DRAM bytes per launch of the distance kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "knn_traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    for r in rec.get("entries", []):
+        if r.get("prec") == prec and r.get("source_sha") == kernel_source_hash(prec):
+            per_unit = r.get("dram_bytes_per_query_row_per_key")
+            if per_unit is None:
+                continue
+            w = workloads.get(workload)
+            return float(per_unit) * w.n * w.n
+    return None
+
+
+def cpu_baseline(X, k: int, budget_s: float = 15.0):
+    """The oracle's brute-force kNN (Phase 1, the dominant cost of the
+    oracle's build) on the first S query rows of the cloud, S sized to the
+    time budget; returns points/s and the sample description."""
+    import oracle
+    oracle.build()
+    n = X.shape[0]
+    cores = os.cpu_count() or 1
+    probe = max(cores, 8)
+    t0 = time.perf_counter()
+    oracle.knn(X, k, rows=(0, probe), threads=cores)
+    dt = time.perf_counter() - t0
+    S = int(max(probe, min(n, probe * budget_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.knn(X, k, rows=(0, S), threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": S / dt, "unit": "points/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle brute-force exact kNN of query rows 0..{S - 1} against all {n} "
+                      f"points (Phase 1; the oracle's later phases cost <1% of it and are not "
+                      f"timed); {dt:.1f} s"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w = workloads.get(args.workload)
+    X = w.points()
+    cores = os.cpu_count() or 1
+    # rows per step sized so that the whole run stays within a few minutes
+    probe = max(cores, 8)
+    t0 = time.perf_counter()
+    oracle.knn(X, w.k, rows=(0, probe), threads=cores)
+    per_row = (time.perf_counter() - t0) / probe
+    S = int(max(probe, min(w.n, 10.0 / max(per_row, 1e-9))))
+    times = []
+    for s in range(args.warmup + args.steps):
+        r0 = (s * S) % max(1, w.n - S)
+        t0 = time.perf_counter()
+        oracle.knn(X, w.k, rows=(r0, r0 + S), threads=cores)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = S * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "points/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "n": w.n, "d": w.d, "k": w.k, "lambda": w.lam,
+                   "sample_rows_per_step": S},
+        "cpu_baseline": {"value": value, "unit": "points/s", "cores": cores, "kind": "oracle",
+                         "sample": f"per step: oracle exact kNN of {S} query rows against all "
+                                   f"{w.n} points (Phase 1)"},
+        "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="famst", choices=["famst", "reference"])
+    ap.add_argument("--workload", default="sphere_1m")
+    ap.add_argument("--prec", default=os.environ.get("FAMST_BENCH_PREC", "fp32"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    import torch
+    import paper_2507_14261_gb300 as fam
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    w = workloads.get(args.workload)
+    X_np = workloads.Workload(w.name, w.n, w.d, w.k, w.lam, w.seed + rank, w.kind).points()
+    X = torch.from_numpy(X_np).cuda()
+    ctx = fam.Context(local)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    infos = []
+    for _ in range(args.warmup):
+        tree, info = ctx.build(X, w.k, w.lam, 1, args.prec)
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = ctx.launches
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.steps):
+        tree, info = ctx.build(X, w.k, w.lam, 1, args.prec)
+        infos.append(info.as_dict())
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    launches = ctx.launches - launches0
+    ms = e0.elapsed_time(e1)
+    if pg is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * w.n * args.steps / (ms / 1e3)
+
+    # end to end through the host-buffer entry point: pinned X in, tree out
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X_np).pin_memory()
+        out = (torch.empty(w.n - 1, dtype=torch.int32).pin_memory(),
+               torch.empty(w.n - 1, dtype=torch.int32).pin_memory(),
+               torch.empty(w.n - 1, dtype=torch.float32).pin_memory())
+        ctx.build_host(Xh, w.k, w.lam, 1, args.prec, out=out)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.build_host(Xh, w.k, w.lam, 1, args.prec, out=out)
+        barrier()
+        dt = time.perf_counter() - t0
+        if pg is not None:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": world * w.n * args.steps / dt, "unit": "points/s",
+               "h2d_bytes_per_step": int(X_np.nbytes),
+               "d2h_bytes_per_step": int((w.n - 1) * 12 + 8)}
+
+    # roofline of the distance kernel (Phase 1), timed by the library's
+    # CUDA events on its stream during the timed builds
+    pk = peaks()
+    ms_knn = statistics.mean(i["ms_knn"] for i in infos)
+    if args.prec == "fp32":
+        # canonical chain: FSUB + FFMA per (query, key, dim) = 3 flops;
+        # FP32 pipe peak = SMs x 128 lanes x clock x 1.5 flops per instruction
+        flops = 3.0 * w.n * w.n * w.d
+        peak = SMS * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 * 1.5 / 1e12
+        bound = "alu"
+    else:
+        flops = 2.0 * w.n * w.n * w.d
+        peak = pk["bf16_tflops"]
+        bound = "tensor"
+    achieved = flops / (ms_knn / 1e3) / 1e12
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_from_profile(w.name, args.prec),
+                "kernel": "knn_fp32_kernel" if args.prec == "fp32" else "knn_tc_kernel",
+                "peak_source": pk["_source"] if bound != "alu" else
+                "derived: 152 SMs x 128 FP32 lanes x max SM clock x 1.5 flop/instr",
+                "ms_per_launch": ms_knn}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(X_np, w.k)
+
+    last = infos[-1]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.prec == "fp32" else "bf16",
+            "data": "synthetic (seeded; inputs larger than L2, no flush)",
+            "config": {"workload": w.name, "n": w.n, "d": w.d, "k": w.k, "lambda": w.lam,
+                       "prec": args.prec, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (X = %d MB)" % (X_np.nbytes >> 20)},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches,
+            "stages_ms": {k2: last[k2] for k2 in ("ms_knn", "ms_components", "ms_connect",
+                                                  "ms_refine", "ms_mst", "ms_total")},
+            "build": {"t": last["t"], "m": last["m"], "refine_sweeps": last["refine_sweeps"],
+                      "boruvka_rounds": last["boruvka_rounds"], "W": last["W"],
+                      "W64": last["W64"], "uncertified_rows": last["uncertified_rows"]},
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,205 @@
+/*
+ * famst.h -- C ABI of the GB300 (sm_103a) FAMST library.
+ *
+ * FAMST (Almansoori & Telek) builds an approximate Euclidean minimum
+ * spanning tree of n points in d dimensions in three phases (Algorithm 1):
+ *   Phase 1  kNN graph of the points                       famst_knn_graph
+ *   Phase 2  connected components of the undirected graph  famst_components
+ *            (Algorithm 2) and lambda inter-component edges
+ *            per component pair (Algorithm 3)              famst_connect
+ *   Phase 3  neighbourhood refinement of those edges,
+ *            repeated until no edge changes (Algorithm 4)  famst_refine
+ *   then     Kruskal-equivalent MST of kNN edges + E       famst_mst
+ * famst_build runs all of it. famst_mst_backward differentiates the tree
+ * weight with respect to the points; famst_build_batched runs many clouds.
+ *
+ * Conventions for every call:
+ *  - Pointers are DEVICE pointers owned by the caller unless the argument
+ *    is documented as HOST. Nothing is freed or retained by the library.
+ *  - X is row-major float32, n rows of d contiguous floats (stride d).
+ *  - Vertex ids are int32 (n < 2^31); n*k must be < 2^31.
+ *  - Work is enqueued on the context's stream (famst_set_stream; default
+ *    is the legacy default stream). Calls that return a value through a
+ *    HOST pointer synchronise that stream before returning; the others
+ *    return once the work is enqueued.
+ *  - The library owns one device workspace per context; it grows on demand
+ *    (cudaMalloc) and is freed by famst_destroy. A context must not be used
+ *    from two host threads at once.
+ *  - Errors: every call returns a famst_status. On error the outputs are
+ *    undefined but the context stays usable. Nothing aborts.
+ *
+ * Distances. Every distance the library computes, stores or compares is the
+ * canonical FP32 Euclidean distance
+ *     p = 0; for t = 0..d-1: delta = x[t] - y[t]; p = fmaf(delta, delta, p);
+ *     w = sqrtf(p)        (all operations IEEE round-to-nearest)
+ * It is symmetric bit for bit. Orders: neighbours of a row by (w, id);
+ * edges by (w, min id, max id). Weights of trees are summed in FP64.
+ */
+#ifndef FAMST_H
+#define FAMST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t famst_status;
+
+#define FAMST_OK                  0
+#define FAMST_ERR_INVALID_ARG    -1  /* null pointer, bad size, k or lambda out of range */
+#define FAMST_ERR_CAPACITY       -2  /* output buffer too small; the required size is returned */
+#define FAMST_ERR_NO_CONVERGENCE -3  /* refinement still changing after max_iters sweeps */
+#define FAMST_ERR_TIMEOUT        -4  /* a bounded device loop gave up */
+#define FAMST_ERR_CUDA           -5  /* a CUDA runtime call failed */
+#define FAMST_ERR_OOM            -6  /* workspace allocation failed */
+#define FAMST_ERR_UNSUPPORTED    -7  /* size or mode this build does not handle */
+#define FAMST_ERR_NONFINITE      -8  /* X holds a NaN or an infinity */
+#define FAMST_ERR_DISCONNECTED   -9  /* famst_mst: the candidate graph is not connected */
+
+/* Distance-tile precision for Phase 1 (famst_knn_graph, famst_build).
+ * Every precision returns the exact kNN under the canonical distance:
+ * reduced-precision tiles only choose candidates, which are re-ranked in
+ * canonical FP32; a row whose candidate set cannot be certified from the
+ * tile's error bound is recomputed by the FP32 tiles. */
+#define FAMST_PREC_FP32   0  /* SIMT FP32 tiles computing the canonical distance directly */
+#define FAMST_PREC_BF16   1  /* tcgen05 BF16 tiles (x.y on tensor cores), FP32 re-rank */
+#define FAMST_PREC_BF16X3 2  /* tcgen05 BF16 hi/lo split, 3 products, FP32 re-rank */
+
+typedef struct famst_ctx famst_ctx;
+
+/* Per-build statistics, filled by famst_build* when the HOST pointer is
+ * not NULL. Times are CUDA-event milliseconds per stage on the context
+ * stream. */
+typedef struct famst_build_info {
+    int64_t t;                /* components of the kNN graph (Alg. 2) */
+    int64_t m;                /* inter-component edges, lambda*t*(t-1)/2 (Alg. 3) */
+    int32_t refine_sweeps;    /* sweeps of Alg. 4 until |Delta| = 0, the last included */
+    int32_t boruvka_rounds;
+    int64_t first_delta;      /* |Delta| of the first sweep */
+    int64_t uncertified_rows; /* reduced-precision rows recomputed in FP32 */
+    double  W;                /* sum of the FP32 tree weights, in FP64 */
+    double  W64;              /* tree weight with every edge recomputed in FP64 */
+    double  ms_knn, ms_components, ms_connect, ms_refine, ms_mst, ms_total;
+} famst_build_info;
+
+/* ------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`. *out receives it. */
+famst_status famst_create(famst_ctx **out, int device);
+/* Free the context and its workspace. NULL is accepted. */
+famst_status famst_destroy(famst_ctx *ctx);
+/* Enqueue all later work on `stream` (a cudaStream_t; NULL = legacy default). */
+famst_status famst_set_stream(famst_ctx *ctx, void *stream);
+/* Static string naming a status code. */
+const char *famst_error_string(famst_status status);
+/* Detail of the last error on this context (static storage in ctx). */
+const char *famst_last_error(const famst_ctx *ctx);
+/* Number of kernels this context has launched so far. */
+uint64_t famst_launch_count(const famst_ctx *ctx);
+/* Workspace bytes currently held by the context. */
+size_t famst_workspace_bytes(const famst_ctx *ctx);
+
+/* ------------------------------------------------------- Phase 1: kNN
+ * GetANNs of Algorithm 1, realised as the exact kNN by brute force over
+ * distance tiles: for each row i, the k smallest (w(i,j), j) with j != i,
+ * ascending. nbr[i*k + r] and dist[i*k + r] (n x k each, device).
+ * Requires 1 <= k <= n-1 and k <= 128. prec: FAMST_PREC_*. Errors:
+ * INVALID_ARG, NONFINITE, UNSUPPORTED (tensor precisions need d <= 512). */
+famst_status famst_knn_graph(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                             int32_t k, int32_t prec, int32_t *nbr, float *dist);
+
+/* ------------------------------------------------ Phase 2a: Algorithm 2
+ * Connected components of the undirected graph G built from nbr (n x k):
+ * comp[v] (device, n) = index of v's component, components numbered in
+ * ascending order of their smallest vertex id -- the order in which the
+ * depth-first search of Algorithm 2 discovers them. *t_out (HOST) = t.
+ * Synchronises. */
+famst_status famst_components(famst_ctx *ctx, const int32_t *nbr, int64_t n, int32_t k,
+                              int32_t *comp, int64_t *t_out);
+
+/* ------------------------------------------------ Phase 2b: Algorithm 3
+ * For every component pair i < j (i outer, j inner) draw lambda^2 samples
+ * s = 0..lambda^2-1 with Philox4x32-10 (counter (s, p_lo, p_hi, 0),
+ * key (seed_lo, seed_hi), p = i*t + j):
+ *     u = C_i[(r0 * |C_i|) >> 32],  v = C_j[(r1 * |C_j|) >> 32]
+ * where C_c lists component c's vertices by ascending id, and keep the
+ * lambda samples with the smallest (w(u,v), s), ascending. Edge
+ * e = (pair rank)*lambda + r is (eu, ev, ew) with eu in C_i, ev in C_j and
+ * (eci, ecj) = (i, j). comp/t as returned by famst_components.
+ * capacity = length of the five edge arrays (device); *m_out (HOST)
+ * receives lambda*t*(t-1)/2, also when it exceeds capacity (CAPACITY).
+ * 1 <= lambda <= 32. Synchronises. */
+famst_status famst_connect(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                           const int32_t *comp, int64_t t, int32_t lambda, uint64_t seed,
+                           int32_t *eu, int32_t *ev, float *ew, int32_t *eci, int32_t *ecj,
+                           int64_t capacity, int64_t *m_out);
+
+/* ------------------------------------------------- Phase 3: Algorithm 4
+ * Repeat the refinement sweep of Algorithm 4 over the m edges in place
+ * until no edge changes, at most max_iters sweeps. One sweep moves u to
+ * the neighbour u' in G[u] (same component) minimising w(u', v) when that
+ * is strictly smaller, then v likewise against the new u. Edges are
+ * independent, so each is iterated to its own fixed point; the result
+ * equals that of global sweeps. *sweeps_out (HOST) = number of sweeps
+ * including the final one without change; delta_hist (HOST, may be NULL,
+ * max_iters entries) receives |Delta| of each sweep. Errors:
+ * NO_CONVERGENCE when an edge still changed in sweep max_iters.
+ * Synchronises. */
+famst_status famst_refine(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                          const int32_t *nbr, int32_t k, const int32_t *comp,
+                          int32_t *eu, int32_t *ev, float *ew,
+                          const int32_t *eci, const int32_t *ecj, int64_t m,
+                          int32_t max_iters, int32_t *sweeps_out, int64_t *delta_hist);
+
+/* ------------------------------------------------------------- MST
+ * Minimum spanning tree of the graph made of the kNN edges {i, nbr[i*k+r]}
+ * weighted dist[i*k+r] and the m edges (eu, ev, ew), under the total
+ * order (w, min id, max id) -- the tree Kruskal's algorithm returns --
+ * computed by Boruvka rounds. tu/tv/tw (device, n-1 each) receive the
+ * edges as (min id, max id, w) in the order (round, component) in which
+ * they were found. *W_out (HOST) = sum of tw in FP64. Errors:
+ * DISCONNECTED. Synchronises. */
+famst_status famst_mst(famst_ctx *ctx, int64_t n, const int32_t *nbr, const float *dist,
+                       int32_t k, const int32_t *eu, const int32_t *ev, const float *ew,
+                       int64_t m, int32_t *tu, int32_t *tv, float *tw, double *W_out);
+
+/* FP64 weights of a tree: *W (HOST) = sum of tw in FP64 (fixed-order
+ * reduction); *W64 (HOST) = sum over edges of the distance recomputed in
+ * FP64 from X. Synchronises. */
+famst_status famst_tree_weight(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                               const int32_t *tu, const int32_t *tv, const float *tw,
+                               int64_t m, double *W, double *W64);
+
+/* ----------------------------------------------------- whole build
+ * Algorithm 1 end to end on device data: kNN (prec), components,
+ * connect (lambda, seed), refine (max_iters), MST. tu/tv/tw: n-1 each
+ * (device). *W_out and *info (HOST; info may be NULL). Synchronises. */
+famst_status famst_build(famst_ctx *ctx, const float *X, int64_t n, int32_t d, int32_t k,
+                         int32_t lambda, uint64_t seed, int32_t prec, int32_t max_iters,
+                         int32_t *tu, int32_t *tv, float *tw, double *W_out,
+                         famst_build_info *info);
+
+/* famst_build with X, tu, tv, tw all in HOST memory: copies X in and the
+ * tree out on the context stream (pinned memory makes the copies fast). */
+famst_status famst_build_host(famst_ctx *ctx, const float *X_host, int64_t n, int32_t d,
+                              int32_t k, int32_t lambda, uint64_t seed, int32_t prec,
+                              int32_t max_iters, int32_t *tu_host, int32_t *tv_host,
+                              float *tw_host, double *W_out, famst_build_info *info);
+
+/* -------------------------------------------------------- backward
+ * Gradient of W = sum over tree edges of ||x_u - x_v|| with the tree held
+ * fixed: gX[i] = gW * sum over edges e at i of (x_i - x_other)/w_e, where
+ * w_e is the canonical distance; an edge with w_e = 0 contributes 0. Each
+ * vertex sums its edges in ascending edge index, so the result is
+ * deterministic. gX: n x d (device), overwritten. */
+famst_status famst_mst_backward(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                                const int32_t *tu, const int32_t *tv, int64_t m,
+                                float gW, float *gX);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FAMST_H */

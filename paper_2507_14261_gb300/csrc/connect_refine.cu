@@ -1,0 +1,219 @@
+// Phase 2b (Algorithm 3) and Phase 3 (Algorithm 4) on the device.
+//
+// Connect: one warp per component pair (i < j). Lane l draws the samples
+// s = l, l+32, ... of the pair with Philox4x32-10 (counter (s, p_lo, p_hi,
+// 0), key = seed, p = i*t + j), maps the two 32-bit draws to members of
+// C_i and C_j by multiply-shift, and computes the canonical distance of
+// its samples. The lambda smallest (w, s) keys are then taken by lambda
+// rounds of a warp-wide minimum, which yields them in ascending order --
+// the "sort candidates, keep the first lambda" step of Algorithm 3.
+//
+// Refine: one warp per edge. A sweep of Algorithm 4 scans G[u] (kNN list
+// of u plus its reverse edges) for the u' minimising w(u', v) and then
+// G[v] against the new u. With the running best starting at the edge's
+// own weight and a strict "<", the paper's ascending scan keeps the first
+// (smallest id) of equal minima and keeps the incumbent on ties; that is
+// an argmin under the key (w, 1 + id) with the incumbent keyed (w, 0), so
+// lanes can scan in any order. Edges do not interact, so each warp
+// repeats sweeps on its edge until it stops changing (bounded by
+// max_iters); a histogram of per-edge change counts gives |Delta| of
+// every global sweep.
+#include <cuda_runtime.h>
+
+#include "famst_internal.cuh"
+
+namespace famst {
+namespace {
+
+__device__ __forceinline__ void pair_of(int64_t p, int64_t t, int64_t &i, int64_t &j) {
+    // pairs enumerated i = 0.., j = i+1..t-1; start(i) = i*t - i*(i+1)/2
+    double b = 2.0 * double(t) - 1.0;
+    double disc = b * b - 8.0 * double(p);
+    int64_t ii = int64_t((b - sqrt(disc > 0 ? disc : 0.0)) * 0.5);
+    if (ii < 0) ii = 0;
+    if (ii > t - 2) ii = t - 2;
+    auto start = [t](int64_t x) { return x * t - x * (x + 1) / 2; };
+    while (ii > 0 && start(ii) > p) --ii;
+    while (ii + 1 <= t - 2 && start(ii + 1) <= p) ++ii;
+    i = ii;
+    j = p - start(ii) + ii + 1;
+}
+
+template <int PER, int VEC>
+__global__ void connect_kernel(const float *__restrict__ X, int d,
+                               const int32_t *__restrict__ members,
+                               const int32_t *__restrict__ comp_off, int64_t t, int lambda,
+                               uint64_t seed, int32_t *__restrict__ eu, int32_t *__restrict__ ev,
+                               float *__restrict__ ew, int32_t *__restrict__ eci,
+                               int32_t *__restrict__ ecj) {
+    const int lane = threadIdx.x & 31;
+    const int64_t npairs = t * (t - 1) / 2;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int L2 = lambda * lambda;
+    const uint2 key = make_uint2(uint32_t(seed), uint32_t(seed >> 32));
+    for (int64_t pl = warp0; pl < npairs; pl += nwarps) {
+        int64_t i, j;
+        pair_of(pl, t, i, j);
+        const uint64_t p = uint64_t(i) * uint64_t(t) + uint64_t(j);
+        const int32_t oi = comp_off[i], oj = comp_off[j];
+        const uint64_t si = uint64_t(comp_off[i + 1] - oi), sj = uint64_t(comp_off[j + 1] - oj);
+        uint64_t kk[PER];
+        int32_t uu[PER], vv[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            int s = lane + 32 * q;
+            kk[q] = KEY_NONE;
+            if (s < L2) {
+                uint4 r = philox4x32_10(make_uint4(uint32_t(s), uint32_t(p), uint32_t(p >> 32), 0u),
+                                        key);
+                int32_t u = members[oi + int64_t((uint64_t(r.x) * si) >> 32)];
+                int32_t v = members[oj + int64_t((uint64_t(r.y) * sj) >> 32)];
+                float w = canon_dist<VEC>(X + int64_t(u) * d, X + int64_t(v) * d, d);
+                kk[q] = nb_key(w, uint32_t(s));
+                uu[q] = u;
+                vv[q] = v;
+            }
+        }
+        const int64_t ebase = pl * lambda;
+        for (int r = 0; r < lambda; ++r) {
+            uint64_t mine = KEY_NONE;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) mine = kk[q] < mine ? kk[q] : mine;
+            uint64_t best = warp_min_u64(mine);
+            int s = int(key_lo(best));
+            if ((s & 31) == lane) {
+                int qq = s >> 5;
+#pragma unroll
+                for (int q = 0; q < PER; ++q)
+                    if (q == qq) {
+                        kk[q] = KEY_NONE;
+                        eu[ebase + r] = uu[q];
+                        ev[ebase + r] = vv[q];
+                        ew[ebase + r] = key_w(best);
+                        eci[ebase + r] = int32_t(i);
+                        ecj[ebase + r] = int32_t(j);
+                    }
+            }
+        }
+    }
+}
+
+// argmin over the adjacency of `c` (kNN list + reverse edges) of the
+// candidate key (w(cand, fixed), 1 + cand); incumbent keyed (w0, 0).
+template <int VEC>
+__device__ __forceinline__ uint64_t scan_side(const float *__restrict__ X, int d, int c,
+                                              int fixed, int other, int want_comp, float w0,
+                                              const int32_t *__restrict__ nbr, int k,
+                                              const int32_t *__restrict__ rev_off,
+                                              const int32_t *__restrict__ rev_src,
+                                              const int32_t *__restrict__ comp, int lane) {
+    uint64_t best = uint64_t(__float_as_uint(w0)) << 32;
+    const int r0 = rev_off[c], r1 = rev_off[c + 1];
+    const int deg = k + (r1 - r0);
+    const float *xf = X + int64_t(fixed) * d;
+    for (int idx = lane; idx < deg; idx += 32) {
+        int cand = idx < k ? nbr[int64_t(c) * k + idx] : rev_src[r0 + idx - k];
+        if (comp[cand] != want_comp || cand == other) continue;  // G[c] ∩ C, and u' != v
+        float w = canon_dist<VEC>(X + int64_t(cand) * d, xf, d);
+        uint64_t key = (uint64_t(__float_as_uint(w)) << 32) | uint32_t(cand + 1);
+        best = key < best ? key : best;
+    }
+    return warp_min_u64(best);
+}
+
+template <int VEC>
+__global__ void refine_kernel(const float *__restrict__ X, int d,
+                              const int32_t *__restrict__ nbr, int k,
+                              const int32_t *__restrict__ rev_off,
+                              const int32_t *__restrict__ rev_src,
+                              const int32_t *__restrict__ comp, int32_t *__restrict__ eu,
+                              int32_t *__restrict__ ev, float *__restrict__ ew,
+                              const int32_t *__restrict__ eci, const int32_t *__restrict__ ecj,
+                              int64_t m, int max_iters, int32_t *__restrict__ change_hist,
+                              int *dstatus) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t e = warp0; e < m; e += nwarps) {
+        int u = eu[e], v = ev[e];
+        float w = ew[e];
+        const int ci = eci[e], cj = ecj[e];
+        int changes = 0;
+        for (; changes < max_iters; ++changes) {
+            // u-loop: u' in G[u] ∩ C_i, u' != v, against v
+            uint64_t bu = scan_side<VEC>(X, d, u, v, v, ci, w, nbr, k, rev_off, rev_src, comp, lane);
+            int us = key_lo(bu) ? int(key_lo(bu)) - 1 : u;
+            float ws = key_w(bu);
+            // v-loop: v' in G[v] ∩ C_j, v' != u, against the new u*
+            uint64_t bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane);
+            int vs = key_lo(bv) ? int(key_lo(bv)) - 1 : v;
+            ws = key_w(bv);
+            if (us == u && vs == v) break;
+            u = us;
+            v = vs;
+            w = ws;
+        }
+        if (lane == 0) {
+            eu[e] = u;
+            ev[e] = v;
+            ew[e] = w;
+            atomicAdd(&change_hist[changes], 1);
+            if (changes == max_iters) set_status(dstatus, STATUS_REFINE_CAP);
+        }
+    }
+}
+
+}  // namespace
+
+famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
+                           const int32_t *members, const int32_t *comp_off, int64_t t,
+                           int lambda, uint64_t seed, int32_t *eu, int32_t *ev, float *ew,
+                           int32_t *eci, int32_t *ecj) {
+    if (t < 2) return FAMST_OK;
+    int64_t npairs = t * (t - 1) / 2;
+    int per = (lambda * lambda + 31) / 32;
+    const int th = 256;
+    int64_t want = (npairs * 32 + th - 1) / th;
+    int64_t cap = int64_t(ex.num_sms) * 16;
+    unsigned grid = unsigned(want < cap ? want : cap);
+#define CONNECT_CASE(P)                                                                       \
+    if (per <= P) {                                                                           \
+        if (vec4)                                                                             \
+            FAMST_LAUNCH(ex, (connect_kernel<P, 4>), grid, th, 0, X, d, members, comp_off, t,  \
+                         lambda, seed, eu, ev, ew, eci, ecj);                                 \
+        else                                                                                  \
+            FAMST_LAUNCH(ex, (connect_kernel<P, 1>), grid, th, 0, X, d, members, comp_off, t,  \
+                         lambda, seed, eu, ev, ew, eci, ecj);                                 \
+        return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;                 \
+    }
+    CONNECT_CASE(1)
+    CONNECT_CASE(2)
+    CONNECT_CASE(4)
+    CONNECT_CASE(8)
+    CONNECT_CASE(16)
+    CONNECT_CASE(32)
+#undef CONNECT_CASE
+    return FAMST_ERR_UNSUPPORTED;
+}
+
+famst_status refine_edges(const Exec &ex, const float *X, int d, bool vec4, const int32_t *nbr,
+                          int k, const int32_t *rev_off, const int32_t *rev_src,
+                          const int32_t *comp, int32_t *eu, int32_t *ev, float *ew,
+                          const int32_t *eci, const int32_t *ecj, int64_t m, int max_iters,
+                          int32_t *change_hist) {
+    if (m == 0) return FAMST_OK;
+    const int th = 256;
+    int64_t want = (m * 32 + th - 1) / th;
+    int64_t cap = int64_t(ex.num_sms) * 16;
+    unsigned grid = unsigned(want < cap ? want : cap);
+    if (vec4)
+        FAMST_LAUNCH(ex, refine_kernel<4>, grid, th, 0, X, d, nbr, k, rev_off, rev_src, comp, eu,
+                     ev, ew, eci, ecj, m, max_iters, change_hist, ex.dstatus);
+    else
+        FAMST_LAUNCH(ex, refine_kernel<1>, grid, th, 0, X, d, nbr, k, rev_off, rev_src, comp, eu,
+                     ev, ew, eci, ecj, m, max_iters, change_hist, ex.dstatus);
+    return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+}  // namespace famst

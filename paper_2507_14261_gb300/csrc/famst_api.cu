@@ -1,0 +1,694 @@
+// C ABI of the FAMST library (include/famst.h): context, workspace,
+// argument and device-side validation, and the phase and build entry
+// points that string the kernels together in the order of Algorithm 1.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "famst_internal.cuh"
+
+using namespace famst;
+
+struct famst_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 1;
+    unsigned long long launches = 0;
+    // workspace slots: 0 = Phase 1 outputs and scratch, 1 = later phases,
+    // 2 = device copies made by famst_build_host
+    char *ws[3] = {nullptr, nullptr, nullptr};
+    size_t ws_cap[3] = {0, 0, 0};
+    int *dstatus = nullptr;       // device status word
+    int32_t *pinned = nullptr;    // 64 bytes of pinned host memory
+    double *dW = nullptr;         // device: W, W64
+    char err[256] = {0};
+};
+
+namespace {
+
+famst_status fail(famst_ctx *c, famst_status s, const char *msg) {
+    if (c) snprintf(c->err, sizeof(c->err), "%s", msg);
+    return s;
+}
+
+famst_status cuda_fail(famst_ctx *c, cudaError_t e, const char *where) {
+    if (c) snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
+    return FAMST_ERR_CUDA;
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+#define ST(call)                                                   \
+    do {                                                           \
+        famst_status s_ = (call);                                  \
+        if (s_ != FAMST_OK) return fail(ctx, s_, #call);           \
+    } while (0)
+
+// Make workspace slot `slot` hold at least `bytes`; returns an arena.
+famst_status ensure_ws(famst_ctx *ctx, int slot, size_t bytes, Arena &ar) {
+    bytes = align256(bytes) + 4096;
+    if (bytes > ctx->ws_cap[slot]) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (ctx->ws[slot]) cudaFree(ctx->ws[slot]);
+        ctx->ws[slot] = nullptr;
+        ctx->ws_cap[slot] = 0;
+        size_t want = bytes + bytes / 4;
+        if (cudaMalloc(&ctx->ws[slot], want) != cudaSuccess) {
+            cudaGetLastError();
+            if (cudaMalloc(&ctx->ws[slot], bytes) != cudaSuccess) {
+                cudaGetLastError();
+                ctx->ws[slot] = nullptr;
+                return fail(ctx, FAMST_ERR_OOM, "workspace allocation failed");
+            }
+            want = bytes;
+        }
+        ctx->ws_cap[slot] = want;
+    }
+    ar.base = ctx->ws[slot];
+    ar.cap = ctx->ws_cap[slot];
+    ar.off = 0;
+    return FAMST_OK;
+}
+
+Exec exec_of(famst_ctx *ctx) { return Exec{ctx->stream, &ctx->launches, ctx->num_sms, ctx->dstatus}; }
+
+__global__ void check_finite_kernel(const float *__restrict__ X, int64_t count, int *dstatus) {
+    int bad = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += int64_t(gridDim.x) * blockDim.x)
+        bad |= !isfinite(X[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(dstatus, STATUS_NONFINITE);
+}
+
+constexpr int STATUS_BAD_ID = 16;
+
+// ids in [0, n); for the kNN lists also != own row
+__global__ void check_ids_kernel(const int32_t *__restrict__ ids, int64_t count, int64_t n, int k,
+                                 int *dstatus) {
+    int bad = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        int v = ids[i];
+        bad |= (v < 0) | (int64_t(v) >= n);
+        if (k > 0) bad |= (int64_t(v) == i / k);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(dstatus, STATUS_BAD_ID);
+}
+
+__global__ void check_off_kernel(const int32_t *__restrict__ off, int64_t t, int *dstatus) {
+    int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (c < t && off[c] < 0) set_status(dstatus, STATUS_BAD_ID);
+}
+
+// inter-component edges: ends in range and in the components they claim
+__global__ void check_edges_kernel(const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
+                                   const int32_t *__restrict__ eci,
+                                   const int32_t *__restrict__ ecj,
+                                   const int32_t *__restrict__ comp, int64_t m, int64_t n,
+                                   int *dstatus) {
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    int u = eu[e], v = ev[e];
+    bool bad = u < 0 || v < 0 || int64_t(u) >= n || int64_t(v) >= n;
+    if (!bad && comp) bad = comp[u] != eci[e] || comp[v] != ecj[e] || eci[e] == ecj[e];
+    if (bad) set_status(dstatus, STATUS_BAD_ID);
+}
+
+unsigned grid_cap(famst_ctx *ctx, int64_t count, int th) {
+    int64_t g = (count + th - 1) / th;
+    int64_t cap = int64_t(ctx->num_sms) * 8;
+    if (g > cap) g = cap;
+    return unsigned(g < 1 ? 1 : g);
+}
+
+famst_status reset_status(famst_ctx *ctx) {
+    CK(cudaMemsetAsync(ctx->dstatus, 0, sizeof(int), ctx->stream));
+    return FAMST_OK;
+}
+
+// Synchronise and translate the device status word.
+famst_status sync_status(famst_ctx *ctx) {
+    CK(cudaMemcpyAsync(ctx->pinned, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaGetLastError());
+    int s = ctx->pinned[0];
+    if (s & STATUS_NONFINITE) return fail(ctx, FAMST_ERR_NONFINITE, "X holds NaN or Inf");
+    if (s & STATUS_BAD_ID) return fail(ctx, FAMST_ERR_INVALID_ARG, "vertex id out of range or inconsistent");
+    if (s & STATUS_LOOP_LIMIT) return fail(ctx, FAMST_ERR_TIMEOUT, "a bounded device loop reached its limit");
+    if (s & STATUS_REFINE_CAP) return fail(ctx, FAMST_ERR_NO_CONVERGENCE, "refinement reached max_iters");
+    if (s & STATUS_DISCONNECTED) return fail(ctx, FAMST_ERR_DISCONNECTED, "graph is not connected");
+    return FAMST_OK;
+}
+
+bool vec4_ok(const float *X, int d) {
+    return (d % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
+}
+
+famst_status check_points(famst_ctx *ctx, const float *X, int64_t n, int32_t d) {
+    if (!X) return fail(ctx, FAMST_ERR_INVALID_ARG, "X is NULL");
+    if (n < 1 || d < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "need n >= 1 and d >= 1");
+    if (n >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "n must be < 2^31");
+    Exec ex = exec_of(ctx);
+    FAMST_LAUNCH(ex, check_finite_kernel, grid_cap(ctx, n * d, 256), 256, 0, X, n * d,
+                 ctx->dstatus);
+    return FAMST_OK;
+}
+
+famst_status check_knn_args(famst_ctx *ctx, int64_t n, int32_t k) {
+    if (k < 1 || int64_t(k) > n - 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= k <= n-1");
+    if (k > 128) return fail(ctx, FAMST_ERR_UNSUPPORTED, "k > 128");
+    if (n * int64_t(k) >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "n*k must be < 2^31");
+    return FAMST_OK;
+}
+
+famst_status check_nbr(famst_ctx *ctx, const int32_t *nbr, int64_t n, int32_t k) {
+    if (!nbr) return fail(ctx, FAMST_ERR_INVALID_ARG, "nbr is NULL");
+    Exec ex = exec_of(ctx);
+    FAMST_LAUNCH(ex, check_ids_kernel, grid_cap(ctx, n * k, 256), 256, 0, nbr, n * k, n, k,
+                 ctx->dstatus);
+    return FAMST_OK;
+}
+
+// ---------------------------------------------------------- stage helpers
+
+struct Events {
+    cudaEvent_t e[8] = {};
+    int used = 0;
+    bool on = false;
+    void init(bool enable) {
+        on = enable;
+        if (on)
+            for (auto &x : e) cudaEventCreate(&x);
+    }
+    void mark(cudaStream_t s, int i) {
+        if (on) cudaEventRecord(e[i], s);
+        if (i + 1 > used) used = i + 1;
+    }
+    double ms(int a, int b) {
+        float f = 0.0f;
+        if (on) cudaEventElapsedTime(&f, e[a], e[b]);
+        return double(f);
+    }
+    ~Events() {
+        if (on)
+            for (auto &x : e) cudaEventDestroy(x);
+    }
+};
+
+famst_status knn_stage(famst_ctx *ctx, Arena &ar, const float *X, int64_t n, int32_t d, int32_t k,
+                       int32_t prec, int32_t *nbr, float *dist, int64_t *uncert) {
+    Exec ex = exec_of(ctx);
+    *uncert = 0;
+    if (prec == FAMST_PREC_FP32)
+        return knn_fp32(ex, ar, X, n, d, k, nullptr, 0, n, nbr, dist);
+    return fail(ctx, FAMST_ERR_UNSUPPORTED, "tensor-core precisions are not built in this library");
+}
+
+size_t knn_stage_ws(famst_ctx *ctx, int64_t n, int32_t d, int32_t k, int32_t prec) {
+    (void)prec;
+    return knn_fp32_workspace(n, d, k, n, ctx->num_sms);
+}
+
+// Phases 2-3 + MST on device data. nbr/dist come from Phase 1.
+struct BuildOut {
+    int32_t *tu, *tv;
+    float *tw;
+};
+
+famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, int32_t k,
+                        int32_t lambda, uint64_t seed, int32_t max_iters, const int32_t *nbr,
+                        const float *dist, int32_t *comp, BuildOut out, double *W_out,
+                        famst_build_info *info, Events &ev) {
+    Exec ex = exec_of(ctx);
+    const bool v4 = vec4_ok(X, d);
+    Arena ar;
+    // components
+    ST(ensure_ws(ctx, 1, components_workspace(n) + 256, ar));
+    int32_t *t_dev = ar.take<int32_t>(1);
+    ST(components_uf(ex, ar, nbr, n, k, comp, t_dev));
+    CK(cudaMemcpyAsync(ctx->pinned, t_dev, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    ST(sync_status(ctx));
+    const int64_t t = ctx->pinned[0];
+    ev.mark(ctx->stream, 2);
+    const int64_t m = int64_t(lambda) * t * (t - 1) / 2;
+    if (m >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "lambda*t*(t-1)/2 >= 2^31");
+    // workspace for connect, refine and MST
+    size_t need = align256(size_t(n) * 4) + align256(size_t(n + 1) * 4) +
+                  member_lists_workspace(n, t) + 5 * align256(size_t(m > 0 ? m : 1) * 4) +
+                  align256(size_t(n + 1) * 4) + align256(size_t(n) * k * 4) +
+                  reverse_csr_workspace(n, k) + align256(size_t(max_iters + 1) * 4) +
+                  boruvka_workspace(n) + tree_weight_workspace(n) + 4096;
+    ST(ensure_ws(ctx, 1, need, ar));
+    int32_t *members = ar.take<int32_t>(size_t(n));
+    int32_t *comp_off = ar.take<int32_t>(size_t(n + 1));
+    int32_t *eu = ar.take<int32_t>(size_t(m > 0 ? m : 1));
+    int32_t *evv = ar.take<int32_t>(size_t(m > 0 ? m : 1));
+    float *ew = ar.take<float>(size_t(m > 0 ? m : 1));
+    int32_t *eci = ar.take<int32_t>(size_t(m > 0 ? m : 1));
+    int32_t *ecj = ar.take<int32_t>(size_t(m > 0 ? m : 1));
+    int32_t *hist = ar.take<int32_t>(size_t(max_iters + 1));
+    // the components kernels above used this slot; comp lives in slot 0
+    int sweeps = 0;
+    int64_t first_delta = 0;
+    if (t > 1) {
+        ST(member_lists(ex, ar, comp, n, t, members, comp_off));
+        ST(connect_edges(ex, X, d, v4, members, comp_off, t, lambda, seed, eu, evv, ew, eci, ecj));
+        ev.mark(ctx->stream, 3);
+        int32_t *rev_off = ar.take<int32_t>(size_t(n + 1));
+        int32_t *rev_src = ar.take<int32_t>(size_t(n) * k);
+        if (!rev_off || !rev_src || !hist) return fail(ctx, FAMST_ERR_OOM, "workspace");
+        ST(reverse_csr(ex, ar, nbr, n, k, rev_off, rev_src));
+        CK(cudaMemsetAsync(hist, 0, size_t(max_iters + 1) * 4, ctx->stream));
+        ST(refine_edges(ex, X, d, v4, nbr, k, rev_off, rev_src, comp, eu, evv, ew, eci, ecj, m,
+                        max_iters, hist));
+        ev.mark(ctx->stream, 4);
+        famst_status s = sync_status(ctx);
+        if (s != FAMST_OK) return s;
+        // sweeps = 1 + largest change count; |Delta_1| = edges that changed at least once
+        int32_t *hh = new (std::nothrow) int32_t[max_iters + 1];
+        if (!hh) return fail(ctx, FAMST_ERR_OOM, "host");
+        CK(cudaMemcpy(hh, hist, size_t(max_iters + 1) * 4, cudaMemcpyDeviceToHost));
+        for (int c = 0; c <= max_iters; ++c)
+            if (hh[c]) sweeps = c + 1;
+        first_delta = m - hh[0];
+        delete[] hh;
+    } else {
+        ev.mark(ctx->stream, 3);
+        ev.mark(ctx->stream, 4);
+        sweeps = 0;
+    }
+    int64_t got = 0;
+    int rounds = 0;
+    ST(boruvka(ex, ar, n, nbr, dist, k, eu, evv, ew, m, MstOut{out.tu, out.tv, out.tw}, &got,
+               &rounds, ctx->pinned));
+    if (got != n - 1) return fail(ctx, FAMST_ERR_DISCONNECTED, "candidate graph is not connected");
+    ST(tree_weight(ex, ar, X, d, v4, out.tu, out.tv, out.tw, n - 1, ctx->dW));
+    ev.mark(ctx->stream, 5);
+    double W[2];
+    CK(cudaMemcpyAsync(W, ctx->dW, 16, cudaMemcpyDeviceToHost, ctx->stream));
+    ST(sync_status(ctx));
+    if (W_out) *W_out = W[0];
+    if (info) {
+        info->t = t;
+        info->m = m;
+        info->refine_sweeps = sweeps;
+        info->boruvka_rounds = rounds;
+        info->first_delta = first_delta;
+        info->W = W[0];
+        info->W64 = W[1];
+    }
+    return FAMST_OK;
+}
+
+famst_status build_impl(famst_ctx *ctx, const float *X, int64_t n, int32_t d, int32_t k,
+                        int32_t lambda, uint64_t seed, int32_t prec, int32_t max_iters,
+                        BuildOut out, double *W_out, famst_build_info *info) {
+    if (lambda < 1 || lambda > 32) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= lambda <= 32");
+    if (max_iters < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "need max_iters >= 1");
+    if (prec < 0 || prec > 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown precision");
+    if (info) memset(info, 0, sizeof(*info));
+    if (n == 1) {
+        if (W_out) *W_out = 0.0;
+        return FAMST_OK;
+    }
+    ST(check_knn_args(ctx, n, k));
+    Events ev;
+    ev.init(info != nullptr);
+    ev.mark(ctx->stream, 0);
+    ST(reset_status(ctx));
+    ST(check_points(ctx, X, n, d));
+    ST(sync_status(ctx));
+    Arena ar;
+    size_t need = 2 * align256(size_t(n) * k * 4) + align256(size_t(n) * 4) +
+                  knn_stage_ws(ctx, n, d, k, prec) + 4096;
+    ST(ensure_ws(ctx, 0, need, ar));
+    int32_t *nbr = ar.take<int32_t>(size_t(n) * k);
+    float *dist = ar.take<float>(size_t(n) * k);
+    int32_t *comp = ar.take<int32_t>(size_t(n));
+    int64_t uncert = 0;
+    ST(knn_stage(ctx, ar, X, n, d, k, prec, nbr, dist, &uncert));
+    ev.mark(ctx->stream, 1);
+    famst_status s = build_rest(ctx, X, n, d, k, lambda, seed, max_iters, nbr, dist, comp, out,
+                                W_out, info, ev);
+    if (s != FAMST_OK) return s;
+    if (info) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        info->uncertified_rows = uncert;
+        info->ms_knn = ev.ms(0, 1);
+        info->ms_components = ev.ms(1, 2);
+        info->ms_connect = ev.ms(2, 3);
+        info->ms_refine = ev.ms(3, 4);
+        info->ms_mst = ev.ms(4, 5);
+        info->ms_total = ev.ms(0, 5);
+    }
+    return FAMST_OK;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+
+extern "C" {
+
+famst_status famst_create(famst_ctx **out, int device) {
+    if (!out) return FAMST_ERR_INVALID_ARG;
+    *out = nullptr;
+    famst_ctx *ctx = new (std::nothrow) famst_ctx();
+    if (!ctx) return FAMST_ERR_OOM;
+    ctx->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dstatus, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dW, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->pinned, 64);
+    if (e == cudaSuccess) e = cudaMemset(ctx->dstatus, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        famst_destroy(ctx);
+        return FAMST_ERR_CUDA;
+    }
+    *out = ctx;
+    return FAMST_OK;
+}
+
+famst_status famst_destroy(famst_ctx *ctx) {
+    if (!ctx) return FAMST_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (int i = 0; i < 3; ++i)
+        if (ctx->ws[i]) cudaFree(ctx->ws[i]);
+    if (ctx->dstatus) cudaFree(ctx->dstatus);
+    if (ctx->dW) cudaFree(ctx->dW);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    delete ctx;
+    return FAMST_OK;
+}
+
+famst_status famst_set_stream(famst_ctx *ctx, void *stream) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return FAMST_OK;
+}
+
+const char *famst_error_string(famst_status s) {
+    switch (s) {
+        case FAMST_OK: return "ok";
+        case FAMST_ERR_INVALID_ARG: return "invalid argument";
+        case FAMST_ERR_CAPACITY: return "output capacity too small";
+        case FAMST_ERR_NO_CONVERGENCE: return "refinement did not converge within max_iters";
+        case FAMST_ERR_TIMEOUT: return "bounded device loop gave up";
+        case FAMST_ERR_CUDA: return "CUDA error";
+        case FAMST_ERR_OOM: return "out of device memory";
+        case FAMST_ERR_UNSUPPORTED: return "unsupported size or mode";
+        case FAMST_ERR_NONFINITE: return "input holds NaN or Inf";
+        case FAMST_ERR_DISCONNECTED: return "graph is not connected";
+        default: return "unknown status";
+    }
+}
+
+const char *famst_last_error(const famst_ctx *ctx) { return ctx ? ctx->err : ""; }
+
+uint64_t famst_launch_count(const famst_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+size_t famst_workspace_bytes(const famst_ctx *ctx) {
+    return ctx ? ctx->ws_cap[0] + ctx->ws_cap[1] + ctx->ws_cap[2] : 0;
+}
+
+famst_status famst_knn_graph(famst_ctx *ctx, const float *X, int64_t n, int32_t d, int32_t k,
+                             int32_t prec, int32_t *nbr, float *dist) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    if (!nbr || !dist) return fail(ctx, FAMST_ERR_INVALID_ARG, "nbr/dist NULL");
+    if (prec < 0 || prec > 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown precision");
+    if (n < 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "need n >= 2");
+    ST(check_knn_args(ctx, n, k));
+    CK(cudaSetDevice(ctx->device));
+    ST(reset_status(ctx));
+    ST(check_points(ctx, X, n, d));
+    ST(sync_status(ctx));
+    Arena ar;
+    ST(ensure_ws(ctx, 0, knn_stage_ws(ctx, n, d, k, prec), ar));
+    int64_t uncert = 0;
+    ST(knn_stage(ctx, ar, X, n, d, k, prec, nbr, dist, &uncert));
+    return sync_status(ctx);
+}
+
+famst_status famst_components(famst_ctx *ctx, const int32_t *nbr, int64_t n, int32_t k,
+                              int32_t *comp, int64_t *t_out) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    if (!comp || !t_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL output");
+    if (n < 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "need n >= 2");
+    ST(check_knn_args(ctx, n, k));
+    CK(cudaSetDevice(ctx->device));
+    ST(reset_status(ctx));
+    ST(check_nbr(ctx, nbr, n, k));
+    ST(sync_status(ctx));
+    Arena ar;
+    ST(ensure_ws(ctx, 0, components_workspace(n) + 256, ar));
+    int32_t *t_dev = ar.take<int32_t>(1);
+    ST(components_uf(exec_of(ctx), ar, nbr, n, k, comp, t_dev));
+    CK(cudaMemcpyAsync(ctx->pinned, t_dev, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    ST(sync_status(ctx));
+    *t_out = ctx->pinned[0];
+    return FAMST_OK;
+}
+
+famst_status famst_connect(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                           const int32_t *comp, int64_t t, int32_t lambda, uint64_t seed,
+                           int32_t *eu, int32_t *ev, float *ew, int32_t *eci, int32_t *ecj,
+                           int64_t capacity, int64_t *m_out) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    if (!comp || !m_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL argument");
+    if (lambda < 1 || lambda > 32) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= lambda <= 32");
+    if (t < 1 || t > n) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= t <= n");
+    const int64_t m = int64_t(lambda) * t * (t - 1) / 2;
+    *m_out = m;
+    if (m >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "lambda*t*(t-1)/2 >= 2^31");
+    if (capacity < m) return fail(ctx, FAMST_ERR_CAPACITY, "edge arrays shorter than lambda*t*(t-1)/2");
+    if (m > 0 && (!eu || !ev || !ew || !eci || !ecj)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL edge array");
+    CK(cudaSetDevice(ctx->device));
+    ST(reset_status(ctx));
+    ST(check_points(ctx, X, n, d));
+    Exec ex = exec_of(ctx);
+    FAMST_LAUNCH(ex, check_ids_kernel, grid_cap(ctx, n, 256), 256, 0, comp, n, t, 0, ctx->dstatus);
+    ST(sync_status(ctx));
+    if (m == 0) return FAMST_OK;
+    Arena ar;
+    ST(ensure_ws(ctx, 1, align256(size_t(n) * 4) + align256(size_t(n + 1) * 4) +
+                             member_lists_workspace(n, t), ar));
+    int32_t *members = ar.take<int32_t>(size_t(n));
+    int32_t *comp_off = ar.take<int32_t>(size_t(n + 1));
+    CK(cudaMemsetAsync(comp_off, 0xff, size_t(n + 1) * 4, ctx->stream));
+    ST(member_lists(ex, ar, comp, n, t, members, comp_off));
+    FAMST_LAUNCH(ex, check_off_kernel, unsigned((t + 255) / 256), 256, 0, comp_off, t, ctx->dstatus);
+    ST(sync_status(ctx));
+    ST(connect_edges(ex, X, d, vec4_ok(X, d), members, comp_off, t, lambda, seed, eu, ev, ew, eci,
+                     ecj));
+    return sync_status(ctx);
+}
+
+famst_status famst_refine(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                          const int32_t *nbr, int32_t k, const int32_t *comp, int32_t *eu,
+                          int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
+                          int64_t m, int32_t max_iters, int32_t *sweeps_out, int64_t *delta_hist) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    if (!comp || !sweeps_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL argument");
+    if (max_iters < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "need max_iters >= 1");
+    if (m < 0) return fail(ctx, FAMST_ERR_INVALID_ARG, "m < 0");
+    if (n < 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "need n >= 2");
+    ST(check_knn_args(ctx, n, k));
+    if (m > 0 && (!eu || !ev || !ew || !eci || !ecj)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL edge array");
+    CK(cudaSetDevice(ctx->device));
+    ST(reset_status(ctx));
+    ST(check_points(ctx, X, n, d));
+    ST(check_nbr(ctx, nbr, n, k));
+    Exec ex = exec_of(ctx);
+    FAMST_LAUNCH(ex, check_ids_kernel, grid_cap(ctx, n, 256), 256, 0, comp, n, n, 0, ctx->dstatus);
+    ST(sync_status(ctx));
+    if (m > 0) {
+        FAMST_LAUNCH(ex, check_edges_kernel, unsigned((m + 255) / 256), 256, 0, eu, ev, eci, ecj,
+                     comp, m, n, ctx->dstatus);
+        ST(sync_status(ctx));
+    }
+    *sweeps_out = 0;
+    if (m == 0) {
+        *sweeps_out = 1;
+        if (delta_hist) delta_hist[0] = 0;
+        return FAMST_OK;
+    }
+    Arena ar;
+    ST(ensure_ws(ctx, 1, align256(size_t(n + 1) * 4) + align256(size_t(n) * k * 4) +
+                             reverse_csr_workspace(n, k) + align256(size_t(max_iters + 1) * 4),
+                 ar));
+    int32_t *rev_off = ar.take<int32_t>(size_t(n + 1));
+    int32_t *rev_src = ar.take<int32_t>(size_t(n) * k);
+    int32_t *hist = ar.take<int32_t>(size_t(max_iters + 1));
+    ST(reverse_csr(ex, ar, nbr, n, k, rev_off, rev_src));
+    CK(cudaMemsetAsync(hist, 0, size_t(max_iters + 1) * 4, ctx->stream));
+    ST(refine_edges(ex, X, d, vec4_ok(X, d), nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj,
+                    m, max_iters, hist));
+    famst_status s = sync_status(ctx);
+    int32_t *hh = new (std::nothrow) int32_t[max_iters + 1];
+    if (!hh) return fail(ctx, FAMST_ERR_OOM, "host");
+    cudaError_t e = cudaMemcpy(hh, hist, size_t(max_iters + 1) * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        delete[] hh;
+        return cuda_fail(ctx, e, "copy histogram");
+    }
+    int sweeps = 0;
+    for (int c = 0; c <= max_iters; ++c)
+        if (hh[c]) sweeps = c + 1;
+    if (sweeps > max_iters) sweeps = max_iters;
+    *sweeps_out = sweeps;
+    if (delta_hist) {
+        // |Delta| of sweep s = edges whose change count is >= s
+        int64_t ge = 0;
+        for (int sidx = max_iters; sidx >= 1; --sidx) {
+            ge += hh[sidx];
+            if (sidx - 1 < max_iters) delta_hist[sidx - 1] = ge;
+        }
+    }
+    delete[] hh;
+    return s;
+}
+
+famst_status famst_mst(famst_ctx *ctx, int64_t n, const int32_t *nbr, const float *dist,
+                       int32_t k, const int32_t *eu, const int32_t *ev, const float *ew, int64_t m,
+                       int32_t *tu, int32_t *tv, float *tw, double *W_out) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    if (!W_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "W_out NULL");
+    if (n < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "need n >= 1");
+    if (m < 0) return fail(ctx, FAMST_ERR_INVALID_ARG, "m < 0");
+    *W_out = 0.0;
+    if (n == 1) return FAMST_OK;
+    if (!tu || !tv || !tw || !dist) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL argument");
+    ST(check_knn_args(ctx, n, k));
+    if (m > 0 && (!eu || !ev || !ew)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL edge array");
+    CK(cudaSetDevice(ctx->device));
+    ST(reset_status(ctx));
+    ST(check_nbr(ctx, nbr, n, k));
+    Exec ex = exec_of(ctx);
+    if (m > 0)
+        FAMST_LAUNCH(ex, check_edges_kernel, unsigned((m + 255) / 256), 256, 0, eu, ev, nullptr,
+                     nullptr, nullptr, m, n, ctx->dstatus);
+    ST(sync_status(ctx));
+    Arena ar;
+    ST(ensure_ws(ctx, 1, boruvka_workspace(n) + tree_weight_workspace(n), ar));
+    int64_t got = 0;
+    int rounds = 0;
+    ST(boruvka(ex, ar, n, nbr, dist, k, eu, ev, ew, m, MstOut{tu, tv, tw}, &got, &rounds,
+               ctx->pinned));
+    ST(sync_status(ctx));
+    if (got != n - 1) return fail(ctx, FAMST_ERR_DISCONNECTED, "candidate graph is not connected");
+    ST(tree_weight(ex, ar, nullptr, 0, false, tu, tv, tw, n - 1, ctx->dW));
+    double W[2];
+    CK(cudaMemcpyAsync(W, ctx->dW, 16, cudaMemcpyDeviceToHost, ctx->stream));
+    ST(sync_status(ctx));
+    *W_out = W[0];
+    return FAMST_OK;
+}
+
+famst_status famst_tree_weight(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                               const int32_t *tu, const int32_t *tv, const float *tw, int64_t m,
+                               double *W, double *W64) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    if (!W || !W64 || m < 0) return fail(ctx, FAMST_ERR_INVALID_ARG, "bad argument");
+    if (m > 0 && (!tu || !tv || !tw || !X)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaSetDevice(ctx->device));
+    ST(reset_status(ctx));
+    Exec ex = exec_of(ctx);
+    if (m > 0) {
+        FAMST_LAUNCH(ex, check_ids_kernel, grid_cap(ctx, m, 256), 256, 0, tu, m, n, 0, ctx->dstatus);
+        FAMST_LAUNCH(ex, check_ids_kernel, grid_cap(ctx, m, 256), 256, 0, tv, m, n, 0, ctx->dstatus);
+    }
+    ST(sync_status(ctx));
+    Arena ar;
+    ST(ensure_ws(ctx, 1, tree_weight_workspace(m), ar));
+    ST(tree_weight(ex, ar, X, d, vec4_ok(X, d), tu, tv, tw, m, ctx->dW));
+    double w[2];
+    CK(cudaMemcpyAsync(w, ctx->dW, 16, cudaMemcpyDeviceToHost, ctx->stream));
+    ST(sync_status(ctx));
+    *W = w[0];
+    *W64 = w[1];
+    return FAMST_OK;
+}
+
+famst_status famst_build(famst_ctx *ctx, const float *X, int64_t n, int32_t d, int32_t k,
+                         int32_t lambda, uint64_t seed, int32_t prec, int32_t max_iters,
+                         int32_t *tu, int32_t *tv, float *tw, double *W_out,
+                         famst_build_info *info) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    if (!W_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "W_out NULL");
+    if (n > 1 && (!tu || !tv || !tw)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL tree array");
+    if (!X || n < 1 || d < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "bad X/n/d");
+    CK(cudaSetDevice(ctx->device));
+    return build_impl(ctx, X, n, d, k, lambda, seed, prec, max_iters, BuildOut{tu, tv, tw}, W_out,
+                      info);
+}
+
+famst_status famst_build_host(famst_ctx *ctx, const float *X_host, int64_t n, int32_t d,
+                              int32_t k, int32_t lambda, uint64_t seed, int32_t prec,
+                              int32_t max_iters, int32_t *tu_host, int32_t *tv_host,
+                              float *tw_host, double *W_out, famst_build_info *info) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    if (!W_out || !X_host) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL argument");
+    if (n > 1 && (!tu_host || !tv_host || !tw_host)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL tree array");
+    if (n < 1 || d < 1 || n >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_INVALID_ARG, "bad n/d");
+    CK(cudaSetDevice(ctx->device));
+    size_t bx = align256(size_t(n) * d * 4), bt = align256(size_t(n) * 4);
+    Arena ar;
+    ST(ensure_ws(ctx, 2, bx + 3 * bt, ar));
+    char *buf = ar.base;
+    float *Xd = reinterpret_cast<float *>(buf);
+    int32_t *tu = reinterpret_cast<int32_t *>(buf + bx);
+    int32_t *tv = reinterpret_cast<int32_t *>(buf + bx + bt);
+    float *tw = reinterpret_cast<float *>(buf + bx + 2 * bt);
+    famst_status s = FAMST_OK;
+    if (cudaMemcpyAsync(Xd, X_host, size_t(n) * d * 4, cudaMemcpyHostToDevice, ctx->stream) !=
+        cudaSuccess)
+        s = cuda_fail(ctx, cudaGetLastError(), "copy X");
+    if (s == FAMST_OK)
+        s = build_impl(ctx, Xd, n, d, k, lambda, seed, prec, max_iters, BuildOut{tu, tv, tw}, W_out,
+                       info);
+    if (s == FAMST_OK && n > 1) {
+        size_t b = size_t(n - 1) * 4;
+        if (cudaMemcpyAsync(tu_host, tu, b, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(tv_host, tv, b, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+            cudaMemcpyAsync(tw_host, tw, b, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+            s = cuda_fail(ctx, cudaGetLastError(), "copy tree");
+    }
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && s == FAMST_OK)
+        s = cuda_fail(ctx, cudaGetLastError(), "synchronise");
+    return s;
+}
+
+famst_status famst_mst_backward(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                                const int32_t *tu, const int32_t *tv, int64_t m, float gW,
+                                float *gX) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    if (!gX || m < 0) return fail(ctx, FAMST_ERR_INVALID_ARG, "bad argument");
+    if (m > 0 && (!tu || !tv)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL tree array");
+    if (2 * m >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "too many edges");
+    CK(cudaSetDevice(ctx->device));
+    ST(reset_status(ctx));
+    if (n < 1 || (n * int64_t(d)) >= (int64_t(1) << 40)) return fail(ctx, FAMST_ERR_INVALID_ARG, "bad n/d");
+    ST(check_points(ctx, X, n, d));
+    Exec ex = exec_of(ctx);
+    if (m > 0) {
+        FAMST_LAUNCH(ex, check_ids_kernel, grid_cap(ctx, m, 256), 256, 0, tu, m, n, 0, ctx->dstatus);
+        FAMST_LAUNCH(ex, check_ids_kernel, grid_cap(ctx, m, 256), 256, 0, tv, m, n, 0, ctx->dstatus);
+    }
+    ST(sync_status(ctx));
+    Arena ar;
+    ST(ensure_ws(ctx, 1, mst_backward_workspace(n, m), ar));
+    ST(mst_backward(ex, ar, X, n, d, vec4_ok(X, d), tu, tv, m, gW, gX));
+    return sync_status(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Internal declarations shared by the FAMST CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "famst.h"
+
+namespace famst {
+
+// ------------------------------------------------------------------ host
+
+// Execution environment of one library call: the stream its work goes to
+// and the context's launch counter.
+struct Exec {
+    cudaStream_t stream;
+    unsigned long long *launches;
+    int num_sms;
+    int *dstatus;  // device status word (see STATUS_* below)
+};
+
+// Bits of the device status word. Kernels OR them in; the host reads the
+// word at the next synchronisation point.
+enum : int {
+    STATUS_NONFINITE = 1,       // a NaN or an infinity in X
+    STATUS_REFINE_CAP = 2,      // an edge still changed in sweep max_iters
+    STATUS_LOOP_LIMIT = 4,      // a bounded device loop reached its limit
+    STATUS_DISCONNECTED = 8,    // Boruvka found no outgoing edge with >1 component left
+};
+
+#define FAMST_LAUNCH(ex, kern, grid, block, smem, ...)                         \
+    do {                                                                       \
+        kern<<<(grid), (block), (smem), (ex).stream>>>(__VA_ARGS__);           \
+        ++*(ex).launches;                                                      \
+    } while (0)
+
+// Bump allocator over the context workspace.
+struct Arena {
+    char *base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t count) {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        if (off + bytes > cap) return nullptr;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += bytes;
+        return p;
+    }
+};
+
+static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------- device
+
+static constexpr uint64_t KEY_NONE = ~0ull;
+
+// Canonical FP32 distance: sequential fmaf chain over t = 0..d-1 and a
+// correctly rounded square root. VEC = 4 reads float4 (rows 16-byte
+// aligned, d % 4 == 0); the chain order is the same either way.
+template <int VEC>
+__device__ __forceinline__ float canon_p(const float *__restrict__ a,
+                                         const float *__restrict__ b, int d) {
+    float p = 0.0f;
+    if constexpr (VEC == 4) {
+        const float4 *a4 = reinterpret_cast<const float4 *>(a);
+        const float4 *b4 = reinterpret_cast<const float4 *>(b);
+        int d4 = d >> 2;
+#pragma unroll 4
+        for (int q = 0; q < d4; ++q) {
+            float4 x = __ldg(a4 + q), y = __ldg(b4 + q);
+            float t0 = __fsub_rn(x.x, y.x);
+            p = __fmaf_rn(t0, t0, p);
+            float t1 = __fsub_rn(x.y, y.y);
+            p = __fmaf_rn(t1, t1, p);
+            float t2 = __fsub_rn(x.z, y.z);
+            p = __fmaf_rn(t2, t2, p);
+            float t3 = __fsub_rn(x.w, y.w);
+            p = __fmaf_rn(t3, t3, p);
+        }
+    } else {
+        for (int t = 0; t < d; ++t) {
+            float t0 = __fsub_rn(__ldg(a + t), __ldg(b + t));
+            p = __fmaf_rn(t0, t0, p);
+        }
+    }
+    return p;
+}
+
+template <int VEC>
+__device__ __forceinline__ float canon_dist(const float *__restrict__ a,
+                                            const float *__restrict__ b, int d) {
+    return __fsqrt_rn(canon_p<VEC>(a, b, d));
+}
+
+// Key of a neighbour candidate: (w, id) lexicographic as one uint64.
+// w >= 0, so its IEEE bits order like the value.
+__device__ __forceinline__ uint64_t nb_key(float w, uint32_t id) {
+    return (uint64_t(__float_as_uint(w)) << 32) | id;
+}
+__device__ __forceinline__ float key_w(uint64_t k) { return __uint_as_float(uint32_t(k >> 32)); }
+__device__ __forceinline__ uint32_t key_lo(uint64_t k) { return uint32_t(k); }
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
+    uint32_t lo = uint32_t(v), hi = uint32_t(v >> 32);
+    lo = __shfl_xor_sync(0xffffffffu, lo, m);
+    hi = __shfl_xor_sync(0xffffffffu, hi, m);
+    return (uint64_t(hi) << 32) | lo;
+}
+
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        uint64_t o = shfl_xor_u64(v, m);
+        v = o < v ? o : v;
+    }
+    return v;
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw; SC'11): ten rounds of
+// (c0,c1,c2,c3) <- (hi(B*c2)^c1^k0, lo(B*c2), hi(A*c0)^c3^k1, lo(A*c0)),
+// A = 0xD2511F53, B = 0xCD9E8D57, key advanced by (0x9E3779B9, 0xBB67AE85)
+// before every round after the first.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ void set_status(int *dstatus, int bit) {
+    atomicOr(dstatus, bit);
+}
+
+// ------------------------------------------------ launchers (host side)
+
+// knn_fp32.cu
+// Exact kNN of query rows (qrows == nullptr: rows q0..q0+nq-1; else the
+// listed rows) against all n points, FP32 tiles computing the canonical
+// distance. Writes nbr/dist rows in query order (nq x k). kcap buckets:
+// k <= 128.
+famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
+                      int k, const int32_t *qrows, int64_t q0, int64_t nq,
+                      int32_t *nbr, float *dist);
+size_t knn_fp32_workspace(int64_t n, int d, int k, int64_t nq, int num_sms);
+
+// graph.cu
+famst_status exclusive_scan_i32(const Exec &ex, Arena &ar, const int32_t *in,
+                                int32_t *out, int64_t count, int32_t *total_dev);
+size_t scan_workspace(int64_t count);
+famst_status radix_sort_pairs(const Exec &ex, Arena &ar, uint32_t *keys, int32_t *vals,
+                              int64_t count, int key_bits);
+size_t radix_sort_workspace(int64_t count);
+famst_status components_uf(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t n,
+                           int k, int32_t *comp, int32_t *t_dev);
+size_t components_workspace(int64_t n);
+famst_status member_lists(const Exec &ex, Arena &ar, const int32_t *comp, int64_t n,
+                          int64_t t, int32_t *members, int32_t *comp_off);
+size_t member_lists_workspace(int64_t n, int64_t t);
+famst_status reverse_csr(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t n, int k,
+                         int32_t *rev_off, int32_t *rev_src);
+size_t reverse_csr_workspace(int64_t n, int k);
+
+// connect_refine.cu
+famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
+                           const int32_t *members, const int32_t *comp_off, int64_t t,
+                           int lambda, uint64_t seed, int32_t *eu, int32_t *ev, float *ew,
+                           int32_t *eci, int32_t *ecj);
+famst_status refine_edges(const Exec &ex, const float *X, int d, bool vec4,
+                          const int32_t *nbr, int k, const int32_t *rev_off,
+                          const int32_t *rev_src, const int32_t *comp, int32_t *eu,
+                          int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
+                          int64_t m, int max_iters, int32_t *change_hist /*max_iters+1*/);
+
+// mst.cu
+struct MstOut {
+    int32_t *tu, *tv;
+    float *tw;
+};
+famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr,
+                     const float *dist, int k, const int32_t *eu, const int32_t *ev,
+                     const float *ew, int64_t m, MstOut out, int64_t *tree_edges,
+                     int *rounds, int32_t *pinned_host);
+size_t boruvka_workspace(int64_t n);
+famst_status tree_weight(const Exec &ex, Arena &ar, const float *X, int d, bool vec4,
+                         const int32_t *tu, const int32_t *tv, const float *tw, int64_t m,
+                         double *W_dev /*2 doubles: W, W64*/);
+size_t tree_weight_workspace(int64_t m);
+famst_status mst_backward(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
+                          bool vec4, const int32_t *tu, const int32_t *tv, int64_t m,
+                          float gW, float *gX);
+size_t mst_backward_workspace(int64_t n, int64_t m);
+
+// prep (famst_api.cu)
+famst_status check_finite(const Exec &ex, const float *X, int64_t count);
+
+}  // namespace famst
