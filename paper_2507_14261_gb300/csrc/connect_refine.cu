@@ -185,7 +185,7 @@ famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
         else                                                                                  \
             FAMST_LAUNCH(ex, (connect_kernel<P, 1>), grid, th, 0, X, d, members, comp_off, t,  \
                          lambda, seed, eu, ev, ew, eci, ecj);                                 \
-        return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;                 \
+        return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;                 \
     }
     CONNECT_CASE(1)
     CONNECT_CASE(2)
@@ -213,7 +213,7 @@ famst_status refine_edges(const Exec &ex, const float *X, int d, bool vec4, cons
     else
         FAMST_LAUNCH(ex, refine_kernel<1>, grid, th, 0, X, d, nbr, k, rev_off, rev_src, comp, eu,
                      ev, ew, eci, ecj, m, max_iters, change_hist, ex.dstatus);
-    return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 }  // namespace famst

@@ -21,20 +21,28 @@ struct famst_ctx {
     char *ws[3] = {nullptr, nullptr, nullptr};
     size_t ws_cap[3] = {0, 0, 0};
     int *dstatus = nullptr;       // device status word
-    int32_t *pinned = nullptr;    // 64 bytes of pinned host memory
+    int32_t *pinned = nullptr;    // 64 bytes of pinned host memory, slots PIN_*
     double *dW = nullptr;         // device: W, W64
     char err[256] = {0};
 };
 
 namespace {
 
+// slots of the pinned host words: status word, component count, MST counter
+constexpr int PIN_STATUS = 0, PIN_T = 4, PIN_MST = 8;
+
+// Record the first error of a call (the innermost, most specific one).
 famst_status fail(famst_ctx *c, famst_status s, const char *msg) {
-    if (c) snprintf(c->err, sizeof(c->err), "%s", msg);
+    if (!c || c->err[0]) return s;
+    if (s == FAMST_ERR_CUDA)
+        snprintf(c->err, sizeof(c->err), "%s: %s", msg, cudaGetErrorString(cudaGetLastError()));
+    else
+        snprintf(c->err, sizeof(c->err), "%s", msg);
     return s;
 }
 
 famst_status cuda_fail(famst_ctx *c, cudaError_t e, const char *where) {
-    if (c) snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
+    if (c && !c->err[0]) snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
     return FAMST_ERR_CUDA;
 }
 
@@ -134,11 +142,11 @@ famst_status reset_status(famst_ctx *ctx) {
 
 // Synchronise and translate the device status word.
 famst_status sync_status(famst_ctx *ctx) {
-    CK(cudaMemcpyAsync(ctx->pinned, ctx->dstatus, sizeof(int), cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    CK(cudaMemcpyAsync(ctx->pinned + PIN_STATUS, ctx->dstatus, sizeof(int),
+                       cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaGetLastError());
-    int s = ctx->pinned[0];
+    int s = ctx->pinned[PIN_STATUS];
     if (s & STATUS_NONFINITE) return fail(ctx, FAMST_ERR_NONFINITE, "X holds NaN or Inf");
     if (s & STATUS_BAD_ID) return fail(ctx, FAMST_ERR_INVALID_ARG, "vertex id out of range or inconsistent");
     if (s & STATUS_LOOP_LIMIT) return fail(ctx, FAMST_ERR_TIMEOUT, "a bounded device loop reached its limit");
@@ -233,9 +241,9 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     ST(ensure_ws(ctx, 1, components_workspace(n) + 256, ar));
     int32_t *t_dev = ar.take<int32_t>(1);
     ST(components_uf(ex, ar, nbr, n, k, comp, t_dev));
-    CK(cudaMemcpyAsync(ctx->pinned, t_dev, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->pinned + PIN_T, t_dev, 4, cudaMemcpyDeviceToHost, ctx->stream));
     ST(sync_status(ctx));
-    const int64_t t = ctx->pinned[0];
+    const int64_t t = ctx->pinned[PIN_T];
     ev.mark(ctx->stream, 2);
     const int64_t m = int64_t(lambda) * t * (t - 1) / 2;
     if (m >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "lambda*t*(t-1)/2 >= 2^31");
@@ -287,7 +295,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     int64_t got = 0;
     int rounds = 0;
     ST(boruvka(ex, ar, n, nbr, dist, k, eu, evv, ew, m, MstOut{out.tu, out.tv, out.tw}, &got,
-               &rounds, ctx->pinned));
+               &rounds, ctx->pinned + PIN_MST));
     if (got != n - 1) return fail(ctx, FAMST_ERR_DISCONNECTED, "candidate graph is not connected");
     ST(tree_weight(ex, ar, X, d, v4, out.tu, out.tv, out.tw, n - 1, ctx->dW));
     ev.mark(ctx->stream, 5);
@@ -393,6 +401,7 @@ famst_status famst_destroy(famst_ctx *ctx) {
 
 famst_status famst_set_stream(famst_ctx *ctx, void *stream) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
     ctx->stream = static_cast<cudaStream_t>(stream);
     return FAMST_OK;
 }
@@ -424,6 +433,7 @@ size_t famst_workspace_bytes(const famst_ctx *ctx) {
 famst_status famst_knn_graph(famst_ctx *ctx, const float *X, int64_t n, int32_t d, int32_t k,
                              int32_t prec, int32_t *nbr, float *dist) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
     if (!nbr || !dist) return fail(ctx, FAMST_ERR_INVALID_ARG, "nbr/dist NULL");
     if (prec < 0 || prec > 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown precision");
     if (n < 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "need n >= 2");
@@ -442,6 +452,7 @@ famst_status famst_knn_graph(famst_ctx *ctx, const float *X, int64_t n, int32_t 
 famst_status famst_components(famst_ctx *ctx, const int32_t *nbr, int64_t n, int32_t k,
                               int32_t *comp, int64_t *t_out) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
     if (!comp || !t_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL output");
     if (n < 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "need n >= 2");
     ST(check_knn_args(ctx, n, k));
@@ -453,9 +464,9 @@ famst_status famst_components(famst_ctx *ctx, const int32_t *nbr, int64_t n, int
     ST(ensure_ws(ctx, 0, components_workspace(n) + 256, ar));
     int32_t *t_dev = ar.take<int32_t>(1);
     ST(components_uf(exec_of(ctx), ar, nbr, n, k, comp, t_dev));
-    CK(cudaMemcpyAsync(ctx->pinned, t_dev, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->pinned + PIN_T, t_dev, 4, cudaMemcpyDeviceToHost, ctx->stream));
     ST(sync_status(ctx));
-    *t_out = ctx->pinned[0];
+    *t_out = ctx->pinned[PIN_T];
     return FAMST_OK;
 }
 
@@ -464,6 +475,7 @@ famst_status famst_connect(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
                            int32_t *eu, int32_t *ev, float *ew, int32_t *eci, int32_t *ecj,
                            int64_t capacity, int64_t *m_out) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
     if (!comp || !m_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL argument");
     if (lambda < 1 || lambda > 32) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= lambda <= 32");
     if (t < 1 || t > n) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= t <= n");
@@ -498,6 +510,7 @@ famst_status famst_refine(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
                           int64_t m, int32_t max_iters, int32_t *sweeps_out, int64_t *delta_hist) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
     if (!comp || !sweeps_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL argument");
     if (max_iters < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "need max_iters >= 1");
     if (m < 0) return fail(ctx, FAMST_ERR_INVALID_ARG, "m < 0");
@@ -562,6 +575,7 @@ famst_status famst_mst(famst_ctx *ctx, int64_t n, const int32_t *nbr, const floa
                        int32_t k, const int32_t *eu, const int32_t *ev, const float *ew, int64_t m,
                        int32_t *tu, int32_t *tv, float *tw, double *W_out) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
     if (!W_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "W_out NULL");
     if (n < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "need n >= 1");
     if (m < 0) return fail(ctx, FAMST_ERR_INVALID_ARG, "m < 0");
@@ -583,7 +597,7 @@ famst_status famst_mst(famst_ctx *ctx, int64_t n, const int32_t *nbr, const floa
     int64_t got = 0;
     int rounds = 0;
     ST(boruvka(ex, ar, n, nbr, dist, k, eu, ev, ew, m, MstOut{tu, tv, tw}, &got, &rounds,
-               ctx->pinned));
+               ctx->pinned + PIN_MST));
     ST(sync_status(ctx));
     if (got != n - 1) return fail(ctx, FAMST_ERR_DISCONNECTED, "candidate graph is not connected");
     ST(tree_weight(ex, ar, nullptr, 0, false, tu, tv, tw, n - 1, ctx->dW));
@@ -598,6 +612,7 @@ famst_status famst_tree_weight(famst_ctx *ctx, const float *X, int64_t n, int32_
                                const int32_t *tu, const int32_t *tv, const float *tw, int64_t m,
                                double *W, double *W64) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
     if (!W || !W64 || m < 0) return fail(ctx, FAMST_ERR_INVALID_ARG, "bad argument");
     if (m > 0 && (!tu || !tv || !tw || !X)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL argument");
     CK(cudaSetDevice(ctx->device));
@@ -624,6 +639,7 @@ famst_status famst_build(famst_ctx *ctx, const float *X, int64_t n, int32_t d, i
                          int32_t *tu, int32_t *tv, float *tw, double *W_out,
                          famst_build_info *info) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
     if (!W_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "W_out NULL");
     if (n > 1 && (!tu || !tv || !tw)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL tree array");
     if (!X || n < 1 || d < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "bad X/n/d");
@@ -637,6 +653,7 @@ famst_status famst_build_host(famst_ctx *ctx, const float *X_host, int64_t n, in
                               int32_t max_iters, int32_t *tu_host, int32_t *tv_host,
                               float *tw_host, double *W_out, famst_build_info *info) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
     if (!W_out || !X_host) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL argument");
     if (n > 1 && (!tu_host || !tv_host || !tw_host)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL tree array");
     if (n < 1 || d < 1 || n >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_INVALID_ARG, "bad n/d");
@@ -672,6 +689,7 @@ famst_status famst_mst_backward(famst_ctx *ctx, const float *X, int64_t n, int32
                                 const int32_t *tu, const int32_t *tv, int64_t m, float gW,
                                 float *gX) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
     if (!gX || m < 0) return fail(ctx, FAMST_ERR_INVALID_ARG, "bad argument");
     if (m > 0 && (!tu || !tv)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL tree array");
     if (2 * m >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "too many edges");

@@ -274,7 +274,7 @@ famst_status exclusive_scan_i32(const Exec &ex, Arena &ar, const int32_t *in, in
     FAMST_LAUNCH(ex, scan_reduce_kernel, unsigned(nb), SCAN_NT, 0, in, count, bsum);
     FAMST_LAUNCH(ex, scan_blocksums_kernel, 1, 1024, 0, bsum, nb, total_dev);
     FAMST_LAUNCH(ex, scan_apply_kernel, unsigned(nb), SCAN_NT, 0, in, out, count, bsum);
-    return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 size_t radix_sort_workspace(int64_t count) {
@@ -313,7 +313,7 @@ famst_status radix_sort_pairs(const Exec &ex, Arena &ar, uint32_t *keys, int32_t
                 cudaSuccess)
             return FAMST_ERR_CUDA;
     }
-    return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 size_t components_workspace(int64_t n) {
@@ -337,7 +337,7 @@ famst_status components_uf(const Exec &ex, Arena &ar, const int32_t *nbr, int64_
     famst_status st = exclusive_scan_i32(ex, ar, flag, rank, n, t_dev);
     if (st != FAMST_OK) return st;
     FAMST_LAUNCH(ex, uf_label_kernel, blocks_for(n, th), th, 0, root, rank, n, comp);
-    return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 size_t member_lists_workspace(int64_t n, int64_t t) {
@@ -356,7 +356,7 @@ famst_status member_lists(const Exec &ex, Arena &ar, const int32_t *comp, int64_
     famst_status st = radix_sort_pairs(ex, ar, keys, members, n, bits);
     if (st != FAMST_OK) return st;
     FAMST_LAUNCH(ex, segment_starts_kernel, blocks_for(n, th), th, 0, keys, n, t, comp_off);
-    return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 size_t reverse_csr_workspace(int64_t n, int k) {
@@ -379,7 +379,7 @@ famst_status reverse_csr(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t 
     if (st != FAMST_OK) return st;
     FAMST_LAUNCH(ex, fill_rev_kernel, blocks_for(nk, th), th, 0, nbr, nk, k, rev_off, cursor,
                  rev_src);
-    return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 }  // namespace famst

@@ -270,13 +270,9 @@ famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int 
     if (k < 1 || k > 128) return FAMST_ERR_UNSUPPORTED;
     SplitPlan p = plan(n, nq, ex.num_sms);
     size_t smem = KnnSmem::bytes(k);
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(knn_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 227 * 1024) != cudaSuccess)
-            return FAMST_ERR_CUDA;
-        attr_set = true;
-    }
+    if (cudaFuncSetAttribute(knn_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(smem)) != cudaSuccess)
+        return FAMST_ERR_CUDA;
     uint64_t *part = nullptr;
     if (p.S > 1) {
         part = ar.take<uint64_t>(size_t(p.S) * nq * k);
@@ -285,12 +281,12 @@ famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int 
     dim3 grid(p.qblocks, p.S);
     FAMST_LAUNCH(ex, knn_fp32_kernel, grid, NT, smem, X, int(n), d, k, qrows, q0, int(nq),
                  p.tiles_per_split, part, nbr, dist);
-    if (cudaGetLastError() != cudaSuccess) return FAMST_ERR_CUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
     if (p.S > 1) {
         int th = 128;
         FAMST_LAUNCH(ex, knn_merge_kernel, int((nq + th - 1) / th), th, 0, part, p.S, int(nq),
                      k, nbr, dist);
-        if (cudaGetLastError() != cudaSuccess) return FAMST_ERR_CUDA;
+        if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
     }
     return FAMST_OK;
 }

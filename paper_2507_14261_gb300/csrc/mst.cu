@@ -325,7 +325,7 @@ famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr, c
         got += added;
     }
     *tree_edges = got;
-    return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 size_t tree_weight_workspace(int64_t m) {
@@ -346,7 +346,7 @@ famst_status tree_weight(const Exec &ex, Arena &ar, const float *X, int d, bool 
         FAMST_LAUNCH(ex, weight_partial_kernel<1>, unsigned(nb), WR_NT, 0, X, d, tu, tv, tw, m,
                      part);
     FAMST_LAUNCH(ex, weight_final_kernel, 1, WR_NT, 0, part, nb, W_dev);
-    return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 size_t mst_backward_workspace(int64_t n, int64_t m) {
@@ -380,7 +380,7 @@ famst_status mst_backward(const Exec &ex, Arena &ar, const float *X, int64_t n, 
     if (st != FAMST_OK) return st;
     FAMST_LAUNCH(ex, grad_kernel, blocks_for(n * d, th), th, 0, X, n, d, tu, tv, wl, off, inc, gW,
                  gX);
-    return cudaGetLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 }  // namespace famst
