@@ -198,6 +198,35 @@ famst_status famst_mst_backward(famst_ctx *ctx, const float *X, int64_t n, int32
                                 const int32_t *tu, const int32_t *tv, int64_t m,
                                 float gW, float *gX);
 
+/* ----------------------------------------- allocation-free components
+ * The paper has no counterpart to this call: it is an interface variant of
+ * famst_components for callers that cannot allocate device memory -- for
+ * example a host application that reserves all GPU memory for its own
+ * pool allocator at start-up, or a latency-critical loop that cannot
+ * tolerate the device-wide synchronisation cudaMalloc and cudaFree imply.
+ * It needs no famst_ctx and never calls cudaMalloc, cudaFree or any
+ * allocating library routine.
+ *
+ * Same result as famst_components: comp[v] (device, n) = component index
+ * in ascending order of the components' smallest ids; *t_dev (DEVICE
+ * int32) = t, or -1 when nbr holds an id outside [0, n) or a self-loop.
+ * Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default) on
+ * the calling thread's current device; the call returns without
+ * synchronising.
+ *
+ * Scratch: one static device array of about 8.4 MB (2 * FAMST_NOALLOC_MAX_N
+ * int32 plus small tables), present on every GPU that loads this library
+ * until the process exits. n > FAMST_NOALLOC_MAX_N returns
+ * FAMST_ERR_UNSUPPORTED; 1 <= k <= n-1 and n*k < 2^31 are required.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream
+ * capture. Every call on a device shares the array and leaves its contents
+ * behind (each call initialises what it reads); calls whose work overlaps
+ * on the GPU race on it, so serialise them (one stream, or events). */
+#define FAMST_NOALLOC_MAX_N (1 << 20)
+famst_status famst_components_noalloc(const int32_t *nbr, int64_t n, int32_t k,
+                                      int32_t *comp, int32_t *t_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif
