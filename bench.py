@@ -215,7 +215,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="famst", choices=["famst", "reference"])
     ap.add_argument("--workload", default="sphere_1m")
-    ap.add_argument("--prec", default=os.environ.get("FAMST_BENCH_PREC", "fp32"))
+    ap.add_argument("--prec", default=os.environ.get("FAMST_BENCH_PREC", "bf16x3"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

@@ -29,7 +29,7 @@ struct famst_ctx {
 namespace {
 
 // slots of the pinned host words: status word, component count, MST counter
-constexpr int PIN_STATUS = 0, PIN_T = 4, PIN_MST = 8;
+constexpr int PIN_STATUS = 0, PIN_T = 4, PIN_MST = 8, PIN_KNN = 12;
 
 // Record the first error of a call (the innermost, most specific one).
 famst_status fail(famst_ctx *c, famst_status s, const char *msg) {
@@ -210,17 +210,26 @@ struct Events {
     }
 };
 
+// Phase 1 dispatch. Tensor precisions use the tcgen05 tiles when the shape
+// fits them (k <= 63, operand rows fit shared memory); otherwise the FP32
+// tiles compute every row (reported as uncertified rows).
 famst_status knn_stage(famst_ctx *ctx, Arena &ar, const float *X, int64_t n, int32_t d, int32_t k,
                        int32_t prec, int32_t *nbr, float *dist, int64_t *uncert) {
     Exec ex = exec_of(ctx);
     *uncert = 0;
-    if (prec == FAMST_PREC_FP32)
-        return knn_fp32(ex, ar, X, n, d, k, nullptr, 0, n, nbr, dist);
-    return fail(ctx, FAMST_ERR_UNSUPPORTED, "tensor-core precisions are not built in this library");
+    if (prec != FAMST_PREC_FP32) {
+        const bool x3 = prec == FAMST_PREC_BF16X3;
+        if (knn_tc_supported(n, d, k, x3))
+            return knn_tc(ex, ar, X, n, d, k, x3, vec4_ok(X, d), nbr, dist, ctx->pinned + PIN_KNN,
+                          uncert);
+        *uncert = n;
+    }
+    return knn_fp32(ex, ar, X, n, d, k, nullptr, 0, n, nbr, dist);
 }
 
 size_t knn_stage_ws(famst_ctx *ctx, int64_t n, int32_t d, int32_t k, int32_t prec) {
-    (void)prec;
+    if (prec != FAMST_PREC_FP32 && knn_tc_supported(n, d, k, prec == FAMST_PREC_BF16X3))
+        return knn_tc_workspace(n, d, k, prec == FAMST_PREC_BF16X3, ctx->num_sms);
     return knn_fp32_workspace(n, d, k, n, ctx->num_sms);
 }
 

@@ -142,14 +142,23 @@ __device__ __forceinline__ void set_status(int *dstatus, int bit) {
 // ------------------------------------------------ launchers (host side)
 
 // knn_fp32.cu
-// Exact kNN of query rows (qrows == nullptr: rows q0..q0+nq-1; else the
-// listed rows) against all n points, FP32 tiles computing the canonical
-// distance. Writes nbr/dist rows in query order (nq x k). kcap buckets:
-// k <= 128.
+// Exact kNN of query rows (qrows == nullptr: rows q0..q0+nq-1, written to
+// output rows 0..nq-1; else the listed rows, written to their own rows of
+// nbr/dist) against all n points, FP32 tiles computing the canonical
+// distance. k <= 128.
 famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
                       int k, const int32_t *qrows, int64_t q0, int64_t nq,
                       int32_t *nbr, float *dist);
 size_t knn_fp32_workspace(int64_t n, int d, int k, int64_t nq, int num_sms);
+
+// knn_tc.cu
+// Exact kNN through tcgen05 BF16 (x3 = hi/lo split) distance tiles, FP32
+// re-rank, certificate, FP32 recomputation of uncertified rows.
+bool knn_tc_supported(int64_t n, int d, int k, bool x3);
+size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms);
+famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k, bool x3,
+                    bool vec4, int32_t *nbr, float *dist, int32_t *pinned_host,
+                    int64_t *uncertified);
 
 // graph.cu
 famst_status exclusive_scan_i32(const Exec &ex, Arena &ar, const int32_t *in,

@@ -209,8 +209,9 @@ knn_fp32_kernel(const float *__restrict__ X, int n, int d, int k,
             if (part) {
                 part[(size_t(split) * nq + q) * k + o] = best;
             } else {
-                nbr[q * k + o] = best == KEY_NONE ? -1 : int32_t(key_lo(best));
-                dist[q * k + o] = best == KEY_NONE ? __int_as_float(0x7f800000) : key_w(best);
+                const int64_t orow = qrows ? int64_t(qrows[q]) : q;
+                nbr[orow * k + o] = best == KEY_NONE ? -1 : int32_t(key_lo(best));
+                dist[orow * k + o] = best == KEY_NONE ? __int_as_float(0x7f800000) : key_w(best);
             }
         }
     }
@@ -218,7 +219,8 @@ knn_fp32_kernel(const float *__restrict__ X, int n, int d, int k,
 
 // S sorted partial lists per row -> the k smallest keys.
 __global__ void knn_merge_kernel(const uint64_t *__restrict__ part, int S, int nq, int k,
-                                 int32_t *__restrict__ nbr, float *__restrict__ dist) {
+                                 const int32_t *__restrict__ qrows, int32_t *__restrict__ nbr,
+                                 float *__restrict__ dist) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
     int head[64];
@@ -233,8 +235,9 @@ __global__ void knn_merge_kernel(const uint64_t *__restrict__ part, int S, int n
             }
         }
         if (bs >= 0) head[bs]++;
-        nbr[int64_t(q) * k + o] = best == KEY_NONE ? -1 : int32_t(key_lo(best));
-        dist[int64_t(q) * k + o] = best == KEY_NONE ? __int_as_float(0x7f800000) : key_w(best);
+        const int64_t orow = qrows ? int64_t(qrows[q]) : int64_t(q);
+        nbr[orow * k + o] = best == KEY_NONE ? -1 : int32_t(key_lo(best));
+        dist[orow * k + o] = best == KEY_NONE ? __int_as_float(0x7f800000) : key_w(best);
     }
 }
 
@@ -285,7 +288,7 @@ famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int 
     if (p.S > 1) {
         int th = 128;
         FAMST_LAUNCH(ex, knn_merge_kernel, int((nq + th - 1) / th), th, 0, part, p.S, int(nq),
-                     k, nbr, dist);
+                     k, qrows, nbr, dist);
         if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
     }
     return FAMST_OK;

@@ -1,0 +1,738 @@
+// Phase 1 (Algorithm 1, GetANNs) on tcgen05 tensor cores, exact result.
+//
+// Score. With centred coordinates x' = fl(x - mean), the squared distance
+// is ||x'_i||^2 + s(i,j) with s(i,j) = ||x'_j||^2 - 2 x'_i . x'_j; the first
+// term is constant along a row, so rows are ranked by s. The dot products
+// run on the tensor cores in BF16 with FP32 accumulation: BF16 mode uses
+// xh = bf16(x'); BF16X3 mode adds the two correction products of the
+// hi/lo split x' ~ xh + xl (xh.yh + xl.yh + xh.yl), whose error is
+// O(2^-16) instead of O(2^-8).
+//
+// Kernel (one CTA per 128 query rows, 192 threads):
+//   warp 0     TMA producer: the query tile's operand rows once (resident),
+//              then 256-key tiles, one 64-wide K block per ring stage;
+//   warp 1     allocates 512 TMEM columns (two 128 x 256 FP32
+//              accumulators) and one lane issues tcgen05.mma (M=128, N=256,
+//              K=16 per instruction) with SW128 K-major smem descriptors;
+//              tcgen05.commit frees ring stages and publishes accumulators;
+//   warps 2-5  epilogue: thread r owns query row r (TMEM lane r). It loads
+//              32 columns at a time with tcgen05.ld, forms s = ny_j - 2 acc,
+//              and stages the columns that beat its row's threshold in shared
+//              memory. When any lane's stage is nearly full the warp merges
+//              all stages into per-row sorted register lists of the KC
+//              smallest scores (lanes insert in parallel), then tightens the
+//              threshold to the KC-th score.
+// Nothing of the n x n score matrix leaves the SM. Every mbarrier wait is
+// bounded in time; on expiry the CTA sets an error bit, drains its own
+// copies and MMAs, frees its TMEM and returns.
+//
+// Exactness. Row i keeps k' = KC-1 candidates and s+ = its KC-th smallest
+// score. The rerank kernel computes the canonical FP32 distance of every
+// candidate, takes the k smallest (w, id), and certifies the row when a
+// rigorous bound on the score error proves that no unkept point can have a
+// canonical distance <= the k-th. Uncertified rows are recomputed by the
+// FP32 SIMT tiles, so the output equals the exact brute-force kNN.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+
+#include "famst_internal.cuh"
+
+namespace famst {
+namespace {
+
+constexpr int BM = 128;          // query rows per CTA (TMEM lanes)
+constexpr int BN = 256;          // keys per tile (accumulator columns)
+constexpr int BK = 64;           // K elements per stage (one 128-byte swizzle atom)
+constexpr int A_BLOCK = BM * BK * 2;   // 16 KB
+constexpr int B_BLOCK = BN * BK * 2;   // 32 KB
+constexpr int CAPB = 40;         // staged candidates per row
+constexpr int TC_THREADS = 192;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of parity `parity` to complete. Returns false
+// if the CTA aborted or the time limit expired (then it raises the abort).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    uint64_t t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > WAIT_NS) {
+            *abort_flag = 1;
+            set_status(status, STATUS_LOOP_LIMIT);
+            return false;
+        }
+    }
+}
+// Bounded wait that ignores the abort flag (used to drain in-flight work).
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
+    uint64_t t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity) && globaltimer() - t0 < WAIT_NS) {
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
+                                            int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (BF16 inputs, FP32 accumulate)
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// arrive on `bar` once every tcgen05 op issued so far by this thread is done
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "[%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
+// of 128 bytes, 8-row groups 1024 bytes apart (SBO), version 1.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= uint64_t((saddr & 0x3FFFFu) >> 4);   // start address
+    d |= uint64_t(1) << 16;                    // leading byte offset (unused with SW128 K-major)
+    d |= uint64_t(1024 >> 4) << 32;            // stride byte offset
+    d |= uint64_t(1) << 46;                    // descriptor version
+    d |= uint64_t(2) << 61;                    // SWIZZLE_128B
+    return d;
+}
+// Instruction descriptor, kind::f16: D F32, A/B BF16, both K-major.
+constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) |
+           (uint32_t(M >> 4) << 24);
+}
+
+struct TcArgs {
+    int n;
+    int nk_tiles;
+    int nkb;        // 64-wide K blocks of the hi part (d_pad / 64)
+    int x3;         // hi/lo split on
+    int stages;     // B ring depth
+    const float *ny;    // key norms ||x'_j||^2, +inf beyond n (nk_tiles * BN entries)
+    int32_t *cand;      // n x (KC - 1)
+    float *splus;       // n
+    int *status;
+};
+
+template <int KC>
+__device__ __forceinline__ void list_insert(float (&ls)[KC], int (&lj)[KC], float s, int j) {
+#pragma unroll
+    for (int p = 0; p < KC; ++p) {
+        bool sw = s < ls[p];
+        float ts = ls[p];
+        int tj = lj[p];
+        ls[p] = sw ? s : ts;
+        lj[p] = sw ? j : tj;
+        s = sw ? ts : s;
+        j = sw ? tj : j;
+    }
+}
+
+template <int KC>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              TcArgs args) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment for the swizzle atoms
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int nA = (args.x3 ? 2 : 1) * args.nkb;      // resident A blocks
+    unsigned char *sA = base;
+    unsigned char *sB = sA + size_t(nA) * A_BLOCK;
+    float *stg_s = reinterpret_cast<float *>(sB + size_t(args.stages) * B_BLOCK);
+    int *stg_j = reinterpret_cast<int *>(stg_s + CAPB * BM);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(stg_j + CAPB * BM);
+    uint64_t *full = bars;                       // [stages]
+    uint64_t *empty = bars + args.stages;        // [stages]
+    uint64_t *a_full = bars + 2 * args.stages;
+    uint64_t *tfull = a_full + 1;                // [2]
+    uint64_t *tempty = tfull + 2;                // [2]
+    uint64_t *mma_done = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q0 = blockIdx.x * BM;
+    const int nkb_tile = args.x3 ? 2 * args.nkb : args.nkb;   // B blocks per key tile
+    const int total_blocks = args.nk_tiles * nkb_tile;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < args.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(a_full, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_init(mma_done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA))
+                         : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB))
+                         : "memory");
+            mbar_expect_tx(a_full, uint32_t(nA) * A_BLOCK);
+            for (int a = 0; a < nA; ++a) tma_load_2d(sA + size_t(a) * A_BLOCK, &tmA, a_full, a * BK, q0);
+            int it = 0;
+            bool ok = true;
+            for (; it < total_blocks && ok; ++it) {
+                const int s = it % args.stages, r = it / args.stages;
+                if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag, args.status)) {
+                    ok = false;
+                    break;
+                }
+                const int t = it / nkb_tile, blk = it % nkb_tile;
+                // x3 order per key tile: hi_0, lo_0, hi_1, lo_1, ...
+                const int col = args.x3 ? ((blk & 1) ? args.nkb + (blk >> 1) : (blk >> 1)) : blk;
+                mbar_expect_tx(&full[s], B_BLOCK);
+                tma_load_2d(sB + size_t(s) * B_BLOCK, &tmB, &full[s], col * BK, t * BN);
+            }
+            // drain: every issued copy must land before the CTA leaves
+            mbar_drain(a_full, 0);
+            for (int s = 0; s < args.stages && s < it; ++s) {
+                int last = s + ((it - 1 - s) / args.stages) * args.stages;  // last use of stage s
+                mbar_drain(&full[s], (last / args.stages) & 1);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t IDESC = idesc_bf16(BM, BN);
+            bool ok = mbar_wait(a_full, 0, abort_flag, args.status);
+            tc_fence_after();
+            int it = 0;
+            for (int t = 0; t < args.nk_tiles && ok; ++t) {
+                const int b = t & 1, use = t >> 1;
+                if (!mbar_wait(&tempty[b], (use & 1) ^ 1, abort_flag, args.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + uint32_t(b * BN);
+                uint32_t acc = 0;
+                for (int blk = 0; blk < nkb_tile; ++blk, ++it) {
+                    const int s = it % args.stages, r = it / args.stages;
+                    if (!mbar_wait(&full[s], r & 1, abort_flag, args.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t bsm = smem_u32(sB + size_t(s) * B_BLOCK);
+                    const int kb = args.x3 ? (blk >> 1) : blk;
+                    const bool is_lo = args.x3 && (blk & 1);
+                    // which resident A blocks multiply this B block
+                    const int na = args.x3 ? (is_lo ? 1 : 2) : 1;
+                    for (int q = 0; q < na; ++q) {
+                        // hi B block: A_hi then A_lo; lo B block: A_hi
+                        const int ablk = (q == 0) ? kb : args.nkb + kb;
+                        const uint32_t asm_ = smem_u32(sA + size_t(ablk) * A_BLOCK);
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            umma_f16(d_tmem, sdesc_sw128(asm_ + kk * 32), sdesc_sw128(bsm + kk * 32),
+                                     IDESC, acc);
+                            acc = 1;
+                        }
+                    }
+                    umma_commit(&empty[s]);  // stage s is free once these MMAs finish
+                }
+                if (!ok) break;
+                umma_commit(&tfull[b]);      // accumulator b is complete
+            }
+            umma_commit(mma_done);
+            mbar_drain(mma_done, 0);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------ epilogue
+        const int quarter = warp & 3;               // TMEM lanes 32*quarter ..
+        const int row = quarter * 32 + lane;
+        const int i = q0 + row;
+        float ls[KC];
+        int lj[KC];
+#pragma unroll
+        for (int p = 0; p < KC; ++p) {
+            ls[p] = __int_as_float(0x7f800000);
+            lj[p] = -1;
+        }
+        float thr = __int_as_float(0x7f800000);
+        int cnt = 0;
+        float *my_s = stg_s + row;
+        int *my_j = stg_j + row;
+        auto flush = [&]() {
+            const int mx = __reduce_max_sync(0xffffffffu, cnt);
+            for (int q = 0; q < mx; ++q) {
+                if (q < cnt) {
+                    float sv = my_s[q * BM];
+                    int jv = my_j[q * BM];
+                    if (jv != i && sv < ls[KC - 1]) list_insert<KC>(ls, lj, sv, jv);
+                }
+            }
+            cnt = 0;
+            thr = ls[KC - 1];
+        };
+        bool ok = true;
+        for (int t = 0; t < args.nk_tiles; ++t) {
+            const int b = t & 1, use = t >> 1;
+            // every lane waits; the warp proceeds only if all lanes saw the phase
+            const bool got = mbar_wait(&tfull[b], use & 1, abort_flag, args.status);
+            if (!__all_sync(0xffffffffu, got)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tb = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * BN);
+            const float4 *ny4 = reinterpret_cast<const float4 *>(args.ny + size_t(t) * BN);
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                uint32_t v[32];
+                __syncwarp();
+                tmem_ld32(tb + ch * 32, v);
+                tmem_ld_wait();
+                float mn = __int_as_float(0x7f800000);
+#pragma unroll
+                for (int c4 = 0; c4 < 8; ++c4) {
+                    float4 nn = __ldg(ny4 + ch * 8 + c4);
+                    float s0 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 0]), nn.x);
+                    float s1 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 1]), nn.y);
+                    float s2 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 2]), nn.z);
+                    float s3 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 3]), nn.w);
+                    v[4 * c4 + 0] = __float_as_uint(s0);
+                    v[4 * c4 + 1] = __float_as_uint(s1);
+                    v[4 * c4 + 2] = __float_as_uint(s2);
+                    v[4 * c4 + 3] = __float_as_uint(s3);
+                    mn = fminf(mn, fminf(fminf(s0, s1), fminf(s2, s3)));
+                }
+                if (mn < thr) {
+                    const int j0 = t * BN + ch * 32;
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) {
+                        float sc = __uint_as_float(v[c]);
+                        if (sc < thr) {
+                            my_s[cnt * BM] = sc;
+                            my_j[cnt * BM] = j0 + c;
+                            ++cnt;
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, cnt > CAPB - 32)) flush();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
+        }
+        flush();
+        if (ok && i < args.n) {
+            int32_t *out = args.cand + size_t(i) * (KC - 1);
+#pragma unroll
+            for (int p = 0; p < KC - 1; ++p) out[p] = lj[p];
+            args.splus[i] = ls[KC - 1];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ------------------------------------------------------------- prep
+
+// per-block column sums (double) over a contiguous range of rows
+__global__ void colsum_partial_kernel(const float *__restrict__ X, int64_t n, int d, int rows_per,
+                                      double *__restrict__ part) {
+    int64_t r0 = int64_t(blockIdx.x) * rows_per;
+    int64_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
+    for (int c = threadIdx.x; c < d; c += blockDim.x) {
+        double s = 0.0;
+        for (int64_t r = r0; r < r1; ++r) s += double(X[r * d + c]);
+        part[int64_t(blockIdx.x) * d + c] = s;
+    }
+}
+
+__global__ void colsum_final_kernel(const double *__restrict__ part, int nb, int d, int64_t n,
+                                    float *__restrict__ mean) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= d) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[int64_t(b) * d + c];
+    mean[c] = float(s / double(n));
+}
+
+// One warp per row: centred row, BF16 hi (and lo) operand rows, FP32 norm.
+__global__ void tc_prep_kernel(const float *__restrict__ X, int64_t n, int d, int d_pad, int x3,
+                               const float *__restrict__ mean, __nv_bfloat16 *__restrict__ H,
+                               float *__restrict__ ny, float *__restrict__ xnorm,
+                               unsigned *__restrict__ ymax_bits) {
+    int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const int kh = (x3 ? 2 : 1) * d_pad;
+    __nv_bfloat16 *h = H + row * kh;
+    float acc = 0.0f;
+    for (int t = lane; t < d_pad; t += 32) {
+        float xc = t < d ? __fsub_rn(X[row * d + t], mean[t]) : 0.0f;
+        __nv_bfloat16 hi = __float2bfloat16_rn(xc);
+        h[t] = hi;
+        if (x3) h[d_pad + t] = __float2bfloat16_rn(__fsub_rn(xc, __bfloat162float(hi)));
+        acc = fmaf(xc, xc, acc);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        ny[row] = acc;
+        xnorm[row] = acc;
+        atomicMax(ymax_bits, __float_as_uint(sqrtf(acc)));
+    }
+}
+
+__global__ void fill_inf_kernel(float *p, int64_t from, int64_t to) {
+    int64_t i = from + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < to) p[i] = __int_as_float(0x7f800000);
+}
+
+// ------------------------------------------------------------- rerank
+
+struct CertConst {
+    double eps_dot;   // relative error of the tensor-core dot (products + accumulation)
+    double d_plus;    // d + 4, for the canonical distance error
+};
+
+// One warp per row: canonical distances of the k' candidates, bitonic sort
+// of (w, id), top k, certificate.
+template <int VEC, int KC>
+__global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int k,
+                              const int32_t *__restrict__ cand, const float *__restrict__ splus,
+                              const float *__restrict__ xnorm2, const unsigned *__restrict__ ymax_bits,
+                              CertConst cc, int32_t *__restrict__ nbr, float *__restrict__ dist,
+                              int32_t *__restrict__ fail_rows, int32_t *__restrict__ fail_count) {
+    int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    constexpr int KP = KC - 1;
+    uint64_t key[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int c = h * 32 + lane;
+        key[h] = KEY_NONE;
+        if (c < KP) {
+            int j = cand[i * KP + c];
+            if (j >= 0)
+                key[h] = nb_key(canon_dist<VEC>(X + i * d, X + int64_t(j) * d, d), uint32_t(j));
+        }
+    }
+    // bitonic sort of 64 keys, element index = h*32 + lane
+#pragma unroll
+    for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride == 32) {
+                // partner is the other register of the same lane; idx = lane < 32 + lane
+                bool asc = ((lane & size) == 0);  // size == 64: always ascending
+                uint64_t lo = key[0] < key[1] ? key[0] : key[1];
+                uint64_t hi = key[0] < key[1] ? key[1] : key[0];
+                key[0] = asc ? lo : hi;
+                key[1] = asc ? hi : lo;
+            } else {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    int idx = h * 32 + lane;
+                    bool asc = ((idx & size) == 0);
+                    uint64_t other = shfl_xor_u64(key[h], stride);
+                    bool lower = (lane & stride) == 0;
+                    uint64_t mn = key[h] < other ? key[h] : other;
+                    uint64_t mx = key[h] < other ? other : key[h];
+                    key[h] = (lower == asc) ? mn : mx;
+                }
+            }
+        }
+    }
+    // k-th key (index k-1)
+    const int kh = (k - 1) >> 5, kl = (k - 1) & 31;
+    uint64_t kth = __shfl_sync(0xffffffffu, kh ? key[1] : key[0], kl);
+    bool cert = false;
+    if (lane == 0) {
+        float sp = splus[i];
+        if (!(sp < __int_as_float(0x7f800000))) {
+            cert = true;  // fewer than KC points besides i: every one was kept
+        } else {
+            const double u24 = 1.0 / 16777216.0;
+            const double xn2 = double(xnorm2[i]);
+            const double xn = sqrt(xn2);
+            const double ym = double(__uint_as_float(*ymax_bits));
+            // |s~ - s| <= E: tensor-core dot, FP32 key norm, score rounding
+            const double E = 2.0 * cc.eps_dot * xn * ym * 1.01 + (d + 1) * u24 * 1.02 * ym * ym +
+                             2.0 * u24 * (ym * ym + 2.0 * xn * ym) * 1.01 + 1e-30;
+            // lower bound on the centred squared distance of any unkept point
+            const double p_lo = xn2 * (1.0 - (d + 1) * u24 * 1.02) + double(sp) - E;
+            const double dist_lo =
+                (p_lo > 0.0 ? sqrt(p_lo) : 0.0) - 1.02 * u24 * (xn + ym);  // centring rounding
+            const double w_lo = dist_lo * (1.0 - cc.d_plus * u24 * 1.05);   // canonical FP32 error
+            cert = w_lo > double(key_w(kth));
+        }
+    }
+    cert = __shfl_sync(0xffffffffu, cert, 0);
+    if (cert) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int idx = h * 32 + lane;
+            if (idx < k) {
+                nbr[i * k + idx] = int32_t(key_lo(key[h]));
+                dist[i * k + idx] = key_w(key[h]);
+            }
+        }
+    } else if (lane == 0) {
+        fail_rows[atomicAdd(fail_count, 1)] = int32_t(i);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t gdim[2] = {cuuint64_t(cols), cuuint64_t(rows)};
+    cuuint64_t gstride[1] = {cuuint64_t(cols) * 2};
+    cuuint32_t box[2] = {cuuint32_t(BK), cuuint32_t(box_rows)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), gdim, gstride,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+struct TcPlan {
+    int d_pad, nkb, kh, stages, kc;
+    int64_t nq_tiles, nk_tiles;
+    size_t smem;
+};
+
+TcPlan tc_plan(int64_t n, int d, int k, bool x3) {
+    TcPlan p{};
+    p.d_pad = (d + BK - 1) / BK * BK;
+    p.nkb = p.d_pad / BK;
+    p.kh = (x3 ? 2 : 1) * p.d_pad;
+    // keep at least ~10 candidates beyond k so that the certificate has a
+    // gap to work with: k <= 21 -> 31 candidates, k <= 63 -> 63
+    p.kc = (k <= 21) ? 32 : 64;
+    p.nq_tiles = (n + BM - 1) / BM;
+    p.nk_tiles = (n + BN - 1) / BN;
+    const size_t fixed = 1024 + size_t(x3 ? 2 : 1) * p.nkb * A_BLOCK + size_t(CAPB) * BM * 8 + 512;
+    const size_t cap = 227 * 1024;
+    int st = cap > fixed ? int((cap - fixed) / B_BLOCK) : 0;
+    if (st > 6) st = 6;
+    p.stages = st;
+    p.smem = fixed + size_t(st) * B_BLOCK;
+    return p;
+}
+
+}  // namespace
+
+bool knn_tc_supported(int64_t n, int d, int k, bool x3) {
+    if (k + 1 > 64 || n < 2) return false;
+    TcPlan p = tc_plan(n, d, k, x3);
+    return p.stages >= 2 && encode_fn() != nullptr;
+}
+
+size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms) {
+    TcPlan p = tc_plan(n, d, k, x3);
+    size_t b = 0;
+    b += align256(size_t(n) * p.kh * 2);                   // operand rows
+    b += align256(size_t(p.nk_tiles) * BN * 4);            // ny (padded)
+    b += align256(size_t(n) * 4);                          // xnorm2
+    b += align256(size_t(d) * 4) + 256;                    // mean, ymax
+    b += align256(size_t(4096) * d * 8);                   // column partials
+    b += align256(size_t(n) * (p.kc - 1) * 4);             // candidates
+    b += align256(size_t(n) * 4) * 2 + 256;                // splus, fail rows, count
+    b += knn_fp32_workspace(n, d, k, n, num_sms);          // fallback
+    return b;
+}
+
+famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k, bool x3,
+                    bool vec4, int32_t *nbr, float *dist, int32_t *pinned_host,
+                    int64_t *uncertified) {
+    TcPlan p = tc_plan(n, d, k, x3);
+    if (p.stages < 2 || k + 1 > 64) return FAMST_ERR_UNSUPPORTED;
+    __nv_bfloat16 *H = ar.take<__nv_bfloat16>(size_t(n) * p.kh);
+    float *ny = ar.take<float>(size_t(p.nk_tiles) * BN);
+    float *xn2 = ar.take<float>(size_t(n));
+    float *mean = ar.take<float>(size_t(d));
+    unsigned *ymax = ar.take<unsigned>(1);
+    const int rows_per = int((n + 4095) / 4096) > 0 ? int((n + 4095) / 4096) : 1;
+    const int nb = int((n + rows_per - 1) / rows_per);
+    double *part = ar.take<double>(size_t(nb) * d);
+    int32_t *cand = ar.take<int32_t>(size_t(n) * (p.kc - 1));
+    float *splus = ar.take<float>(size_t(n));
+    int32_t *fail_rows = ar.take<int32_t>(size_t(n));
+    int32_t *fail_count = ar.take<int32_t>(1);
+    if (!H || !ny || !xn2 || !mean || !ymax || !part || !cand || !splus || !fail_rows || !fail_count)
+        return FAMST_ERR_OOM;
+    // prep: mean, centred BF16 operands, norms
+    FAMST_LAUNCH(ex, colsum_partial_kernel, nb, 128, 0, X, n, d, rows_per, part);
+    FAMST_LAUNCH(ex, colsum_final_kernel, (d + 127) / 128, 128, 0, part, nb, d, n, mean);
+    if (cudaMemsetAsync(ymax, 0, 4, ex.stream) != cudaSuccess ||
+        cudaMemsetAsync(fail_count, 0, 4, ex.stream) != cudaSuccess)
+        return FAMST_ERR_CUDA;
+    FAMST_LAUNCH(ex, tc_prep_kernel, unsigned((n * 32 + 255) / 256), 256, 0, X, n, d, p.d_pad,
+                 int(x3), mean, H, ny, xn2, ymax);
+    const int64_t npad = p.nk_tiles * BN;
+    if (npad > n)
+        FAMST_LAUNCH(ex, fill_inf_kernel, unsigned((npad - n + 255) / 256), 256, 0, ny, n, npad);
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, H, n, p.kh, BM) || !make_map(&mB, H, n, p.kh, BN)) return FAMST_ERR_CUDA;
+    TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, ny, cand, splus, ex.dstatus};
+    if (p.kc == 32) {
+        if (cudaFuncSetAttribute(knn_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(p.smem)) != cudaSuccess)
+            return FAMST_ERR_CUDA;
+        FAMST_LAUNCH(ex, knn_tc_kernel<32>, unsigned(p.nq_tiles), TC_THREADS, p.smem, mA, mB, a);
+    } else {
+        if (cudaFuncSetAttribute(knn_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(p.smem)) != cudaSuccess)
+            return FAMST_ERR_CUDA;
+        FAMST_LAUNCH(ex, knn_tc_kernel<64>, unsigned(p.nq_tiles), TC_THREADS, p.smem, mA, mB, a);
+    }
+    if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
+    // rerank + certificate
+    const double u8 = 1.0 / 256.0;
+    const double kprod = double(x3 ? 3 * p.d_pad : p.d_pad);
+    CertConst cc;
+    cc.eps_dot = (x3 ? (3.0 * u8 * u8 + 3.0 * u8 * u8 * u8 + u8 * u8 * u8 * u8)
+                     : (2.0 * u8 + u8 * u8)) +
+                 kprod * std::ldexp(1.0, -22) * (1.0 + 4.0 * u8);
+    cc.d_plus = double(d) + 4.0;
+    const unsigned rgrid = unsigned((n * 32 + 255) / 256);
+#define RERANK(V, KCV)                                                                           \
+    FAMST_LAUNCH(ex, (rerank_kernel<V, KCV>), rgrid, 256, 0, X, n, d, k, cand, splus, xn2, ymax, cc, \
+                 nbr, dist, fail_rows, fail_count)
+    if (p.kc == 32) {
+        if (vec4) RERANK(4, 32); else RERANK(1, 32);
+    } else {
+        if (vec4) RERANK(4, 64); else RERANK(1, 64);
+    }
+#undef RERANK
+    if (cudaMemcpyAsync(pinned_host, fail_count, 4, cudaMemcpyDeviceToHost, ex.stream) != cudaSuccess ||
+        cudaStreamSynchronize(ex.stream) != cudaSuccess)
+        return FAMST_ERR_CUDA;
+    const int32_t nfail = *pinned_host;
+    *uncertified = nfail;
+    if (nfail > 0) {
+        famst_status st = knn_fp32(ex, ar, X, n, d, k, fail_rows, 0, nfail, nbr, dist);
+        if (st != FAMST_OK) return st;
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+}  // namespace famst
