@@ -215,6 +215,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="famst", choices=["famst", "reference"])
     ap.add_argument("--workload", default="sphere_1m")
+    ap.add_argument("--n", type=int, default=None,
+                    help="same recipe at another size (profiling runs); default: the workload's n")
     ap.add_argument("--prec", default=os.environ.get("FAMST_BENCH_PREC", "bf16x3"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -235,6 +237,8 @@ def main():
         dist.init_process_group("nccl")
         pg = dist
     w = workloads.get(args.workload)
+    if args.n is not None:
+        w = workloads.Workload(w.name, args.n, w.d, w.k, w.lam, w.seed, w.kind)
     X_np = workloads.Workload(w.name, w.n, w.d, w.k, w.lam, w.seed + rank, w.kind).points()
     X = torch.from_numpy(X_np).cuda()
     ctx = fam.Context(local)

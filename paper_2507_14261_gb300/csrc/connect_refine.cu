@@ -101,6 +101,7 @@ __global__ void connect_kernel(const float *__restrict__ X, int d,
 
 // argmin over the adjacency of `c` (kNN list + reverse edges) of the
 // candidate key (w(cand, fixed), 1 + cand); incumbent keyed (w0, 0).
+// Direct version: each lane streams its candidate's row from global memory.
 template <int VEC>
 __device__ __forceinline__ uint64_t scan_side(const float *__restrict__ X, int d, int c,
                                               int fixed, int other, int want_comp, float w0,
@@ -122,46 +123,149 @@ __device__ __forceinline__ uint64_t scan_side(const float *__restrict__ X, int d
     return warp_min_u64(best);
 }
 
-template <int VEC>
-__global__ void refine_kernel(const float *__restrict__ X, int d,
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Staged version (rows 16-byte aligned, d % 4 == 0): per round of 32
+// candidates the warp copies their rows into shared memory with coalesced
+// 16-byte cp.async (one row per step, all rows in flight together), then
+// lane l runs the canonical chain of candidate l from shared memory.
+// srow: 32 rows of `ld` floats; sfix: the fixed row (d floats).
+__device__ __forceinline__ uint64_t scan_side_staged(
+    const float *__restrict__ X, int d, int ld, int c, int fixed, int other, int want_comp,
+    float w0, const int32_t *__restrict__ nbr, int k, const int32_t *__restrict__ rev_off,
+    const int32_t *__restrict__ rev_src, const int32_t *__restrict__ comp, int lane,
+    float *srow, float *sfix) {
+    const int d4 = d >> 2;
+    __syncwarp();
+    for (int q = lane; q < d4; q += 32) cp_async16(sfix + 4 * q, X + int64_t(fixed) * d + 4 * q);
+    uint64_t best = uint64_t(__float_as_uint(w0)) << 32;
+    const int r0 = rev_off[c], r1 = rev_off[c + 1];
+    const int deg = k + (r1 - r0);
+    for (int base = 0; base < deg; base += 32) {
+        const int idx = base + lane;
+        int cand = -1;
+        if (idx < deg) {
+            cand = idx < k ? nbr[int64_t(c) * k + idx] : rev_src[r0 + idx - k];
+            if (comp[cand] != want_comp || cand == other) cand = -1;  // G[c] ∩ C, u' != v
+        }
+        const unsigned live = __ballot_sync(0xffffffffu, cand >= 0);
+        unsigned todo = live;
+        while (todo) {
+            const int sl = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int id = __shfl_sync(0xffffffffu, cand, sl);
+            const float *g = X + int64_t(id) * d;
+            for (int q = lane; q < d4; q += 32) cp_async16(srow + sl * ld + 4 * q, g + 4 * q);
+        }
+        cp_async_wait_all();
+        __syncwarp();
+        if (cand >= 0) {
+            const float4 *a4 = reinterpret_cast<const float4 *>(srow + lane * ld);
+            const float4 *b4 = reinterpret_cast<const float4 *>(sfix);
+            float p = 0.0f;
+#pragma unroll 8
+            for (int q = 0; q < d4; ++q) {
+                float4 x = a4[q], y = b4[q];
+                float t0 = __fsub_rn(x.x, y.x);
+                p = __fmaf_rn(t0, t0, p);
+                float t1 = __fsub_rn(x.y, y.y);
+                p = __fmaf_rn(t1, t1, p);
+                float t2 = __fsub_rn(x.z, y.z);
+                p = __fmaf_rn(t2, t2, p);
+                float t3 = __fsub_rn(x.w, y.w);
+                p = __fmaf_rn(t3, t3, p);
+            }
+            uint64_t key = (uint64_t(__float_as_uint(__fsqrt_rn(p))) << 32) | uint32_t(cand + 1);
+            best = key < best ? key : best;
+        }
+        __syncwarp();  // the next round overwrites srow
+    }
+    return warp_min_u64(best);
+}
+
+// Process edges in the order `order` (component-pair tiles, so the rows in
+// flight stay in L2), each to its own fixed point.
+template <int VEC, bool STAGED>
+__global__ void refine_kernel(const float *__restrict__ X, int d, int ld,
                               const int32_t *__restrict__ nbr, int k,
                               const int32_t *__restrict__ rev_off,
                               const int32_t *__restrict__ rev_src,
                               const int32_t *__restrict__ comp, int32_t *__restrict__ eu,
                               int32_t *__restrict__ ev, float *__restrict__ ew,
                               const int32_t *__restrict__ eci, const int32_t *__restrict__ ecj,
-                              int64_t m, int max_iters, int32_t *__restrict__ change_hist,
-                              int *dstatus) {
+                              const int32_t *__restrict__ order, int64_t m, int max_iters,
+                              int32_t *__restrict__ change_hist,
+                              unsigned long long *__restrict__ next_item, int *dstatus) {
+    extern __shared__ __align__(16) float rsm[];
     const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t e = warp0; e < m; e += nwarps) {
+    const int wib = threadIdx.x >> 5;
+    float *srow = rsm + size_t(wib) * (32 * ld + d);
+    float *sfix = srow + 32 * ld;
+    // Edges are handed out one at a time from a global counter, so the
+    // edges in flight stay a narrow window of `order` (and their rows in L2)
+    // even though edges need different numbers of sweeps.
+    while (true) {
+        unsigned long long w0 = 0;
+        if (lane == 0) w0 = atomicAdd(next_item, 1ull);
+        const int64_t w = int64_t(__shfl_sync(0xffffffffu, w0, 0));
+        if (w >= m) break;
+        const int64_t e = order ? int64_t(order[w]) : w;
         int u = eu[e], v = ev[e];
-        float w = ew[e];
+        float wt = ew[e];
         const int ci = eci[e], cj = ecj[e];
         int changes = 0;
         for (; changes < max_iters; ++changes) {
+            uint64_t bu, bv;
+            int us, vs;
+            float ws;
             // u-loop: u' in G[u] ∩ C_i, u' != v, against v
-            uint64_t bu = scan_side<VEC>(X, d, u, v, v, ci, w, nbr, k, rev_off, rev_src, comp, lane);
-            int us = key_lo(bu) ? int(key_lo(bu)) - 1 : u;
-            float ws = key_w(bu);
+            if constexpr (STAGED)
+                bu = scan_side_staged(X, d, ld, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp,
+                                      lane, srow, sfix);
+            else
+                bu = scan_side<VEC>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp, lane);
+            us = key_lo(bu) ? int(key_lo(bu)) - 1 : u;
+            ws = key_w(bu);
             // v-loop: v' in G[v] ∩ C_j, v' != u, against the new u*
-            uint64_t bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane);
-            int vs = key_lo(bv) ? int(key_lo(bv)) - 1 : v;
+            if constexpr (STAGED)
+                bv = scan_side_staged(X, d, ld, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp,
+                                      lane, srow, sfix);
+            else
+                bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane);
+            vs = key_lo(bv) ? int(key_lo(bv)) - 1 : v;
             ws = key_w(bv);
             if (us == u && vs == v) break;
             u = us;
             v = vs;
-            w = ws;
+            wt = ws;
         }
         if (lane == 0) {
             eu[e] = u;
             ev[e] = v;
-            ew[e] = w;
+            ew[e] = wt;
             atomicAdd(&change_hist[changes], 1);
             if (changes == max_iters) set_status(dstatus, STATUS_REFINE_CAP);
         }
     }
+}
+
+// tile key of an edge: its component pair's (ci / TT, cj / TT) cell
+__global__ void edge_tile_key_kernel(const int32_t *__restrict__ eci,
+                                     const int32_t *__restrict__ ecj, int64_t m, int tt, int T,
+                                     uint32_t *__restrict__ keys, int32_t *__restrict__ vals) {
+    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (e >= m) return;
+    keys[e] = uint32_t(eci[e] / tt) * uint32_t(T) + uint32_t(ecj[e] / tt);
+    vals[e] = int32_t(e);
 }
 
 }  // namespace
@@ -197,22 +301,53 @@ famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
     return FAMST_ERR_UNSUPPORTED;
 }
 
-famst_status refine_edges(const Exec &ex, const float *X, int d, bool vec4, const int32_t *nbr,
-                          int k, const int32_t *rev_off, const int32_t *rev_src,
-                          const int32_t *comp, int32_t *eu, int32_t *ev, float *ew,
-                          const int32_t *eci, const int32_t *ecj, int64_t m, int max_iters,
-                          int32_t *change_hist) {
+size_t refine_workspace(int64_t m) {
+    return align256(size_t(m) * 4) * 2 + 256 + radix_sort_workspace(m);
+}
+
+famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool vec4,
+                          const int32_t *nbr, int k, const int32_t *rev_off,
+                          const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
+                          int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
+                          int64_t m, int max_iters, int32_t *change_hist) {
     if (m == 0) return FAMST_OK;
-    const int th = 256;
+    // order: stable sort of the edges by component-pair tile
+    constexpr int TT = 24;
+    const int T = int((t + TT - 1) / TT);
+    uint32_t *keys = ar.take<uint32_t>(size_t(m));
+    int32_t *order = ar.take<int32_t>(size_t(m));
+    unsigned long long *next_item = ar.take<unsigned long long>(1);
+    if (!keys || !order || !next_item) return FAMST_ERR_OOM;
+    if (cudaMemsetAsync(next_item, 0, 8, ex.stream) != cudaSuccess) return FAMST_ERR_CUDA;
+    FAMST_LAUNCH(ex, edge_tile_key_kernel, unsigned((m + 255) / 256), 256, 0, eci, ecj, m, TT, T,
+                 keys, order);
+    int bits = 0;
+    while ((int64_t(1) << bits) < int64_t(T) * T) ++bits;
+    famst_status st = radix_sort_pairs(ex, ar, keys, order, m, bits);
+    if (st != FAMST_OK) return st;
+    const bool staged = vec4 && d <= 512;
+    const int ld = d + ((d % 8 == 0) ? 4 : 8);
+    const int th = staged ? 128 : 256;
+    const size_t smem = staged ? size_t(th / 32) * (32 * ld + d) * sizeof(float) : 0;
     int64_t want = (m * 32 + th - 1) / th;
-    int64_t cap = int64_t(ex.num_sms) * 16;
+    int64_t cap = int64_t(ex.num_sms) * (staged ? 12 : 16);
     unsigned grid = unsigned(want < cap ? want : cap);
-    if (vec4)
-        FAMST_LAUNCH(ex, refine_kernel<4>, grid, th, 0, X, d, nbr, k, rev_off, rev_src, comp, eu,
-                     ev, ew, eci, ecj, m, max_iters, change_hist, ex.dstatus);
-    else
-        FAMST_LAUNCH(ex, refine_kernel<1>, grid, th, 0, X, d, nbr, k, rev_off, rev_src, comp, eu,
-                     ev, ew, eci, ecj, m, max_iters, change_hist, ex.dstatus);
+    if (staged) {
+        if (cudaFuncSetAttribute(refine_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem)) != cudaSuccess)
+            return FAMST_ERR_CUDA;
+        FAMST_LAUNCH(ex, (refine_kernel<4, true>), grid, th, smem, X, d, ld, nbr, k, rev_off, rev_src,
+                     comp, eu, ev, ew, eci, ecj, order, m, max_iters, change_hist, next_item,
+                     ex.dstatus);
+    } else if (vec4) {
+        FAMST_LAUNCH(ex, (refine_kernel<4, false>), grid, th, 0, X, d, ld, nbr, k, rev_off, rev_src,
+                     comp, eu, ev, ew, eci, ecj, order, m, max_iters, change_hist, next_item,
+                     ex.dstatus);
+    } else {
+        FAMST_LAUNCH(ex, (refine_kernel<1, false>), grid, th, 0, X, d, ld, nbr, k, rev_off, rev_src,
+                     comp, eu, ev, ew, eci, ecj, order, m, max_iters, change_hist, next_item,
+                     ex.dstatus);
+    }
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 

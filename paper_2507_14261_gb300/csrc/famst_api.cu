@@ -128,6 +128,15 @@ __global__ void check_edges_kernel(const int32_t *__restrict__ eu, const int32_t
     if (bad) set_status(dstatus, STATUS_BAD_ID);
 }
 
+__global__ void max_i32_kernel(const int32_t *__restrict__ a, int64_t count, int32_t *out) {
+    int mx = 0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+         i += int64_t(gridDim.x) * blockDim.x)
+        mx = a[i] > mx ? a[i] : mx;
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    if ((threadIdx.x & 31) == 0) atomicMax(out, mx);
+}
+
 unsigned grid_cap(famst_ctx *ctx, int64_t count, int th) {
     int64_t g = (count + th - 1) / th;
     int64_t cap = int64_t(ctx->num_sms) * 8;
@@ -261,7 +270,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
                   member_lists_workspace(n, t) + 5 * align256(size_t(m > 0 ? m : 1) * 4) +
                   align256(size_t(n + 1) * 4) + align256(size_t(n) * k * 4) +
                   reverse_csr_workspace(n, k) + align256(size_t(max_iters + 1) * 4) +
-                  boruvka_workspace(n) + tree_weight_workspace(n) + 4096;
+                  refine_workspace(m) + boruvka_workspace(n) + tree_weight_workspace(n) + 4096;
     ST(ensure_ws(ctx, 1, need, ar));
     int32_t *members = ar.take<int32_t>(size_t(n));
     int32_t *comp_off = ar.take<int32_t>(size_t(n + 1));
@@ -283,7 +292,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         if (!rev_off || !rev_src || !hist) return fail(ctx, FAMST_ERR_OOM, "workspace");
         ST(reverse_csr(ex, ar, nbr, n, k, rev_off, rev_src));
         CK(cudaMemsetAsync(hist, 0, size_t(max_iters + 1) * 4, ctx->stream));
-        ST(refine_edges(ex, X, d, v4, nbr, k, rev_off, rev_src, comp, eu, evv, ew, eci, ecj, m,
+        ST(refine_edges(ex, ar, X, d, v4, nbr, k, rev_off, rev_src, comp, t, eu, evv, ew, eci, ecj, m,
                         max_iters, hist));
         ev.mark(ctx->stream, 4);
         famst_status s = sync_status(ctx);
@@ -546,14 +555,22 @@ famst_status famst_refine(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
     }
     Arena ar;
     ST(ensure_ws(ctx, 1, align256(size_t(n + 1) * 4) + align256(size_t(n) * k * 4) +
-                             reverse_csr_workspace(n, k) + align256(size_t(max_iters + 1) * 4),
+                             reverse_csr_workspace(n, k) + align256(size_t(max_iters + 1) * 4) +
+                             refine_workspace(m) + 256,
                  ar));
     int32_t *rev_off = ar.take<int32_t>(size_t(n + 1));
     int32_t *rev_src = ar.take<int32_t>(size_t(n) * k);
     int32_t *hist = ar.take<int32_t>(size_t(max_iters + 1));
     ST(reverse_csr(ex, ar, nbr, n, k, rev_off, rev_src));
     CK(cudaMemsetAsync(hist, 0, size_t(max_iters + 1) * 4, ctx->stream));
-    ST(refine_edges(ex, X, d, vec4_ok(X, d), nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj,
+    // number of components: one more than the largest component index in E
+    int32_t *tmax = ar.take<int32_t>(1);
+    CK(cudaMemsetAsync(tmax, 0, 4, ctx->stream));
+    FAMST_LAUNCH(ex, max_i32_kernel, grid_cap(ctx, m, 256), 256, 0, ecj, m, tmax);
+    CK(cudaMemcpyAsync(ctx->pinned + PIN_T, tmax, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int64_t t_e = int64_t(ctx->pinned[PIN_T]) + 1;
+    ST(refine_edges(ex, ar, X, d, vec4_ok(X, d), nbr, k, rev_off, rev_src, comp, t_e, eu, ev, ew, eci, ecj,
                     m, max_iters, hist));
     famst_status s = sync_status(ctx);
     int32_t *hh = new (std::nothrow) int32_t[max_iters + 1];

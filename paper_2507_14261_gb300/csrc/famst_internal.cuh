@@ -182,11 +182,12 @@ famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
                            const int32_t *members, const int32_t *comp_off, int64_t t,
                            int lambda, uint64_t seed, int32_t *eu, int32_t *ev, float *ew,
                            int32_t *eci, int32_t *ecj);
-famst_status refine_edges(const Exec &ex, const float *X, int d, bool vec4,
+famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool vec4,
                           const int32_t *nbr, int k, const int32_t *rev_off,
-                          const int32_t *rev_src, const int32_t *comp, int32_t *eu,
+                          const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
                           int64_t m, int max_iters, int32_t *change_hist /*max_iters+1*/);
+size_t refine_workspace(int64_t m);
 
 // mst.cu
 struct MstOut {

@@ -166,8 +166,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[31])
         : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_ld_wait() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// Wait for this thread's tcgen05.ld results. The registers of the load
+// being waited for are tied to the wait as in/out operands, so no use of
+// them can be scheduled before it.
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                   "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                   "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+__device__ __forceinline__ void epilogue_bar() {  // the four epilogue warps
+    asm volatile("bar.sync 1, 128;" ::: "memory");
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
@@ -226,7 +240,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     unsigned char *sB = sA + size_t(nA) * A_BLOCK;
     float *stg_s = reinterpret_cast<float *>(sB + size_t(args.stages) * B_BLOCK);
     int *stg_j = reinterpret_cast<int *>(stg_s + CAPB * BM);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(stg_j + CAPB * BM);
+    float *sny = reinterpret_cast<float *>(stg_j + CAPB * BM);   // [2][BN] key norms
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sny + 2 * BN);
     uint64_t *full = bars;                       // [stages]
     uint64_t *empty = bars + args.stages;        // [stages]
     uint64_t *a_full = bars + 2 * args.stages;
@@ -382,17 +397,22 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
             tc_fence_after();
             const uint32_t tb = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * BN);
-            const float4 *ny4 = reinterpret_cast<const float4 *>(args.ny + size_t(t) * BN);
-#pragma unroll 1
-            for (int ch = 0; ch < BN / 32; ++ch) {
-                uint32_t v[32];
-                __syncwarp();
-                tmem_ld32(tb + ch * 32, v);
-                tmem_ld_wait();
+            // key norms of this tile into shared memory (double buffered by b;
+            // the barrier of tile t-1 orders every read of buffer b from tile
+            // t-2 before these writes)
+            {
+                const int e = (warp - 2) * 32 + lane;
+                const float *g = args.ny + size_t(t) * BN;
+                sny[b * BN + e] = __ldg(g + e);
+                sny[b * BN + 128 + e] = __ldg(g + 128 + e);
+            }
+            epilogue_bar();
+            const float *nyt = sny + b * BN;
+            auto process = [&](uint32_t(&v)[32], int ch) {
                 float mn = __int_as_float(0x7f800000);
 #pragma unroll
                 for (int c4 = 0; c4 < 8; ++c4) {
-                    float4 nn = __ldg(ny4 + ch * 8 + c4);
+                    float4 nn = *reinterpret_cast<const float4 *>(nyt + ch * 32 + 4 * c4);
                     float s0 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 0]), nn.x);
                     float s1 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 1]), nn.y);
                     float s2 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 2]), nn.z);
@@ -416,6 +436,22 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     }
                 }
                 if (__any_sync(0xffffffffu, cnt > CAPB - 32)) flush();
+            };
+            // two register buffers: the load of chunk c+1 overlaps the
+            // processing of chunk c
+            uint32_t va[32], vb[32];
+            __syncwarp();
+            tmem_ld32(tb, va);
+#pragma unroll 1
+            for (int ch = 0; ch < BN / 32; ch += 2) {
+                tmem_ld_wait(va);
+                __syncwarp();
+                tmem_ld32(tb + (ch + 1) * 32, vb);
+                process(va, ch);
+                tmem_ld_wait(vb);
+                __syncwarp();
+                if (ch + 2 < BN / 32) tmem_ld32(tb + (ch + 2) * 32, va);
+                process(vb, ch + 1);
             }
             tc_fence_before();
             __syncwarp();
@@ -625,11 +661,12 @@ TcPlan tc_plan(int64_t n, int d, int k, bool x3) {
     p.nkb = p.d_pad / BK;
     p.kh = (x3 ? 2 : 1) * p.d_pad;
     // keep at least ~10 candidates beyond k so that the certificate has a
-    // gap to work with: k <= 21 -> 31 candidates, k <= 63 -> 63
-    p.kc = (k <= 21) ? 32 : 64;
+    // gap to work with: k <= 21 -> 31 candidates, k <= 37 -> 47, k <= 63 -> 63
+    p.kc = (k <= 21) ? 32 : (k <= 37 ? 48 : 64);
     p.nq_tiles = (n + BM - 1) / BM;
     p.nk_tiles = (n + BN - 1) / BN;
-    const size_t fixed = 1024 + size_t(x3 ? 2 : 1) * p.nkb * A_BLOCK + size_t(CAPB) * BM * 8 + 512;
+    const size_t fixed = 1024 + size_t(x3 ? 2 : 1) * p.nkb * A_BLOCK + size_t(CAPB) * BM * 8 +
+                         2 * BN * 4 + 512;
     const size_t cap = 227 * 1024;
     int st = cap > fixed ? int((cap - fixed) / B_BLOCK) : 0;
     if (st > 6) st = 6;
@@ -693,17 +730,17 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     CUtensorMap mA, mB;
     if (!make_map(&mA, H, n, p.kh, BM) || !make_map(&mB, H, n, p.kh, BN)) return FAMST_ERR_CUDA;
     TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, ny, cand, splus, ex.dstatus};
-    if (p.kc == 32) {
-        if (cudaFuncSetAttribute(knn_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(p.smem)) != cudaSuccess)
-            return FAMST_ERR_CUDA;
-        FAMST_LAUNCH(ex, knn_tc_kernel<32>, unsigned(p.nq_tiles), TC_THREADS, p.smem, mA, mB, a);
-    } else {
-        if (cudaFuncSetAttribute(knn_tc_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(p.smem)) != cudaSuccess)
-            return FAMST_ERR_CUDA;
-        FAMST_LAUNCH(ex, knn_tc_kernel<64>, unsigned(p.nq_tiles), TC_THREADS, p.smem, mA, mB, a);
-    }
+#define TC_LAUNCH(KCV)                                                                           \
+    do {                                                                                         \
+        if (cudaFuncSetAttribute(knn_tc_kernel<KCV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 int(p.smem)) != cudaSuccess)                                    \
+            return FAMST_ERR_CUDA;                                                               \
+        FAMST_LAUNCH(ex, knn_tc_kernel<KCV>, unsigned(p.nq_tiles), TC_THREADS, p.smem, mA, mB, a); \
+    } while (0)
+    if (p.kc == 32) TC_LAUNCH(32);
+    else if (p.kc == 48) TC_LAUNCH(48);
+    else TC_LAUNCH(64);
+#undef TC_LAUNCH
     if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
     // rerank + certificate
     const double u8 = 1.0 / 256.0;
@@ -719,6 +756,8 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
                  nbr, dist, fail_rows, fail_count)
     if (p.kc == 32) {
         if (vec4) RERANK(4, 32); else RERANK(1, 32);
+    } else if (p.kc == 48) {
+        if (vec4) RERANK(4, 48); else RERANK(1, 48);
     } else {
         if (vec4) RERANK(4, 64); else RERANK(1, 64);
     }
