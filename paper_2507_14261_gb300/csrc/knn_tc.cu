@@ -49,7 +49,7 @@ constexpr int BN = 256;          // keys per tile (accumulator columns)
 constexpr int BK = 64;           // K elements per stage (one 128-byte swizzle atom)
 constexpr int A_BLOCK = BM * BK * 2;   // 16 KB
 constexpr int B_BLOCK = BN * BK * 2;   // 32 KB
-constexpr int CAPB = 40;         // staged candidates per row
+constexpr int CAPB = 24;         // staged candidates per row (flush check every 16 columns)
 constexpr int TC_THREADS = 192;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
 
@@ -387,6 +387,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             thr = ls[KC - 1];
         };
         bool ok = true;
+        const int e_id = (warp - 2) * 32 + lane;   // 0..127 within the epilogue warps
+        float ny_next0 = __ldg(args.ny + e_id), ny_next1 = __ldg(args.ny + 128 + e_id);
         for (int t = 0; t < args.nk_tiles; ++t) {
             const int b = t & 1, use = t >> 1;
             // every lane waits; the warp proceeds only if all lanes saw the phase
@@ -400,16 +402,20 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             // key norms of this tile into shared memory (double buffered by b;
             // the barrier of tile t-1 orders every read of buffer b from tile
             // t-2 before these writes)
-            {
-                const int e = (warp - 2) * 32 + lane;
-                const float *g = args.ny + size_t(t) * BN;
-                sny[b * BN + e] = __ldg(g + e);
-                sny[b * BN + 128 + e] = __ldg(g + 128 + e);
+            sny[b * BN + e_id] = ny_next0;
+            sny[b * BN + 128 + e_id] = ny_next1;
+            if (t + 1 < args.nk_tiles) {   // the next tile's norms load under this tile's work
+                const float *g = args.ny + size_t(t + 1) * BN;
+                ny_next0 = __ldg(g + e_id);
+                ny_next1 = __ldg(g + 128 + e_id);
             }
             epilogue_bar();
             const float *nyt = sny + b * BN;
+            // Candidate staging for 32 columns. The divergent parts only touch
+            // this lane's stage; the warp-collective flush checks sit at
+            // warp-uniform points between the two 16-column halves.
             auto process = [&](uint32_t(&v)[32], int ch) {
-                float mn = __int_as_float(0x7f800000);
+                float mn0 = __int_as_float(0x7f800000), mn1 = mn0;
 #pragma unroll
                 for (int c4 = 0; c4 < 8; ++c4) {
                     float4 nn = *reinterpret_cast<const float4 *>(nyt + ch * 32 + 4 * c4);
@@ -421,12 +427,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     v[4 * c4 + 1] = __float_as_uint(s1);
                     v[4 * c4 + 2] = __float_as_uint(s2);
                     v[4 * c4 + 3] = __float_as_uint(s3);
-                    mn = fminf(mn, fminf(fminf(s0, s1), fminf(s2, s3)));
+                    float m4 = fminf(fminf(s0, s1), fminf(s2, s3));
+                    if (c4 < 4) mn0 = fminf(mn0, m4); else mn1 = fminf(mn1, m4);
                 }
-                if (mn < thr) {
-                    const int j0 = t * BN + ch * 32;
+                const int j0 = t * BN + ch * 32;
+                if (mn0 < thr) {
 #pragma unroll
-                    for (int c = 0; c < 32; ++c) {
+                    for (int c = 0; c < 16; ++c) {
                         float sc = __uint_as_float(v[c]);
                         if (sc < thr) {
                             my_s[cnt * BM] = sc;
@@ -435,7 +442,20 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         }
                     }
                 }
-                if (__any_sync(0xffffffffu, cnt > CAPB - 32)) flush();
+                // at most 16 more per half: flush before a stage could overflow
+                if (__any_sync(0xffffffffu, cnt > CAPB - 16)) flush();
+                if (mn1 < thr) {
+#pragma unroll
+                    for (int c = 16; c < 32; ++c) {
+                        float sc = __uint_as_float(v[c]);
+                        if (sc < thr) {
+                            my_s[cnt * BM] = sc;
+                            my_j[cnt * BM] = j0 + c;
+                            ++cnt;
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, cnt > CAPB - 16)) flush();
             };
             // two register buffers: the load of chunk c+1 overlaps the
             // processing of chunk c
