@@ -153,7 +153,8 @@ def cpu_baseline(X, k: int, budget_s: float = 15.0):
     oracle.build()
     n = X.shape[0]
     cores = os.cpu_count() or 1
-    probe = max(cores, 8)
+    probe = 4 * cores
+    oracle.knn(X, k, rows=(0, cores), threads=cores)  # warm the threads and caches
     t0 = time.perf_counter()
     oracle.knn(X, k, rows=(0, probe), threads=cores)
     dt = time.perf_counter() - t0
@@ -176,7 +177,8 @@ def run_reference(args, world, rank):
     X = w.points()
     cores = os.cpu_count() or 1
     # rows per step sized so that the whole run stays within a few minutes
-    probe = max(cores, 8)
+    probe = 4 * cores
+    oracle.knn(X, w.k, rows=(0, cores), threads=cores)  # warm the threads and caches
     t0 = time.perf_counter()
     oracle.knn(X, w.k, rows=(0, probe), threads=cores)
     per_row = (time.perf_counter() - t0) / probe
