@@ -116,6 +116,27 @@ def dist_setup():
     return world, rank, local
 
 
+def rank_workload(w, rank: int):
+    """Each rank builds its own independent cloud of the same recipe
+    (seed + rank): weak scaling with no data-path exchange."""
+    return workloads.Workload(w.name, w.n, w.d, w.k, w.lam, w.seed + rank, w.kind)
+
+
+def max_over_ranks(x: float, pg, device) -> float:
+    """The slowest rank's time (all_reduce MAX); identity without a group."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(world: int, n: int, steps: int, seconds: float) -> float:
+    """Whole-job points per second: every rank builds `steps` clouds of n."""
+    return world * n * steps / seconds
+
+
 def kernel_source_hash(prec: str) -> str:
     f = "knn_fp32.cu" if prec == "fp32" else "knn_tc.cu"
     p = os.path.join(ROOT, "paper_2507_14261_gb300", "csrc", f)
@@ -241,7 +262,7 @@ def main():
     w = workloads.get(args.workload)
     if args.n is not None:
         w = workloads.Workload(w.name, args.n, w.d, w.k, w.lam, w.seed, w.kind)
-    X_np = workloads.Workload(w.name, w.n, w.d, w.k, w.lam, w.seed + rank, w.kind).points()
+    X_np = rank_workload(w, rank).points()
     X = torch.from_numpy(X_np).cuda()
     ctx = fam.Context(local)
     stream = torch.cuda.current_stream()
@@ -268,12 +289,8 @@ def main():
     barrier()
     clocks = sampler.stop()
     launches = ctx.launches - launches0
-    ms = e0.elapsed_time(e1)
-    if pg is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * w.n * args.steps / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1), pg, "cuda")
+    value = throughput(world, w.n, args.steps, ms / 1e3)
 
     # end to end through the host-buffer entry point: pinned X in, tree out
     e2e = None
@@ -288,12 +305,8 @@ def main():
         for _ in range(args.steps):
             ctx.build_host(Xh, w.k, w.lam, 1, args.prec, out=out)
         barrier()
-        dt = time.perf_counter() - t0
-        if pg is not None:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * w.n * args.steps / dt, "unit": "points/s",
+        dt = max_over_ranks(time.perf_counter() - t0, pg, "cuda")
+        e2e = {"value": throughput(world, w.n, args.steps, dt), "unit": "points/s",
                "h2d_bytes_per_step": int(X_np.nbytes),
                "d2h_bytes_per_step": int((w.n - 1) * 12 + 8)}
 
