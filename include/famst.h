@@ -12,6 +12,7 @@
  *   then     Kruskal-equivalent MST of kNN edges + E       famst_mst
  * famst_build runs all of it. famst_mst_backward differentiates the tree
  * weight with respect to the points; famst_build_batched runs many clouds.
+ * famst_components_noalloc labels components without any allocation.
  *
  * Conventions for every call:
  *  - Pointers are DEVICE pointers owned by the caller unless the argument
@@ -187,6 +188,39 @@ famst_status famst_build_host(famst_ctx *ctx, const float *X_host, int64_t n, in
                               int32_t k, int32_t lambda, uint64_t seed, int32_t prec,
                               int32_t max_iters, int32_t *tu_host, int32_t *tv_host,
                               float *tw_host, double *W_out, famst_build_info *info);
+
+/* ----------------------------------------------------- many clouds
+ * Builds of B independent clouds in one call. X (device) holds the clouds
+ * back to back: cloud b is n_b = offsets[b+1] - offsets[b] rows of dims[b]
+ * floats (offsets: HOST, B+1 entries, offsets[0] = 0; dims: HOST, B).
+ * Cloud b's result is bit-identical to famst_build of that cloud alone with
+ * seed + b. Every phase runs once over the whole batch (a fixed sequence of
+ * launches whose data-dependent counts stay on the device); the first call
+ * for a given shape, parameters and pointers runs it and captures it in a
+ * CUDA graph, later identical calls replay the graph. Phase 1 uses the
+ * tensor tiles or the FP32 tiles per cloud, as an autotuner measured
+ * faster on this device for that cloud's (d, n) class (cached per process;
+ * appended to the file named by FAMST_AUTOTUNE_CACHE when set).
+ * tu/tv/tw (device, offsets[B] - B entries): cloud b's n_b - 1 tree edges at
+ * [offsets[b] - b, offsets[b+1] - b - 1), as cloud-local ids in
+ * (round, component) order. W (HOST, B): FP64 tree weight per cloud; t_out
+ * (HOST, B, may be NULL): components of each cloud's kNN graph.
+ * Requires n_b >= k + 1, 1 <= k <= 64, dims <= 512. Synchronises. */
+typedef struct famst_batch_info {
+    int64_t m;                /* inter-component edges of all clouds */
+    int32_t refine_sweeps;    /* largest sweep count of any cloud */
+    int32_t boruvka_rounds;
+    int64_t uncertified_rows; /* tensor-tile rows recomputed in FP32 */
+    int32_t tensor_clouds;    /* clouds whose Phase 1 ran on the tensor tiles */
+    int32_t graph_replayed;   /* 1 if this call replayed a captured graph */
+    int64_t graph_kernels;    /* kernels in the captured sequence */
+} famst_batch_info;
+
+famst_status famst_build_batched(famst_ctx *ctx, const float *X, const int64_t *offsets,
+                                 const int32_t *dims, int32_t B, int32_t k, int32_t lambda,
+                                 uint64_t seed, int32_t prec, int32_t max_iters, int32_t *tu,
+                                 int32_t *tv, float *tw, double *W, int64_t *t_out,
+                                 famst_batch_info *info);
 
 /* -------------------------------------------------------- backward
  * Gradient of W = sum over tree edges of ||x_u - x_v|| with the tree held

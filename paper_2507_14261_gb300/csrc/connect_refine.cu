@@ -99,6 +99,87 @@ __global__ void connect_kernel(const float *__restrict__ X, int d,
     }
 }
 
+// Batched connect: pairs of every cloud in one index space. pp[b] (B+1,
+// device) = number of pairs of clouds before b, cbase[b] (B+1) = the first
+// global component index of cloud b; cloud b draws with key seed + b and the
+// cloud-local pair index, exactly as a build of that cloud alone.
+template <int PER, int VEC>
+__global__ void connect_batched_kernel(const float *__restrict__ X, int ld, int dc,
+                                       const int32_t *__restrict__ members,
+                                       const int32_t *__restrict__ comp_off,
+                                       const long long *__restrict__ pp,
+                                       const int32_t *__restrict__ cbase, int B, int lambda,
+                                       uint64_t seed, int64_t m_cap, int32_t *__restrict__ eu,
+                                       int32_t *__restrict__ ev, float *__restrict__ ew,
+                                       int32_t *__restrict__ eci, int32_t *__restrict__ ecj) {
+    const int lane = threadIdx.x & 31;
+    const int64_t npairs = pp[B];
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int L2 = lambda * lambda;
+    for (int64_t pg = warp0; pg < npairs; pg += nwarps) {
+        int lo = 0, hi = B;  // pp[lo] <= pg < pp[hi]
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (pp[mid] <= pg) lo = mid; else hi = mid;
+        }
+        const int b = lo;
+        const int64_t t = cbase[b + 1] - cbase[b];
+        const int64_t pl = pg - pp[b];
+        int64_t i, j;
+        pair_of(pl, t, i, j);
+        const uint64_t p = uint64_t(i) * uint64_t(t) + uint64_t(j);
+        const uint64_t sb = seed + uint64_t(b);
+        const uint2 key = make_uint2(uint32_t(sb), uint32_t(sb >> 32));
+        const int gi = cbase[b] + int(i), gj = cbase[b] + int(j);
+        const int32_t oi = comp_off[gi], oj = comp_off[gj];
+        const uint64_t si = uint64_t(comp_off[gi + 1] - oi), sj = uint64_t(comp_off[gj + 1] - oj);
+        uint64_t kk[PER];
+        int32_t uu[PER], vv[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            int s = lane + 32 * q;
+            kk[q] = KEY_NONE;
+            if (s < L2) {
+                uint4 r = philox4x32_10(make_uint4(uint32_t(s), uint32_t(p), uint32_t(p >> 32), 0u),
+                                        key);
+                int32_t u = members[oi + int64_t((uint64_t(r.x) * si) >> 32)];
+                int32_t v = members[oj + int64_t((uint64_t(r.y) * sj) >> 32)];
+                float w = canon_dist<VEC>(X + int64_t(u) * ld, X + int64_t(v) * ld, dc);
+                kk[q] = nb_key(w, uint32_t(s));
+                uu[q] = u;
+                vv[q] = v;
+            }
+        }
+        const int64_t ebase = pg * lambda;
+        for (int r = 0; r < lambda; ++r) {
+            uint64_t mine = KEY_NONE;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) mine = kk[q] < mine ? kk[q] : mine;
+            uint64_t best = warp_min_u64(mine);
+            int s = int(key_lo(best));
+            if ((s & 31) == lane && ebase + r < m_cap) {
+                int qq = s >> 5;
+#pragma unroll
+                for (int q = 0; q < PER; ++q)
+                    if (q == qq) {
+                        kk[q] = KEY_NONE;
+                        eu[ebase + r] = uu[q];
+                        ev[ebase + r] = vv[q];
+                        ew[ebase + r] = key_w(best);
+                        eci[ebase + r] = gi;
+                        ecj[ebase + r] = gj;
+                    }
+            } else if ((s & 31) == lane) {
+                int qq = s >> 5;
+#pragma unroll
+                for (int q = 0; q < PER; ++q)
+                    if (q == qq) kk[q] = KEY_NONE;
+            }
+        }
+    }
+}
+
 // argmin over the adjacency of `c` (kNN list + reverse edges) of the
 // candidate key (w(cand, fixed), 1 + cand); incumbent keyed (w0, 0).
 // Direct version: each lane streams its candidate's row from global memory.
@@ -202,9 +283,11 @@ __global__ void refine_kernel(const float *__restrict__ X, int d, int ld,
                               const int32_t *__restrict__ comp, int32_t *__restrict__ eu,
                               int32_t *__restrict__ ev, float *__restrict__ ew,
                               const int32_t *__restrict__ eci, const int32_t *__restrict__ ecj,
-                              const int32_t *__restrict__ order, int64_t m, int max_iters,
+                              const int32_t *__restrict__ order, int64_t m,
+                              const int64_t *__restrict__ m_dev, int max_iters,
                               int32_t *__restrict__ change_hist,
                               unsigned long long *__restrict__ next_item, int *dstatus) {
+    if (m_dev) m = *m_dev < m ? *m_dev : m;  // device-side edge count, capped by capacity
     extern __shared__ __align__(16) float rsm[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -333,22 +416,90 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
     int64_t cap = int64_t(ex.num_sms) * (staged ? 12 : 16);
     unsigned grid = unsigned(want < cap ? want : cap);
     if (staged) {
-        if (cudaFuncSetAttribute(refine_kernel<4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 int(smem)) != cudaSuccess)
+        if (set_smem_attr(refine_kernel<4, true>, smem, ex.stream) != cudaSuccess)
             return FAMST_ERR_CUDA;
         FAMST_LAUNCH(ex, (refine_kernel<4, true>), grid, th, smem, X, d, ld, nbr, k, rev_off, rev_src,
-                     comp, eu, ev, ew, eci, ecj, order, m, max_iters, change_hist, next_item,
-                     ex.dstatus);
+                     comp, eu, ev, ew, eci, ecj, order, m, nullptr, max_iters, change_hist,
+                     next_item, ex.dstatus);
     } else if (vec4) {
         FAMST_LAUNCH(ex, (refine_kernel<4, false>), grid, th, 0, X, d, ld, nbr, k, rev_off, rev_src,
-                     comp, eu, ev, ew, eci, ecj, order, m, max_iters, change_hist, next_item,
-                     ex.dstatus);
+                     comp, eu, ev, ew, eci, ecj, order, m, nullptr, max_iters, change_hist,
+                     next_item, ex.dstatus);
     } else {
         FAMST_LAUNCH(ex, (refine_kernel<1, false>), grid, th, 0, X, d, ld, nbr, k, rev_off, rev_src,
-                     comp, eu, ev, ew, eci, ecj, order, m, max_iters, change_hist, next_item,
-                     ex.dstatus);
+                     comp, eu, ev, ew, eci, ecj, order, m, nullptr, max_iters, change_hist,
+                     next_item, ex.dstatus);
     }
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+}  // namespace famst
+
+namespace famst {
+
+// Refinement of E with a device-side edge count (at most m_cap), edges in
+// their stored order; nothing here synchronises with the host.
+famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, bool vec4,
+                              const int32_t *nbr, int k, const int32_t *rev_off,
+                              const int32_t *rev_src, const int32_t *comp, int32_t *eu,
+                              int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
+                              int64_t m_cap, const int64_t *m_dev, int max_iters,
+                              int32_t *change_hist) {
+    if (m_cap == 0) return FAMST_OK;
+    unsigned long long *next_item = ar.take<unsigned long long>(1);
+    if (!next_item) return FAMST_ERR_OOM;
+    if (cudaMemsetAsync(next_item, 0, 8, ex.stream) != cudaSuccess) return FAMST_ERR_CUDA;
+    const bool staged = vec4 && d <= 512;
+    const int ld = d + ((d % 8 == 0) ? 4 : 8);
+    const int th = staged ? 128 : 256;
+    const size_t smem = staged ? size_t(th / 32) * (32 * ld + d) * sizeof(float) : 0;
+    int64_t want = (m_cap * 32 + th - 1) / th;
+    int64_t cap = int64_t(ex.num_sms) * (staged ? 12 : 16);
+    unsigned grid = unsigned(want < cap ? want : cap);
+    if (staged) {
+        if (set_smem_attr(refine_kernel<4, true>, smem, ex.stream) != cudaSuccess)
+            return FAMST_ERR_CUDA;
+        FAMST_LAUNCH(ex, (refine_kernel<4, true>), grid, th, smem, X, d, ld, nbr, k, rev_off, rev_src,
+                     comp, eu, ev, ew, eci, ecj, nullptr, m_cap, m_dev, max_iters, change_hist,
+                     next_item, ex.dstatus);
+    } else if (vec4) {
+        FAMST_LAUNCH(ex, (refine_kernel<4, false>), grid, th, 0, X, d, ld, nbr, k, rev_off, rev_src,
+                     comp, eu, ev, ew, eci, ecj, nullptr, m_cap, m_dev, max_iters, change_hist,
+                     next_item, ex.dstatus);
+    } else {
+        FAMST_LAUNCH(ex, (refine_kernel<1, false>), grid, th, 0, X, d, ld, nbr, k, rev_off, rev_src,
+                     comp, eu, ev, ew, eci, ecj, nullptr, m_cap, m_dev, max_iters, change_hist,
+                     next_item, ex.dstatus);
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+}  // namespace famst
+
+namespace famst {
+
+famst_status connect_edges_batched(const Exec &ex, const float *X, int ld, int dc,
+                                   const int32_t *members, const int32_t *comp_off,
+                                   const long long *pp, const int32_t *cbase, int B, int lambda,
+                                   uint64_t seed, int64_t m_cap, int32_t *eu, int32_t *ev,
+                                   float *ew, int32_t *eci, int32_t *ecj) {
+    int per = (lambda * lambda + 31) / 32;
+    const int th = 256;
+    unsigned grid = unsigned(ex.num_sms) * 16;
+#define CONNECT_B_CASE(P)                                                                          \
+    if (per <= P) {                                                                                \
+        FAMST_LAUNCH(ex, (connect_batched_kernel<P, 4>), grid, th, 0, X, ld, dc, members, comp_off, \
+                     pp, cbase, B, lambda, seed, m_cap, eu, ev, ew, eci, ecj);                     \
+        return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;                   \
+    }
+    CONNECT_B_CASE(1)
+    CONNECT_B_CASE(2)
+    CONNECT_B_CASE(4)
+    CONNECT_B_CASE(8)
+    CONNECT_B_CASE(16)
+    CONNECT_B_CASE(32)
+#undef CONNECT_B_CASE
+    return FAMST_ERR_UNSUPPORTED;
 }
 
 }  // namespace famst

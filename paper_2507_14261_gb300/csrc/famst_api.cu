@@ -4,12 +4,45 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 
+#include <vector>
+
+#include "batch.cuh"
 #include "famst_internal.cuh"
 
 using namespace famst;
+
+// The last batched build's plan and its instantiated CUDA graph.
+struct BatchCache {
+    bool valid = false;
+    std::vector<int64_t> offsets;
+    std::vector<int32_t> dims;
+    int B = 0, k = 0, lambda = 0, prec = 0, max_iters = 0;
+    uint64_t seed = 0;
+    const float *X = nullptr;
+    int32_t *tu = nullptr, *tv = nullptr;
+    float *tw = nullptr;
+    BatchPlan plan;
+    BatchHost host;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long graph_kernels = 0;
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        if (host.W) cudaFreeHost(host.W);
+        if (host.cbase) cudaFreeHost(host.cbase);
+        if (host.hist) cudaFreeHost(host.hist);
+        if (host.words) cudaFreeHost(host.words);
+        host = BatchHost();
+        valid = false;
+    }
+};
 
 struct famst_ctx {
     int device = 0;
@@ -17,9 +50,11 @@ struct famst_ctx {
     int num_sms = 1;
     unsigned long long launches = 0;
     // workspace slots: 0 = Phase 1 outputs and scratch, 1 = later phases,
-    // 2 = device copies made by famst_build_host
-    char *ws[3] = {nullptr, nullptr, nullptr};
-    size_t ws_cap[3] = {0, 0, 0};
+    // 2 = device copies made by famst_build_host, 3 = batched builds
+    char *ws[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t ws_cap[4] = {0, 0, 0, 0};
+    cudaStream_t bstream = nullptr;  // private stream of batched builds (graph capture)
+    BatchCache batch;
     int *dstatus = nullptr;       // device status word
     int32_t *pinned = nullptr;    // 64 bytes of pinned host memory, slots PIN_*
     double *dW = nullptr;         // device: W, W64
@@ -395,6 +430,7 @@ famst_status famst_create(famst_ctx **out, int device) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->dW, 2 * sizeof(double));
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->pinned, 64);
     if (e == cudaSuccess) e = cudaMemset(ctx->dstatus, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->bstream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         cudaGetLastError();
         famst_destroy(ctx);
@@ -408,7 +444,9 @@ famst_status famst_destroy(famst_ctx *ctx) {
     if (!ctx) return FAMST_OK;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    for (int i = 0; i < 3; ++i)
+    ctx->batch.release();
+    if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
+    for (int i = 0; i < 4; ++i)
         if (ctx->ws[i]) cudaFree(ctx->ws[i]);
     if (ctx->dstatus) cudaFree(ctx->dstatus);
     if (ctx->dW) cudaFree(ctx->dW);
@@ -445,7 +483,7 @@ const char *famst_last_error(const famst_ctx *ctx) { return ctx ? ctx->err : "";
 uint64_t famst_launch_count(const famst_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 size_t famst_workspace_bytes(const famst_ctx *ctx) {
-    return ctx ? ctx->ws_cap[0] + ctx->ws_cap[1] + ctx->ws_cap[2] : 0;
+    return ctx ? ctx->ws_cap[0] + ctx->ws_cap[1] + ctx->ws_cap[2] + ctx->ws_cap[3] : 0;
 }
 
 famst_status famst_knn_graph(famst_ctx *ctx, const float *X, int64_t n, int32_t d, int32_t k,
@@ -709,6 +747,166 @@ famst_status famst_build_host(famst_ctx *ctx, const float *X_host, int64_t n, in
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && s == FAMST_OK)
         s = cuda_fail(ctx, cudaGetLastError(), "synchronise");
     return s;
+}
+
+static famst_status batch_results(famst_ctx *ctx, const BatchCache &c, double *W, int64_t *t_out,
+                                  famst_batch_info *info) {
+    const int64_t *w = c.host.words;
+    const int st = int(w[3]);
+    if (st & batch_status_capacity()) return fail(ctx, FAMST_ERR_CAPACITY, "edge capacity");
+    if (st & STATUS_NONFINITE) return fail(ctx, FAMST_ERR_NONFINITE, "X holds NaN or Inf");
+    if (st & STATUS_LOOP_LIMIT) return fail(ctx, FAMST_ERR_TIMEOUT, "a bounded device loop reached its limit");
+    if (st & STATUS_REFINE_CAP) return fail(ctx, FAMST_ERR_NO_CONVERGENCE, "refinement reached max_iters");
+    if (st & (STATUS_DISCONNECTED | STATUS_BAD_ID)) return fail(ctx, FAMST_ERR_DISCONNECTED, "forest incomplete");
+    for (int b = 0; b < c.B; ++b) {
+        if (W) W[b] = c.host.W[b];
+        if (t_out) t_out[b] = c.host.cbase[b + 1] - c.host.cbase[b];
+    }
+    if (info) {
+        memset(info, 0, sizeof(*info));
+        info->m = w[0];
+        int sweeps = 0;
+        for (int q = 0; q <= c.max_iters; ++q)
+            if (c.host.hist[q]) sweeps = q + 1;
+        info->refine_sweeps = sweeps;
+        info->boruvka_rounds = int32_t(w[2]);
+        info->uncertified_rows = c.plan.any_tc ? w[4] : 0;
+        info->tensor_clouds = 0;
+        for (int b = 0; b < c.B; ++b) info->tensor_clouds += c.plan.cl[b].use_tc;
+        info->graph_kernels = int64_t(c.graph_kernels);
+    }
+    return FAMST_OK;
+}
+
+famst_status famst_build_batched(famst_ctx *ctx, const float *X, const int64_t *offsets,
+                                 const int32_t *dims, int32_t B, int32_t k, int32_t lambda,
+                                 uint64_t seed, int32_t prec, int32_t max_iters, int32_t *tu,
+                                 int32_t *tv, float *tw, double *W, int64_t *t_out,
+                                 famst_batch_info *info) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!X || !offsets || !dims || B < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "bad batch");
+    if (lambda < 1 || lambda > 32) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= lambda <= 32");
+    if (max_iters < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "need max_iters >= 1");
+    if (prec < 0 || prec > 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown precision");
+    if (k < 1 || k > 64) return fail(ctx, FAMST_ERR_UNSUPPORTED, "batched builds need 1 <= k <= 64");
+    if (offsets[0] != 0) return fail(ctx, FAMST_ERR_INVALID_ARG, "offsets[0] must be 0");
+    int dmax = 0;
+    for (int b = 0; b < B; ++b) {
+        const int64_t nb = offsets[b + 1] - offsets[b];
+        if (nb < int64_t(k) + 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "every cloud needs n_b >= k + 1");
+        if (dims[b] < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "dims must be >= 1");
+        dmax = dims[b] > dmax ? dims[b] : dmax;
+    }
+    const int64_t N = offsets[B];
+    if (N * int64_t(k) >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "sum(n)*k must be < 2^31");
+    if (dmax > 512) return fail(ctx, FAMST_ERR_UNSUPPORTED, "batched builds need d <= 512");
+    if (!tu || !tv || !tw) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL tree array");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));  // inputs are ordered before the private stream
+    BatchCache &c = ctx->batch;
+    const bool hit = c.valid && c.exec && c.B == B && c.k == k && c.lambda == lambda &&
+                     c.prec == prec && c.max_iters == max_iters && c.seed == seed &&
+                     int(c.offsets.size()) == B + 1 &&
+                     std::equal(c.offsets.begin(), c.offsets.end(), offsets) &&
+                     std::equal(c.dims.begin(), c.dims.end(), dims);
+    // the captured sequence works on its own buffers: copy the clouds in
+    // before it and the trees out after it
+    auto copy_in = [&]() {
+        return cudaMemcpyAsync(c.plan.dev.Xin, X, size_t(c.plan.xoff.back()) * 4,
+                               cudaMemcpyDeviceToDevice, ctx->bstream);
+    };
+    auto copy_out = [&]() {
+        const size_t m = size_t(N - B);
+        cudaError_t e = cudaSuccess;
+        if (m > 0) {
+            e = cudaMemcpyAsync(tu, c.plan.dev.out_u, m * 4, cudaMemcpyDeviceToDevice, ctx->bstream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(tv, c.plan.dev.out_v, m * 4, cudaMemcpyDeviceToDevice, ctx->bstream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(tw, c.plan.dev.out_w, m * 4, cudaMemcpyDeviceToDevice, ctx->bstream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->bstream);
+        return e;
+    };
+    if (hit) {
+        CK(copy_in());
+        CK(cudaGraphLaunch(c.exec, ctx->bstream));
+        CK(copy_out());
+        ctx->launches += c.graph_kernels;
+        famst_status s = batch_results(ctx, c, W, t_out, info);
+        if (info) info->graph_replayed = 1;
+        return s;
+    }
+    c.release();
+    c.offsets.assign(offsets, offsets + B + 1);
+    c.dims.assign(dims, dims + B);
+    c.B = B; c.k = k; c.lambda = lambda; c.prec = prec; c.max_iters = max_iters; c.seed = seed;
+    c.X = X; c.tu = tu; c.tv = tv; c.tw = tw;
+    Exec ex{ctx->bstream, &ctx->launches, ctx->num_sms, ctx->dstatus};
+    // first guess for the edge capacity: up to 48 components per cloud
+    int64_t m_cap = 0;
+    for (int b = 0; b < B; ++b) {
+        int64_t tb = (offsets[b + 1] - offsets[b]) / (k + 1);
+        tb = tb < 48 ? tb : 48;
+        m_cap += int64_t(lambda) * tb * (tb - 1) / 2;
+    }
+    famst_status s = FAMST_OK;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        s = batch_plan(ex, offsets, dims, B, k, lambda, prec, max_iters, m_cap, &c.plan);
+        if (s != FAMST_OK) return fail(ctx, s, "batch plan");
+        Arena ar;
+        ST(ensure_ws(ctx, 3, batch_workspace(c.plan), ar));
+        ST(batch_bind(c.plan, ar.base, ar.cap, ctx->bstream));
+        if (!c.host.W) {
+            CK(cudaMallocHost(&c.host.W, size_t(B) * 8));
+            CK(cudaMallocHost(&c.host.cbase, size_t(B + 1) * 4));
+            CK(cudaMallocHost(&c.host.hist, size_t(max_iters + 1) * 4));
+            CK(cudaMallocHost(&c.host.words, 8 * 8));
+        }
+        memset(c.host.words, 0, 64);
+        CK(copy_in());
+        s = batch_enqueue(ex, c.plan, ar.base, ar.cap, seed, &c.host);
+        if (s != FAMST_OK) return fail(ctx, s, "batch enqueue");
+        CK(copy_out());
+        if ((int(c.host.words[3]) & batch_status_capacity()) && attempt == 0) {
+            m_cap = c.host.words[0] + c.host.words[0] / 4 + 1;  // the device reported what it needs
+            continue;
+        }
+        break;
+    }
+    s = batch_results(ctx, c, W, t_out, info);
+    if (s != FAMST_OK) return s;
+    // capture the same sequence once; later calls with this key replay it
+    unsigned long long counted = 0;
+    Exec cap_ex{ctx->bstream, &counted, ctx->num_sms, ctx->dstatus};
+    CK(cudaStreamBeginCapture(ctx->bstream, cudaStreamCaptureModeRelaxed));
+    famst_status se = batch_enqueue(cap_ex, c.plan, ctx->ws[3], ctx->ws_cap[3], seed, &c.host);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(ctx->bstream, &g);
+    if (se != FAMST_OK || ee != cudaSuccess || !g) {
+        // the eager run's results stand; no graph is cached (reason kept)
+        snprintf(ctx->err, sizeof(ctx->err), "graph capture failed: %s / %s",
+                 famst_error_string(se), cudaGetErrorString(ee));
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (info) info->graph_kernels = -1;
+        return FAMST_OK;
+    }
+    cudaError_t ei = cudaGraphInstantiate(&c.exec, g, 0);
+    if (ei != cudaSuccess) {
+        snprintf(ctx->err, sizeof(ctx->err), "graph instantiation failed: %s", cudaGetErrorString(ei));
+        cudaGraphDestroy(g);
+        cudaGetLastError();
+        c.exec = nullptr;
+        if (info) info->graph_kernels = -1;
+        return FAMST_OK;
+    }
+    c.graph = g;
+    c.graph_kernels = counted;
+    c.valid = true;
+    if (info) info->graph_kernels = int64_t(counted);
+    return FAMST_OK;
 }
 
 famst_status famst_mst_backward(famst_ctx *ctx, const float *X, int64_t n, int32_t d,

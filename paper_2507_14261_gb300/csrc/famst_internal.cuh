@@ -51,6 +51,19 @@ struct Arena {
 
 static inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Shared-memory opt-in of a kernel. Skipped while the stream is being
+// captured into a CUDA graph: the attribute persists from the eager run that
+// always precedes a capture, and setting it is not a stream operation.
+static inline bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive;
+}
+template <class K>
+static inline cudaError_t set_smem_attr(K *kernel, size_t bytes, cudaStream_t s) {
+    if (stream_capturing(s)) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+}
+
 // ---------------------------------------------------------------- device
 
 static constexpr uint64_t KEY_NONE = ~0ull;
@@ -151,6 +164,38 @@ famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int 
                       int32_t *nbr, float *dist);
 size_t knn_fp32_workspace(int64_t n, int d, int k, int64_t nq, int num_sms);
 
+// Batched launches lay the clouds out in a padded row space: cloud b
+// occupies rows roff[b] .. roff[b] + n_b - 1 of a zero-padded copy whose
+// clouds start on 256-row boundaries, so a query or key tile never straddles
+// two clouds. Compact (unpadded) ids are padded row - shift.
+struct TcTile {
+    int q0;        // first padded query row of the CTA (128 rows)
+    int kt0, kt1;  // the cloud's 256-key tiles [kt0, kt1)
+    int nkb;       // active 64-wide K blocks of the hi part
+    int row_end;   // padded rows >= row_end are padding
+    int shift;     // compact id = padded row - shift
+};
+struct F32Tile {
+    int qbase;     // first query row of the block (64 rows)
+    int nq;        // valid queries in the block
+    int tile0, tile1;  // key tiles [tile0, tile1) of 128 rows starting at key_base
+    int key_base;  // row of key tile 0
+    int key_end;   // rows >= key_end are not keys of this cloud
+    int d;         // active dimensions of the cloud
+    int shift;     // output id = row - shift
+};
+// Per-cloud description used by the batched re-rank / fallback kernels.
+struct CloudDev {
+    long long voff;   // first compact id
+    int n;            // points
+    int d;            // dimensions
+    int d_pad;        // tensor-tile K extent (multiple of 64)
+    int use_tc;       // 1: rows come from the tensor tiles (re-rank them)
+};
+
+famst_status knn_fp32_batched(const Exec &ex, const float *Xp, int ld, int k, const F32Tile *tiles,
+                              int64_t nblocks, int32_t *nbr, float *dist);
+
 // knn_tc.cu
 // Exact kNN through tcgen05 BF16 (x3 = hi/lo split) distance tiles, FP32
 // re-rank, certificate, FP32 recomputation of uncertified rows.
@@ -159,6 +204,21 @@ size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms);
 famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k, bool x3,
                     bool vec4, int32_t *nbr, float *dist, int32_t *pinned_host,
                     int64_t *uncertified);
+
+}  // namespace famst
+#include <cuda.h>
+#include <cuda_bf16.h>
+namespace famst {
+bool knn_tc_batched_plan(int D, int k, bool x3, int *stages, size_t *smem, int *kc);
+famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, int64_t NP,
+                            const long long *voff, const long long *roff, int B,
+                            const CloudDev *cl, const TcTile *tiles, int64_t nctas, int k,
+                            bool x3, int stages, size_t smem, int kc, __nv_bfloat16 *H, float *ny,
+                            float *xn2, float *mean, unsigned *ymax, int32_t *cand, float *splus,
+                            int32_t *fail_rows, int32_t *fail_count, int32_t *nbr, float *dist,
+                            const CUtensorMap *mA, const CUtensorMap *mB);
+bool knn_tc_batched_maps(const void *H, int64_t NP, int D, bool x3, CUtensorMap *mA,
+                         CUtensorMap *mB);
 
 // graph.cu
 famst_status exclusive_scan_i32(const Exec &ex, Arena &ar, const int32_t *in,
@@ -182,12 +242,23 @@ famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
                            const int32_t *members, const int32_t *comp_off, int64_t t,
                            int lambda, uint64_t seed, int32_t *eu, int32_t *ev, float *ew,
                            int32_t *eci, int32_t *ecj);
+famst_status connect_edges_batched(const Exec &ex, const float *X, int ld, int dc,
+                                   const int32_t *members, const int32_t *comp_off,
+                                   const long long *pp, const int32_t *cbase, int B, int lambda,
+                                   uint64_t seed, int64_t m_cap, int32_t *eu, int32_t *ev,
+                                   float *ew, int32_t *eci, int32_t *ecj);
 famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool vec4,
                           const int32_t *nbr, int k, const int32_t *rev_off,
                           const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
                           int64_t m, int max_iters, int32_t *change_hist /*max_iters+1*/);
 size_t refine_workspace(int64_t m);
+famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, bool vec4,
+                              const int32_t *nbr, int k, const int32_t *rev_off,
+                              const int32_t *rev_src, const int32_t *comp, int32_t *eu,
+                              int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
+                              int64_t m_cap, const int64_t *m_dev, int max_iters,
+                              int32_t *change_hist);
 
 // mst.cu
 struct MstOut {
@@ -199,6 +270,10 @@ famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr,
                      const float *ew, int64_t m, MstOut out, int64_t *tree_edges,
                      int *rounds, int32_t *pinned_host);
 size_t boruvka_workspace(int64_t n);
+famst_status boruvka_dev(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr,
+                         const float *dist, int k, const int32_t *eu, const int32_t *ev,
+                         const float *ew, int64_t m_cap, const int64_t *m_dev, MstOut out,
+                         int64_t out_cap, int max_rounds, long long *edges_dev, int *rounds_dev);
 famst_status tree_weight(const Exec &ex, Arena &ar, const float *X, int d, bool vec4,
                          const int32_t *tu, const int32_t *tv, const float *tw, int64_t m,
                          double *W_dev /*2 doubles: W, W64*/);

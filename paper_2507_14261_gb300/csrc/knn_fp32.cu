@@ -42,10 +42,11 @@ struct KnnSmem {
 };
 
 __global__ void __launch_bounds__(NT, 1)
-knn_fp32_kernel(const float *__restrict__ X, int n, int d, int k,
+knn_fp32_kernel(const float *__restrict__ X, int n, int d, int ld, int k,
                 const int32_t *__restrict__ qrows, int64_t q0, int nq,
                 int tiles_per_split, uint64_t *__restrict__ part,
-                int32_t *__restrict__ nbr, float *__restrict__ dist) {
+                int32_t *__restrict__ nbr, float *__restrict__ dist,
+                const F32Tile *__restrict__ btab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int spr = spr_for(k);
     const int nsel = QM * spr;
@@ -57,11 +58,26 @@ knn_fp32_kernel(const float *__restrict__ X, int n, int d, int k,
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int qbase = blockIdx.x * QM;
+    int qbase = blockIdx.x * QM;
     const int split = blockIdx.y;
-    const int ntiles_total = (n + KN - 1) / KN;
-    const int tile_begin = split * tiles_per_split;
-    const int tile_end = min(ntiles_total, tile_begin + tiles_per_split);
+    int tile_begin, tile_end, shift = 0, key_base = 0;
+    if (btab) {
+        // batched: one block per 64 query rows of one cloud, keys = the cloud
+        const F32Tile T = btab[blockIdx.x];
+        tile_begin = T.tile0;
+        tile_end = T.tile1;
+        key_base = T.key_base;
+        n = T.key_end;
+        d = T.d;
+        shift = T.shift;
+        nq = T.nq;
+        q0 = T.qbase;
+        qbase = 0;
+    } else {
+        const int ntiles_total = (n + KN - 1) / KN;
+        tile_begin = split * tiles_per_split;
+        tile_end = min(ntiles_total, tile_begin + tiles_per_split);
+    }
     const int nchunks = (d + DC - 1) / DC;
 
     // query ids of this block's rows (for the self test and the loads)
@@ -82,21 +98,21 @@ knn_fp32_kernel(const float *__restrict__ X, int n, int d, int k,
     // register prefetch of one chunk: 16 key floats + 8 query floats
     float kreg[16], qreg[8];
     auto load_chunk = [&](int tile, int c) {
-        int key0 = tile * KN;
+        int key0 = key_base + tile * KN;
         int t0 = c * DC;
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
             int idx = tid + NT * r;
             int j = idx >> 5, t = idx & 31;
             int row = key0 + j, col = t0 + t;
-            kreg[r] = (row < n && col < d) ? __ldg(X + int64_t(row) * d + col) : 0.0f;
+            kreg[r] = (row < n && col < d) ? __ldg(X + int64_t(row) * ld + col) : 0.0f;
         }
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
             int idx = tid + NT * r;
             int i = idx >> 5, t = idx & 31;
             int qi = qid_s[i], col = t0 + t;
-            qreg[r] = (qi >= 0 && col < d) ? __ldg(X + int64_t(qi) * d + col) : 0.0f;
+            qreg[r] = (qi >= 0 && col < d) ? __ldg(X + int64_t(qi) * ld + col) : 0.0f;
         }
     };
     auto store_chunk = [&](int buf) {
@@ -160,7 +176,7 @@ knn_fp32_kernel(const float *__restrict__ X, int n, int d, int k,
         }
         __syncthreads();
         if (selector && my_qid >= 0) {
-            const int key0 = tile * KN;
+            const int key0 = key_base + tile * KN;
             const float *prow = Ps + srow * PS_STRIDE;
             uint64_t *Lme = L + tid;
             for (int cidx = sslice; cidx < KN; cidx += spr) {
@@ -209,8 +225,8 @@ knn_fp32_kernel(const float *__restrict__ X, int n, int d, int k,
             if (part) {
                 part[(size_t(split) * nq + q) * k + o] = best;
             } else {
-                const int64_t orow = qrows ? int64_t(qrows[q]) : q;
-                nbr[orow * k + o] = best == KEY_NONE ? -1 : int32_t(key_lo(best));
+                const int64_t orow = btab ? int64_t(q0 + q - shift) : (qrows ? int64_t(qrows[q]) : q);
+                nbr[orow * k + o] = best == KEY_NONE ? -1 : int32_t(key_lo(best)) - shift;
                 dist[orow * k + o] = best == KEY_NONE ? __int_as_float(0x7f800000) : key_w(best);
             }
         }
@@ -273,8 +289,7 @@ famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int 
     if (k < 1 || k > 128) return FAMST_ERR_UNSUPPORTED;
     SplitPlan p = plan(n, nq, ex.num_sms);
     size_t smem = KnnSmem::bytes(k);
-    if (cudaFuncSetAttribute(knn_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(smem)) != cudaSuccess)
+    if (set_smem_attr(knn_fp32_kernel, int(smem), ex.stream) != cudaSuccess)
         return FAMST_ERR_CUDA;
     uint64_t *part = nullptr;
     if (p.S > 1) {
@@ -282,8 +297,8 @@ famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int 
         if (!part) return FAMST_ERR_OOM;
     }
     dim3 grid(p.qblocks, p.S);
-    FAMST_LAUNCH(ex, knn_fp32_kernel, grid, NT, smem, X, int(n), d, k, qrows, q0, int(nq),
-                 p.tiles_per_split, part, nbr, dist);
+    FAMST_LAUNCH(ex, knn_fp32_kernel, grid, NT, smem, X, int(n), d, d, k, qrows, q0, int(nq),
+                 p.tiles_per_split, part, nbr, dist, nullptr);
     if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
     if (p.S > 1) {
         int th = 128;
@@ -292,6 +307,25 @@ famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int 
         if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
     }
     return FAMST_OK;
+}
+
+}  // namespace famst
+
+namespace famst {
+
+// Batched exact kNN on FP32 tiles: one block per entry of `tiles` (64 query
+// rows of one cloud against that cloud's keys), X in the padded row space
+// with row stride ld; ids are written in the compact space.
+famst_status knn_fp32_batched(const Exec &ex, const float *Xp, int ld, int k, const F32Tile *tiles,
+                              int64_t nblocks, int32_t *nbr, float *dist) {
+    if (nblocks == 0) return FAMST_OK;
+    if (k < 1 || k > 128) return FAMST_ERR_UNSUPPORTED;
+    size_t smem = KnnSmem::bytes(k);
+    if (set_smem_attr(knn_fp32_kernel, int(smem), ex.stream) != cudaSuccess)
+        return FAMST_ERR_CUDA;
+    FAMST_LAUNCH(ex, knn_fp32_kernel, dim3(unsigned(nblocks), 1), NT, smem, Xp, 0, 0, ld, k,
+                 nullptr, 0, 0, 0, nullptr, nbr, dist, tiles);
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 }  // namespace famst

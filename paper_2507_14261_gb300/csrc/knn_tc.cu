@@ -211,6 +211,7 @@ struct TcArgs {
     int32_t *cand;      // n x (KC - 1)
     float *splus;       // n
     int *status;
+    const TcTile *tiles;  // null: one cloud, CTA b = query tile b over all keys
 };
 
 template <int KC>
@@ -235,7 +236,16 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // 1024-byte alignment for the swizzle atoms
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int nA = (args.x3 ? 2 : 1) * args.nkb;      // resident A blocks
+    int q0, kt0, kt1, nkb, row_end, shift;
+    if (args.tiles) {
+        const TcTile T = args.tiles[blockIdx.x];
+        q0 = T.q0; kt0 = T.kt0; kt1 = T.kt1; nkb = T.nkb; row_end = T.row_end; shift = T.shift;
+    } else {
+        q0 = blockIdx.x * BM; kt0 = 0; kt1 = args.nk_tiles; nkb = args.nkb; row_end = args.n;
+        shift = 0;
+    }
+    const int ntiles = kt1 - kt0;
+    const int nA = (args.x3 ? 2 : 1) * nkb;           // resident A blocks
     unsigned char *sA = base;
     unsigned char *sB = sA + size_t(nA) * A_BLOCK;
     float *stg_s = reinterpret_cast<float *>(sB + size_t(args.stages) * B_BLOCK);
@@ -252,9 +262,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q0 = blockIdx.x * BM;
-    const int nkb_tile = args.x3 ? 2 * args.nkb : args.nkb;   // B blocks per key tile
-    const int total_blocks = args.nk_tiles * nkb_tile;
+    const int nkb_tile = args.x3 ? 2 * nkb : nkb;     // B blocks per key tile
+    const int total_blocks = ntiles * nkb_tile;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < args.stages; ++s) {
@@ -287,7 +296,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB))
                          : "memory");
             mbar_expect_tx(a_full, uint32_t(nA) * A_BLOCK);
-            for (int a = 0; a < nA; ++a) tma_load_2d(sA + size_t(a) * A_BLOCK, &tmA, a_full, a * BK, q0);
+            // resident A blocks: hi blocks 0..nkb-1, then lo blocks (at column
+            // block args.nkb + kb of the operand rows)
+            for (int a = 0; a < nA; ++a) {
+                const int col = a < nkb ? a : args.nkb + (a - nkb);
+                tma_load_2d(sA + size_t(a) * A_BLOCK, &tmA, a_full, col * BK, q0);
+            }
             int it = 0;
             bool ok = true;
             for (; it < total_blocks && ok; ++it) {
@@ -296,7 +310,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     ok = false;
                     break;
                 }
-                const int t = it / nkb_tile, blk = it % nkb_tile;
+                const int t = kt0 + it / nkb_tile, blk = it % nkb_tile;
                 // x3 order per key tile: hi_0, lo_0, hi_1, lo_1, ...
                 const int col = args.x3 ? ((blk & 1) ? args.nkb + (blk >> 1) : (blk >> 1)) : blk;
                 mbar_expect_tx(&full[s], B_BLOCK);
@@ -317,7 +331,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             bool ok = mbar_wait(a_full, 0, abort_flag, args.status);
             tc_fence_after();
             int it = 0;
-            for (int t = 0; t < args.nk_tiles && ok; ++t) {
+            for (int t = 0; t < ntiles && ok; ++t) {
                 const int b = t & 1, use = t >> 1;
                 if (!mbar_wait(&tempty[b], (use & 1) ^ 1, abort_flag, args.status)) {
                     ok = false;
@@ -340,7 +354,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     const int na = args.x3 ? (is_lo ? 1 : 2) : 1;
                     for (int q = 0; q < na; ++q) {
                         // hi B block: A_hi then A_lo; lo B block: A_hi
-                        const int ablk = (q == 0) ? kb : args.nkb + kb;
+                        const int ablk = (q == 0) ? kb : nkb + kb;
                         const uint32_t asm_ = smem_u32(sA + size_t(ablk) * A_BLOCK);
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
@@ -388,8 +402,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         };
         bool ok = true;
         const int e_id = (warp - 2) * 32 + lane;   // 0..127 within the epilogue warps
-        float ny_next0 = __ldg(args.ny + e_id), ny_next1 = __ldg(args.ny + 128 + e_id);
-        for (int t = 0; t < args.nk_tiles; ++t) {
+        float ny_next0 = __ldg(args.ny + size_t(kt0) * BN + e_id);
+        float ny_next1 = __ldg(args.ny + size_t(kt0) * BN + 128 + e_id);
+        for (int t = 0; t < ntiles; ++t) {
             const int b = t & 1, use = t >> 1;
             // every lane waits; the warp proceeds only if all lanes saw the phase
             const bool got = mbar_wait(&tfull[b], use & 1, abort_flag, args.status);
@@ -404,8 +419,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             // t-2 before these writes)
             sny[b * BN + e_id] = ny_next0;
             sny[b * BN + 128 + e_id] = ny_next1;
-            if (t + 1 < args.nk_tiles) {   // the next tile's norms load under this tile's work
-                const float *g = args.ny + size_t(t + 1) * BN;
+            if (t + 1 < ntiles) {   // the next tile's norms load under this tile's work
+                const float *g = args.ny + size_t(kt0 + t + 1) * BN;
                 ny_next0 = __ldg(g + e_id);
                 ny_next1 = __ldg(g + 128 + e_id);
             }
@@ -430,7 +445,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     float m4 = fminf(fminf(s0, s1), fminf(s2, s3));
                     if (c4 < 4) mn0 = fminf(mn0, m4); else mn1 = fminf(mn1, m4);
                 }
-                const int j0 = t * BN + ch * 32;
+                const int j0 = (kt0 + t) * BN + ch * 32;
                 if (mn0 < thr) {
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
@@ -478,11 +493,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             if (lane == 0) mbar_arrive(&tempty[b]);
         }
         flush();
-        if (ok && i < args.n) {
-            int32_t *out = args.cand + size_t(i) * (KC - 1);
+        if (ok && i < row_end) {
+            int32_t *out = args.cand + size_t(i - shift) * (KC - 1);
 #pragma unroll
-            for (int p = 0; p < KC - 1; ++p) out[p] = lj[p];
-            args.splus[i] = ls[KC - 1];
+            for (int p = 0; p < KC - 1; ++p) out[p] = lj[p] >= 0 ? lj[p] - shift : -1;
+            args.splus[i - shift] = ls[KC - 1];
         }
     }
     tc_fence_before();
@@ -556,16 +571,18 @@ struct CertConst {
 };
 
 // One warp per row: canonical distances of the k' candidates, bitonic sort
-// of (w, id), top k, certificate.
+// of (w, id), top k, certificate. Row i's point is xi; candidate ids index
+// rows of X (row stride ld, chain length dc >= d: columns beyond d are zero
+// and leave the canonical chain unchanged). d is the true dimension used in
+// the error bounds. Returns whether the row was certified (then the k
+// results are written).
 template <int VEC, int KC>
-__global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int k,
-                              const int32_t *__restrict__ cand, const float *__restrict__ splus,
-                              const float *__restrict__ xnorm2, const unsigned *__restrict__ ymax_bits,
-                              CertConst cc, int32_t *__restrict__ nbr, float *__restrict__ dist,
-                              int32_t *__restrict__ fail_rows, int32_t *__restrict__ fail_count) {
-    int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (i >= n) return;
+__device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, int dc, int d,
+                                           const float *__restrict__ xi, int k,
+                                           const int32_t *__restrict__ cand_row, float sp,
+                                           float xn2f, float ymf, double eps_dot, int lane,
+                                           int32_t *__restrict__ nbr_row,
+                                           float *__restrict__ dist_row) {
     constexpr int KP = KC - 1;
     uint64_t key[2];
 #pragma unroll
@@ -573,9 +590,8 @@ __global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int
         int c = h * 32 + lane;
         key[h] = KEY_NONE;
         if (c < KP) {
-            int j = cand[i * KP + c];
-            if (j >= 0)
-                key[h] = nb_key(canon_dist<VEC>(X + i * d, X + int64_t(j) * d, d), uint32_t(j));
+            int j = cand_row[c];
+            if (j >= 0) key[h] = nb_key(canon_dist<VEC>(xi, X + int64_t(j) * ld, dc), uint32_t(j));
         }
     }
     // bitonic sort of 64 keys, element index = h*32 + lane
@@ -584,12 +600,11 @@ __global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int
 #pragma unroll
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             if (stride == 32) {
-                // partner is the other register of the same lane; idx = lane < 32 + lane
-                bool asc = ((lane & size) == 0);  // size == 64: always ascending
+                // partner is the other register of the same lane (size == 64: ascending)
                 uint64_t lo = key[0] < key[1] ? key[0] : key[1];
                 uint64_t hi = key[0] < key[1] ? key[1] : key[0];
-                key[0] = asc ? lo : hi;
-                key[1] = asc ? hi : lo;
+                key[0] = lo;
+                key[1] = hi;
             } else {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -609,22 +624,21 @@ __global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int
     uint64_t kth = __shfl_sync(0xffffffffu, kh ? key[1] : key[0], kl);
     bool cert = false;
     if (lane == 0) {
-        float sp = splus[i];
         if (!(sp < __int_as_float(0x7f800000))) {
             cert = true;  // fewer than KC points besides i: every one was kept
         } else {
             const double u24 = 1.0 / 16777216.0;
-            const double xn2 = double(xnorm2[i]);
+            const double xn2 = double(xn2f);
             const double xn = sqrt(xn2);
-            const double ym = double(__uint_as_float(*ymax_bits));
+            const double ym = double(ymf);
             // |s~ - s| <= E: tensor-core dot, FP32 key norm, score rounding
-            const double E = 2.0 * cc.eps_dot * xn * ym * 1.01 + (d + 1) * u24 * 1.02 * ym * ym +
+            const double E = 2.0 * eps_dot * xn * ym * 1.01 + (d + 1) * u24 * 1.02 * ym * ym +
                              2.0 * u24 * (ym * ym + 2.0 * xn * ym) * 1.01 + 1e-30;
             // lower bound on the centred squared distance of any unkept point
             const double p_lo = xn2 * (1.0 - (d + 1) * u24 * 1.02) + double(sp) - E;
             const double dist_lo =
                 (p_lo > 0.0 ? sqrt(p_lo) : 0.0) - 1.02 * u24 * (xn + ym);  // centring rounding
-            const double w_lo = dist_lo * (1.0 - cc.d_plus * u24 * 1.05);   // canonical FP32 error
+            const double w_lo = dist_lo * (1.0 - (d + 4.0) * u24 * 1.05);  // canonical FP32 error
             cert = w_lo > double(key_w(kth));
         }
     }
@@ -634,12 +648,172 @@ __global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int
         for (int h = 0; h < 2; ++h) {
             int idx = h * 32 + lane;
             if (idx < k) {
-                nbr[i * k + idx] = int32_t(key_lo(key[h]));
-                dist[i * k + idx] = key_w(key[h]);
+                nbr_row[idx] = int32_t(key_lo(key[h]));
+                dist_row[idx] = key_w(key[h]);
             }
         }
-    } else if (lane == 0) {
-        fail_rows[atomicAdd(fail_count, 1)] = int32_t(i);
+    }
+    return cert;
+}
+
+template <int VEC, int KC>
+__global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int k,
+                              const int32_t *__restrict__ cand, const float *__restrict__ splus,
+                              const float *__restrict__ xnorm2, const unsigned *__restrict__ ymax_bits,
+                              CertConst cc, int32_t *__restrict__ nbr, float *__restrict__ dist,
+                              int32_t *__restrict__ fail_rows, int32_t *__restrict__ fail_count) {
+    int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    bool cert = rerank_row<VEC, KC>(X, d, d, d, X + i * d, k, cand + i * (KC - 1), splus[i],
+                                    xnorm2[i], __uint_as_float(*ymax_bits), cc.eps_dot, lane,
+                                    nbr + i * k, dist + i * k);
+    if (!cert && lane == 0) fail_rows[atomicAdd(fail_count, 1)] = int32_t(i);
+}
+
+__device__ __forceinline__ int cloud_of(const long long *__restrict__ off, int B, long long v) {
+    int lo = 0, hi = B;  // off[lo] <= v < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= v) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Batched re-rank: one warp per compact row of a cloud that used the tensor
+// tiles. Xc holds the clouds' rows back to back with row stride ld (zero
+// beyond each cloud's d).
+template <int KC>
+__global__ void rerank_batched_kernel(const float *__restrict__ Xc, int ld, int64_t N,
+                                      const long long *__restrict__ voff, int B,
+                                      const CloudDev *__restrict__ cl, int x3, int k,
+                                      const int32_t *__restrict__ cand,
+                                      const float *__restrict__ splus,
+                                      const float *__restrict__ xnorm2,
+                                      const unsigned *__restrict__ ymax_bits,
+                                      int32_t *__restrict__ nbr, float *__restrict__ dist,
+                                      int32_t *__restrict__ fail_rows,
+                                      int32_t *__restrict__ fail_count) {
+    int64_t v = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (v >= N) return;
+    const int b = cloud_of(voff, B, v);
+    const CloudDev c = cl[b];
+    if (!c.use_tc) return;
+    const double u8 = 1.0 / 256.0;
+    const double kprod = double(x3 ? 3 * c.d_pad : c.d_pad);
+    const double eps = (x3 ? (3.0 * u8 * u8 + 3.0 * u8 * u8 * u8 + u8 * u8 * u8 * u8)
+                           : (2.0 * u8 + u8 * u8)) +
+                       kprod * (1.0 / 4194304.0) * (1.0 + 4.0 * u8);
+    const int dc = (c.d + 3) & ~3;
+    bool cert = rerank_row<4, KC>(Xc, ld, dc, c.d, Xc + v * ld, k, cand + v * (KC - 1), splus[v],
+                                  xnorm2[v], __uint_as_float(ymax_bits[b]), eps, lane, nbr + v * k,
+                                  dist + v * k);
+    if (!cert && lane == 0) fail_rows[atomicAdd(fail_count, 1)] = int32_t(v);
+}
+
+// Exact kNN of single rows by brute force within their cloud: one warp per
+// listed row (the count lives on the device); lane l scans keys l, l+32, ...
+// with the canonical chain and keeps its k best (w, id) in shared memory;
+// the warp then merges the 32 sorted lists. k <= 64.
+constexpr int FB_WARPS = 2;  // 32 KB of static shared lists per block
+__global__ void fallback_rows_kernel(const float *__restrict__ Xc, int ld,
+                                     const long long *__restrict__ voff, int B,
+                                     const CloudDev *__restrict__ cl, int k,
+                                     const int32_t *__restrict__ rows,
+                                     const int32_t *__restrict__ count,
+                                     int32_t *__restrict__ nbr, float *__restrict__ dist) {
+    __shared__ uint64_t lists[FB_WARPS][64][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nrows = *count;
+    for (int64_t q = int64_t(blockIdx.x) * FB_WARPS + w; q < nrows;
+         q += int64_t(gridDim.x) * FB_WARPS) {
+        const int64_t v = rows[q];
+        const int b = cloud_of(voff, B, v);
+        const CloudDev c = cl[b];
+        const int dc = (c.d + 3) & ~3;
+        const float *xi = Xc + v * ld;
+        int have = 0;
+        uint64_t kth = KEY_NONE;
+        for (int64_t j = c.voff + lane; j < c.voff + c.n; j += 32) {
+            if (j == v) continue;
+            uint64_t key = nb_key(canon_dist<4>(xi, Xc + j * ld, dc), uint32_t(j));
+            if (key >= kth) continue;
+            int pos = have < k ? have++ : k - 1;
+            while (pos > 0 && lists[w][pos - 1][lane] > key) {
+                lists[w][pos][lane] = lists[w][pos - 1][lane];
+                --pos;
+            }
+            lists[w][pos][lane] = key;
+            if (have == k) kth = lists[w][k - 1][lane];
+        }
+        __syncwarp();
+        int head = 0;
+        for (int o = 0; o < k; ++o) {
+            uint64_t mine = head < have ? lists[w][head][lane] : KEY_NONE;
+            uint64_t best = warp_min_u64(mine);
+            if (mine == best && best != KEY_NONE) ++head;  // keys are unique (distinct ids)
+            if (lane == 0) {
+                nbr[v * k + o] = best == KEY_NONE ? -1 : int32_t(key_lo(best));
+                dist[v * k + o] = best == KEY_NONE ? __int_as_float(0x7f800000) : key_w(best);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Batched prep: per padded row r of the operand array, the cloud's centred
+// BF16 hi (and lo) operand, its FP32 squared norm (key norms in padded rows,
+// +inf on padding rows; row norms in compact rows) and the cloud's largest
+// norm. mean holds the clouds' column means (B x ld).
+__global__ void tc_prep_batched_kernel(const float *__restrict__ Xc, int ld, int64_t NP,
+                                       const long long *__restrict__ roff,
+                                       const long long *__restrict__ voff, int B,
+                                       const CloudDev *__restrict__ cl, int kh_half, int x3,
+                                       const float *__restrict__ mean,
+                                       __nv_bfloat16 *__restrict__ H, float *__restrict__ ny,
+                                       float *__restrict__ xnorm, unsigned *__restrict__ ymax_bits) {
+    int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (r >= NP) return;
+    const int b = cloud_of(roff, B, r);
+    const CloudDev c = cl[b];
+    const int64_t q = r - roff[b];
+    const int kh = (x3 ? 2 : 1) * kh_half;
+    __nv_bfloat16 *h = H + r * kh;
+    if (q >= c.n || !c.use_tc) {
+        for (int t = lane; t < kh; t += 32) h[t] = __float2bfloat16_rn(0.0f);
+        if (lane == 0) ny[r] = __int_as_float(0x7f800000);
+        return;
+    }
+    const int64_t v = voff[b] + q;
+    float acc = 0.0f;
+    for (int t = lane; t < kh_half; t += 32) {
+        float xc = t < c.d ? __fsub_rn(Xc[v * ld + t], mean[int64_t(b) * ld + t]) : 0.0f;
+        __nv_bfloat16 hi = __float2bfloat16_rn(xc);
+        h[t] = hi;
+        if (x3) h[kh_half + t] = __float2bfloat16_rn(__fsub_rn(xc, __bfloat162float(hi)));
+        acc = fmaf(xc, xc, acc);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        ny[r] = acc;
+        xnorm[v] = acc;
+        atomicMax(ymax_bits + b, __float_as_uint(sqrtf(acc)));
+    }
+}
+
+// column means of every cloud (one block per cloud, double sums)
+__global__ void cloud_mean_kernel(const float *__restrict__ Xc, int ld,
+                                  const CloudDev *__restrict__ cl, float *__restrict__ mean) {
+    const int b = blockIdx.x;
+    const CloudDev c = cl[b];
+    for (int t = threadIdx.x; t < ld; t += blockDim.x) {
+        double s = 0.0;
+        if (t < c.d)
+            for (long long v = c.voff; v < c.voff + c.n; ++v) s += double(Xc[v * ld + t]);
+        mean[int64_t(b) * ld + t] = t < c.d ? float(s / double(c.n)) : 0.0f;
     }
 }
 
@@ -749,11 +923,11 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         FAMST_LAUNCH(ex, fill_inf_kernel, unsigned((npad - n + 255) / 256), 256, 0, ny, n, npad);
     CUtensorMap mA, mB;
     if (!make_map(&mA, H, n, p.kh, BM) || !make_map(&mB, H, n, p.kh, BN)) return FAMST_ERR_CUDA;
-    TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, ny, cand, splus, ex.dstatus};
+    TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, ny, cand, splus, ex.dstatus, nullptr};
 #define TC_LAUNCH(KCV)                                                                           \
     do {                                                                                         \
-        if (cudaFuncSetAttribute(knn_tc_kernel<KCV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 int(p.smem)) != cudaSuccess)                                    \
+        if (set_smem_attr(knn_tc_kernel<KCV>, \
+                                 int(p.smem), ex.stream) != cudaSuccess)                                    \
             return FAMST_ERR_CUDA;                                                               \
         FAMST_LAUNCH(ex, knn_tc_kernel<KCV>, unsigned(p.nq_tiles), TC_THREADS, p.smem, mA, mB, a); \
     } while (0)
@@ -792,6 +966,75 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         if (st != FAMST_OK) return st;
     }
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+}  // namespace famst
+
+namespace famst {
+
+// Shared-memory plan of the batched tensor path for operand width D (the
+// largest cloud's K extent).
+bool knn_tc_batched_plan(int D, int k, bool x3, int *stages, size_t *smem, int *kc) {
+    if (k + 1 > 64) return false;
+    TcPlan p = tc_plan(int64_t(1) << 20, D, k, x3);
+    if (p.stages < 2 || encode_fn() == nullptr) return false;
+    *stages = p.stages;
+    *smem = p.smem;
+    *kc = p.kc;
+    return true;
+}
+
+// Everything of the batched tensor path that runs on the device; buffers
+// come from the caller's plan, so nothing here allocates or synchronises.
+famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, int64_t NP,
+                            const long long *voff, const long long *roff, int B,
+                            const CloudDev *cl, const TcTile *tiles, int64_t nctas, int k,
+                            bool x3, int stages, size_t smem, int kc, __nv_bfloat16 *H, float *ny,
+                            float *xn2, float *mean, unsigned *ymax, int32_t *cand, float *splus,
+                            int32_t *fail_rows, int32_t *fail_count, int32_t *nbr, float *dist,
+                            const CUtensorMap *mA, const CUtensorMap *mB) {
+    FAMST_LAUNCH(ex, cloud_mean_kernel, B, 128, 0, Xc, D, cl, mean);
+    if (cudaMemsetAsync(ymax, 0, size_t(B) * 4, ex.stream) != cudaSuccess ||
+        cudaMemsetAsync(fail_count, 0, 4, ex.stream) != cudaSuccess)
+        return FAMST_ERR_CUDA;
+    const int nkb = D / BK;
+    FAMST_LAUNCH(ex, tc_prep_batched_kernel, unsigned((NP * 32 + 255) / 256), 256, 0, Xc, D, NP,
+                 roff, voff, B, cl, D, int(x3), mean, H, ny, xn2, ymax);
+    if (nctas > 0) {
+        TcArgs a{0, 0, nkb, int(x3), stages, ny, cand, splus, ex.dstatus, tiles};
+#define TCB_LAUNCH(KCV)                                                                          \
+    do {                                                                                         \
+        if (set_smem_attr(knn_tc_kernel<KCV>, \
+                                 int(smem), ex.stream) != cudaSuccess)                                      \
+            return FAMST_ERR_CUDA;                                                               \
+        FAMST_LAUNCH(ex, knn_tc_kernel<KCV>, unsigned(nctas), TC_THREADS, smem, *mA, *mB, a);   \
+    } while (0)
+        if (kc == 32) TCB_LAUNCH(32);
+        else if (kc == 48) TCB_LAUNCH(48);
+        else TCB_LAUNCH(64);
+#undef TCB_LAUNCH
+    }
+    const unsigned rgrid = unsigned((N * 32 + 255) / 256);
+    if (kc == 32)
+        FAMST_LAUNCH(ex, rerank_batched_kernel<32>, rgrid, 256, 0, Xc, D, N, voff, B, cl, int(x3),
+                     k, cand, splus, xn2, ymax, nbr, dist, fail_rows, fail_count);
+    else if (kc == 48)
+        FAMST_LAUNCH(ex, rerank_batched_kernel<48>, rgrid, 256, 0, Xc, D, N, voff, B, cl, int(x3),
+                     k, cand, splus, xn2, ymax, nbr, dist, fail_rows, fail_count);
+    else
+        FAMST_LAUNCH(ex, rerank_batched_kernel<64>, rgrid, 256, 0, Xc, D, N, voff, B, cl, int(x3),
+                     k, cand, splus, xn2, ymax, nbr, dist, fail_rows, fail_count);
+    FAMST_LAUNCH(ex, fallback_rows_kernel, unsigned(ex.num_sms) * 16, FB_WARPS * 32, 0, Xc, D, voff,
+                 B, cl, k, fail_rows, fail_count, nbr, dist);
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+// Tensor maps over the padded operand rows (queries 128-row boxes, keys
+// 256-row boxes); made on the host before any capture.
+bool knn_tc_batched_maps(const void *H, int64_t NP, int D, bool x3, CUtensorMap *mA,
+                         CUtensorMap *mB) {
+    const int64_t kh = (x3 ? 2 : 1) * int64_t(D);
+    return make_map(mA, H, NP, kh, BM) && make_map(mB, H, NP, kh, BN);
 }
 
 }  // namespace famst

@@ -35,6 +35,10 @@ struct EdgeSrc {
     const int32_t *eu, *ev;
     const float *ew;
     int64_t m;
+    const int64_t *m_dev;   // optional device-side count of E edges (<= m)
+    __device__ __forceinline__ int64_t total() const {
+        return nk + (m_dev ? (*m_dev < m ? *m_dev : m) : m);
+    }
     __device__ __forceinline__ void get(int64_t e, int &a, int &b, float &w) const {
         if (e < nk) {
             a = int(e / k);
@@ -55,8 +59,9 @@ __global__ void bv_init_kernel(int32_t *comp, int64_t n) {
 }
 
 __global__ void bv_min1_kernel(EdgeSrc es, const int32_t *__restrict__ comp,
-                               unsigned long long *__restrict__ best1) {
-    int64_t total = es.nk + es.m;
+                               unsigned long long *__restrict__ best1, const int *__restrict__ done) {
+    if (done && *done) return;
+    int64_t total = es.total();
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
         int a, b;
@@ -72,8 +77,9 @@ __global__ void bv_min1_kernel(EdgeSrc es, const int32_t *__restrict__ comp,
 
 __global__ void bv_min2_kernel(EdgeSrc es, const int32_t *__restrict__ comp,
                                const unsigned long long *__restrict__ best1,
-                               unsigned int *__restrict__ best2) {
-    int64_t total = es.nk + es.m;
+                               unsigned int *__restrict__ best2, const int *__restrict__ done) {
+    if (done && *done) return;
+    int64_t total = es.total();
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
         int a, b;
@@ -264,12 +270,106 @@ __global__ void grad_kernel(const float *__restrict__ X, int64_t n, int d,
     gX[idx] = __fmul_rn(gW, acc);
 }
 
+// Record the round's tree edges at base + pos (base and the round's count
+// live on the device), then advance base and raise `done` when a round
+// added no edge: the later rounds of a fixed budget become no-ops.
+__global__ void bv_record_dev_kernel(const int32_t *__restrict__ flag,
+                                     const int32_t *__restrict__ pos, int64_t n,
+                                     const long long *__restrict__ base,
+                                     const int32_t *__restrict__ rmn, const int32_t *__restrict__ rmx,
+                                     const float *__restrict__ rw, int32_t *__restrict__ tu,
+                                     int32_t *__restrict__ tv, float *__restrict__ tw,
+                                     int64_t cap, const int *__restrict__ done) {
+    if (*done) return;
+    int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (c >= n || !flag[c]) return;
+    int64_t o = *base + pos[c];
+    if (o >= cap) return;
+    tu[o] = rmn[c];
+    tv[o] = rmx[c];
+    tw[o] = rw[c];
+}
+
+__global__ void bv_advance_kernel(long long *base, const int32_t *__restrict__ added, int *done,
+                                  int *rounds) {
+    if (*done) return;
+    if (*added == 0) {
+        *done = 1;
+    } else {
+        *base += *added;
+        *rounds += 1;
+    }
+}
+
+__global__ void bv_gate_kernel(const int *__restrict__ done, int32_t *__restrict__ flag, int64_t n) {
+    // a finished forest records nothing more
+    if (!*done) return;
+    int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (c < n) flag[c] = 0;
+}
+
 inline unsigned blocks_for(int64_t count, int th) { return unsigned((count + th - 1) / th); }
 
 }  // namespace
 
 size_t boruvka_workspace(int64_t n) {
     return align256(size_t(n) * 8) + align256(size_t(n) * 4) * 8 + scan_workspace(n) + 256;
+}
+
+// Boruvka with no host synchronisation: a fixed budget of rounds, the
+// edge count of E and the termination live on the device (for CUDA-graph
+// capture). Finds the minimum spanning forest of the candidate graph.
+famst_status boruvka_dev(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr,
+                         const float *dist, int k, const int32_t *eu, const int32_t *ev,
+                         const float *ew, int64_t m_cap, const int64_t *m_dev, MstOut out,
+                         int64_t out_cap, int max_rounds, long long *edges_dev, int *rounds_dev) {
+    if (n <= 1) return FAMST_OK;
+    unsigned long long *best1 = ar.take<unsigned long long>(size_t(n));
+    unsigned int *best2 = ar.take<unsigned int>(size_t(n));
+    int32_t *comp = ar.take<int32_t>(size_t(n));
+    int32_t *newp = ar.take<int32_t>(size_t(n));
+    int32_t *flag = ar.take<int32_t>(size_t(n));
+    int32_t *pos = ar.take<int32_t>(size_t(n));
+    int32_t *rmn = ar.take<int32_t>(size_t(n));
+    int32_t *rmx = ar.take<int32_t>(size_t(n));
+    float *rw = ar.take<float>(size_t(n));
+    int32_t *added = ar.take<int32_t>(1);
+    int *done = ar.take<int>(1);
+    if (!best1 || !best2 || !comp || !newp || !flag || !pos || !rmn || !rmx || !rw || !added ||
+        !done)
+        return FAMST_ERR_OOM;
+    EdgeSrc es{nbr, dist, k, n * int64_t(k), eu, ev, ew, m_cap, m_dev};
+    const int th = 256;
+    int64_t nedges = es.nk + m_cap;
+    unsigned egrid = blocks_for(nedges, th);
+    unsigned ecap = unsigned(ex.num_sms) * 32;
+    if (egrid > ecap) egrid = ecap;
+    if (egrid == 0) egrid = 1;
+    if (cudaMemsetAsync(done, 0, sizeof(int), ex.stream) != cudaSuccess ||
+        cudaMemsetAsync(edges_dev, 0, sizeof(long long), ex.stream) != cudaSuccess ||
+        cudaMemsetAsync(rounds_dev, 0, sizeof(int), ex.stream) != cudaSuccess)
+        return FAMST_ERR_CUDA;
+    FAMST_LAUNCH(ex, bv_init_kernel, blocks_for(n, th), th, 0, comp, n);
+    for (int r = 0; r < max_rounds; ++r) {
+        if (cudaMemsetAsync(best1, 0xff, size_t(n) * 8, ex.stream) != cudaSuccess ||
+            cudaMemsetAsync(best2, 0xff, size_t(n) * 4, ex.stream) != cudaSuccess)
+            return FAMST_ERR_CUDA;
+        FAMST_LAUNCH(ex, bv_min1_kernel, egrid, th, 0, es, comp, best1, done);
+        FAMST_LAUNCH(ex, bv_min2_kernel, egrid, th, 0, es, comp, best1, best2, done);
+        FAMST_LAUNCH(ex, bv_hook_kernel, blocks_for(n, th), th, 0, comp, n, best1, best2, newp,
+                     flag, rmn, rmx, rw);
+        FAMST_LAUNCH(ex, bv_gate_kernel, blocks_for(n, th), th, 0, done, flag, n);
+        FAMST_LAUNCH(ex, bv_jump_kernel, blocks_for(n, th), th, 0, comp, n, newp, ex.dstatus);
+        FAMST_LAUNCH(ex, bv_relabel_kernel, blocks_for(n, th), th, 0, comp, n, newp);
+        size_t mark = ar.off;
+        famst_status st = exclusive_scan_i32(ex, ar, flag, pos, n, added);
+        ar.off = mark;
+        if (st != FAMST_OK) return st;
+        FAMST_LAUNCH(ex, bv_record_dev_kernel, blocks_for(n, th), th, 0, flag, pos, n, edges_dev,
+                     rmn, rmx, rw, out.tu, out.tv, out.tw, out_cap, done);
+        FAMST_LAUNCH(ex, bv_advance_kernel, 1, 1, 0, edges_dev, added, done, rounds_dev);
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr, const float *dist,
@@ -290,7 +390,7 @@ famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr, c
     int32_t *total = ar.take<int32_t>(1);
     if (!best1 || !best2 || !comp || !newp || !flag || !pos || !rmn || !rmx || !rw || !total)
         return FAMST_ERR_OOM;
-    EdgeSrc es{nbr, dist, k, n * int64_t(k), eu, ev, ew, m};
+    EdgeSrc es{nbr, dist, k, n * int64_t(k), eu, ev, ew, m, nullptr};
     const int th = 256;
     int64_t nedges = es.nk + es.m;
     unsigned egrid = blocks_for(nedges, th);
@@ -303,8 +403,8 @@ famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr, c
         if (cudaMemsetAsync(best1, 0xff, size_t(n) * 8, ex.stream) != cudaSuccess ||
             cudaMemsetAsync(best2, 0xff, size_t(n) * 4, ex.stream) != cudaSuccess)
             return FAMST_ERR_CUDA;
-        FAMST_LAUNCH(ex, bv_min1_kernel, egrid, th, 0, es, comp, best1);
-        FAMST_LAUNCH(ex, bv_min2_kernel, egrid, th, 0, es, comp, best1, best2);
+        FAMST_LAUNCH(ex, bv_min1_kernel, egrid, th, 0, es, comp, best1, nullptr);
+        FAMST_LAUNCH(ex, bv_min2_kernel, egrid, th, 0, es, comp, best1, best2, nullptr);
         FAMST_LAUNCH(ex, bv_hook_kernel, blocks_for(n, th), th, 0, comp, n, best1, best2, newp,
                      flag, rmn, rmx, rw);
         FAMST_LAUNCH(ex, bv_jump_kernel, blocks_for(n, th), th, 0, comp, n, newp, ex.dstatus);

@@ -45,6 +45,18 @@ class BuildInfo(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [
+        ("m", ctypes.c_int64), ("refine_sweeps", ctypes.c_int32),
+        ("boruvka_rounds", ctypes.c_int32), ("uncertified_rows", ctypes.c_int64),
+        ("tensor_clouds", ctypes.c_int32), ("graph_replayed", ctypes.c_int32),
+        ("graph_kernels", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _LIB = None
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -76,6 +88,8 @@ _SIGS = {
     "famst_build_host": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _U64, _I32, _I32, _P, _P, _P,
                                 _PD, ctypes.POINTER(BuildInfo)]),
     "famst_mst_backward": (_I32, [_P, _P, _I64, _I32, _P, _P, _I64, _F32, _P]),
+    "famst_build_batched": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _U64, _I32, _I32, _P, _P,
+                                   _P, _P, _P, ctypes.POINTER(BatchInfo)]),
 }
 
 
@@ -274,6 +288,41 @@ class Context:
                                     ctypes.byref(W), ctypes.byref(info))
         self._check(st, "famst_build_host")
         return Tree(tu[: n - 1], tv[: n - 1], tw[: n - 1], W.value), info
+
+    def build_batched(self, X_concat, offsets, dims, k: int, lam: int, seed: int = 0,
+                      prec: str = "bf16x3", max_iters: int = 10000, out=None):
+        """famst_build_batched. X_concat: 1-D float32 device tensor holding
+        the clouds back to back (cloud b: n_b x dims[b], row-major);
+        offsets: B+1 point offsets; dims: B. Returns per-cloud trees (views
+        of one edge array with cloud-local ids), W per cloud, t per cloud
+        and the BatchInfo."""
+        import numpy as np
+        _need(X_concat, torch.float32, "X_concat")
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        dm = np.ascontiguousarray(dims, dtype=np.int32)
+        B = dm.size
+        N = int(off[-1])
+        dev = X_concat.device
+        if out is None:
+            out = (torch.empty(max(N - B, 1), dtype=torch.int32, device=dev),
+                   torch.empty(max(N - B, 1), dtype=torch.int32, device=dev),
+                   torch.empty(max(N - B, 1), dtype=torch.float32, device=dev))
+        tu, tv, tw = out
+        W = np.zeros(B, np.float64)
+        t = np.zeros(B, np.int64)
+        info = BatchInfo()
+        self._stream()
+        st = lib().famst_build_batched(
+            self._h, _ptr(X_concat), off.ctypes.data_as(ctypes.c_void_p),
+            dm.ctypes.data_as(ctypes.c_void_p), B, k, lam, seed & (2**64 - 1), PREC[prec],
+            max_iters, _ptr(tu), _ptr(tv), _ptr(tw), W.ctypes.data_as(ctypes.c_void_p),
+            t.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info))
+        self._check(st, "famst_build_batched")
+        trees = []
+        for b in range(B):
+            a, e = int(off[b]) - b, int(off[b + 1]) - b - 1
+            trees.append(Tree(tu[a:e], tv[a:e], tw[a:e], float(W[b])))
+        return trees, W, t, info
 
     def mst_backward(self, X, tu, tv, gW: float = 1.0, out=None):
         _need(X, torch.float32, "X")
