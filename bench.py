@@ -231,6 +231,72 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_batch(args, world, rank, local):
+    """256 clouds (n_b ~ U{500..20000}, d_b in {3, 32, 128}, 5-20 clusters,
+    k=16, lambda=5) per step through famst_build_batched: one captured CUDA
+    graph replay per step. Each rank builds its own batch (seed offset)."""
+    import torch
+    import paper_2507_14261_gb300 as fam
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    clouds = workloads.batch_clouds(base_seed=1000 + 100000 * rank)
+    off = np.zeros(len(clouds) + 1, np.int64)
+    for b, c in enumerate(clouds):
+        off[b + 1] = off[b] + c.shape[0]
+    dims = np.array([c.shape[1] for c in clouds], np.int32)
+    flat = np.concatenate([c.ravel() for c in clouds]).astype(np.float32)
+    X = torch.from_numpy(flat).cuda()
+    N = int(off[-1])
+    ctx = fam.Context(local)
+    k, lam = 16, 5
+    for _ in range(args.warmup):
+        trees, W, t, info = ctx.build_batched(X, off, dims, k, lam, 1, args.prec)
+    torch.cuda.synchronize()
+    if pg is not None:
+        pg.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = ctx.launches
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        trees, W, t, info = ctx.build_batched(X, off, dims, k, lam, 1, args.prec)
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, pg, "cuda")
+    clocks = sampler.stop()
+    launches = ctx.launches - launches0
+    # algorithmic work of the distance tiles: 2 n_b^2 d_b per cloud
+    flops = float(sum(2.0 * (off[b + 1] - off[b]) ** 2 * dims[b] for b in range(len(clouds))))
+    pk = peaks()
+    achieved = flops * args.steps / dt / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": throughput(world, N, args.steps, dt), "unit": "points/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if args.prec != "fp32" else "f32",
+            "data": "synthetic (seeded; 256 clouds, inputs larger than L2)",
+            "config": {"workload": "batch_256", "clouds": len(clouds), "points": N, "k": k,
+                       "lambda": lam, "prec": args.prec, "parallelism": f"replicas x{world}",
+                       "graph": "one captured CUDA graph replay per step"},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"], "traffic": None,
+                         "kernel": "whole batched build (distance FLOPs / step time; a lower bound "
+                                   "on the distance kernel's own rate)"},
+            "cpu_baseline": None, "e2e": None, "clocks": clocks, "gpu_launches": launches,
+            "build": {"tensor_clouds": info.tensor_clouds, "uncertified_rows": info.uncertified_rows,
+                      "m": info.m, "refine_sweeps": info.refine_sweeps,
+                      "graph_kernels": info.graph_kernels, "graph_replayed": info.graph_replayed},
+        }
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -243,6 +309,8 @@ def main():
     ap.add_argument("--prec", default=os.environ.get("FAMST_BENCH_PREC", "bf16x3"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-quality", action="store_true",
+                    help="skip the exact EMST (Eq. 1 relative error, after the timed region)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -253,6 +321,8 @@ def main():
     import torch
     import paper_2507_14261_gb300 as fam
 
+    if args.workload == "batch_256":
+        return run_batch(args, world, rank, local)
     torch.cuda.set_device(local)
     pg = None
     if world > 1:
@@ -332,6 +402,18 @@ def main():
                 "derived: 152 SMs x 128 FP32 lanes x max SM clock x 1.5 flop/instr",
                 "ms_per_launch": ms_knn}
 
+    # Eq. 1: relative error of the FAMST tree against the exact EMST, both
+    # on the GPU, outside the timed region
+    quality = None
+    if not args.no_quality:
+        t0 = time.perf_counter()
+        T, rounds = ctx.emst_exact(X, args.prec)
+        torch.cuda.synchronize()
+        quality = {"W_famst": tree.W, "W_exact": T.W,
+                   "rel_err": (tree.W - T.W) / T.W if T.W > 0 else 0.0,
+                   "exact": "GPU Boruvka over masked exact 1-NN passes",
+                   "emst_rounds": rounds, "emst_s": time.perf_counter() - t0}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(X_np, w.k)
@@ -348,7 +430,7 @@ def main():
                        "prec": args.prec, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (X = %d MB)" % (X_np.nbytes >> 20)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches,
+            "gpu_launches": launches, "quality": quality,
             "stages_ms": {k2: last[k2] for k2 in ("ms_knn", "ms_components", "ms_connect",
                                                   "ms_refine", "ms_mst", "ms_total")},
             "build": {"t": last["t"], "m": last["m"], "refine_sweeps": last["refine_sweeps"],

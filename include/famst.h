@@ -12,7 +12,8 @@
  *   then     Kruskal-equivalent MST of kNN edges + E       famst_mst
  * famst_build runs all of it. famst_mst_backward differentiates the tree
  * weight with respect to the points; famst_build_batched runs many clouds.
- * famst_components_noalloc labels components without any allocation.
+ * famst_components_noalloc labels components without any allocation;
+ * famst_emst_exact computes the exact EMST T* that Eq. 1 compares with.
  *
  * Conventions for every call:
  *  - Pointers are DEVICE pointers owned by the caller unless the argument
@@ -231,6 +232,26 @@ famst_status famst_build_batched(famst_ctx *ctx, const float *X, const int64_t *
 famst_status famst_mst_backward(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
                                 const int32_t *tu, const int32_t *tv, int64_t m,
                                 float gW, float *gX);
+
+/* ------------------------------------------------------ exact EMST
+ * The exact Euclidean MST T* of the complete graph on the n points: the
+ * reference tree of the relative error (W - W*) / W* of Eq. 1, computed on
+ * the GPU so it is available at sizes where an O(n^2) CPU Prim is not.
+ * Boruvka on the complete graph: each round finds every point's nearest
+ * neighbour outside its current component with an exact masked 1-NN pass
+ * (the Phase 1 distance tiles, precision `prec`, with the same FP32
+ * re-rank and certificate), then hooks every component by its minimum
+ * outgoing edge under (w, min id, max id). The tree is the unique MST
+ * under that order, identical to Prim's or Kruskal's on the complete graph
+ * with canonical FP32 weights.
+ * X (device, n x d). tu/tv/tw (device, n - 1): tree edges in (round,
+ * component) order, tu < tv. *W_out (HOST): FP64 sum of tw; *rounds_out
+ * (HOST, may be NULL): Boruvka rounds. Requires n >= 1 (n = 1: empty
+ * tree), 1 <= d. Cost: one all-pairs distance pass per round, at most
+ * ceil(log2 n) rounds. Synchronises. */
+famst_status famst_emst_exact(famst_ctx *ctx, const float *X, int64_t n, int32_t d, int32_t prec,
+                              int32_t *tu, int32_t *tv, float *tw, double *W_out,
+                              int32_t *rounds_out);
 
 /* ----------------------------------------- allocation-free components
  * The paper has no counterpart to this call: it is an interface variant of

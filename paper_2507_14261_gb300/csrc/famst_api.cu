@@ -672,6 +672,42 @@ famst_status famst_mst(famst_ctx *ctx, int64_t n, const int32_t *nbr, const floa
     return FAMST_OK;
 }
 
+famst_status famst_emst_exact(famst_ctx *ctx, const float *X, int64_t n, int32_t d, int32_t prec,
+                              int32_t *tu, int32_t *tv, float *tw, double *W_out,
+                              int32_t *rounds_out) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!W_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "W_out NULL");
+    if (prec < 0 || prec > 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown precision");
+    if (n < 1 || n >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= n < 2^31");
+    *W_out = 0.0;
+    if (rounds_out) *rounds_out = 0;
+    if (n == 1) return FAMST_OK;
+    if (!tu || !tv || !tw) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaSetDevice(ctx->device));
+    ST(reset_status(ctx));
+    ST(check_points(ctx, X, n, d));
+    ST(sync_status(ctx));
+    const bool x3 = prec == FAMST_PREC_BF16X3;
+    const bool tc = prec != FAMST_PREC_FP32 && knn_tc_supported(n, d, 1, x3);
+    Arena ar;
+    ST(ensure_ws(ctx, 1, emst_workspace(n, d, tc, x3, ctx->num_sms) + tree_weight_workspace(n), ar));
+    Exec ex = exec_of(ctx);
+    int64_t got = 0, unc = 0;
+    int rounds = 0;
+    ST(emst_exact(ex, ar, X, n, d, tc, x3, vec4_ok(X, d), MstOut{tu, tv, tw}, &got, &rounds, &unc,
+                  ctx->pinned + PIN_KNN, ctx->pinned + PIN_MST));
+    ST(sync_status(ctx));
+    if (got != n - 1) return fail(ctx, FAMST_ERR_TIMEOUT, "Boruvka stopped before n - 1 edges");
+    if (rounds_out) *rounds_out = rounds;
+    ST(tree_weight(ex, ar, nullptr, 0, false, tu, tv, tw, n - 1, ctx->dW));
+    double W[2];
+    CK(cudaMemcpyAsync(W, ctx->dW, 16, cudaMemcpyDeviceToHost, ctx->stream));
+    ST(sync_status(ctx));
+    *W_out = W[0];
+    return FAMST_OK;
+}
+
 famst_status famst_tree_weight(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
                                const int32_t *tu, const int32_t *tv, const float *tw, int64_t m,
                                double *W, double *W64) {

@@ -159,9 +159,11 @@ __device__ __forceinline__ void set_status(int *dstatus, int bit) {
 // output rows 0..nq-1; else the listed rows, written to their own rows of
 // nbr/dist) against all n points, FP32 tiles computing the canonical
 // distance. k <= 128.
+// colcomp (optional): component of every point; a query's keys in its own
+// component are skipped (nearest foreign neighbours).
 famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
                       int k, const int32_t *qrows, int64_t q0, int64_t nq,
-                      int32_t *nbr, float *dist);
+                      int32_t *nbr, float *dist, const int32_t *colcomp = nullptr);
 size_t knn_fp32_workspace(int64_t n, int d, int k, int64_t nq, int num_sms);
 
 // Batched launches lay the clouds out in a padded row space: cloud b
@@ -203,7 +205,7 @@ bool knn_tc_supported(int64_t n, int d, int k, bool x3);
 size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms);
 famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k, bool x3,
                     bool vec4, int32_t *nbr, float *dist, int32_t *pinned_host,
-                    int64_t *uncertified);
+                    int64_t *uncertified, const int32_t *colcomp = nullptr);
 
 }  // namespace famst
 #include <cuda.h>
@@ -265,6 +267,20 @@ struct MstOut {
     int32_t *tu, *tv;
     float *tw;
 };
+// Boruvka state for callers that drive the rounds themselves (exact EMST).
+struct BvState {
+    int64_t n = 0;
+    unsigned long long *best1 = nullptr;
+    unsigned int *best2 = nullptr;
+    int32_t *comp = nullptr;   // component representative of every vertex
+    int32_t *newp = nullptr, *flag = nullptr, *pos = nullptr, *rmn = nullptr, *rmx = nullptr;
+    float *rw = nullptr;
+    int32_t *total = nullptr;
+};
+famst_status bv_state_init(const Exec &ex, Arena &ar, int64_t n, BvState *S);
+famst_status bv_round(const Exec &ex, Arena &ar, BvState &S, const int32_t *nbr, const float *dist,
+                      int k, const int32_t *eu, const int32_t *ev, const float *ew, int64_t m,
+                      MstOut out, int64_t base, int32_t *added_host);
 famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr,
                      const float *dist, int k, const int32_t *eu, const int32_t *ev,
                      const float *ew, int64_t m, MstOut out, int64_t *tree_edges,
@@ -282,6 +298,14 @@ famst_status mst_backward(const Exec &ex, Arena &ar, const float *X, int64_t n, 
                           bool vec4, const int32_t *tu, const int32_t *tv, int64_t m,
                           float gW, float *gX);
 size_t mst_backward_workspace(int64_t n, int64_t m);
+
+// emst.cu
+// Exact EMST of the complete graph: Boruvka rounds over masked exact 1-NN
+// passes (tc: tensor tiles with precision x3, else FP32 tiles).
+size_t emst_workspace(int64_t n, int d, bool tc, bool x3, int num_sms);
+famst_status emst_exact(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, bool tc,
+                        bool x3, bool vec4, MstOut out, int64_t *tree_edges, int *rounds,
+                        int64_t *uncertified, int32_t *pin_knn, int32_t *pin_bv);
 
 // prep (famst_api.cu)
 famst_status check_finite(const Exec &ex, const float *X, int64_t count);

@@ -46,7 +46,7 @@ knn_fp32_kernel(const float *__restrict__ X, int n, int d, int ld, int k,
                 const int32_t *__restrict__ qrows, int64_t q0, int nq,
                 int tiles_per_split, uint64_t *__restrict__ part,
                 int32_t *__restrict__ nbr, float *__restrict__ dist,
-                const F32Tile *__restrict__ btab) {
+                const F32Tile *__restrict__ btab, const int32_t *__restrict__ colcomp) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int spr = spr_for(k);
     const int nsel = QM * spr;
@@ -94,6 +94,8 @@ knn_fp32_kernel(const float *__restrict__ X, int n, int d, int ld, int k,
     float pthr = __int_as_float(0x7f800000);
     __syncthreads();
     const int my_qid = selector ? qid_s[srow] : -1;
+    // optional component mask: keys in the query's own component are skipped
+    const int my_comp = (colcomp && my_qid >= 0) ? colcomp[my_qid] : -1;
 
     // register prefetch of one chunk: 16 key floats + 8 query floats
     float kreg[16], qreg[8];
@@ -183,6 +185,7 @@ knn_fp32_kernel(const float *__restrict__ X, int n, int d, int ld, int k,
                 int j = key0 + cidx;
                 float p = prow[cidx];
                 if (!(p <= pthr) || j >= n || j == my_qid) continue;
+                if (colcomp && colcomp[j] == my_comp) continue;
                 uint64_t key = nb_key(__fsqrt_rn(p), uint32_t(j));
                 if (key >= kth) continue;
                 int pos = lcount < k ? lcount++ : k - 1;
@@ -283,8 +286,8 @@ size_t knn_fp32_workspace(int64_t n, int d, int k, int64_t nq, int num_sms) {
 }
 
 famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k,
-                      const int32_t *qrows, int64_t q0, int64_t nq, int32_t *nbr,
-                      float *dist) {
+                      const int32_t *qrows, int64_t q0, int64_t nq, int32_t *nbr, float *dist,
+                      const int32_t *colcomp) {
     if (nq == 0) return FAMST_OK;
     if (k < 1 || k > 128) return FAMST_ERR_UNSUPPORTED;
     SplitPlan p = plan(n, nq, ex.num_sms);
@@ -298,7 +301,7 @@ famst_status knn_fp32(const Exec &ex, Arena &ar, const float *X, int64_t n, int 
     }
     dim3 grid(p.qblocks, p.S);
     FAMST_LAUNCH(ex, knn_fp32_kernel, grid, NT, smem, X, int(n), d, d, k, qrows, q0, int(nq),
-                 p.tiles_per_split, part, nbr, dist, nullptr);
+                 p.tiles_per_split, part, nbr, dist, nullptr, colcomp);
     if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
     if (p.S > 1) {
         int th = 128;
@@ -324,7 +327,7 @@ famst_status knn_fp32_batched(const Exec &ex, const float *Xp, int ld, int k, co
     if (set_smem_attr(knn_fp32_kernel, int(smem), ex.stream) != cudaSuccess)
         return FAMST_ERR_CUDA;
     FAMST_LAUNCH(ex, knn_fp32_kernel, dim3(unsigned(nblocks), 1), NT, smem, Xp, 0, 0, ld, k,
-                 nullptr, 0, 0, 0, nullptr, nbr, dist, tiles);
+                 nullptr, 0, 0, 0, nullptr, nbr, dist, tiles, nullptr);
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 

@@ -212,6 +212,7 @@ struct TcArgs {
     float *splus;       // n
     int *status;
     const TcTile *tiles;  // null: one cloud, CTA b = query tile b over all keys
+    const int32_t *colcomp;  // MASK: component of every (padded) row; pairs in one component are skipped
 };
 
 template <int KC>
@@ -228,7 +229,7 @@ __device__ __forceinline__ void list_insert(float (&ls)[KC], int (&lj)[KC], floa
     }
 }
 
-template <int KC>
+template <int KC, bool MASK>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               TcArgs args) {
@@ -251,7 +252,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     float *stg_s = reinterpret_cast<float *>(sB + size_t(args.stages) * B_BLOCK);
     int *stg_j = reinterpret_cast<int *>(stg_s + CAPB * BM);
     float *sny = reinterpret_cast<float *>(stg_j + CAPB * BM);   // [2][BN] key norms
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sny + 2 * BN);
+    int *scm = reinterpret_cast<int *>(sny + 2 * BN);            // [2][BN] key components (MASK)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(scm + 2 * BN);
     uint64_t *full = bars;                       // [stages]
     uint64_t *empty = bars + args.stages;        // [stages]
     uint64_t *a_full = bars + 2 * args.stages;
@@ -404,6 +406,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const int e_id = (warp - 2) * 32 + lane;   // 0..127 within the epilogue warps
         float ny_next0 = __ldg(args.ny + size_t(kt0) * BN + e_id);
         float ny_next1 = __ldg(args.ny + size_t(kt0) * BN + 128 + e_id);
+        int cm_next0 = 0, cm_next1 = 0, my_comp = 0;
+        if constexpr (MASK) {
+            cm_next0 = __ldg(args.colcomp + size_t(kt0) * BN + e_id);
+            cm_next1 = __ldg(args.colcomp + size_t(kt0) * BN + 128 + e_id);
+            my_comp = __ldg(args.colcomp + i);
+        }
         for (int t = 0; t < ntiles; ++t) {
             const int b = t & 1, use = t >> 1;
             // every lane waits; the warp proceeds only if all lanes saw the phase
@@ -419,13 +427,23 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             // t-2 before these writes)
             sny[b * BN + e_id] = ny_next0;
             sny[b * BN + 128 + e_id] = ny_next1;
+            if constexpr (MASK) {
+                scm[b * BN + e_id] = cm_next0;
+                scm[b * BN + 128 + e_id] = cm_next1;
+            }
             if (t + 1 < ntiles) {   // the next tile's norms load under this tile's work
                 const float *g = args.ny + size_t(kt0 + t + 1) * BN;
                 ny_next0 = __ldg(g + e_id);
                 ny_next1 = __ldg(g + 128 + e_id);
+                if constexpr (MASK) {
+                    const int32_t *gc = args.colcomp + size_t(kt0 + t + 1) * BN;
+                    cm_next0 = __ldg(gc + e_id);
+                    cm_next1 = __ldg(gc + 128 + e_id);
+                }
             }
             epilogue_bar();
             const float *nyt = sny + b * BN;
+            const int *cmt = scm + b * BN;
             // Candidate staging for 32 columns. The divergent parts only touch
             // this lane's stage; the warp-collective flush checks sit at
             // warp-uniform points between the two 16-column halves.
@@ -438,6 +456,14 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     float s1 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 1]), nn.y);
                     float s2 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 2]), nn.z);
                     float s3 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 3]), nn.w);
+                    if constexpr (MASK) {  // same component: not a candidate
+                        const int4 cc = *reinterpret_cast<const int4 *>(cmt + ch * 32 + 4 * c4);
+                        const float inf = __int_as_float(0x7f800000);
+                        s0 = cc.x == my_comp ? inf : s0;
+                        s1 = cc.y == my_comp ? inf : s1;
+                        s2 = cc.z == my_comp ? inf : s2;
+                        s3 = cc.w == my_comp ? inf : s3;
+                    }
                     v[4 * c4 + 0] = __float_as_uint(s0);
                     v[4 * c4 + 1] = __float_as_uint(s1);
                     v[4 * c4 + 2] = __float_as_uint(s2);
@@ -860,7 +886,7 @@ TcPlan tc_plan(int64_t n, int d, int k, bool x3) {
     p.nq_tiles = (n + BM - 1) / BM;
     p.nk_tiles = (n + BN - 1) / BN;
     const size_t fixed = 1024 + size_t(x3 ? 2 : 1) * p.nkb * A_BLOCK + size_t(CAPB) * BM * 8 +
-                         2 * BN * 4 + 512;
+                         4 * BN * 4 + 512;
     const size_t cap = 227 * 1024;
     int st = cap > fixed ? int((cap - fixed) / B_BLOCK) : 0;
     if (st > 6) st = 6;
@@ -881,7 +907,7 @@ size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms) {
     TcPlan p = tc_plan(n, d, k, x3);
     size_t b = 0;
     b += align256(size_t(n) * p.kh * 2);                   // operand rows
-    b += align256(size_t(p.nk_tiles) * BN * 4);            // ny (padded)
+    b += align256(size_t(p.nk_tiles) * BN * 4) * 2;        // ny, components (padded)
     b += align256(size_t(n) * 4);                          // xnorm2
     b += align256(size_t(d) * 4) + 256;                    // mean, ymax
     b += align256(size_t(4096) * d * 8);                   // column partials
@@ -893,7 +919,7 @@ size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms) {
 
 famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k, bool x3,
                     bool vec4, int32_t *nbr, float *dist, int32_t *pinned_host,
-                    int64_t *uncertified) {
+                    int64_t *uncertified, const int32_t *colcomp) {
     TcPlan p = tc_plan(n, d, k, x3);
     if (p.stages < 2 || k + 1 > 64) return FAMST_ERR_UNSUPPORTED;
     __nv_bfloat16 *H = ar.take<__nv_bfloat16>(size_t(n) * p.kh);
@@ -923,17 +949,32 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         FAMST_LAUNCH(ex, fill_inf_kernel, unsigned((npad - n + 255) / 256), 256, 0, ny, n, npad);
     CUtensorMap mA, mB;
     if (!make_map(&mA, H, n, p.kh, BM) || !make_map(&mB, H, n, p.kh, BN)) return FAMST_ERR_CUDA;
-    TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, ny, cand, splus, ex.dstatus, nullptr};
-#define TC_LAUNCH(KCV)                                                                           \
+    int32_t *cpad = nullptr;   // components over the padded rows (-1 beyond n)
+    if (colcomp) {
+        cpad = ar.take<int32_t>(size_t(npad));
+        if (cudaMemsetAsync(cpad, 0xff, size_t(npad) * 4, ex.stream) != cudaSuccess ||
+            cudaMemcpyAsync(cpad, colcomp, size_t(n) * 4, cudaMemcpyDeviceToDevice, ex.stream) !=
+                cudaSuccess)
+            return FAMST_ERR_CUDA;
+    }
+    TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, ny, cand, splus, ex.dstatus, nullptr,
+             cpad};
+#define TC_LAUNCH(KCV, M)                                                                        \
     do {                                                                                         \
-        if (set_smem_attr(knn_tc_kernel<KCV>, \
-                                 int(p.smem), ex.stream) != cudaSuccess)                                    \
+        if (set_smem_attr(knn_tc_kernel<KCV, M>, int(p.smem), ex.stream) != cudaSuccess)         \
             return FAMST_ERR_CUDA;                                                               \
-        FAMST_LAUNCH(ex, knn_tc_kernel<KCV>, unsigned(p.nq_tiles), TC_THREADS, p.smem, mA, mB, a); \
+        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, M>), unsigned(p.nq_tiles), TC_THREADS, p.smem, mA,  \
+                     mB, a);                                                                     \
     } while (0)
-    if (p.kc == 32) TC_LAUNCH(32);
-    else if (p.kc == 48) TC_LAUNCH(48);
-    else TC_LAUNCH(64);
+    if (cpad) {
+        if (p.kc == 32) TC_LAUNCH(32, true);
+        else if (p.kc == 48) TC_LAUNCH(48, true);
+        else TC_LAUNCH(64, true);
+    } else {
+        if (p.kc == 32) TC_LAUNCH(32, false);
+        else if (p.kc == 48) TC_LAUNCH(48, false);
+        else TC_LAUNCH(64, false);
+    }
 #undef TC_LAUNCH
     if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
     // rerank + certificate
@@ -962,7 +1003,7 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     const int32_t nfail = *pinned_host;
     *uncertified = nfail;
     if (nfail > 0) {
-        famst_status st = knn_fp32(ex, ar, X, n, d, k, fail_rows, 0, nfail, nbr, dist);
+        famst_status st = knn_fp32(ex, ar, X, n, d, k, fail_rows, 0, nfail, nbr, dist, colcomp);
         if (st != FAMST_OK) return st;
     }
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
@@ -1001,13 +1042,13 @@ famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, i
     FAMST_LAUNCH(ex, tc_prep_batched_kernel, unsigned((NP * 32 + 255) / 256), 256, 0, Xc, D, NP,
                  roff, voff, B, cl, D, int(x3), mean, H, ny, xn2, ymax);
     if (nctas > 0) {
-        TcArgs a{0, 0, nkb, int(x3), stages, ny, cand, splus, ex.dstatus, tiles};
+        TcArgs a{0, 0, nkb, int(x3), stages, ny, cand, splus, ex.dstatus, tiles, nullptr};
 #define TCB_LAUNCH(KCV)                                                                          \
     do {                                                                                         \
-        if (set_smem_attr(knn_tc_kernel<KCV>, \
+        if (set_smem_attr(knn_tc_kernel<KCV, false>, \
                                  int(smem), ex.stream) != cudaSuccess)                                      \
             return FAMST_ERR_CUDA;                                                               \
-        FAMST_LAUNCH(ex, knn_tc_kernel<KCV>, unsigned(nctas), TC_THREADS, smem, *mA, *mB, a);   \
+        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false>), unsigned(nctas), TC_THREADS, smem, *mA, *mB, a);   \
     } while (0)
         if (kc == 32) TCB_LAUNCH(32);
         else if (kc == 48) TCB_LAUNCH(48);

@@ -372,24 +372,33 @@ famst_status boruvka_dev(const Exec &ex, Arena &ar, int64_t n, const int32_t *nb
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
-famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr, const float *dist,
-                     int k, const int32_t *eu, const int32_t *ev, const float *ew, int64_t m,
-                     MstOut out, int64_t *tree_edges, int *rounds, int32_t *pinned_host) {
-    *tree_edges = 0;
-    *rounds = 0;
-    if (n <= 1) return FAMST_OK;
-    unsigned long long *best1 = ar.take<unsigned long long>(size_t(n));
-    unsigned int *best2 = ar.take<unsigned int>(size_t(n));
-    int32_t *comp = ar.take<int32_t>(size_t(n));
-    int32_t *newp = ar.take<int32_t>(size_t(n));
-    int32_t *flag = ar.take<int32_t>(size_t(n));
-    int32_t *pos = ar.take<int32_t>(size_t(n));
-    int32_t *rmn = ar.take<int32_t>(size_t(n));
-    int32_t *rmx = ar.take<int32_t>(size_t(n));
-    float *rw = ar.take<float>(size_t(n));
-    int32_t *total = ar.take<int32_t>(1);
-    if (!best1 || !best2 || !comp || !newp || !flag || !pos || !rmn || !rmx || !rw || !total)
+famst_status bv_state_init(const Exec &ex, Arena &ar, int64_t n, BvState *S) {
+    S->n = n;
+    S->best1 = ar.take<unsigned long long>(size_t(n));
+    S->best2 = ar.take<unsigned int>(size_t(n));
+    S->comp = ar.take<int32_t>(size_t(n));
+    S->newp = ar.take<int32_t>(size_t(n));
+    S->flag = ar.take<int32_t>(size_t(n));
+    S->pos = ar.take<int32_t>(size_t(n));
+    S->rmn = ar.take<int32_t>(size_t(n));
+    S->rmx = ar.take<int32_t>(size_t(n));
+    S->rw = ar.take<float>(size_t(n));
+    S->total = ar.take<int32_t>(1);
+    if (!S->best1 || !S->best2 || !S->comp || !S->newp || !S->flag || !S->pos || !S->rmn ||
+        !S->rmx || !S->rw || !S->total)
         return FAMST_ERR_OOM;
+    FAMST_LAUNCH(ex, bv_init_kernel, blocks_for(n, 256), 256, 0, S->comp, n);
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+// One Boruvka round over the kNN-style edges (i -> nbr[i*k + r]) plus
+// (eu, ev): every component's minimum outgoing edge under (w, min, max)
+// is hooked and recorded at out[base ...]; *added_host (pinned) receives
+// the number of edges added. Synchronises.
+famst_status bv_round(const Exec &ex, Arena &ar, BvState &S, const int32_t *nbr, const float *dist,
+                      int k, const int32_t *eu, const int32_t *ev, const float *ew, int64_t m,
+                      MstOut out, int64_t base, int32_t *added_host) {
+    const int64_t n = S.n;
     EdgeSrc es{nbr, dist, k, n * int64_t(k), eu, ev, ew, m, nullptr};
     const int th = 256;
     int64_t nedges = es.nk + es.m;
@@ -397,35 +406,47 @@ famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr, c
     unsigned ecap = unsigned(ex.num_sms) * 32;
     if (egrid > ecap) egrid = ecap;
     if (egrid == 0) egrid = 1;
-    FAMST_LAUNCH(ex, bv_init_kernel, blocks_for(n, th), th, 0, comp, n);
+    if (cudaMemsetAsync(S.best1, 0xff, size_t(n) * 8, ex.stream) != cudaSuccess ||
+        cudaMemsetAsync(S.best2, 0xff, size_t(n) * 4, ex.stream) != cudaSuccess)
+        return FAMST_ERR_CUDA;
+    FAMST_LAUNCH(ex, bv_min1_kernel, egrid, th, 0, es, S.comp, S.best1, nullptr);
+    FAMST_LAUNCH(ex, bv_min2_kernel, egrid, th, 0, es, S.comp, S.best1, S.best2, nullptr);
+    FAMST_LAUNCH(ex, bv_hook_kernel, blocks_for(n, th), th, 0, S.comp, n, S.best1, S.best2, S.newp,
+                 S.flag, S.rmn, S.rmx, S.rw);
+    FAMST_LAUNCH(ex, bv_jump_kernel, blocks_for(n, th), th, 0, S.comp, n, S.newp, ex.dstatus);
+    FAMST_LAUNCH(ex, bv_relabel_kernel, blocks_for(n, th), th, 0, S.comp, n, S.newp);
+    size_t mark = ar.off;  // the scan's scratch is reused by every round
+    famst_status st = exclusive_scan_i32(ex, ar, S.flag, S.pos, n, S.total);
+    ar.off = mark;
+    if (st != FAMST_OK) return st;
+    FAMST_LAUNCH(ex, bv_record_kernel, blocks_for(n, th), th, 0, S.flag, S.pos, n, base, S.rmn,
+                 S.rmx, S.rw, out.tu, out.tv, out.tw);
+    if (cudaMemcpyAsync(added_host, S.total, 4, cudaMemcpyDeviceToHost, ex.stream) != cudaSuccess ||
+        cudaStreamSynchronize(ex.stream) != cudaSuccess)
+        return FAMST_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr, const float *dist,
+                     int k, const int32_t *eu, const int32_t *ev, const float *ew, int64_t m,
+                     MstOut out, int64_t *tree_edges, int *rounds, int32_t *pinned_host) {
+    *tree_edges = 0;
+    *rounds = 0;
+    if (n <= 1) return FAMST_OK;
+    BvState S;
+    famst_status st = bv_state_init(ex, ar, n, &S);
+    if (st != FAMST_OK) return st;
     int64_t got = 0;
     for (int r = 0; r < 64 && got < n - 1; ++r) {
-        if (cudaMemsetAsync(best1, 0xff, size_t(n) * 8, ex.stream) != cudaSuccess ||
-            cudaMemsetAsync(best2, 0xff, size_t(n) * 4, ex.stream) != cudaSuccess)
-            return FAMST_ERR_CUDA;
-        FAMST_LAUNCH(ex, bv_min1_kernel, egrid, th, 0, es, comp, best1, nullptr);
-        FAMST_LAUNCH(ex, bv_min2_kernel, egrid, th, 0, es, comp, best1, best2, nullptr);
-        FAMST_LAUNCH(ex, bv_hook_kernel, blocks_for(n, th), th, 0, comp, n, best1, best2, newp,
-                     flag, rmn, rmx, rw);
-        FAMST_LAUNCH(ex, bv_jump_kernel, blocks_for(n, th), th, 0, comp, n, newp, ex.dstatus);
-        FAMST_LAUNCH(ex, bv_relabel_kernel, blocks_for(n, th), th, 0, comp, n, newp);
-        size_t mark = ar.off;  // the scan's scratch is reused by every round
-        famst_status st = exclusive_scan_i32(ex, ar, flag, pos, n, total);
-        ar.off = mark;
+        st = bv_round(ex, ar, S, nbr, dist, k, eu, ev, ew, m, out, got, pinned_host);
         if (st != FAMST_OK) return st;
-        FAMST_LAUNCH(ex, bv_record_kernel, blocks_for(n, th), th, 0, flag, pos, n, got, rmn, rmx,
-                     rw, out.tu, out.tv, out.tw);
-        if (cudaMemcpyAsync(pinned_host, total, 4, cudaMemcpyDeviceToHost, ex.stream) !=
-                cudaSuccess ||
-            cudaStreamSynchronize(ex.stream) != cudaSuccess)
-            return FAMST_ERR_CUDA;
         *rounds = r + 1;
         int32_t added = *pinned_host;
         if (added == 0) break;
         got += added;
     }
     *tree_edges = got;
-    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return FAMST_OK;
 }
 
 size_t tree_weight_workspace(int64_t m) {

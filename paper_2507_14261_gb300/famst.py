@@ -88,6 +88,7 @@ _SIGS = {
     "famst_build_host": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _U64, _I32, _I32, _P, _P, _P,
                                 _PD, ctypes.POINTER(BuildInfo)]),
     "famst_mst_backward": (_I32, [_P, _P, _I64, _I32, _P, _P, _I64, _F32, _P]),
+    "famst_emst_exact": (_I32, [_P, _P, _I64, _I32, _I32, _P, _P, _P, _PD, _PI32]),
     "famst_build_batched": (_I32, [_P, _P, _P, _P, _I32, _I32, _I32, _U64, _I32, _I32, _P, _P,
                                    _P, _P, _P, ctypes.POINTER(BatchInfo)]),
 }
@@ -241,6 +242,23 @@ class Context:
                              ctypes.byref(W))
         self._check(st, "famst_mst")
         return tu[: n - 1], tv[: n - 1], tw[: n - 1], W.value
+
+    def emst_exact(self, X, prec: str = "bf16x3"):
+        """Exact EMST of the complete graph (the tree T* of Eq. 1) by Boruvka
+        rounds over masked exact 1-NN passes. Returns (Tree, rounds)."""
+        _need(X, torch.float32, "X")
+        n, d = X.shape
+        dev = X.device
+        tu = torch.empty(max(n - 1, 1), dtype=torch.int32, device=dev)
+        tv = torch.empty_like(tu)
+        tw = torch.empty(max(n - 1, 1), dtype=torch.float32, device=dev)
+        W = ctypes.c_double(0)
+        rounds = ctypes.c_int32(0)
+        self._stream()
+        st = lib().famst_emst_exact(self._h, _ptr(X), n, d, PREC[prec], _ptr(tu), _ptr(tv),
+                                    _ptr(tw), ctypes.byref(W), ctypes.byref(rounds))
+        self._check(st, "famst_emst_exact")
+        return Tree(tu[: n - 1], tv[: n - 1], tw[: n - 1], W.value), rounds.value
 
     def tree_weight(self, X, tu, tv, tw):
         n, d = X.shape
