@@ -20,6 +20,8 @@
 // every global sweep.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "famst_internal.cuh"
 
 namespace famst {
@@ -204,33 +206,37 @@ __device__ __forceinline__ uint64_t scan_side(const float *__restrict__ X, int d
     return warp_min_u64(best);
 }
 
-__device__ __forceinline__ uint32_t smem_addr(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem)), "l"(gmem)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
-// Staged version (rows 16-byte aligned, d % 4 == 0): per round of 32
-// candidates the warp copies their rows into shared memory with coalesced
-// 16-byte cp.async (one row per step, all rows in flight together), then
-// lane l runs the canonical chain of candidate l from shared memory.
-// srow: 32 rows of `ld` floats; sfix: the fixed row (d floats).
-__device__ __forceinline__ uint64_t scan_side_staged(
-    const float *__restrict__ X, int d, int ld, int c, int fixed, int other, int want_comp,
-    float w0, const int32_t *__restrict__ nbr, int k, const int32_t *__restrict__ rev_off,
-    const int32_t *__restrict__ rev_src, const int32_t *__restrict__ comp, int lane,
-    float *srow, float *sfix) {
+// Filtered version (rows 16-byte aligned, d % 4 == 0, d <= 128 * FR): the
+// warp first computes a fast squared distance for its 32 candidates -- row
+// j read by the whole warp at once (lane l holds float4 columns l, l+32,
+// ...), 32 independent partial sums per lane, a butterfly transpose-sum so
+// that lane l ends with candidate l's total -- then runs the canonical chain
+// only for candidates the fast value cannot rule out. The fast and the
+// canonical sums add the same rounded terms fl(x_t - y_t)^2 in different
+// orders, so both lie within gamma_n of the exact sum (n = roundings on the
+// longest path): p_canon / p_fast is within [1 - rho, 1 + rho]. A candidate
+// whose lower bound exceeds (a) the smallest upper bound in the round or
+// (b) the current best weight squared, both widened by 2^-20 for the
+// rounding of sqrtf, cannot be the argmin under (w, id); the others are
+// decided on canonical weights, so the result equals scan_side's.
+template <int FR>
+__device__ __forceinline__ uint64_t scan_side_filtered(
+    const float *__restrict__ X, int d, int c, int fixed, int other, int want_comp, float w0,
+    const int32_t *__restrict__ nbr, int k, const int32_t *__restrict__ rev_off,
+    const int32_t *__restrict__ rev_src, const int32_t *__restrict__ comp, int lane, float rho) {
     const int d4 = d >> 2;
-    __syncwarp();
-    for (int q = lane; q < d4; q += 32) cp_async16(sfix + 4 * q, X + int64_t(fixed) * d + 4 * q);
+    const float *xf = X + int64_t(fixed) * d;
+    float4 fx[FR];
+#pragma unroll
+    for (int r = 0; r < FR; ++r) {
+        const int q = lane + 32 * r;
+        fx[r] = q < d4 ? __ldg(reinterpret_cast<const float4 *>(xf) + q)
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     uint64_t best = uint64_t(__float_as_uint(w0)) << 32;
     const int r0 = rev_off[c], r1 = rev_off[c + 1];
     const int deg = k + (r1 - r0);
+    const float widen = 1.0f + 0x1p-20f;
     for (int base = 0; base < deg; base += 32) {
         const int idx = base + lane;
         int cand = -1;
@@ -239,44 +245,66 @@ __device__ __forceinline__ uint64_t scan_side_staged(
             if (comp[cand] != want_comp || cand == other) cand = -1;  // G[c] ∩ C, u' != v
         }
         const unsigned live = __ballot_sync(0xffffffffu, cand >= 0);
-        unsigned todo = live;
-        while (todo) {
-            const int sl = __ffs(todo) - 1;
-            todo &= todo - 1;
+        if (live == 0u) continue;
+        float acc[32];
+#pragma unroll
+        for (int sl = 0; sl < 32; ++sl) {
+            // dead slots read the fixed row (in L1) so every load is unconditional
             const int id = __shfl_sync(0xffffffffu, cand, sl);
-            const float *g = X + int64_t(id) * d;
-            for (int q = lane; q < d4; q += 32) cp_async16(srow + sl * ld + 4 * q, g + 4 * q);
-        }
-        cp_async_wait_all();
-        __syncwarp();
-        if (cand >= 0) {
-            const float4 *a4 = reinterpret_cast<const float4 *>(srow + lane * ld);
-            const float4 *b4 = reinterpret_cast<const float4 *>(sfix);
-            float p = 0.0f;
-#pragma unroll 8
-            for (int q = 0; q < d4; ++q) {
-                float4 x = a4[q], y = b4[q];
-                float t0 = __fsub_rn(x.x, y.x);
-                p = __fmaf_rn(t0, t0, p);
-                float t1 = __fsub_rn(x.y, y.y);
-                p = __fmaf_rn(t1, t1, p);
-                float t2 = __fsub_rn(x.z, y.z);
-                p = __fmaf_rn(t2, t2, p);
-                float t3 = __fsub_rn(x.w, y.w);
-                p = __fmaf_rn(t3, t3, p);
+            const float4 *g =
+                reinterpret_cast<const float4 *>(X + int64_t(id >= 0 ? id : fixed) * d);
+            float a = 0.0f;
+#pragma unroll
+            for (int r = 0; r < FR; ++r) {
+                const int q = lane + 32 * r;
+                if (q < d4) {
+                    const float4 y = __ldg(g + q);
+                    const float t0 = __fsub_rn(y.x, fx[r].x);
+                    a = __fmaf_rn(t0, t0, a);
+                    const float t1 = __fsub_rn(y.y, fx[r].y);
+                    a = __fmaf_rn(t1, t1, a);
+                    const float t2 = __fsub_rn(y.z, fx[r].z);
+                    a = __fmaf_rn(t2, t2, a);
+                    const float t3 = __fsub_rn(y.w, fx[r].w);
+                    a = __fmaf_rn(t3, t3, a);
+                }
             }
-            uint64_t key = (uint64_t(__float_as_uint(__fsqrt_rn(p))) << 32) | uint32_t(cand + 1);
+            acc[sl] = a;
+        }
+        // butterfly transpose-sum: lane l ends with slot l's total in acc[0]
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < o; ++i) {
+                const float send = up ? acc[i] : acc[i + o];
+                const float keep = up ? acc[i + o] : acc[i];
+                acc[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+            }
+        }
+        const float pf = acc[0];
+        const float inf = __int_as_float(0x7f800000);
+        const float lo = cand >= 0 ? __fsub_rd(__fmul_rd(pf, 1.0f - rho), 1e-35f) : inf;
+        const float hi = cand >= 0 ? __fadd_ru(__fmul_ru(pf, 1.0f + rho), 1e-35f) : inf;
+        float mh = hi;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) mh = fminf(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+        const float wb = key_w(best);
+        const float bound = fminf(__fmul_ru(mh, widen), __fmul_ru(__fmul_ru(wb, wb), widen));
+        if (cand >= 0 && lo <= bound) {
+            const float w = canon_dist<4>(X + int64_t(cand) * d, xf, d);
+            const uint64_t key = (uint64_t(__float_as_uint(w)) << 32) | uint32_t(cand + 1);
             best = key < best ? key : best;
         }
-        __syncwarp();  // the next round overwrites srow
+        best = warp_min_u64(best);
     }
-    return warp_min_u64(best);
+    return best;
 }
 
 // Process edges in the order `order` (component-pair tiles, so the rows in
 // flight stay in L2), each to its own fixed point.
-template <int VEC, bool STAGED>
-__global__ void refine_kernel(const float *__restrict__ X, int d, int ld,
+template <int VEC, int FR>
+__global__ void refine_kernel(const float *__restrict__ X, int d,
                               const int32_t *__restrict__ nbr, int k,
                               const int32_t *__restrict__ rev_off,
                               const int32_t *__restrict__ rev_src,
@@ -286,13 +314,10 @@ __global__ void refine_kernel(const float *__restrict__ X, int d, int ld,
                               const int32_t *__restrict__ order, int64_t m,
                               const int64_t *__restrict__ m_dev, int max_iters,
                               int32_t *__restrict__ change_hist,
-                              unsigned long long *__restrict__ next_item, int *dstatus) {
+                              unsigned long long *__restrict__ next_item, int *dstatus,
+                              float rho) {
     if (m_dev) m = *m_dev < m ? *m_dev : m;  // device-side edge count, capped by capacity
-    extern __shared__ __align__(16) float rsm[];
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    float *srow = rsm + size_t(wib) * (32 * ld + d);
-    float *sfix = srow + 32 * ld;
     // Edges are handed out one at a time from a global counter, so the
     // edges in flight stay a narrow window of `order` (and their rows in L2)
     // even though edges need different numbers of sweeps.
@@ -311,17 +336,17 @@ __global__ void refine_kernel(const float *__restrict__ X, int d, int ld,
             int us, vs;
             float ws;
             // u-loop: u' in G[u] ∩ C_i, u' != v, against v
-            if constexpr (STAGED)
-                bu = scan_side_staged(X, d, ld, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp,
-                                      lane, srow, sfix);
+            if constexpr (FR > 0)
+                bu = scan_side_filtered<FR>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp,
+                                            lane, rho);
             else
                 bu = scan_side<VEC>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp, lane);
             us = key_lo(bu) ? int(key_lo(bu)) - 1 : u;
             ws = key_w(bu);
             // v-loop: v' in G[v] ∩ C_j, v' != u, against the new u*
-            if constexpr (STAGED)
-                bv = scan_side_staged(X, d, ld, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp,
-                                      lane, srow, sfix);
+            if constexpr (FR > 0)
+                bv = scan_side_filtered<FR>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src,
+                                            comp, lane, rho);
             else
                 bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane);
             vs = key_lo(bv) ? int(key_lo(bv)) - 1 : v;
@@ -339,6 +364,55 @@ __global__ void refine_kernel(const float *__restrict__ X, int d, int ld,
             if (changes == max_iters) set_status(dstatus, STATUS_REFINE_CAP);
         }
     }
+}
+
+// Launch of the refinement kernel in the variant the shape allows: the
+// filtered scan for 16-byte rows with 64 <= d <= 512, the per-lane
+// canonical chain otherwise. Persistent grid; edges are fetched from
+// *next_item (zeroed by the caller).
+famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, const int32_t *nbr,
+                           int k, const int32_t *rev_off, const int32_t *rev_src,
+                           const int32_t *comp, int32_t *eu, int32_t *ev, float *ew,
+                           const int32_t *eci, const int32_t *ecj, const int32_t *order,
+                           int64_t m, const int64_t *m_dev, int max_iters, int32_t *change_hist,
+                           unsigned long long *next_item) {
+    const int th = 256;
+    const int fr = d <= 128 ? 1 : (d <= 256 ? 2 : 4);
+    const bool filtered = vec4 && d >= 64 && d <= 512;
+    // persistent grid: as many blocks as stay resident
+    int per_sm = 0;
+    const void *fn = !filtered ? (vec4 ? (const void *)refine_kernel<4, 0> : (const void *)refine_kernel<1, 0>)
+                     : fr == 1 ? (const void *)refine_kernel<4, 1>
+                     : fr == 2 ? (const void *)refine_kernel<4, 2>
+                               : (const void *)refine_kernel<4, 4>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, th, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    int64_t want = (m * 32 + th - 1) / th;
+    int64_t cap = int64_t(ex.num_sms) * per_sm;
+    unsigned grid = unsigned(want < cap ? want : cap);
+    if (grid == 0) grid = 1;
+    // p_canon / p_fast within 1 +- rho: gamma_n = n u / (1 - n u) for both
+    // sums, n = d + 4 FR + 5 roundings at most; 4u more for the bounds' own
+    // products
+    const double u = std::ldexp(1.0, -24);
+    const double nu = double(d + 4 * fr + 5) * u;
+    const float rho = float(2.01 * nu / (1.0 - nu) + 4.0 * u);
+#define REFINE_LAUNCH(V, F)                                                                    \
+    FAMST_LAUNCH(ex, (refine_kernel<V, F>), grid, th, 0, X, d, nbr, k, rev_off, rev_src, comp, eu, \
+                 ev, ew, eci, ecj, order, m, m_dev, max_iters, change_hist, next_item,         \
+                 ex.dstatus, rho)
+    if (filtered) {
+        if (fr == 1) REFINE_LAUNCH(4, 1);
+        else if (fr == 2) REFINE_LAUNCH(4, 2);
+        else REFINE_LAUNCH(4, 4);
+    } else if (vec4) {
+        REFINE_LAUNCH(4, 0);
+    } else {
+        REFINE_LAUNCH(1, 0);
+    }
+#undef REFINE_LAUNCH
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 // tile key of an edge: its component pair's (ci / TT, cj / TT) cell
@@ -408,29 +482,8 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
     while ((int64_t(1) << bits) < int64_t(T) * T) ++bits;
     famst_status st = radix_sort_pairs(ex, ar, keys, order, m, bits);
     if (st != FAMST_OK) return st;
-    const bool staged = vec4 && d <= 512;
-    const int ld = d + ((d % 8 == 0) ? 4 : 8);
-    const int th = staged ? 128 : 256;
-    const size_t smem = staged ? size_t(th / 32) * (32 * ld + d) * sizeof(float) : 0;
-    int64_t want = (m * 32 + th - 1) / th;
-    int64_t cap = int64_t(ex.num_sms) * (staged ? 12 : 16);
-    unsigned grid = unsigned(want < cap ? want : cap);
-    if (staged) {
-        if (set_smem_attr(refine_kernel<4, true>, smem, ex.stream) != cudaSuccess)
-            return FAMST_ERR_CUDA;
-        FAMST_LAUNCH(ex, (refine_kernel<4, true>), grid, th, smem, X, d, ld, nbr, k, rev_off, rev_src,
-                     comp, eu, ev, ew, eci, ecj, order, m, nullptr, max_iters, change_hist,
-                     next_item, ex.dstatus);
-    } else if (vec4) {
-        FAMST_LAUNCH(ex, (refine_kernel<4, false>), grid, th, 0, X, d, ld, nbr, k, rev_off, rev_src,
-                     comp, eu, ev, ew, eci, ecj, order, m, nullptr, max_iters, change_hist,
-                     next_item, ex.dstatus);
-    } else {
-        FAMST_LAUNCH(ex, (refine_kernel<1, false>), grid, th, 0, X, d, ld, nbr, k, rev_off, rev_src,
-                     comp, eu, ev, ew, eci, ecj, order, m, nullptr, max_iters, change_hist,
-                     next_item, ex.dstatus);
-    }
-    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj, order,
+                         m, nullptr, max_iters, change_hist, next_item);
 }
 
 }  // namespace famst
@@ -449,29 +502,8 @@ famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, 
     unsigned long long *next_item = ar.take<unsigned long long>(1);
     if (!next_item) return FAMST_ERR_OOM;
     if (cudaMemsetAsync(next_item, 0, 8, ex.stream) != cudaSuccess) return FAMST_ERR_CUDA;
-    const bool staged = vec4 && d <= 512;
-    const int ld = d + ((d % 8 == 0) ? 4 : 8);
-    const int th = staged ? 128 : 256;
-    const size_t smem = staged ? size_t(th / 32) * (32 * ld + d) * sizeof(float) : 0;
-    int64_t want = (m_cap * 32 + th - 1) / th;
-    int64_t cap = int64_t(ex.num_sms) * (staged ? 12 : 16);
-    unsigned grid = unsigned(want < cap ? want : cap);
-    if (staged) {
-        if (set_smem_attr(refine_kernel<4, true>, smem, ex.stream) != cudaSuccess)
-            return FAMST_ERR_CUDA;
-        FAMST_LAUNCH(ex, (refine_kernel<4, true>), grid, th, smem, X, d, ld, nbr, k, rev_off, rev_src,
-                     comp, eu, ev, ew, eci, ecj, nullptr, m_cap, m_dev, max_iters, change_hist,
-                     next_item, ex.dstatus);
-    } else if (vec4) {
-        FAMST_LAUNCH(ex, (refine_kernel<4, false>), grid, th, 0, X, d, ld, nbr, k, rev_off, rev_src,
-                     comp, eu, ev, ew, eci, ecj, nullptr, m_cap, m_dev, max_iters, change_hist,
-                     next_item, ex.dstatus);
-    } else {
-        FAMST_LAUNCH(ex, (refine_kernel<1, false>), grid, th, 0, X, d, ld, nbr, k, rev_off, rev_src,
-                     comp, eu, ev, ew, eci, ecj, nullptr, m_cap, m_dev, max_iters, change_hist,
-                     next_item, ex.dstatus);
-    }
-    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj,
+                         nullptr, m_cap, m_dev, max_iters, change_hist, next_item);
 }
 
 }  // namespace famst
