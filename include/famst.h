@@ -84,6 +84,7 @@ typedef struct famst_build_info {
     double  W;                /* sum of the FP32 tree weights, in FP64 */
     double  W64;              /* tree weight with every edge recomputed in FP64 */
     double  ms_knn, ms_components, ms_connect, ms_refine, ms_mst, ms_total;
+    double  knn_tile_fraction; /* (query, key) tile pairs Phase 1 computed / all pairs */
 } famst_build_info;
 
 /* ------------------------------------------------------------ context */
@@ -94,6 +95,13 @@ famst_status famst_create(famst_ctx **out, int device);
 famst_status famst_destroy(famst_ctx *ctx);
 /* Enqueue all later work on `stream` (a cudaStream_t; NULL = legacy default). */
 famst_status famst_set_stream(famst_ctx *ctx, void *stream);
+/* Phase 1 tile pruning (exact either way): 1 = on where the shape allows it
+ * (the default), 0 = every (query, key) tile pair is computed. With pruning
+ * the points are partitioned into cells around evenly spaced pivots and a
+ * query tile skips the key tiles that a triangle-inequality bound places
+ * beyond an upper bound on its rows' k-th neighbour distance; the
+ * certificate covers the skipped keys, so the kNN graph is unchanged. */
+famst_status famst_set_knn_pruning(famst_ctx *ctx, int32_t enable);
 /* Static string naming a status code. */
 const char *famst_error_string(famst_status status);
 /* Detail of the last error on this context (static storage in ctx). */

@@ -224,15 +224,9 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
     const float *__restrict__ X, int d, int c, int fixed, int other, int want_comp, float w0,
     const int32_t *__restrict__ nbr, int k, const int32_t *__restrict__ rev_off,
     const int32_t *__restrict__ rev_src, const int32_t *__restrict__ comp, int lane, float rho) {
-    const int d4 = d >> 2;
     const float *xf = X + int64_t(fixed) * d;
     float4 fx[FR];
-#pragma unroll
-    for (int r = 0; r < FR; ++r) {
-        const int q = lane + 32 * r;
-        fx[r] = q < d4 ? __ldg(reinterpret_cast<const float4 *>(xf) + q)
-                       : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    row_slices<FR>(xf, d >> 2, lane, fx);
     uint64_t best = uint64_t(__float_as_uint(w0)) << 32;
     const int r0 = rev_off[c], r1 = rev_off[c + 1];
     const int deg = k + (r1 - r0);
@@ -244,45 +238,8 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
             cand = idx < k ? nbr[int64_t(c) * k + idx] : rev_src[r0 + idx - k];
             if (comp[cand] != want_comp || cand == other) cand = -1;  // G[c] ∩ C, u' != v
         }
-        const unsigned live = __ballot_sync(0xffffffffu, cand >= 0);
-        if (live == 0u) continue;
-        float acc[32];
-#pragma unroll
-        for (int sl = 0; sl < 32; ++sl) {
-            // dead slots read the fixed row (in L1) so every load is unconditional
-            const int id = __shfl_sync(0xffffffffu, cand, sl);
-            const float4 *g =
-                reinterpret_cast<const float4 *>(X + int64_t(id >= 0 ? id : fixed) * d);
-            float a = 0.0f;
-#pragma unroll
-            for (int r = 0; r < FR; ++r) {
-                const int q = lane + 32 * r;
-                if (q < d4) {
-                    const float4 y = __ldg(g + q);
-                    const float t0 = __fsub_rn(y.x, fx[r].x);
-                    a = __fmaf_rn(t0, t0, a);
-                    const float t1 = __fsub_rn(y.y, fx[r].y);
-                    a = __fmaf_rn(t1, t1, a);
-                    const float t2 = __fsub_rn(y.z, fx[r].z);
-                    a = __fmaf_rn(t2, t2, a);
-                    const float t3 = __fsub_rn(y.w, fx[r].w);
-                    a = __fmaf_rn(t3, t3, a);
-                }
-            }
-            acc[sl] = a;
-        }
-        // butterfly transpose-sum: lane l ends with slot l's total in acc[0]
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            const bool up = (lane & o) != 0;
-#pragma unroll
-            for (int i = 0; i < o; ++i) {
-                const float send = up ? acc[i] : acc[i + o];
-                const float keep = up ? acc[i + o] : acc[i];
-                acc[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
-            }
-        }
-        const float pf = acc[0];
+        if (__ballot_sync(0xffffffffu, cand >= 0) == 0u) continue;
+        const float pf = warp_sqdist32<FR>(X, d, fx, fixed, cand, lane);
         const float inf = __int_as_float(0x7f800000);
         const float lo = cand >= 0 ? __fsub_rd(__fmul_rd(pf, 1.0f - rho), 1e-35f) : inf;
         const float hi = cand >= 0 ? __fadd_ru(__fmul_ru(pf, 1.0f + rho), 1e-35f) : inf;
@@ -392,12 +349,7 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
     int64_t cap = int64_t(ex.num_sms) * per_sm;
     unsigned grid = unsigned(want < cap ? want : cap);
     if (grid == 0) grid = 1;
-    // p_canon / p_fast within 1 +- rho: gamma_n = n u / (1 - n u) for both
-    // sums, n = d + 4 FR + 5 roundings at most; 4u more for the bounds' own
-    // products
-    const double u = std::ldexp(1.0, -24);
-    const double nu = double(d + 4 * fr + 5) * u;
-    const float rho = float(2.01 * nu / (1.0 - nu) + 4.0 * u);
+    const float rho = fast_rho(d, fr);
 #define REFINE_LAUNCH(V, F)                                                                    \
     FAMST_LAUNCH(ex, (refine_kernel<V, F>), grid, th, 0, X, d, nbr, k, rev_off, rev_src, comp, eu, \
                  ev, ew, eci, ecj, order, m, m_dev, max_iters, change_hist, next_item,         \

@@ -58,6 +58,8 @@ struct famst_ctx {
     int *dstatus = nullptr;       // device status word
     int32_t *pinned = nullptr;    // 64 bytes of pinned host memory, slots PIN_*
     double *dW = nullptr;         // device: W, W64
+    int prune = 1;                // Phase 1 tile pruning
+    double tile_fraction = 1.0;   // of the last Phase 1
     char err[256] = {0};
 };
 
@@ -263,9 +265,16 @@ famst_status knn_stage(famst_ctx *ctx, Arena &ar, const float *X, int64_t n, int
     *uncert = 0;
     if (prec != FAMST_PREC_FP32) {
         const bool x3 = prec == FAMST_PREC_BF16X3;
-        if (knn_tc_supported(n, d, k, x3))
-            return knn_tc(ex, ar, X, n, d, k, x3, vec4_ok(X, d), nbr, dist, ctx->pinned + PIN_KNN,
-                          uncert);
+        if (knn_tc_supported(n, d, k, x3)) {
+            int64_t visited = 0;
+            ctx->tile_fraction = 1.0;
+            famst_status st = knn_tc(ex, ar, X, n, d, k, x3, vec4_ok(X, d), nbr, dist,
+                                     ctx->pinned + PIN_KNN, uncert, nullptr, ctx->prune != 0,
+                                     &visited);
+            const double all = double((n + 127) / 128) * double((n + 255) / 256);
+            if (st == FAMST_OK) ctx->tile_fraction = double(visited) / all;
+            return st;
+        }
         *uncert = n;
     }
     return knn_fp32(ex, ar, X, n, d, k, nullptr, 0, n, nbr, dist);
@@ -273,7 +282,8 @@ famst_status knn_stage(famst_ctx *ctx, Arena &ar, const float *X, int64_t n, int
 
 size_t knn_stage_ws(famst_ctx *ctx, int64_t n, int32_t d, int32_t k, int32_t prec) {
     if (prec != FAMST_PREC_FP32 && knn_tc_supported(n, d, k, prec == FAMST_PREC_BF16X3))
-        return knn_tc_workspace(n, d, k, prec == FAMST_PREC_BF16X3, ctx->num_sms);
+        return knn_tc_workspace(n, d, k, prec == FAMST_PREC_BF16X3, ctx->num_sms,
+                                ctx->prune != 0 && prune_supported(n, d, k, true));
     return knn_fp32_workspace(n, d, k, n, ctx->num_sms);
 }
 
@@ -402,6 +412,7 @@ famst_status build_impl(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     if (info) {
         CK(cudaStreamSynchronize(ctx->stream));
         info->uncertified_rows = uncert;
+        info->knn_tile_fraction = prec == FAMST_PREC_FP32 ? 1.0 : ctx->tile_fraction;
         info->ms_knn = ev.ms(0, 1);
         info->ms_components = ev.ms(1, 2);
         info->ms_connect = ev.ms(2, 3);
@@ -459,6 +470,13 @@ famst_status famst_set_stream(famst_ctx *ctx, void *stream) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
     ctx->err[0] = 0;
     ctx->stream = static_cast<cudaStream_t>(stream);
+    return FAMST_OK;
+}
+
+famst_status famst_set_knn_pruning(famst_ctx *ctx, int32_t enable) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    ctx->prune = enable ? 1 : 0;
     return FAMST_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations shared by the FAMST CUDA translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -130,6 +131,95 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
     return v;
 }
 
+// ---------------------------------------------- fast squared distances
+// Warp-cooperative squared distances for filters and bounds (never for a
+// stored weight). Rows are 16-byte aligned with d % 4 == 0; lane l holds
+// float4 columns l, l + 32, ..., FR of them (d <= 128 FR). Each term is
+// fl(y_t - x_t)^2 accumulated by fmaf as in the canonical chain, only in
+// another order, so the result is within gamma_n of the exact sum of the
+// rounded differences, n = d + 4 FR + 5 roundings at most (the canonical
+// chain: gamma_d). fast_rho(d, FR) bounds both ratios p_canon / p_fast and
+// S / p_fast (S the exact sum) to [1 - rho, 1 + rho].
+inline float fast_rho(int d, int fr) {
+    const double u = 1.0 / 16777216.0;
+    const double nu = double(d + 4 * fr + 5) * u;
+    return float(2.01 * nu / (1.0 - nu) + 4.0 * u);
+}
+
+template <int FR>
+__device__ __forceinline__ void row_slices(const float *__restrict__ row, int d4, int lane,
+                                           float4 (&f)[FR]) {
+#pragma unroll
+    for (int r = 0; r < FR; ++r) {
+        const int q = lane + 32 * r;
+        f[r] = q < d4 ? __ldg(reinterpret_cast<const float4 *>(row) + q)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+template <int FR>
+__device__ __forceinline__ float slice_sq(const float *__restrict__ row, int d4, int lane,
+                                          const float4 (&fx)[FR]) {
+    float a = 0.0f;
+#pragma unroll
+    for (int r = 0; r < FR; ++r) {
+        const int q = lane + 32 * r;
+        if (q < d4) {
+            const float4 y = __ldg(reinterpret_cast<const float4 *>(row) + q);
+            const float t0 = __fsub_rn(y.x, fx[r].x);
+            a = __fmaf_rn(t0, t0, a);
+            const float t1 = __fsub_rn(y.y, fx[r].y);
+            a = __fmaf_rn(t1, t1, a);
+            const float t2 = __fsub_rn(y.z, fx[r].z);
+            a = __fmaf_rn(t2, t2, a);
+            const float t3 = __fsub_rn(y.w, fx[r].w);
+            a = __fmaf_rn(t3, t3, a);
+        }
+    }
+    return a;
+}
+
+// Squared distances from the fixed row (slices fx, row id `fixed`) to the
+// 32 lanes' candidates `cand` (row ids; < 0: none). Every candidate row is
+// read by the whole warp at once; a butterfly transpose-sum leaves
+// candidate l's total in lane l. Lanes without a candidate get 0.
+template <int FR>
+__device__ __forceinline__ float warp_sqdist32(const float *__restrict__ X, int d,
+                                               const float4 (&fx)[FR], int fixed, int cand,
+                                               int lane) {
+    const int d4 = d >> 2;
+    float acc[32];
+#pragma unroll
+    for (int sl = 0; sl < 32; ++sl) {
+        // dead slots read the fixed row (in L1) so every load is unconditional
+        const int id = __shfl_sync(0xffffffffu, cand, sl);
+        acc[sl] = slice_sq<FR>(X + int64_t(id >= 0 ? id : fixed) * d, d4, lane, fx);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? acc[i] : acc[i + o];
+            const float keep = up ? acc[i + o] : acc[i];
+            acc[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+        }
+    }
+    return cand >= 0 ? acc[0] : 0.0f;
+}
+
+// One pair per warp: squared distance of rows a and b, in every lane.
+template <int FR>
+__device__ __forceinline__ float warp_sqdist1(const float *__restrict__ a,
+                                              const float *__restrict__ b, int d, int lane) {
+    float4 fa[FR];
+    row_slices<FR>(a, d >> 2, lane, fa);
+    float s = slice_sq<FR>(b, d >> 2, lane, fa);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
+    return s;
+}
+
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw; SC'11): ten rounds of
 // (c0,c1,c2,c3) <- (hi(B*c2)^c1^k0, lo(B*c2), hi(A*c0)^c3^k1, lo(A*c0)),
 // A = 0xD2511F53, B = 0xCD9E8D57, key advanced by (0x9E3779B9, 0xBB67AE85)
@@ -202,10 +292,38 @@ famst_status knn_fp32_batched(const Exec &ex, const float *Xp, int ld, int k, co
 // Exact kNN through tcgen05 BF16 (x3 = hi/lo split) distance tiles, FP32
 // re-rank, certificate, FP32 recomputation of uncertified rows.
 bool knn_tc_supported(int64_t n, int d, int k, bool x3);
-size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms);
+size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prune = false);
 famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k, bool x3,
                     bool vec4, int32_t *nbr, float *dist, int32_t *pinned_host,
-                    int64_t *uncertified, const int32_t *colcomp = nullptr);
+                    int64_t *uncertified, const int32_t *colcomp = nullptr, bool prune = false,
+                    int64_t *tiles_visited = nullptr);
+
+// prune.cu
+// Tile pruning of Phase 1: locality partition (pivot cells), ball bounds,
+// per-query-tile lists of the key tiles that may hold a neighbour, and the
+// lower bound skip_Q on the distance to every skipped key.
+struct PruneOut {
+    int32_t *perm = nullptr;        // sorted position -> point
+    __nv_bfloat16 *Hs = nullptr;    // operand rows in sorted order
+    float *nys = nullptr;           // key norms in sorted order (+inf padding)
+    int32_t *klist = nullptr;       // key tiles per query tile
+    TcTile *tab = nullptr;          // per query tile: its range of klist
+    float *skipQ = nullptr;         // per query tile
+    int32_t *visited = nullptr;     // device: number of visited (query, key) tile pairs
+    int64_t nq = 0, nk = 0;
+};
+int prune_pivots(int64_t n);
+bool prune_supported(int64_t n, int d, int k, bool vec4);
+size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk);
+famst_status prune_pivot_operands(const Exec &ex, const __nv_bfloat16 *H, int kh, const float *ny,
+                                  int64_t n, int K, int32_t *piv, __nv_bfloat16 *Hp, float *nyp);
+famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, int64_t n, int k,
+                             const __nv_bfloat16 *H, int kh, const float *ny, int nkb, int K,
+                             const int32_t *piv, const int32_t *acand, int akp,
+                             int32_t *pinned_host, PruneOut *out);
+famst_status prune_scatter(const Exec &ex, const PruneOut &P, int64_t n, int kp,
+                           const int32_t *cand_s, const float *splus_s, int32_t *cand,
+                           float *splus, float *skip);
 
 }  // namespace famst
 #include <cuda.h>

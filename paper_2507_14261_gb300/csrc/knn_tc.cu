@@ -213,6 +213,8 @@ struct TcArgs {
     int *status;
     const TcTile *tiles;  // null: one cloud, CTA b = query tile b over all keys
     const int32_t *colcomp;  // MASK: component of every (padded) row; pairs in one component are skipped
+    const int32_t *klist;    // non-null: CTA key tiles are klist[kt0 .. kt1) instead of kt0 .. kt1
+    int cross;               // queries and keys are different sets: no self-exclusion
 };
 
 template <int KC>
@@ -246,6 +248,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         shift = 0;
     }
     const int ntiles = kt1 - kt0;
+    // key tile of the t-th step of this CTA
+    auto ktile = [&](int t) { return args.klist ? __ldg(args.klist + kt0 + t) : kt0 + t; };
     const int nA = (args.x3 ? 2 : 1) * nkb;           // resident A blocks
     unsigned char *sA = base;
     unsigned char *sB = sA + size_t(nA) * A_BLOCK;
@@ -312,7 +316,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     ok = false;
                     break;
                 }
-                const int t = kt0 + it / nkb_tile, blk = it % nkb_tile;
+                const int t = ktile(it / nkb_tile), blk = it % nkb_tile;
                 // x3 order per key tile: hi_0, lo_0, hi_1, lo_1, ...
                 const int col = args.x3 ? ((blk & 1) ? args.nkb + (blk >> 1) : (blk >> 1)) : blk;
                 mbar_expect_tx(&full[s], B_BLOCK);
@@ -396,7 +400,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 if (q < cnt) {
                     float sv = my_s[q * BM];
                     int jv = my_j[q * BM];
-                    if (jv != i && sv < ls[KC - 1]) list_insert<KC>(ls, lj, sv, jv);
+                    if ((args.cross || jv != i) && sv < ls[KC - 1]) list_insert<KC>(ls, lj, sv, jv);
                 }
             }
             cnt = 0;
@@ -404,14 +408,16 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         };
         bool ok = true;
         const int e_id = (warp - 2) * 32 + lane;   // 0..127 within the epilogue warps
-        float ny_next0 = __ldg(args.ny + size_t(kt0) * BN + e_id);
-        float ny_next1 = __ldg(args.ny + size_t(kt0) * BN + 128 + e_id);
+        const int kt_first = ntiles > 0 ? ktile(0) : 0;
+        float ny_next0 = __ldg(args.ny + size_t(kt_first) * BN + e_id);
+        float ny_next1 = __ldg(args.ny + size_t(kt_first) * BN + 128 + e_id);
         int cm_next0 = 0, cm_next1 = 0, my_comp = 0;
         if constexpr (MASK) {
-            cm_next0 = __ldg(args.colcomp + size_t(kt0) * BN + e_id);
-            cm_next1 = __ldg(args.colcomp + size_t(kt0) * BN + 128 + e_id);
+            cm_next0 = __ldg(args.colcomp + size_t(kt_first) * BN + e_id);
+            cm_next1 = __ldg(args.colcomp + size_t(kt_first) * BN + 128 + e_id);
             my_comp = __ldg(args.colcomp + i);
         }
+        int kt_cur = kt_first;
         for (int t = 0; t < ntiles; ++t) {
             const int b = t & 1, use = t >> 1;
             // every lane waits; the warp proceeds only if all lanes saw the phase
@@ -431,12 +437,14 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 scm[b * BN + e_id] = cm_next0;
                 scm[b * BN + 128 + e_id] = cm_next1;
             }
+            const int kt_this = kt_cur;
             if (t + 1 < ntiles) {   // the next tile's norms load under this tile's work
-                const float *g = args.ny + size_t(kt0 + t + 1) * BN;
+                kt_cur = ktile(t + 1);
+                const float *g = args.ny + size_t(kt_cur) * BN;
                 ny_next0 = __ldg(g + e_id);
                 ny_next1 = __ldg(g + 128 + e_id);
                 if constexpr (MASK) {
-                    const int32_t *gc = args.colcomp + size_t(kt0 + t + 1) * BN;
+                    const int32_t *gc = args.colcomp + size_t(kt_cur) * BN;
                     cm_next0 = __ldg(gc + e_id);
                     cm_next1 = __ldg(gc + 128 + e_id);
                 }
@@ -471,7 +479,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     float m4 = fminf(fminf(s0, s1), fminf(s2, s3));
                     if (c4 < 4) mn0 = fminf(mn0, m4); else mn1 = fminf(mn1, m4);
                 }
-                const int j0 = (kt0 + t) * BN + ch * 32;
+                const int j0 = kt_this * BN + ch * 32;
                 if (mn0 < thr) {
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
@@ -606,7 +614,8 @@ template <int VEC, int KC>
 __device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, int dc, int d,
                                            const float *__restrict__ xi, int k,
                                            const int32_t *__restrict__ cand_row, float sp,
-                                           float xn2f, float ymf, double eps_dot, int lane,
+                                           float skip, float xn2f, float ymf, double eps_dot,
+                                           int lane,
                                            int32_t *__restrict__ nbr_row,
                                            float *__restrict__ dist_row) {
     constexpr int KP = KC - 1;
@@ -650,8 +659,15 @@ __device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, 
     uint64_t kth = __shfl_sync(0xffffffffu, kh ? key[1] : key[0], kl);
     bool cert = false;
     if (lane == 0) {
-        if (!(sp < __int_as_float(0x7f800000))) {
-            cert = true;  // fewer than KC points besides i: every one was kept
+        const double u24c = 1.0 / 16777216.0;
+        // keys of skipped tiles lie at true distance >= skip; their canonical
+        // distance is then above the k-th when skip (1 - eps_canon) is
+        const bool skip_ok = !(skip < __int_as_float(0x7f800000)) ||
+                             double(skip) * (1.0 - (d + 4.0) * u24c * 1.05) > double(key_w(kth));
+        if (!skip_ok) {
+            cert = false;
+        } else if (!(sp < __int_as_float(0x7f800000))) {
+            cert = true;  // fewer than KC points besides i among the visited keys: all kept
         } else {
             const double u24 = 1.0 / 16777216.0;
             const double xn2 = double(xn2f);
@@ -685,13 +701,15 @@ __device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, 
 template <int VEC, int KC>
 __global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int k,
                               const int32_t *__restrict__ cand, const float *__restrict__ splus,
+                              const float *__restrict__ skip,
                               const float *__restrict__ xnorm2, const unsigned *__restrict__ ymax_bits,
                               CertConst cc, int32_t *__restrict__ nbr, float *__restrict__ dist,
                               int32_t *__restrict__ fail_rows, int32_t *__restrict__ fail_count) {
     int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (i >= n) return;
-    bool cert = rerank_row<VEC, KC>(X, d, d, d, X + i * d, k, cand + i * (KC - 1), splus[i],
+    const float sk = skip ? skip[i] : __int_as_float(0x7f800000);
+    bool cert = rerank_row<VEC, KC>(X, d, d, d, X + i * d, k, cand + i * (KC - 1), splus[i], sk,
                                     xnorm2[i], __uint_as_float(*ymax_bits), cc.eps_dot, lane,
                                     nbr + i * k, dist + i * k);
     if (!cert && lane == 0) fail_rows[atomicAdd(fail_count, 1)] = int32_t(i);
@@ -733,6 +751,7 @@ __global__ void rerank_batched_kernel(const float *__restrict__ Xc, int ld, int6
                        kprod * (1.0 / 4194304.0) * (1.0 + 4.0 * u8);
     const int dc = (c.d + 3) & ~3;
     bool cert = rerank_row<4, KC>(Xc, ld, dc, c.d, Xc + v * ld, k, cand + v * (KC - 1), splus[v],
+                                  __int_as_float(0x7f800000),
                                   xnorm2[v], __uint_as_float(ymax_bits[b]), eps, lane, nbr + v * k,
                                   dist + v * k);
     if (!cert && lane == 0) fail_rows[atomicAdd(fail_count, 1)] = int32_t(v);
@@ -903,9 +922,14 @@ bool knn_tc_supported(int64_t n, int d, int k, bool x3) {
     return p.stages >= 2 && encode_fn() != nullptr;
 }
 
-size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms) {
+size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prune) {
     TcPlan p = tc_plan(n, d, k, x3);
     size_t b = 0;
+    if (prune) {
+        const int64_t K = prune_pivots(n), Kpad = (K + BN - 1) / BN * BN;
+        b += align256(size_t(K) * 4) + align256(size_t(K) * p.kh * 2) + align256(size_t(Kpad) * 4);
+        b += prune_workspace(n, d, p.kh, p.kc - 1, p.nq_tiles, p.nk_tiles);
+    }
     b += align256(size_t(n) * p.kh * 2);                   // operand rows
     b += align256(size_t(p.nk_tiles) * BN * 4) * 2;        // ny, components (padded)
     b += align256(size_t(n) * 4);                          // xnorm2
@@ -919,7 +943,8 @@ size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms) {
 
 famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k, bool x3,
                     bool vec4, int32_t *nbr, float *dist, int32_t *pinned_host,
-                    int64_t *uncertified, const int32_t *colcomp) {
+                    int64_t *uncertified, const int32_t *colcomp, bool prune,
+                    int64_t *tiles_visited) {
     TcPlan p = tc_plan(n, d, k, x3);
     if (p.stages < 2 || k + 1 > 64) return FAMST_ERR_UNSUPPORTED;
     __nv_bfloat16 *H = ar.take<__nv_bfloat16>(size_t(n) * p.kh);
@@ -947,8 +972,47 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     const int64_t npad = p.nk_tiles * BN;
     if (npad > n)
         FAMST_LAUNCH(ex, fill_inf_kernel, unsigned((npad - n + 255) / 256), 256, 0, ny, n, npad);
+    const bool use_prune = prune && !colcomp && prune_supported(n, d, k, vec4);
+    float *skip = nullptr;
+    PruneOut P;
+    if (use_prune) {
+        // pivot cells: top-1 pivot of every point on the tensor tiles (BF16)
+        const int K = prune_pivots(n);
+        const int Kpad = (K + BN - 1) / BN * BN;
+        int32_t *piv = ar.take<int32_t>(size_t(K));
+        __nv_bfloat16 *Hp = ar.take<__nv_bfloat16>(size_t(K) * p.kh);
+        float *nyp = ar.take<float>(size_t(Kpad));
+        if (!piv || !Hp || !nyp) return FAMST_ERR_OOM;
+        famst_status st = prune_pivot_operands(ex, H, p.kh, ny, n, K, piv, Hp, nyp);
+        if (st != FAMST_OK) return st;
+        const TcPlan p1 = tc_plan(n, d, 1, false);
+        CUtensorMap mA1, mB1;
+        if (!make_map(&mA1, H, n, p.kh, BM) || !make_map(&mB1, Hp, K, p.kh, BN))
+            return FAMST_ERR_CUDA;
+        TcArgs a1{int(n), Kpad / BN, p.nkb, 0, p1.stages, nyp, cand, splus, ex.dstatus, nullptr,
+                  nullptr, nullptr, 1};
+        if (set_smem_attr(knn_tc_kernel<32, false>, int(p1.smem), ex.stream) != cudaSuccess)
+            return FAMST_ERR_CUDA;
+        FAMST_LAUNCH(ex, (knn_tc_kernel<32, false>), unsigned(p.nq_tiles), TC_THREADS, p1.smem, mA1,
+                     mB1, a1);
+        st = prune_partition(ex, ar, X, d, n, k, H, p.kh, ny, p.nkb, K, piv, cand, 31,
+                             pinned_host + 2, &P);
+        if (st != FAMST_OK) return st;
+        skip = ar.take<float>(size_t(n));
+        if (!skip) return FAMST_ERR_OOM;
+    }
+    // candidates of the tensor pass: directly in cand / splus, or (pruned)
+    // in sorted order first
+    int32_t *cand_t = cand;
+    float *splus_t = splus;
+    if (use_prune) {
+        cand_t = ar.take<int32_t>(size_t(n) * (p.kc - 1));
+        splus_t = ar.take<float>(size_t(n));
+        if (!cand_t || !splus_t) return FAMST_ERR_OOM;
+    }
+    const __nv_bfloat16 *Hop = use_prune ? P.Hs : H;
     CUtensorMap mA, mB;
-    if (!make_map(&mA, H, n, p.kh, BM) || !make_map(&mB, H, n, p.kh, BN)) return FAMST_ERR_CUDA;
+    if (!make_map(&mA, Hop, n, p.kh, BM) || !make_map(&mB, Hop, n, p.kh, BN)) return FAMST_ERR_CUDA;
     int32_t *cpad = nullptr;   // components over the padded rows (-1 beyond n)
     if (colcomp) {
         cpad = ar.take<int32_t>(size_t(npad));
@@ -957,8 +1021,9 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
                 cudaSuccess)
             return FAMST_ERR_CUDA;
     }
-    TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, ny, cand, splus, ex.dstatus, nullptr,
-             cpad};
+    TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, use_prune ? P.nys : ny, cand_t,
+             splus_t, ex.dstatus, use_prune ? P.tab : nullptr, cpad,
+             use_prune ? P.klist : nullptr, 0};
 #define TC_LAUNCH(KCV, M)                                                                        \
     do {                                                                                         \
         if (set_smem_attr(knn_tc_kernel<KCV, M>, int(p.smem), ex.stream) != cudaSuccess)         \
@@ -977,6 +1042,10 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     }
 #undef TC_LAUNCH
     if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
+    if (use_prune) {
+        famst_status st = prune_scatter(ex, P, n, p.kc - 1, cand_t, splus_t, cand, splus, skip);
+        if (st != FAMST_OK) return st;
+    }
     // rerank + certificate
     const double u8 = 1.0 / 256.0;
     const double kprod = double(x3 ? 3 * p.d_pad : p.d_pad);
@@ -987,8 +1056,8 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     cc.d_plus = double(d) + 4.0;
     const unsigned rgrid = unsigned((n * 32 + 255) / 256);
 #define RERANK(V, KCV)                                                                           \
-    FAMST_LAUNCH(ex, (rerank_kernel<V, KCV>), rgrid, 256, 0, X, n, d, k, cand, splus, xn2, ymax, cc, \
-                 nbr, dist, fail_rows, fail_count)
+    FAMST_LAUNCH(ex, (rerank_kernel<V, KCV>), rgrid, 256, 0, X, n, d, k, cand, splus, skip, xn2, \
+                 ymax, cc, nbr, dist, fail_rows, fail_count)
     if (p.kc == 32) {
         if (vec4) RERANK(4, 32); else RERANK(1, 32);
     } else if (p.kc == 48) {
@@ -998,10 +1067,13 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     }
 #undef RERANK
     if (cudaMemcpyAsync(pinned_host, fail_count, 4, cudaMemcpyDeviceToHost, ex.stream) != cudaSuccess ||
+        (use_prune && cudaMemcpyAsync(pinned_host + 1, P.visited, 4, cudaMemcpyDeviceToHost,
+                                      ex.stream) != cudaSuccess) ||
         cudaStreamSynchronize(ex.stream) != cudaSuccess)
         return FAMST_ERR_CUDA;
     const int32_t nfail = *pinned_host;
     *uncertified = nfail;
+    if (tiles_visited) *tiles_visited = use_prune ? int64_t(pinned_host[1]) : p.nq_tiles * p.nk_tiles;
     if (nfail > 0) {
         famst_status st = knn_fp32(ex, ar, X, n, d, k, fail_rows, 0, nfail, nbr, dist, colcomp);
         if (st != FAMST_OK) return st;
@@ -1042,7 +1114,7 @@ famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, i
     FAMST_LAUNCH(ex, tc_prep_batched_kernel, unsigned((NP * 32 + 255) / 256), 256, 0, Xc, D, NP,
                  roff, voff, B, cl, D, int(x3), mean, H, ny, xn2, ymax);
     if (nctas > 0) {
-        TcArgs a{0, 0, nkb, int(x3), stages, ny, cand, splus, ex.dstatus, tiles, nullptr};
+        TcArgs a{0, 0, nkb, int(x3), stages, ny, cand, splus, ex.dstatus, tiles, nullptr, nullptr, 0};
 #define TCB_LAUNCH(KCV)                                                                          \
     do {                                                                                         \
         if (set_smem_attr(knn_tc_kernel<KCV, false>, \

@@ -1,0 +1,622 @@
+// Tile pruning for Phase 1 (exact kNN). Brute force visits every (query
+// tile, key tile) pair; on data with structure most pairs cannot hold a
+// neighbour, and the triangle inequality proves it cheaply:
+//
+//   1. Locality partition. K pivots (evenly spaced rows); every point joins
+//      the cell of its nearest pivot (the tensor-core distance tiles with
+//      pivots as keys, BF16, top-1 -- any assignment is valid, a good one
+//      only makes cells tight). Points are sorted by cell, so a 128-row
+//      query tile or a 256-row key tile of the sorted order covers a few
+//      consecutive cells.
+//   2. Balls. R_c >= max over members of |x - p_c| and D_lo(a, b) <=
+//      |p_a - p_b| (warp-wide fast sums with rigorous rounding bounds).
+//      For x in cell a and y in cell b: |x - y| >= D_lo(a, b) - R_a - R_b.
+//   3. Radius of interest. For every point, any k other points give an
+//      upper bound on its k-th neighbour distance: tau_r = the largest
+//      distance (rounded up) to k points next to it in the sorted order,
+//      inside its cell when the cell is large enough. tau_Q = max over the
+//      query tile.
+//   4. Lists. Key tile T is visited by query tile Q unless
+//      LB(Q, T) = min over cells a of Q, b of T of D_lo - R_a - R_b exceeds
+//      tau_Q (with a margin for the canonical rounding). skip_Q = the
+//      smallest LB of the skipped tiles: every skipped key is at true
+//      distance >= skip_Q from every point of Q.
+//
+// The re-rank certificate then also requires skip (1 - eps_canon) to exceed
+// the k-th canonical distance; rows that fail fall back to the exact FP32
+// tiles, so the output is the exact kNN whatever the data.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <utility>
+#include <vector>
+
+#include "famst_internal.cuh"
+
+namespace famst {
+namespace {
+
+constexpr int QT = 128;    // query tile rows
+constexpr int KT = 256;    // key tile rows
+constexpr int NPMAX = 8;   // cells per tile beyond which a tile is never skipped
+
+inline unsigned nblk(int64_t n, int th) { return unsigned((n + th - 1) / th); }
+
+__device__ __forceinline__ float sq_hi(float p, float rho) {
+    return __fadd_ru(__fmul_ru(p, 1.0f + rho), 1e-30f);
+}
+__device__ __forceinline__ float sq_lo(float p, float rho) {
+    return fmaxf(__fsub_rd(__fmul_rd(p, 1.0f - rho), 1e-30f), 0.0f);
+}
+
+// pivot c = row c n / K: its operand row and norm; nyp padded with +inf
+__global__ void pivots_kernel(const __nv_bfloat16 *__restrict__ H, int kh,
+                              const float *__restrict__ ny, int64_t n, int K, int Kpad,
+                              int32_t *__restrict__ piv, __nv_bfloat16 *__restrict__ Hp,
+                              float *__restrict__ nyp) {
+    const int64_t c = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= Kpad) return;
+    if (c >= K) {
+        if (lane == 0) nyp[c] = __int_as_float(0x7f800000);
+        return;
+    }
+    const int64_t row = c * n / K;
+    if (lane == 0) {
+        piv[c] = int32_t(row);
+        nyp[c] = ny[row];
+    }
+    const uint4 *src = reinterpret_cast<const uint4 *>(H + row * kh);
+    uint4 *dst = reinterpret_cast<uint4 *>(Hp + c * kh);
+    for (int q = lane; q < kh / 8; q += 32) dst[q] = src[q];
+}
+
+// cell of every point = the rank of its best pivot candidate; sort keys and
+// cell sizes
+__global__ void assign_kernel(const int32_t *__restrict__ cand, int kp, int64_t n, int K,
+                              const int32_t *__restrict__ rank, uint32_t *__restrict__ keys,
+                              int32_t *__restrict__ vals, int32_t *__restrict__ ccount) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int c = cand[i * kp];
+    if (c < 0 || c >= K) c = 0;
+    c = rank[c];
+    keys[i] = uint32_t(c);
+    vals[i] = int32_t(i);
+    atomicAdd(ccount + c, 1);
+}
+
+// sorted operand rows and key norms (+inf beyond n)
+__global__ void gather_kernel(const __nv_bfloat16 *__restrict__ H, int kh,
+                              const float *__restrict__ ny, const int32_t *__restrict__ perm,
+                              int64_t n, int64_t npad, __nv_bfloat16 *__restrict__ Hs,
+                              float *__restrict__ nys) {
+    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= npad) return;
+    if (r >= n) {
+        if (lane == 0) nys[r] = __int_as_float(0x7f800000);
+        return;
+    }
+    const int64_t i = perm[r];
+    if (lane == 0) nys[r] = ny[i];
+    const uint4 *src = reinterpret_cast<const uint4 *>(H + i * kh);
+    uint4 *dst = reinterpret_cast<uint4 *>(Hs + r * kh);
+    for (int q = lane; q < kh / 8; q += 32) dst[q] = src[q];
+}
+
+// R_c: upper bound on the distance of every member of cell c to its pivot
+template <int FR>
+__global__ void radius_kernel(const float *__restrict__ X, int d, int64_t n,
+                              const int32_t *__restrict__ perm, const uint32_t *__restrict__ skey,
+                              const int32_t *__restrict__ piv, const int32_t *__restrict__ order,
+                              float rho, unsigned *__restrict__ R_bits) {
+    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int c = int(skey[r]);
+    const float s =
+        warp_sqdist1<FR>(X + int64_t(perm[r]) * d, X + int64_t(piv[order[c]]) * d, d, lane);
+    if (lane == 0) {
+        const float h = __fmul_ru(__fsqrt_ru(sq_hi(s, rho)), 1.0f + 0x1p-22f);
+        atomicMax(R_bits + c, __float_as_uint(h));
+    }
+}
+
+// tau_Q: upper bound on the k-th neighbour distance of every row of query
+// tile Q, from k other points next to each row in the sorted order, taken
+// inside the row's group of cells when the group holds k + 1 points
+template <int FR>
+__global__ void tau_kernel(const float *__restrict__ X, int d, int64_t n, int k,
+                           const int32_t *__restrict__ perm, const uint32_t *__restrict__ skey,
+                           const int32_t *__restrict__ cstart, const int32_t *__restrict__ gfirst,
+                           const int32_t *__restrict__ glast, float rho,
+                           unsigned *__restrict__ tau_bits) {
+    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int c = int(skey[r]);
+    const int64_t cs = cstart[gfirst[c]], ce = cstart[glast[c] + 1];
+    int64_t lo, hi;
+    if (ce - cs >= k + 1) {
+        lo = cs;
+        hi = ce - (k + 1);
+    } else {
+        lo = 0;
+        hi = n - (k + 1);
+    }
+    int64_t w0 = r - k / 2;
+    w0 = w0 < lo ? lo : (w0 > hi ? hi : w0);
+    const int self = int(perm[r]);
+    float4 fx[FR];
+    row_slices<FR>(X + int64_t(self) * d, d >> 2, lane, fx);
+    float t = 0.0f;
+    for (int base = 0; base < k + 1; base += 32) {
+        const int idx = base + lane;
+        const int64_t pos = w0 + idx;
+        const int cand = (idx < k + 1 && pos != r) ? int(perm[pos]) : -1;
+        const float s = warp_sqdist32<FR>(X, d, fx, self, cand, lane);
+        if (cand >= 0) t = fmaxf(t, __fmul_ru(__fsqrt_ru(sq_hi(s, rho)), 1.0f + 0x1p-22f));
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+    if (lane == 0) atomicMax(tau_bits + r / QT, __float_as_uint(t));
+}
+
+// DP[a][b] <= |p_a - p_b|: warp per (a, 32 consecutive b)
+template <int FR>
+__global__ void pivot_dist_kernel(const float *__restrict__ X, int d, int K,
+                                  const int32_t *__restrict__ piv, float rho,
+                                  float *__restrict__ DP) {
+    const int64_t w = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nbb = (K + 31) / 32;
+    if (w >= int64_t(K) * nbb) return;
+    const int a = int(w / nbb);
+    const int b = int(w % nbb) * 32 + lane;
+    const int pa = piv[a];
+    float4 fx[FR];
+    row_slices<FR>(X + int64_t(pa) * d, d >> 2, lane, fx);
+    const int cand = b < K ? piv[b] : -1;
+    const float s = warp_sqdist32<FR>(X, d, fx, pa, cand, lane);
+    if (b < K)
+        DP[int64_t(a) * K + b] =
+            a == b ? 0.0f : __fmul_rd(__fsqrt_rd(sq_lo(s, rho)), 1.0f - 0x1p-22f);
+}
+
+// DP[a][b] = DP[b][a] = the smaller of the two bounds (both are valid)
+__global__ void sym_kernel(float *__restrict__ DP, int K) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= int64_t(K) * K) return;
+    const int a = int(t / K), b = int(t % K);
+    if (b <= a) return;
+    const float v = fminf(DP[int64_t(a) * K + b], DP[int64_t(b) * K + a]);
+    DP[int64_t(a) * K + b] = v;
+    DP[int64_t(b) * K + a] = v;
+}
+
+// Boruvka step on the complete pivot graph: nearest pivot of another
+// component under (DP, id), one warp per pivot
+__global__ void pivot_nearest_kernel(const float *__restrict__ DP, int K,
+                                     const int32_t *__restrict__ comp, int32_t *__restrict__ nb,
+                                     float *__restrict__ nw) {
+    const int64_t a = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (a >= K) return;
+    const int ca = comp[a];
+    uint64_t best = KEY_NONE;
+    for (int b = lane; b < K; b += 32) {
+        if (comp[b] == ca) continue;
+        const uint64_t key = nb_key(DP[a * K + b], uint32_t(b));
+        best = key < best ? key : best;
+    }
+    best = warp_min_u64(best);
+    if (lane == 0) {
+        nb[a] = best == KEY_NONE ? int32_t(a) : int32_t(key_lo(best));
+        nw[a] = best == KEY_NONE ? __int_as_float(0x7f800000) : key_w(best);
+    }
+}
+
+// DPr[a][b] = DP[order[a]][order[b]] (cells in rank order)
+__global__ void dp_gather_kernel(const float *__restrict__ DP, int K,
+                                 const int32_t *__restrict__ order, float *__restrict__ DPr) {
+    const int64_t a = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (a >= K) return;
+    const float *src = DP + int64_t(order[a]) * K;
+    for (int b = lane; b < K; b += 32) DPr[a * K + b] = src[order[b]];
+}
+
+// first and last cell of every query tile and key tile
+__global__ void tile_cells_kernel(const uint32_t *__restrict__ skey, int64_t n, int64_t nq,
+                                  int64_t nk, int32_t *__restrict__ qc, int32_t *__restrict__ kc) {
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t < nq) {
+        const int64_t r0 = t * QT, r1 = (r0 + QT < n ? r0 + QT : n) - 1;
+        qc[2 * t] = int32_t(skey[r0]);
+        qc[2 * t + 1] = int32_t(skey[r1]);
+    }
+    if (t < nk) {
+        const int64_t r0 = t * KT, r1 = (r0 + KT < n ? r0 + KT : n) - 1;
+        kc[2 * t] = int32_t(skey[r0]);
+        kc[2 * t + 1] = int32_t(skey[r1]);
+    }
+}
+
+// Per query tile (one block): which key tiles to visit. FILL = false counts
+// them into cnt[Q]; FILL = true writes them, ascending, at klist + off[Q]
+// and the smallest lower bound of the skipped tiles into skipQ[Q].
+template <bool FILL>
+__global__ void __launch_bounds__(256)
+tile_pairs_kernel(const int32_t *__restrict__ qc, const int32_t *__restrict__ kc, int64_t nk,
+                  int K, const float *__restrict__ DP, const float *__restrict__ R,
+                  const float *__restrict__ tauQ, float margin, int32_t *__restrict__ cnt,
+                  const int32_t *__restrict__ off, int32_t *__restrict__ klist,
+                  float *__restrict__ skipQ) {
+    __shared__ int wsum[8];
+    __shared__ float wmin[8];
+    __shared__ int base_s;
+    const int Q = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int a0 = qc[2 * Q], a1 = qc[2 * Q + 1];
+    const bool q_open = a1 - a0 + 1 > NPMAX;   // too many cells: visit every tile
+    const float tau = __fmul_ru(tauQ[Q], margin);
+    const float inf = __int_as_float(0x7f800000);
+    float ra[NPMAX];
+#pragma unroll
+    for (int q = 0; q < NPMAX; ++q) ra[q] = (!q_open && a0 + q <= a1) ? R[a0 + q] : 0.0f;
+    int count = 0;
+    float smin = inf;
+    if (threadIdx.x == 0) base_s = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < nk; c0 += 256) {
+        const int64_t T = c0 + threadIdx.x;
+        bool visit = false;
+        float lb = inf;
+        if (T < nk) {
+            const int b0 = kc[2 * T], b1 = kc[2 * T + 1];
+            if (q_open || b1 - b0 + 1 > NPMAX) {
+                lb = -inf;
+            } else {
+#pragma unroll
+                for (int q = 0; q < NPMAX; ++q) {
+                    if (a0 + q > a1) break;
+                    const float *dp = DP + int64_t(a0 + q) * K;
+                    for (int b = b0; b <= b1; ++b)
+                        lb = fminf(lb, __fsub_rd(__fsub_rd(dp[b], ra[q]), R[b]));
+                }
+            }
+            visit = !(lb > tau);
+            if (!visit) smin = fminf(smin, lb);
+        }
+        if constexpr (FILL) {
+            const unsigned bal = __ballot_sync(0xffffffffu, visit);
+            if (lane == 0) wsum[warp] = __popc(bal);
+            __syncthreads();
+            int pre = base_s;
+            for (int w = 0; w < warp; ++w) pre += wsum[w];
+            if (visit) klist[off[Q] + pre + __popc(bal & ((1u << lane) - 1u))] = int32_t(T);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int s = 0;
+                for (int w = 0; w < 8; ++w) s += wsum[w];
+                base_s += s;
+            }
+            __syncthreads();
+        } else {
+            count += visit ? 1 : 0;
+        }
+    }
+    if constexpr (FILL) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) smin = fminf(smin, __shfl_xor_sync(0xffffffffu, smin, o));
+        if (lane == 0) wmin[warp] = smin;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = inf;
+            for (int w = 0; w < 8; ++w) m = fminf(m, wmin[w]);
+            skipQ[Q] = m;
+        }
+    } else {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) count += __shfl_xor_sync(0xffffffffu, count, o);
+        if (lane == 0) wsum[warp] = count;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int s = 0;
+            for (int w = 0; w < 8; ++w) s += wsum[w];
+            cnt[Q] = s;
+        }
+    }
+}
+
+__global__ void table_kernel(const int32_t *__restrict__ off, int64_t nq, int nkb, int64_t n,
+                             TcTile *__restrict__ tab) {
+    const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    TcTile t;
+    t.q0 = int(q * QT);
+    t.kt0 = off[q];
+    t.kt1 = off[q + 1];
+    t.nkb = nkb;
+    t.row_end = int(n);
+    t.shift = 0;
+    tab[q] = t;
+}
+
+// candidates, s+ and skip bound of sorted row r to original row perm[r],
+// candidate ids translated to original ids
+__global__ void scatter_kernel(const int32_t *__restrict__ perm, int64_t n, int kp,
+                               const int32_t *__restrict__ cand_s,
+                               const float *__restrict__ splus_s,
+                               const float *__restrict__ skipQ, int32_t *__restrict__ cand,
+                               float *__restrict__ splus, float *__restrict__ skip) {
+    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int64_t i = perm[r];
+    for (int p = lane; p < kp; p += 32) {
+        const int j = cand_s[r * kp + p];
+        cand[i * kp + p] = j >= 0 ? perm[j] : -1;
+    }
+    if (lane == 0) {
+        splus[i] = splus_s[r];
+        skip[i] = skipQ[r / QT];
+    }
+}
+
+// Order of the cells. The minimum spanning tree of the pivots is cut at
+// edges longer than twice its median edge into groups (single linkage);
+// groups are laid out one after another, each by a depth-first walk over
+// its short edges, shortest first. Cells next to each other in the order
+// are then close, and every group is one contiguous run. Output (4 K ints):
+// order[rank] = pivot, rank[pivot], and per rank the first and last rank of
+// its group.
+void order_cells(int K, const std::vector<int32_t> &tu, const std::vector<int32_t> &tv,
+                 const std::vector<float> &tw, int32_t *out) {
+    const size_t m = tu.size();
+    std::vector<float> ws(tw);
+    float theta = 0.0f;
+    if (m > 0) {
+        std::nth_element(ws.begin(), ws.begin() + m / 2, ws.end());
+        theta = 2.0f * ws[m / 2];
+    }
+    std::vector<std::vector<std::pair<float, int32_t>>> adj(static_cast<size_t>(K));
+    for (size_t e = 0; e < m; ++e) {
+        adj[size_t(tu[e])].push_back({tw[e], tv[e]});
+        adj[size_t(tv[e])].push_back({tw[e], tu[e]});
+    }
+    for (auto &l : adj) std::sort(l.begin(), l.end());
+    int32_t *order = out, *rank = out + K, *gfirst = out + 2 * K, *glast = out + 3 * K;
+    std::vector<char> seen(static_cast<size_t>(K), 0);
+    std::vector<int32_t> groups, stack;
+    int32_t pos = 0;
+    for (int32_t root = 0; root < K; ++root) {   // every tree component (the forest case too)
+        if (seen[size_t(root)]) continue;
+        seen[size_t(root)] = 1;
+        groups.push_back(root);
+        while (!groups.empty()) {
+            const int32_t g = groups.back();
+            groups.pop_back();
+            const int32_t first = pos;
+            stack.push_back(g);
+            while (!stack.empty()) {
+                const int32_t u = stack.back();
+                stack.pop_back();
+                order[pos++] = u;
+                const auto &l = adj[size_t(u)];
+                for (size_t q = l.size(); q-- > 0;) {   // shortest edge popped first
+                    const int32_t v = l[q].second;
+                    if (seen[size_t(v)]) continue;
+                    seen[size_t(v)] = 1;
+                    if (l[q].first <= theta) stack.push_back(v);
+                    else groups.push_back(v);
+                }
+            }
+            for (int32_t r = first; r < pos; ++r) {
+                gfirst[r] = first;
+                glast[r] = pos - 1;
+            }
+        }
+    }
+    for (int32_t r = 0; r < K; ++r) rank[order[r]] = r;
+}
+
+}  // namespace
+
+int prune_pivots(int64_t n) {
+    int64_t K = n / 128;
+    if (K < 32) K = 32;
+    if (K > 8192) K = 8192;
+    return int(K);
+}
+
+bool prune_supported(int64_t n, int d, int k, bool vec4) {
+    return vec4 && d >= 4 && d <= 512 && n >= 4 * int64_t(k + 1) && n >= 4096;
+}
+
+size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk) {
+    const int64_t K = prune_pivots(n);
+    const int64_t Kpad = (K + KT - 1) / KT * KT;
+    size_t b = 0;
+    b += align256(size_t(K) * 4) + align256(size_t(K) * kh * 2) + align256(size_t(Kpad) * 4);
+    b += align256(size_t(n) * 4) * 2 + align256(size_t(K + 1) * 4) * 2;        // keys, perm, cells
+    b += radix_sort_workspace(n) + scan_workspace(K + 1) + 256;
+    b += align256(size_t(n) * kh * 2) + align256(size_t(nk) * KT * 4);         // sorted operand
+    b += align256(size_t(K) * 4) + align256(size_t(nq) * 4);                   // R, tau
+    b += align256(size_t(K) * K * 4) * 2;                                      // DP, DPr
+    b += align256(size_t(4 * K) * 4) + align256(size_t(K) * 4) * 5;             // order, tree
+    b += boruvka_workspace(K);                                                 // pivot tree
+    b += align256(size_t(nq) * 8) + align256(size_t(nk) * 8);                  // tile cells
+    b += align256(size_t(nq + 1) * 4) * 2 + scan_workspace(nq + 1) + 256;      // counts, offsets
+    b += align256(size_t(nq) * nk * 4);                                        // lists (worst case)
+    b += align256(size_t(nq) * 4) + align256(size_t(nq) * sizeof(TcTile));     // skip, table
+    b += align256(size_t(n) * kp * 4) + align256(size_t(n) * 4) * 2;           // sorted outputs
+    return b;
+}
+
+famst_status prune_pivot_operands(const Exec &ex, const __nv_bfloat16 *H, int kh, const float *ny,
+                                  int64_t n, int K, int32_t *piv, __nv_bfloat16 *Hp, float *nyp) {
+    const int Kpad = (K + KT - 1) / KT * KT;
+    FAMST_LAUNCH(ex, pivots_kernel, nblk(int64_t(Kpad) * 32, 256), 256, 0, H, kh, ny, n, K, Kpad,
+                 piv, Hp, nyp);
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, int64_t n, int k,
+                             const __nv_bfloat16 *H, int kh, const float *ny, int nkb, int K,
+                             const int32_t *piv, const int32_t *acand, int akp,
+                             int32_t *pinned_host, PruneOut *out) {
+    const int64_t nq = (n + QT - 1) / QT, nk = (n + KT - 1) / KT;
+    uint32_t *keys = ar.take<uint32_t>(size_t(n));
+    int32_t *perm = ar.take<int32_t>(size_t(n));
+    int32_t *ccount = ar.take<int32_t>(size_t(K + 1));
+    int32_t *cstart = ar.take<int32_t>(size_t(K + 1));
+    __nv_bfloat16 *Hs = ar.take<__nv_bfloat16>(size_t(n) * kh);
+    float *nys = ar.take<float>(size_t(nk) * KT);
+    float *R = ar.take<float>(size_t(K));
+    float *tauQ = ar.take<float>(size_t(nq));
+    float *DP = ar.take<float>(size_t(K) * K);
+    float *DPr = ar.take<float>(size_t(K) * K);
+    int32_t *ord = ar.take<int32_t>(size_t(4) * K);   // order, rank, gfirst, glast
+    int32_t *tu = ar.take<int32_t>(size_t(K));
+    int32_t *tv = ar.take<int32_t>(size_t(K));
+    float *tw = ar.take<float>(size_t(K));
+    int32_t *nb = ar.take<int32_t>(size_t(K));
+    float *nw = ar.take<float>(size_t(K));
+    int32_t *qc = ar.take<int32_t>(size_t(nq) * 2);
+    int32_t *kc = ar.take<int32_t>(size_t(nk) * 2);
+    int32_t *cnt = ar.take<int32_t>(size_t(nq + 1));
+    int32_t *off = ar.take<int32_t>(size_t(nq + 1));
+    int32_t *klist = ar.take<int32_t>(size_t(nq) * nk);
+    float *skipQ = ar.take<float>(size_t(nq));
+    TcTile *tab = ar.take<TcTile>(size_t(nq));
+    int32_t *total = ar.take<int32_t>(1);
+    if (!keys || !perm || !ccount || !cstart || !Hs || !nys || !R || !tauQ || !DP || !DPr || !ord ||
+        !tu || !tv || !tw || !nb || !nw || !qc || !kc || !cnt || !off || !klist || !skipQ || !tab ||
+        !total)
+        return FAMST_ERR_OOM;
+    const float rho = fast_rho(d, d <= 128 ? 1 : (d <= 256 ? 2 : 4));
+    if (cudaMemsetAsync(ccount, 0, size_t(K + 1) * 4, ex.stream) != cudaSuccess ||
+        cudaMemsetAsync(cnt, 0, size_t(nq + 1) * 4, ex.stream) != cudaSuccess ||
+        cudaMemsetAsync(R, 0, size_t(K) * 4, ex.stream) != cudaSuccess ||
+        cudaMemsetAsync(tauQ, 0, size_t(nq) * 4, ex.stream) != cudaSuccess)
+        return FAMST_ERR_CUDA;
+    const int64_t nbb = (K + 31) / 32;
+    const int fr = d <= 128 ? 1 : (d <= 256 ? 2 : 4);
+    // 1. pivot distances (lower bounds, symmetric)
+    if (fr == 1)
+        FAMST_LAUNCH(ex, pivot_dist_kernel<1>, nblk(int64_t(K) * nbb * 32, 256), 256, 0, X, d, K,
+                     piv, rho, DP);
+    else if (fr == 2)
+        FAMST_LAUNCH(ex, pivot_dist_kernel<2>, nblk(int64_t(K) * nbb * 32, 256), 256, 0, X, d, K,
+                     piv, rho, DP);
+    else
+        FAMST_LAUNCH(ex, pivot_dist_kernel<4>, nblk(int64_t(K) * nbb * 32, 256), 256, 0, X, d, K,
+                     piv, rho, DP);
+    FAMST_LAUNCH(ex, sym_kernel, nblk(int64_t(K) * K, 256), 256, 0, DP, K);
+    // 2. order of the cells: minimum spanning tree of the pivots (Boruvka)
+    famst_status st;
+    {
+        const size_t mark = ar.off;
+        BvState S;
+        st = bv_state_init(ex, ar, K, &S);
+        int64_t got = 0;
+        for (int r = 0; r < 64 && got < K - 1 && st == FAMST_OK; ++r) {
+            FAMST_LAUNCH(ex, pivot_nearest_kernel, nblk(int64_t(K) * 32, 256), 256, 0, DP, K,
+                         S.comp, nb, nw);
+            st = bv_round(ex, ar, S, nb, nw, 1, nullptr, nullptr, nullptr, 0, MstOut{tu, tv, tw},
+                          got, pinned_host);
+            if (st != FAMST_OK) break;
+            if (*pinned_host == 0) break;
+            got += *pinned_host;
+        }
+        ar.off = mark;
+        if (st != FAMST_OK) return st;
+        std::vector<int32_t> hu(static_cast<size_t>(got)), hv(static_cast<size_t>(got));
+        std::vector<float> hw(static_cast<size_t>(got));
+        if (got > 0 &&
+            (cudaMemcpyAsync(hu.data(), tu, size_t(got) * 4, cudaMemcpyDeviceToHost, ex.stream) !=
+                 cudaSuccess ||
+             cudaMemcpyAsync(hv.data(), tv, size_t(got) * 4, cudaMemcpyDeviceToHost, ex.stream) !=
+                 cudaSuccess ||
+             cudaMemcpyAsync(hw.data(), tw, size_t(got) * 4, cudaMemcpyDeviceToHost, ex.stream) !=
+                 cudaSuccess ||
+             cudaStreamSynchronize(ex.stream) != cudaSuccess))
+            return FAMST_ERR_CUDA;
+        std::vector<int32_t> h_ord(static_cast<size_t>(4) * K);
+        order_cells(K, hu, hv, hw, h_ord.data());
+        if (cudaMemcpyAsync(ord, h_ord.data(), size_t(4) * K * 4, cudaMemcpyHostToDevice,
+                            ex.stream) != cudaSuccess ||
+            cudaStreamSynchronize(ex.stream) != cudaSuccess)
+            return FAMST_ERR_CUDA;
+    }
+    const int32_t *order = ord, *rank = ord + K, *gfirst = ord + 2 * K, *glast = ord + 3 * K;
+    // 3. cells in rank order, sorted points
+    FAMST_LAUNCH(ex, assign_kernel, nblk(n, 256), 256, 0, acand, akp, n, K, rank, keys, perm,
+                 ccount);
+    int bits = 0;
+    while ((int64_t(1) << bits) < K) ++bits;
+    {
+        const size_t mark = ar.off;
+        st = radix_sort_pairs(ex, ar, keys, perm, n, bits);
+        if (st == FAMST_OK) st = exclusive_scan_i32(ex, ar, ccount, cstart, K + 1, total);
+        ar.off = mark;
+        if (st != FAMST_OK) return st;
+    }
+    FAMST_LAUNCH(ex, gather_kernel, nblk(nk * KT * 32, 256), 256, 0, H, kh, ny, perm, n, nk * KT,
+                 Hs, nys);
+    FAMST_LAUNCH(ex, dp_gather_kernel, nblk(int64_t(K) * 32, 256), 256, 0, DP, K, order, DPr);
+    // 4. balls and radii of interest
+    const unsigned wgrid = nblk(n * 32, 256);
+#define PRUNE_GEOM(F)                                                                            \
+    do {                                                                                         \
+        FAMST_LAUNCH(ex, radius_kernel<F>, wgrid, 256, 0, X, d, n, perm, keys, piv, order, rho,  \
+                     reinterpret_cast<unsigned *>(R));                                           \
+        FAMST_LAUNCH(ex, tau_kernel<F>, wgrid, 256, 0, X, d, n, k, perm, keys, cstart, gfirst,   \
+                     glast, rho, reinterpret_cast<unsigned *>(tauQ));                            \
+    } while (0)
+    if (fr == 1) PRUNE_GEOM(1);
+    else if (fr == 2) PRUNE_GEOM(2);
+    else PRUNE_GEOM(4);
+#undef PRUNE_GEOM
+    // 5. lists
+    FAMST_LAUNCH(ex, tile_cells_kernel, nblk(nq > nk ? nq : nk, 256), 256, 0, keys, n, nq, nk, qc,
+                 kc);
+    // visit unless LB > tau (1 + margin): the margin covers the canonical
+    // rounding on both sides of the certificate's comparison
+    const float margin = float(1.0 + 4.0 * (d + 4) * std::ldexp(1.0, -24) + std::ldexp(1.0, -20));
+    FAMST_LAUNCH(ex, tile_pairs_kernel<false>, unsigned(nq), 256, 0, qc, kc, nk, K, DPr, R, tauQ,
+                 margin, cnt, nullptr, nullptr, nullptr);
+    {
+        const size_t mark = ar.off;
+        st = exclusive_scan_i32(ex, ar, cnt, off, nq + 1, total);
+        ar.off = mark;
+        if (st != FAMST_OK) return st;
+    }
+    FAMST_LAUNCH(ex, tile_pairs_kernel<true>, unsigned(nq), 256, 0, qc, kc, nk, K, DPr, R, tauQ,
+                 margin, nullptr, off, klist, skipQ);
+    FAMST_LAUNCH(ex, table_kernel, nblk(nq, 256), 256, 0, off, nq, nkb, n, tab);
+    out->perm = perm;
+    out->Hs = Hs;
+    out->nys = nys;
+    out->klist = klist;
+    out->tab = tab;
+    out->skipQ = skipQ;
+    out->visited = total;
+    out->nq = nq;
+    out->nk = nk;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+famst_status prune_scatter(const Exec &ex, const PruneOut &P, int64_t n, int kp,
+                           const int32_t *cand_s, const float *splus_s, int32_t *cand,
+                           float *splus, float *skip) {
+    FAMST_LAUNCH(ex, scatter_kernel, nblk(n * 32, 256), 256, 0, P.perm, n, kp, cand_s, splus_s,
+                 P.skipQ, cand, splus, skip);
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+}  // namespace famst

@@ -39,6 +39,7 @@ class BuildInfo(ctypes.Structure):
         ("ms_knn", ctypes.c_double), ("ms_components", ctypes.c_double),
         ("ms_connect", ctypes.c_double), ("ms_refine", ctypes.c_double),
         ("ms_mst", ctypes.c_double), ("ms_total", ctypes.c_double),
+        ("knn_tile_fraction", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -71,6 +72,7 @@ _SIGS = {
     "famst_create": (_I32, [ctypes.POINTER(_P), ctypes.c_int]),
     "famst_destroy": (_I32, [_P]),
     "famst_set_stream": (_I32, [_P, _P]),
+    "famst_set_knn_pruning": (_I32, [_P, _I32]),
     "famst_error_string": (ctypes.c_char_p, [_I32]),
     "famst_last_error": (ctypes.c_char_p, [_P]),
     "famst_launch_count": (ctypes.c_uint64, [_P]),
@@ -169,6 +171,12 @@ class Context:
     @property
     def workspace_bytes(self) -> int:
         return int(lib().famst_workspace_bytes(self._h))
+
+    def set_knn_pruning(self, enable: bool):
+        """Phase 1 tile pruning on (default) or off; the kNN graph is exact
+        either way."""
+        self._check(lib().famst_set_knn_pruning(self._h, 1 if enable else 0),
+                    "famst_set_knn_pruning")
 
     # ----------------------------------------------------------- phases
     def knn_graph(self, X: torch.Tensor, k: int, prec: str = "fp32"):
