@@ -380,27 +380,41 @@ def main():
                "h2d_bytes_per_step": int(X_np.nbytes),
                "d2h_bytes_per_step": int((w.n - 1) * 12 + 8)}
 
-    # roofline of the distance kernel (Phase 1), timed by the library's
-    # CUDA events on its stream during the timed builds
+    # Roofline of the dominant kernel, timed by the library's CUDA events on
+    # its stream during the timed builds. Phase 1: the tensor tiles actually
+    # computed (2 d flops per query-key pair of a visited tile pair).
+    # Algorithm 4: every candidate distance it evaluated (3 d flops: d
+    # subtractions, d fused multiply-adds) against the FP32 pipe.
     pk = peaks()
     ms_knn = statistics.mean(i["ms_knn"] for i in infos)
+    ms_refine = statistics.mean(i["ms_refine"] for i in infos)
+    frac_tiles = statistics.mean(i["knn_tile_fraction"] for i in infos)
+    evals = statistics.mean(i["refine_distance_evals"] for i in infos)
+    fp32_peak = SMS * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 * 1.5 / 1e12
+    nq, nk = (w.n + 127) // 128, (w.n + 255) // 256
     if args.prec == "fp32":
-        # canonical chain: FSUB + FFMA per (query, key, dim) = 3 flops;
-        # FP32 pipe peak = SMs x 128 lanes x clock x 1.5 flops per instruction
-        flops = 3.0 * w.n * w.n * w.d
-        peak = SMS * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 * 1.5 / 1e12
-        bound = "alu"
+        knn_flops, knn_peak, knn_bound = 3.0 * w.n * w.n * w.d, fp32_peak, "alu"
     else:
-        flops = 2.0 * w.n * w.n * w.d
-        peak = pk["bf16_tflops"]
-        bound = "tensor"
-    achieved = flops / (ms_knn / 1e3) / 1e12
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_from_profile(w.name, args.prec),
+        knn_flops = 2.0 * nq * nk * 128 * 256 * w.d * frac_tiles
+        knn_peak, knn_bound = pk["bf16_tflops"], "tensor"
+    kernels = {
+        "knn": {"bound": knn_bound, "ms": ms_knn, "achieved": knn_flops / (ms_knn / 1e3) / 1e12,
+                "peak": knn_peak, "unit": "TFLOP/s", "tile_fraction": frac_tiles,
                 "kernel": "knn_fp32_kernel" if args.prec == "fp32" else "knn_tc_kernel",
-                "peak_source": pk["_source"] if bound != "alu" else
-                "derived: 152 SMs x 128 FP32 lanes x max SM clock x 1.5 flop/instr",
-                "ms_per_launch": ms_knn}
+                "note": "stage time (prep, partition, tiles, re-rank) over the visited tiles' "
+                        "flops"},
+        "refine": {"bound": "alu", "ms": ms_refine,
+                   "achieved": 3.0 * w.d * evals / (ms_refine / 1e3) / 1e12, "peak": fp32_peak,
+                   "unit": "TFLOP/s", "distance_evals": evals, "kernel": "refine_kernel"},
+    }
+    dom = "refine" if ms_refine >= ms_knn else "knn"
+    kd = kernels[dom]
+    roofline = {"bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
+                "unit": kd["unit"], "frac": kd["achieved"] / kd["peak"],
+                "traffic": traffic_from_profile(w.name, args.prec) if dom == "knn" else None,
+                "kernel": kd["kernel"], "ms_per_launch": kd["ms"],
+                "peak_source": (pk["_source"] if kd["bound"] == "tensor" else
+                                "derived: 152 SMs x 128 FP32 lanes x max SM clock x 1.5 flop/instr")}
 
     # Eq. 1: relative error of the FAMST tree against the exact EMST, both
     # on the GPU, outside the timed region
@@ -430,12 +444,14 @@ def main():
                        "prec": args.prec, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (X = %d MB)" % (X_np.nbytes >> 20)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": launches, "quality": quality,
+            "gpu_launches": launches, "quality": quality, "kernels": kernels,
             "stages_ms": {k2: last[k2] for k2 in ("ms_knn", "ms_components", "ms_connect",
                                                   "ms_refine", "ms_mst", "ms_total")},
             "build": {"t": last["t"], "m": last["m"], "refine_sweeps": last["refine_sweeps"],
                       "boruvka_rounds": last["boruvka_rounds"], "W": last["W"],
-                      "W64": last["W64"], "uncertified_rows": last["uncertified_rows"]},
+                      "W64": last["W64"], "uncertified_rows": last["uncertified_rows"],
+                      "knn_tile_fraction": last["knn_tile_fraction"],
+                      "refine_distance_evals": last["refine_distance_evals"]},
         }
         print(json.dumps(line), flush=True)
     if pg is not None:

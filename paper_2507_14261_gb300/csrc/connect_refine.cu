@@ -191,7 +191,8 @@ __device__ __forceinline__ uint64_t scan_side(const float *__restrict__ X, int d
                                               const int32_t *__restrict__ nbr, int k,
                                               const int32_t *__restrict__ rev_off,
                                               const int32_t *__restrict__ rev_src,
-                                              const int32_t *__restrict__ comp, int lane) {
+                                              const int32_t *__restrict__ comp, int lane,
+                                              unsigned &evals) {
     uint64_t best = uint64_t(__float_as_uint(w0)) << 32;
     const int r0 = rev_off[c], r1 = rev_off[c + 1];
     const int deg = k + (r1 - r0);
@@ -199,6 +200,7 @@ __device__ __forceinline__ uint64_t scan_side(const float *__restrict__ X, int d
     for (int idx = lane; idx < deg; idx += 32) {
         int cand = idx < k ? nbr[int64_t(c) * k + idx] : rev_src[r0 + idx - k];
         if (comp[cand] != want_comp || cand == other) continue;  // G[c] ∩ C, and u' != v
+        ++evals;
         float w = canon_dist<VEC>(X + int64_t(cand) * d, xf, d);
         uint64_t key = (uint64_t(__float_as_uint(w)) << 32) | uint32_t(cand + 1);
         best = key < best ? key : best;
@@ -206,31 +208,31 @@ __device__ __forceinline__ uint64_t scan_side(const float *__restrict__ X, int d
     return warp_min_u64(best);
 }
 
-// Filtered version (rows 16-byte aligned, d % 4 == 0, d <= 128 * FR): the
-// warp first computes a fast squared distance for its 32 candidates -- row
-// j read by the whole warp at once (lane l holds float4 columns l, l+32,
-// ...), 32 independent partial sums per lane, a butterfly transpose-sum so
-// that lane l ends with candidate l's total -- then runs the canonical chain
-// only for candidates the fast value cannot rule out. The fast and the
-// canonical sums add the same rounded terms fl(x_t - y_t)^2 in different
-// orders, so both lie within gamma_n of the exact sum (n = roundings on the
-// longest path): p_canon / p_fast is within [1 - rho, 1 + rho]. A candidate
+// Filtered version (rows 16-byte aligned, d % 4 == 0, d <= 512): the warp
+// first computes fast squared distances of its 32 candidates with the
+// grouped warp-wide sums (every row read contiguously by G lanes), then
+// runs the canonical chain only for candidates the fast value cannot rule
+// out. The fast and the canonical sums add the same rounded terms
+// fl(x_t - y_t)^2 in different orders, so both lie within gamma_n of the
+// exact sum: p_canon / p_fast is within [1 - rho, 1 + rho]. A candidate
 // whose lower bound exceeds (a) the smallest upper bound in the round or
 // (b) the current best weight squared, both widened by 2^-20 for the
 // rounding of sqrtf, cannot be the argmin under (w, id); the others are
 // decided on canonical weights, so the result equals scan_side's.
-template <int FR>
+template <int G>
 __device__ __forceinline__ uint64_t scan_side_filtered(
     const float *__restrict__ X, int d, int c, int fixed, int other, int want_comp, float w0,
     const int32_t *__restrict__ nbr, int k, const int32_t *__restrict__ rev_off,
-    const int32_t *__restrict__ rev_src, const int32_t *__restrict__ comp, int lane, float rho) {
+    const int32_t *__restrict__ rev_src, const int32_t *__restrict__ comp, int lane, float rho,
+    unsigned &evals) {
     const float *xf = X + int64_t(fixed) * d;
-    float4 fx[FR];
-    row_slices<FR>(xf, d >> 2, lane, fx);
+    float4 fx[4];
+    row_slices_g<G, 4>(xf, d >> 2, lane, fx);
     uint64_t best = uint64_t(__float_as_uint(w0)) << 32;
     const int r0 = rev_off[c], r1 = rev_off[c + 1];
     const int deg = k + (r1 - r0);
     const float widen = 1.0f + 0x1p-20f;
+    const float inf = __int_as_float(0x7f800000);
     for (int base = 0; base < deg; base += 32) {
         const int idx = base + lane;
         int cand = -1;
@@ -238,9 +240,10 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
             cand = idx < k ? nbr[int64_t(c) * k + idx] : rev_src[r0 + idx - k];
             if (comp[cand] != want_comp || cand == other) cand = -1;  // G[c] ∩ C, u' != v
         }
-        if (__ballot_sync(0xffffffffu, cand >= 0) == 0u) continue;
-        const float pf = warp_sqdist32<FR>(X, d, fx, fixed, cand, lane);
-        const float inf = __int_as_float(0x7f800000);
+        const unsigned live = __ballot_sync(0xffffffffu, cand >= 0);
+        if (live == 0u) continue;
+        if (lane == 0) evals += unsigned(__popc(live));
+        const float pf = warp_sqdist32g<G, 4>(X, d, fx, fixed, cand, lane);
         const float lo = cand >= 0 ? __fsub_rd(__fmul_rd(pf, 1.0f - rho), 1e-35f) : inf;
         const float hi = cand >= 0 ? __fadd_ru(__fmul_ru(pf, 1.0f + rho), 1e-35f) : inf;
         float mh = hi;
@@ -260,8 +263,10 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
 
 // Process edges in the order `order` (component-pair tiles, so the rows in
 // flight stay in L2), each to its own fixed point.
-template <int VEC, int FR>
-__global__ void refine_kernel(const float *__restrict__ X, int d,
+// Four resident blocks per SM (64 registers): the scans are latency bound,
+// and occupancy buys more than the few spilled registers cost.
+template <int VEC, int G>
+__global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict__ X, int d,
                               const int32_t *__restrict__ nbr, int k,
                               const int32_t *__restrict__ rev_off,
                               const int32_t *__restrict__ rev_src,
@@ -272,9 +277,10 @@ __global__ void refine_kernel(const float *__restrict__ X, int d,
                               const int64_t *__restrict__ m_dev, int max_iters,
                               int32_t *__restrict__ change_hist,
                               unsigned long long *__restrict__ next_item, int *dstatus,
-                              float rho) {
+                              float rho, unsigned long long *__restrict__ evals_out) {
     if (m_dev) m = *m_dev < m ? *m_dev : m;  // device-side edge count, capped by capacity
     const int lane = threadIdx.x & 31;
+    unsigned long long evals_total = 0;   // distance evaluations of this lane
     // Edges are handed out one at a time from a global counter, so the
     // edges in flight stay a narrow window of `order` (and their rows in L2)
     // even though edges need different numbers of sweeps.
@@ -288,24 +294,27 @@ __global__ void refine_kernel(const float *__restrict__ X, int d,
         float wt = ew[e];
         const int ci = eci[e], cj = ecj[e];
         int changes = 0;
+        unsigned evals = 0;
         for (; changes < max_iters; ++changes) {
             uint64_t bu, bv;
             int us, vs;
             float ws;
             // u-loop: u' in G[u] ∩ C_i, u' != v, against v
-            if constexpr (FR > 0)
-                bu = scan_side_filtered<FR>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp,
-                                            lane, rho);
+            if constexpr (G > 0)
+                bu = scan_side_filtered<G>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp,
+                                           lane, rho, evals);
             else
-                bu = scan_side<VEC>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp, lane);
+                bu = scan_side<VEC>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp, lane,
+                                    evals);
             us = key_lo(bu) ? int(key_lo(bu)) - 1 : u;
             ws = key_w(bu);
             // v-loop: v' in G[v] ∩ C_j, v' != u, against the new u*
-            if constexpr (FR > 0)
-                bv = scan_side_filtered<FR>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src,
-                                            comp, lane, rho);
+            if constexpr (G > 0)
+                bv = scan_side_filtered<G>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src,
+                                           comp, lane, rho, evals);
             else
-                bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane);
+                bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane,
+                                    evals);
             vs = key_lo(bv) ? int(key_lo(bv)) - 1 : v;
             ws = key_w(bv);
             if (us == u && vs == v) break;
@@ -320,11 +329,18 @@ __global__ void refine_kernel(const float *__restrict__ X, int d,
             atomicAdd(&change_hist[changes], 1);
             if (changes == max_iters) set_status(dstatus, STATUS_REFINE_CAP);
         }
+        evals_total += evals;
+    }
+    if (evals_out) {
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1)
+            evals_total += __shfl_xor_sync(0xffffffffu, evals_total, o);
+        if (lane == 0) atomicAdd(evals_out, evals_total);
     }
 }
 
 // Launch of the refinement kernel in the variant the shape allows: the
-// filtered scan for 16-byte rows with 64 <= d <= 512, the per-lane
+// filtered scan for 16-byte rows with 32 <= d <= 512, the per-lane
 // canonical chain otherwise. Persistent grid; edges are fetched from
 // *next_item (zeroed by the caller).
 famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, const int32_t *nbr,
@@ -332,16 +348,16 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
                            const int32_t *comp, int32_t *eu, int32_t *ev, float *ew,
                            const int32_t *eci, const int32_t *ecj, const int32_t *order,
                            int64_t m, const int64_t *m_dev, int max_iters, int32_t *change_hist,
-                           unsigned long long *next_item) {
+                           unsigned long long *next_item, unsigned long long *evals) {
     const int th = 256;
-    const int fr = d <= 128 ? 1 : (d <= 256 ? 2 : 4);
-    const bool filtered = vec4 && d >= 64 && d <= 512;
+    const int G = (vec4 && d >= 32) ? sq_group(d) : 0;
     // persistent grid: as many blocks as stay resident
+    const void *fns[6] = {(const void *)refine_kernel<4, 2>, (const void *)refine_kernel<4, 4>,
+                          (const void *)refine_kernel<4, 8>, (const void *)refine_kernel<4, 16>,
+                          (const void *)refine_kernel<4, 32>, (const void *)refine_kernel<4, 0>};
+    const void *fn = G == 2 ? fns[0] : G == 4 ? fns[1] : G == 8 ? fns[2] : G == 16 ? fns[3]
+                   : G == 32 ? fns[4] : (vec4 ? fns[5] : (const void *)refine_kernel<1, 0>);
     int per_sm = 0;
-    const void *fn = !filtered ? (vec4 ? (const void *)refine_kernel<4, 0> : (const void *)refine_kernel<1, 0>)
-                     : fr == 1 ? (const void *)refine_kernel<4, 1>
-                     : fr == 2 ? (const void *)refine_kernel<4, 2>
-                               : (const void *)refine_kernel<4, 4>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, th, 0) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
@@ -349,19 +365,20 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
     int64_t cap = int64_t(ex.num_sms) * per_sm;
     unsigned grid = unsigned(want < cap ? want : cap);
     if (grid == 0) grid = 1;
-    const float rho = fast_rho(d, fr);
-#define REFINE_LAUNCH(V, F)                                                                    \
-    FAMST_LAUNCH(ex, (refine_kernel<V, F>), grid, th, 0, X, d, nbr, k, rev_off, rev_src, comp, eu, \
-                 ev, ew, eci, ecj, order, m, m_dev, max_iters, change_hist, next_item,         \
-                 ex.dstatus, rho)
-    if (filtered) {
-        if (fr == 1) REFINE_LAUNCH(4, 1);
-        else if (fr == 2) REFINE_LAUNCH(4, 2);
-        else REFINE_LAUNCH(4, 4);
-    } else if (vec4) {
-        REFINE_LAUNCH(4, 0);
-    } else {
-        REFINE_LAUNCH(1, 0);
+    const float rho = fast_rho(d, 1);
+#define REFINE_LAUNCH(V, GG)                                                                   \
+    FAMST_LAUNCH(ex, (refine_kernel<V, GG>), grid, th, 0, X, d, nbr, k, rev_off, rev_src, comp,   \
+                 eu, ev, ew, eci, ecj, order, m, m_dev, max_iters, change_hist, next_item,     \
+                 ex.dstatus, rho, evals)
+    switch (G) {
+        case 2: REFINE_LAUNCH(4, 2); break;
+        case 4: REFINE_LAUNCH(4, 4); break;
+        case 8: REFINE_LAUNCH(4, 8); break;
+        case 16: REFINE_LAUNCH(4, 16); break;
+        case 32: REFINE_LAUNCH(4, 32); break;
+        default:
+            if (vec4) REFINE_LAUNCH(4, 0);
+            else REFINE_LAUNCH(1, 0);
     }
 #undef REFINE_LAUNCH
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
@@ -418,7 +435,8 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
                           const int32_t *nbr, int k, const int32_t *rev_off,
                           const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
-                          int64_t m, int max_iters, int32_t *change_hist) {
+                          int64_t m, int max_iters, int32_t *change_hist,
+                          unsigned long long *evals) {
     if (m == 0) return FAMST_OK;
     // order: stable sort of the edges by component-pair tile
     constexpr int TT = 24;
@@ -435,7 +453,7 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
     famst_status st = radix_sort_pairs(ex, ar, keys, order, m, bits);
     if (st != FAMST_OK) return st;
     return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj, order,
-                         m, nullptr, max_iters, change_hist, next_item);
+                         m, nullptr, max_iters, change_hist, next_item, evals);
 }
 
 }  // namespace famst
@@ -455,7 +473,7 @@ famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, 
     if (!next_item) return FAMST_ERR_OOM;
     if (cudaMemsetAsync(next_item, 0, 8, ex.stream) != cudaSuccess) return FAMST_ERR_CUDA;
     return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj,
-                         nullptr, m_cap, m_dev, max_iters, change_hist, next_item);
+                         nullptr, m_cap, m_dev, max_iters, change_hist, next_item, nullptr);
 }
 
 }  // namespace famst

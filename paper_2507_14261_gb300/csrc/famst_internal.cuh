@@ -179,35 +179,6 @@ __device__ __forceinline__ float slice_sq(const float *__restrict__ row, int d4,
     return a;
 }
 
-// Squared distances from the fixed row (slices fx, row id `fixed`) to the
-// 32 lanes' candidates `cand` (row ids; < 0: none). Every candidate row is
-// read by the whole warp at once; a butterfly transpose-sum leaves
-// candidate l's total in lane l. Lanes without a candidate get 0.
-template <int FR>
-__device__ __forceinline__ float warp_sqdist32(const float *__restrict__ X, int d,
-                                               const float4 (&fx)[FR], int fixed, int cand,
-                                               int lane) {
-    const int d4 = d >> 2;
-    float acc[32];
-#pragma unroll
-    for (int sl = 0; sl < 32; ++sl) {
-        // dead slots read the fixed row (in L1) so every load is unconditional
-        const int id = __shfl_sync(0xffffffffu, cand, sl);
-        acc[sl] = slice_sq<FR>(X + int64_t(id >= 0 ? id : fixed) * d, d4, lane, fx);
-    }
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const float send = up ? acc[i] : acc[i + o];
-            const float keep = up ? acc[i + o] : acc[i];
-            acc[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
-        }
-    }
-    return cand >= 0 ? acc[0] : 0.0f;
-}
-
 // One pair per warp: squared distance of rows a and b, in every lane.
 template <int FR>
 __device__ __forceinline__ float warp_sqdist1(const float *__restrict__ a,
@@ -218,6 +189,132 @@ __device__ __forceinline__ float warp_sqdist1(const float *__restrict__ a,
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) s = __fadd_rn(s, __shfl_xor_sync(0xffffffffu, s, o));
     return s;
+}
+
+// Packed FP32 pairs (sm_100 f32x2 instructions): two lanes of IEEE
+// round-to-nearest arithmetic per instruction.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_sqacc(unsigned long long t, unsigned long long a) {
+    unsigned long long r;   // t * t + a, each lane one rounding
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(t), "l"(a));
+    return r;
+}
+__device__ __forceinline__ float f2_hsum(unsigned long long a) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+    return __fadd_rn(lo, hi);
+}
+
+// Fast squared distance of global row y and row f (any address space, read
+// with plain loads), d % 4 == 0, both 16-byte aligned: eight independent
+// chains of fl(y_t - f_t)^2 (four packed accumulators), then a tree of
+// three adds -- at most d / 8 + 4 roundings on any path, inside the bound
+// fast_rho states for the warp-wide sums.
+__device__ __forceinline__ float row_sqdist_fast(const float *__restrict__ y, const float *f,
+                                                 int d) {
+    const float4 *y4 = reinterpret_cast<const float4 *>(y);
+    const float4 *f4 = reinterpret_cast<const float4 *>(f);
+    const int d4 = d >> 2;
+    unsigned long long a0 = 0ull, a1 = 0ull, a2 = 0ull, a3 = 0ull;
+    int q = 0;
+#pragma unroll 2
+    for (; q + 2 <= d4; q += 2) {
+        const float4 ya = __ldg(y4 + q), yb = __ldg(y4 + q + 1);
+        const float4 fa = f4[q], fb = f4[q + 1];
+        a0 = f2_sqacc(f2_sub(f2_pack(ya.x, ya.y), f2_pack(fa.x, fa.y)), a0);
+        a1 = f2_sqacc(f2_sub(f2_pack(ya.z, ya.w), f2_pack(fa.z, fa.w)), a1);
+        a2 = f2_sqacc(f2_sub(f2_pack(yb.x, yb.y), f2_pack(fb.x, fb.y)), a2);
+        a3 = f2_sqacc(f2_sub(f2_pack(yb.z, yb.w), f2_pack(fb.z, fb.w)), a3);
+    }
+    if (q < d4) {
+        const float4 ya = __ldg(y4 + q);
+        const float4 fa = f4[q];
+        a0 = f2_sqacc(f2_sub(f2_pack(ya.x, ya.y), f2_pack(fa.x, fa.y)), a0);
+        a1 = f2_sqacc(f2_sub(f2_pack(ya.z, ya.w), f2_pack(fa.z, fa.w)), a1);
+    }
+    return f2_hsum(f2_add(f2_add(a0, a1), f2_add(a2, a3)));
+}
+
+// Grouped warp-wide fast squared distances. Every candidate row is read by
+// a group of G lanes (float4 columns g, g + G, ..., V of them per lane,
+// G V 4 >= d), so 32 / G rows are read per load instruction, each
+// contiguously. Each lane keeps G partial sums (one per step, in packed FP32
+// pairs), a butterfly transpose-sum inside the group gathers each row's
+// total, and one shuffle hands candidate l's total to lane l. Roundings on
+// any path: V + 2 + log2 G, inside the bound fast_rho(d, 1) states.
+template <int G, int V>
+__device__ __forceinline__ void row_slices_g(const float *__restrict__ row, int d4, int lane,
+                                             float4 (&f)[V]) {
+    const int g = lane % G;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int q = g + G * v;
+        f[v] = q < d4 ? __ldg(reinterpret_cast<const float4 *>(row) + q)
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+template <int G, int V>
+__device__ __forceinline__ float warp_sqdist32g(const float *__restrict__ X, int d,
+                                                const float4 (&fx)[V], int fixed, int cand,
+                                                int lane) {
+    constexpr int R = 32 / G;   // rows per step
+    const int d4 = d >> 2, g = lane % G, h = lane / G;
+    float acc[G];
+#pragma unroll
+    for (int s = 0; s < G; ++s) {
+        // dead slots read the fixed row (in L1) so every load is unconditional
+        const int id = __shfl_sync(0xffffffffu, cand, s * R + h);
+        const float4 *row = reinterpret_cast<const float4 *>(X + int64_t(id >= 0 ? id : fixed) * d);
+        unsigned long long a0 = 0ull, a1 = 0ull;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int q = g + G * v;
+            if (q < d4) {
+                const float4 y = __ldg(row + q);
+                a0 = f2_sqacc(f2_sub(f2_pack(y.x, y.y), f2_pack(fx[v].x, fx[v].y)), a0);
+                a1 = f2_sqacc(f2_sub(f2_pack(y.z, y.w), f2_pack(fx[v].z, fx[v].w)), a1);
+            }
+        }
+        acc[s] = f2_hsum(f2_add(a0, a1));
+    }
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? acc[i] : acc[i + o];
+            const float keep = up ? acc[i + o] : acc[i];
+            acc[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+        }
+    }
+    // lane (h, g) holds slot g R + h; slot l sits in lane (l % R) G + l / R
+    const float tot = __shfl_sync(0xffffffffu, acc[0], (lane % R) * G + lane / R);
+    return cand >= 0 ? tot : 0.0f;
+}
+
+// Lanes per row for the grouped sums with V = 4 float4 per lane (0: d too
+// large or not a multiple of 4).
+inline int sq_group(int d) {
+    if (d % 4 != 0) return 0;
+    const int need = (d / 4 + 3) / 4;
+    int g = 2;
+    while (g < need) g <<= 1;
+    return g <= 32 ? g : 0;
 }
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw; SC'11): ten rounds of
@@ -371,7 +468,8 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
                           const int32_t *nbr, int k, const int32_t *rev_off,
                           const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
-                          int64_t m, int max_iters, int32_t *change_hist /*max_iters+1*/);
+                          int64_t m, int max_iters, int32_t *change_hist,
+                          unsigned long long *evals = nullptr /*max_iters+1*/);
 size_t refine_workspace(int64_t m);
 famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, bool vec4,
                               const int32_t *nbr, int k, const int32_t *rev_off,

@@ -528,9 +528,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         flush();
         if (ok && i < row_end) {
-            int32_t *out = args.cand + size_t(i - shift) * (KC - 1);
+            if constexpr (KC == 1) {   // top-1 mode: the best key and its score
+                args.cand[i - shift] = lj[0] >= 0 ? lj[0] - shift : -1;
+            } else {
+                int32_t *out = args.cand + size_t(i - shift) * (KC - 1);
 #pragma unroll
-            for (int p = 0; p < KC - 1; ++p) out[p] = lj[p] >= 0 ? lj[p] - shift : -1;
+                for (int p = 0; p < KC - 1; ++p) out[p] = lj[p] >= 0 ? lj[p] - shift : -1;
+            }
             args.splus[i - shift] = ls[KC - 1];
         }
     }
@@ -991,11 +995,11 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
             return FAMST_ERR_CUDA;
         TcArgs a1{int(n), Kpad / BN, p.nkb, 0, p1.stages, nyp, cand, splus, ex.dstatus, nullptr,
                   nullptr, nullptr, 1};
-        if (set_smem_attr(knn_tc_kernel<32, false>, int(p1.smem), ex.stream) != cudaSuccess)
+        if (set_smem_attr(knn_tc_kernel<1, false>, int(p1.smem), ex.stream) != cudaSuccess)
             return FAMST_ERR_CUDA;
-        FAMST_LAUNCH(ex, (knn_tc_kernel<32, false>), unsigned(p.nq_tiles), TC_THREADS, p1.smem, mA1,
+        FAMST_LAUNCH(ex, (knn_tc_kernel<1, false>), unsigned(p.nq_tiles), TC_THREADS, p1.smem, mA1,
                      mB1, a1);
-        st = prune_partition(ex, ar, X, d, n, k, H, p.kh, ny, p.nkb, K, piv, cand, 31,
+        st = prune_partition(ex, ar, X, d, n, k, H, p.kh, ny, p.nkb, K, piv, cand, 1,
                              pinned_host + 2, &P);
         if (st != FAMST_OK) return st;
         skip = ar.take<float>(size_t(n));

@@ -128,7 +128,7 @@ __global__ void radius_kernel(const float *__restrict__ X, int d, int64_t n,
 // tau_Q: upper bound on the k-th neighbour distance of every row of query
 // tile Q, from k other points next to each row in the sorted order, taken
 // inside the row's group of cells when the group holds k + 1 points
-template <int FR>
+template <int G>
 __global__ void tau_kernel(const float *__restrict__ X, int d, int64_t n, int k,
                            const int32_t *__restrict__ perm, const uint32_t *__restrict__ skey,
                            const int32_t *__restrict__ cstart, const int32_t *__restrict__ gfirst,
@@ -150,14 +150,14 @@ __global__ void tau_kernel(const float *__restrict__ X, int d, int64_t n, int k,
     int64_t w0 = r - k / 2;
     w0 = w0 < lo ? lo : (w0 > hi ? hi : w0);
     const int self = int(perm[r]);
-    float4 fx[FR];
-    row_slices<FR>(X + int64_t(self) * d, d >> 2, lane, fx);
+    float4 fx[4];
+    row_slices_g<G, 4>(X + int64_t(self) * d, d >> 2, lane, fx);
     float t = 0.0f;
     for (int base = 0; base < k + 1; base += 32) {
         const int idx = base + lane;
         const int64_t pos = w0 + idx;
         const int cand = (idx < k + 1 && pos != r) ? int(perm[pos]) : -1;
-        const float s = warp_sqdist32<FR>(X, d, fx, self, cand, lane);
+        const float s = warp_sqdist32g<G, 4>(X, d, fx, self, cand, lane);
         if (cand >= 0) t = fmaxf(t, __fmul_ru(__fsqrt_ru(sq_hi(s, rho)), 1.0f + 0x1p-22f));
     }
 #pragma unroll
@@ -166,7 +166,7 @@ __global__ void tau_kernel(const float *__restrict__ X, int d, int64_t n, int k,
 }
 
 // DP[a][b] <= |p_a - p_b|: warp per (a, 32 consecutive b)
-template <int FR>
+template <int G>
 __global__ void pivot_dist_kernel(const float *__restrict__ X, int d, int K,
                                   const int32_t *__restrict__ piv, float rho,
                                   float *__restrict__ DP) {
@@ -177,10 +177,10 @@ __global__ void pivot_dist_kernel(const float *__restrict__ X, int d, int K,
     const int a = int(w / nbb);
     const int b = int(w % nbb) * 32 + lane;
     const int pa = piv[a];
-    float4 fx[FR];
-    row_slices<FR>(X + int64_t(pa) * d, d >> 2, lane, fx);
+    float4 fx[4];
+    row_slices_g<G, 4>(X + int64_t(pa) * d, d >> 2, lane, fx);
     const int cand = b < K ? piv[b] : -1;
-    const float s = warp_sqdist32<FR>(X, d, fx, pa, cand, lane);
+    const float s = warp_sqdist32g<G, 4>(X, d, fx, pa, cand, lane);
     if (b < K)
         DP[int64_t(a) * K + b] =
             a == b ? 0.0f : __fmul_rd(__fsqrt_rd(sq_lo(s, rho)), 1.0f - 0x1p-22f);
@@ -498,7 +498,7 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
         !tu || !tv || !tw || !nb || !nw || !qc || !kc || !cnt || !off || !klist || !skipQ || !tab ||
         !total)
         return FAMST_ERR_OOM;
-    const float rho = fast_rho(d, d <= 128 ? 1 : (d <= 256 ? 2 : 4));
+    const float rho = fast_rho(d, 4);
     if (cudaMemsetAsync(ccount, 0, size_t(K + 1) * 4, ex.stream) != cudaSuccess ||
         cudaMemsetAsync(cnt, 0, size_t(nq + 1) * 4, ex.stream) != cudaSuccess ||
         cudaMemsetAsync(R, 0, size_t(K) * 4, ex.stream) != cudaSuccess ||
@@ -506,16 +506,16 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
         return FAMST_ERR_CUDA;
     const int64_t nbb = (K + 31) / 32;
     const int fr = d <= 128 ? 1 : (d <= 256 ? 2 : 4);
+    const int G = sq_group(d);
     // 1. pivot distances (lower bounds, symmetric)
-    if (fr == 1)
-        FAMST_LAUNCH(ex, pivot_dist_kernel<1>, nblk(int64_t(K) * nbb * 32, 256), 256, 0, X, d, K,
-                     piv, rho, DP);
-    else if (fr == 2)
-        FAMST_LAUNCH(ex, pivot_dist_kernel<2>, nblk(int64_t(K) * nbb * 32, 256), 256, 0, X, d, K,
-                     piv, rho, DP);
-    else
-        FAMST_LAUNCH(ex, pivot_dist_kernel<4>, nblk(int64_t(K) * nbb * 32, 256), 256, 0, X, d, K,
-                     piv, rho, DP);
+    const unsigned pgrid = nblk(int64_t(K) * nbb * 32, 256);
+    switch (G) {
+        case 2: FAMST_LAUNCH(ex, pivot_dist_kernel<2>, pgrid, 256, 0, X, d, K, piv, rho, DP); break;
+        case 4: FAMST_LAUNCH(ex, pivot_dist_kernel<4>, pgrid, 256, 0, X, d, K, piv, rho, DP); break;
+        case 8: FAMST_LAUNCH(ex, pivot_dist_kernel<8>, pgrid, 256, 0, X, d, K, piv, rho, DP); break;
+        case 16: FAMST_LAUNCH(ex, pivot_dist_kernel<16>, pgrid, 256, 0, X, d, K, piv, rho, DP); break;
+        default: FAMST_LAUNCH(ex, pivot_dist_kernel<32>, pgrid, 256, 0, X, d, K, piv, rho, DP);
+    }
     FAMST_LAUNCH(ex, sym_kernel, nblk(int64_t(K) * K, 256), 256, 0, DP, K);
     // 2. order of the cells: minimum spanning tree of the pivots (Boruvka)
     famst_status st;
@@ -571,17 +571,26 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     FAMST_LAUNCH(ex, dp_gather_kernel, nblk(int64_t(K) * 32, 256), 256, 0, DP, K, order, DPr);
     // 4. balls and radii of interest
     const unsigned wgrid = nblk(n * 32, 256);
-#define PRUNE_GEOM(F)                                                                            \
-    do {                                                                                         \
-        FAMST_LAUNCH(ex, radius_kernel<F>, wgrid, 256, 0, X, d, n, perm, keys, piv, order, rho,  \
-                     reinterpret_cast<unsigned *>(R));                                           \
-        FAMST_LAUNCH(ex, tau_kernel<F>, wgrid, 256, 0, X, d, n, k, perm, keys, cstart, gfirst,   \
-                     glast, rho, reinterpret_cast<unsigned *>(tauQ));                            \
-    } while (0)
-    if (fr == 1) PRUNE_GEOM(1);
-    else if (fr == 2) PRUNE_GEOM(2);
-    else PRUNE_GEOM(4);
-#undef PRUNE_GEOM
+    if (fr == 1)
+        FAMST_LAUNCH(ex, radius_kernel<1>, wgrid, 256, 0, X, d, n, perm, keys, piv, order, rho,
+                     reinterpret_cast<unsigned *>(R));
+    else if (fr == 2)
+        FAMST_LAUNCH(ex, radius_kernel<2>, wgrid, 256, 0, X, d, n, perm, keys, piv, order, rho,
+                     reinterpret_cast<unsigned *>(R));
+    else
+        FAMST_LAUNCH(ex, radius_kernel<4>, wgrid, 256, 0, X, d, n, perm, keys, piv, order, rho,
+                     reinterpret_cast<unsigned *>(R));
+#define TAU(GG)                                                                                  \
+    FAMST_LAUNCH(ex, tau_kernel<GG>, wgrid, 256, 0, X, d, n, k, perm, keys, cstart, gfirst, glast, \
+                 rho, reinterpret_cast<unsigned *>(tauQ))
+    switch (G) {
+        case 2: TAU(2); break;
+        case 4: TAU(4); break;
+        case 8: TAU(8); break;
+        case 16: TAU(16); break;
+        default: TAU(32);
+    }
+#undef TAU
     // 5. lists
     FAMST_LAUNCH(ex, tile_cells_kernel, nblk(nq > nk ? nq : nk, 256), 256, 0, keys, n, nq, nk, qc,
                  kc);
