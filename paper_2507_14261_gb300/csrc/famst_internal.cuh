@@ -409,11 +409,17 @@ struct PruneOut {
     int32_t *visited = nullptr;     // device: number of visited (query, key) tile pairs
     int64_t nq = 0, nk = 0;
 };
-int prune_pivots(int64_t n);
+int prune_pivots(int64_t n);      // evenly spaced pivots
+int prune_extra(int64_t n);       // pivots added by each of the two coverage passes
+int prune_pivots_max(int64_t n);
 bool prune_supported(int64_t n, int d, int k, bool vec4);
 size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk);
 famst_status prune_pivot_operands(const Exec &ex, const __nv_bfloat16 *H, int kh, const float *ny,
-                                  int64_t n, int K, int32_t *piv, __nv_bfloat16 *Hp, float *nyp);
+                                  int64_t n, int K, int Kpad, int32_t *piv, __nv_bfloat16 *Hp,
+                                  float *nyp);
+famst_status prune_augment(const Exec &ex, Arena &ar, const float *xn2, const float *s1, int64_t n,
+                           const __nv_bfloat16 *H, int kh, const float *ny, int M, int K,
+                           int32_t *piv, __nv_bfloat16 *Hp, float *nyp);
 famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, int64_t n, int k,
                              const __nv_bfloat16 *H, int kh, const float *ny, int nkb, int K,
                              const int32_t *piv, const int32_t *acand, int akp,

@@ -930,7 +930,7 @@ size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prun
     TcPlan p = tc_plan(n, d, k, x3);
     size_t b = 0;
     if (prune) {
-        const int64_t K = prune_pivots(n), Kpad = (K + BN - 1) / BN * BN;
+        const int64_t K = prune_pivots_max(n), Kpad = (K + BN - 1) / BN * BN;
         b += align256(size_t(K) * 4) + align256(size_t(K) * p.kh * 2) + align256(size_t(Kpad) * 4);
         b += prune_workspace(n, d, p.kh, p.kc - 1, p.nq_tiles, p.nk_tiles);
     }
@@ -980,25 +980,37 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     float *skip = nullptr;
     PruneOut P;
     if (use_prune) {
-        // pivot cells: top-1 pivot of every point on the tensor tiles (BF16)
-        const int K = prune_pivots(n);
-        const int Kpad = (K + BN - 1) / BN * BN;
-        int32_t *piv = ar.take<int32_t>(size_t(K));
-        __nv_bfloat16 *Hp = ar.take<__nv_bfloat16>(size_t(K) * p.kh);
-        float *nyp = ar.take<float>(size_t(Kpad));
+        // pivot cells: top-1 pivot of every point on the tensor tiles (BF16),
+        // evenly spaced pivots plus two coverage passes
+        const int K0 = prune_pivots(n), M = prune_extra(n), Kmax = prune_pivots_max(n);
+        const int Kpadmax = (Kmax + BN - 1) / BN * BN;
+        int32_t *piv = ar.take<int32_t>(size_t(Kmax));
+        __nv_bfloat16 *Hp = ar.take<__nv_bfloat16>(size_t(Kmax) * p.kh);
+        float *nyp = ar.take<float>(size_t(Kpadmax));
         if (!piv || !Hp || !nyp) return FAMST_ERR_OOM;
-        famst_status st = prune_pivot_operands(ex, H, p.kh, ny, n, K, piv, Hp, nyp);
+        famst_status st = prune_pivot_operands(ex, H, p.kh, ny, n, K0, Kpadmax, piv, Hp, nyp);
         if (st != FAMST_OK) return st;
         const TcPlan p1 = tc_plan(n, d, 1, false);
-        CUtensorMap mA1, mB1;
-        if (!make_map(&mA1, H, n, p.kh, BM) || !make_map(&mB1, Hp, K, p.kh, BN))
-            return FAMST_ERR_CUDA;
-        TcArgs a1{int(n), Kpad / BN, p.nkb, 0, p1.stages, nyp, cand, splus, ex.dstatus, nullptr,
-                  nullptr, nullptr, 1};
         if (set_smem_attr(knn_tc_kernel<1, false>, int(p1.smem), ex.stream) != cudaSuccess)
             return FAMST_ERR_CUDA;
-        FAMST_LAUNCH(ex, (knn_tc_kernel<1, false>), unsigned(p.nq_tiles), TC_THREADS, p1.smem, mA1,
-                     mB1, a1);
+        auto assign = [&](int Kc) -> famst_status {
+            CUtensorMap mA1, mB1;
+            if (!make_map(&mA1, H, n, p.kh, BM) || !make_map(&mB1, Hp, Kc, p.kh, BN))
+                return FAMST_ERR_CUDA;
+            TcArgs a1{int(n), (Kc + BN - 1) / BN, p.nkb, 0, p1.stages, nyp, cand, splus,
+                      ex.dstatus, nullptr, nullptr, nullptr, 1};
+            FAMST_LAUNCH(ex, (knn_tc_kernel<1, false>), unsigned(p.nq_tiles), TC_THREADS, p1.smem,
+                         mA1, mB1, a1);
+            return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+        };
+        int K = K0;
+        st = assign(K);
+        for (int pass = 0; pass < 2 && st == FAMST_OK; ++pass) {
+            st = prune_augment(ex, ar, xn2, splus, n, H, p.kh, ny, M, K, piv, Hp, nyp);
+            K += M;
+            if (st == FAMST_OK) st = assign(K);
+        }
+        if (st != FAMST_OK) return st;
         st = prune_partition(ex, ar, X, d, n, k, H, p.kh, ny, p.nkb, K, piv, cand, 1,
                              pinned_host + 2, &P);
         if (st != FAMST_OK) return st;

@@ -2,12 +2,16 @@
 // tile, key tile) pair; on data with structure most pairs cannot hold a
 // neighbour, and the triangle inequality proves it cheaply:
 //
-//   1. Locality partition. K pivots (evenly spaced rows); every point joins
-//      the cell of its nearest pivot (the tensor-core distance tiles with
-//      pivots as keys, BF16, top-1 -- any assignment is valid, a good one
-//      only makes cells tight). Points are sorted by cell, so a 128-row
-//      query tile or a 256-row key tile of the sorted order covers a few
-//      consecutive cells.
+//   1. Locality partition. Pivots: evenly spaced rows, then two coverage
+//      passes that add pivots among the points far from every pivot (a
+//      cluster without a pivot would otherwise scatter into foreign cells).
+//      Every point joins the cell of its nearest pivot (the tensor-core
+//      distance tiles with pivots as keys, BF16, top-1 -- any assignment is
+//      valid, a good one only makes cells tight). Cells are ordered along the
+//      pivots' minimum spanning tree, group by group (single linkage), and
+//      points sorted by cell, so a 128-row query tile or a 256-row key tile
+//      of the sorted order covers a few neighbouring cells (a tile with more
+//      than NPMAX cells gets one ball of its own).
 //   2. Balls. R_c >= max over members of |x - p_c| and D_lo(a, b) <=
 //      |p_a - p_b| (warp-wide fast sums with rigorous rounding bounds).
 //      For x in cell a and y in cell b: |x - y| >= D_lo(a, b) - R_a - R_b.
@@ -40,7 +44,7 @@ namespace {
 
 constexpr int QT = 128;    // query tile rows
 constexpr int KT = 256;    // key tile rows
-constexpr int NPMAX = 8;   // cells per tile beyond which a tile is never skipped
+constexpr int NPMAX = 8;   // cells per tile beyond which a tile uses one enclosing ball
 
 inline unsigned nblk(int64_t n, int th) { return unsigned((n + th - 1) / th); }
 
@@ -51,11 +55,12 @@ __device__ __forceinline__ float sq_lo(float p, float rho) {
     return fmaxf(__fsub_rd(__fmul_rd(p, 1.0f - rho), 1e-30f), 0.0f);
 }
 
-// pivot c = row c n / K: its operand row and norm; nyp padded with +inf
+// pivot c = rows[c] (null: row c n / K): its operand row and norm; nyp
+// padded with +inf up to Kpad
 __global__ void pivots_kernel(const __nv_bfloat16 *__restrict__ H, int kh,
                               const float *__restrict__ ny, int64_t n, int K, int Kpad,
-                              int32_t *__restrict__ piv, __nv_bfloat16 *__restrict__ Hp,
-                              float *__restrict__ nyp) {
+                              const int32_t *__restrict__ rows, int32_t *__restrict__ piv,
+                              __nv_bfloat16 *__restrict__ Hp, float *__restrict__ nyp) {
     const int64_t c = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (c >= Kpad) return;
@@ -63,7 +68,7 @@ __global__ void pivots_kernel(const __nv_bfloat16 *__restrict__ H, int kh,
         if (lane == 0) nyp[c] = __int_as_float(0x7f800000);
         return;
     }
-    const int64_t row = c * n / K;
+    const int64_t row = rows ? int64_t(rows[c]) : c * n / K;
     if (lane == 0) {
         piv[c] = int32_t(row);
         nyp[c] = ny[row];
@@ -71,6 +76,44 @@ __global__ void pivots_kernel(const __nv_bfloat16 *__restrict__ H, int kh,
     const uint4 *src = reinterpret_cast<const uint4 *>(H + row * kh);
     uint4 *dst = reinterpret_cast<uint4 *>(Hp + c * kh);
     for (int q = lane; q < kh / 8; q += 32) dst[q] = src[q];
+}
+
+// sort key of the points farthest from their pivot first: the approximate
+// squared distance ||x'||^2 + s of the top-1 score s, descending
+__global__ void far_key_kernel(const float *__restrict__ xn2, const float *__restrict__ s,
+                               int64_t n, uint32_t *__restrict__ keys, int32_t *__restrict__ vals) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float d2 = fmaxf(xn2[i] + s[i], 0.0f);
+    keys[i] = ~__float_as_uint(d2 == d2 ? d2 : 0.0f);
+    vals[i] = int32_t(i);
+}
+
+// Picks among the points sorted by distance to their pivot, farthest first:
+// F = how many lie beyond twice the median distance (4x in squared terms);
+// pick j takes sorted entry floor(j F / Me), so the picks spread evenly over
+// the far points instead of piling into the few most isolated groups.
+__global__ void far_pick_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ vals,
+                                int64_t n, int M, int32_t *__restrict__ rows) {
+    __shared__ long long F_s;
+    if (threadIdx.x == 0) {
+        const float med = __uint_as_float(~keys[n / 2]);
+        const float thr = 4.0f * med;
+        // keys ascend = distances descend: first index with distance <= thr
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) / 2;
+            if (__uint_as_float(~keys[mid]) > thr) lo = mid + 1; else hi = mid;
+        }
+        F_s = lo;
+    }
+    __syncthreads();
+    // about one new pivot per 32 far points; the remaining slots repeat the
+    // point nearest its pivot (a pivot itself), which adds no cell
+    const int64_t F = F_s;
+    const int64_t Me = F / 32 < M ? F / 32 : M;
+    for (int j = threadIdx.x; j < M; j += blockDim.x)
+        rows[j] = j < Me ? vals[int64_t(j) * F / Me] : vals[n - 1];
 }
 
 // cell of every point = the rank of its best pivot candidate; sort keys and
@@ -229,19 +272,59 @@ __global__ void dp_gather_kernel(const float *__restrict__ DP, int K,
     for (int b = lane; b < K; b += 32) DPr[a * K + b] = src[order[b]];
 }
 
-// first and last cell of every query tile and key tile
+// Parts of every query tile and key tile: the range of its cells, or, when
+// it spans more than NPMAX cells, one ball around the pivot of its middle
+// row's cell (cell range = that cell alone; its radius comes from
+// tile_radius_kernel, -1 meanwhile; Rt = -2 marks a tile of few cells)
 __global__ void tile_cells_kernel(const uint32_t *__restrict__ skey, int64_t n, int64_t nq,
-                                  int64_t nk, int32_t *__restrict__ qc, int32_t *__restrict__ kc) {
+                                  int64_t nk, int32_t *__restrict__ qc, int32_t *__restrict__ kc,
+                                  float *__restrict__ qR, float *__restrict__ kR) {
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t < nq) {
         const int64_t r0 = t * QT, r1 = (r0 + QT < n ? r0 + QT : n) - 1;
-        qc[2 * t] = int32_t(skey[r0]);
-        qc[2 * t + 1] = int32_t(skey[r1]);
+        int32_t c0 = int32_t(skey[r0]), c1 = int32_t(skey[r1]);
+        const bool open = c1 - c0 + 1 > NPMAX;
+        if (open) c0 = c1 = int32_t(skey[(r0 + r1) / 2]);
+        qc[2 * t] = c0;
+        qc[2 * t + 1] = c1;
+        qR[t] = open ? 0.0f : -2.0f;
     }
     if (t < nk) {
         const int64_t r0 = t * KT, r1 = (r0 + KT < n ? r0 + KT : n) - 1;
-        kc[2 * t] = int32_t(skey[r0]);
-        kc[2 * t + 1] = int32_t(skey[r1]);
+        int32_t c0 = int32_t(skey[r0]), c1 = int32_t(skey[r1]);
+        const bool open = c1 - c0 + 1 > NPMAX;
+        if (open) c0 = c1 = int32_t(skey[(r0 + r1) / 2]);
+        kc[2 * t] = c0;
+        kc[2 * t + 1] = c1;
+        kR[t] = open ? 0.0f : -2.0f;
+    }
+}
+
+// Ball radius of every open tile: the largest distance (rounded up) of its
+// rows to its centre pivot, one warp per sorted row
+template <int FR>
+__global__ void tile_radius_kernel(const float *__restrict__ X, int d, int64_t n,
+                                   const int32_t *__restrict__ perm,
+                                   const int32_t *__restrict__ piv,
+                                   const int32_t *__restrict__ order,
+                                   const int32_t *__restrict__ qc, const int32_t *__restrict__ kc,
+                                   float rho, float *__restrict__ qR, float *__restrict__ kR) {
+    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int64_t q = r / QT, t = r / KT;
+    const float *x = X + int64_t(perm[r]) * d;
+    if (qR[q] > -1.0f) {
+        const float s = warp_sqdist1<FR>(x, X + int64_t(piv[order[qc[2 * q]]]) * d, d, lane);
+        if (lane == 0)
+            atomicMax(reinterpret_cast<unsigned *>(qR) + q,
+                      __float_as_uint(__fmul_ru(__fsqrt_ru(sq_hi(s, rho)), 1.0f + 0x1p-22f)));
+    }
+    if (kR[t] > -1.0f) {
+        const float s = warp_sqdist1<FR>(x, X + int64_t(piv[order[kc[2 * t]]]) * d, d, lane);
+        if (lane == 0)
+            atomicMax(reinterpret_cast<unsigned *>(kR) + t,
+                      __float_as_uint(__fmul_ru(__fsqrt_ru(sq_hi(s, rho)), 1.0f + 0x1p-22f)));
     }
 }
 
@@ -250,7 +333,8 @@ __global__ void tile_cells_kernel(const uint32_t *__restrict__ skey, int64_t n, 
 // and the smallest lower bound of the skipped tiles into skipQ[Q].
 template <bool FILL>
 __global__ void __launch_bounds__(256)
-tile_pairs_kernel(const int32_t *__restrict__ qc, const int32_t *__restrict__ kc, int64_t nk,
+tile_pairs_kernel(const int32_t *__restrict__ qc, const int32_t *__restrict__ kc,
+                  const float *__restrict__ qR, const float *__restrict__ kR, int64_t nk,
                   int K, const float *__restrict__ DP, const float *__restrict__ R,
                   const float *__restrict__ tauQ, float margin, int32_t *__restrict__ cnt,
                   const int32_t *__restrict__ off, int32_t *__restrict__ klist,
@@ -261,12 +345,12 @@ tile_pairs_kernel(const int32_t *__restrict__ qc, const int32_t *__restrict__ kc
     const int Q = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int a0 = qc[2 * Q], a1 = qc[2 * Q + 1];
-    const bool q_open = a1 - a0 + 1 > NPMAX;   // too many cells: visit every tile
+    const float qball = qR[Q];   // >= 0: one ball for the whole tile
     const float tau = __fmul_ru(tauQ[Q], margin);
     const float inf = __int_as_float(0x7f800000);
     float ra[NPMAX];
 #pragma unroll
-    for (int q = 0; q < NPMAX; ++q) ra[q] = (!q_open && a0 + q <= a1) ? R[a0 + q] : 0.0f;
+    for (int q = 0; q < NPMAX; ++q) ra[q] = a0 + q <= a1 ? (qball >= 0.0f ? qball : R[a0 + q]) : 0.0f;
     int count = 0;
     float smin = inf;
     if (threadIdx.x == 0) base_s = 0;
@@ -277,16 +361,13 @@ tile_pairs_kernel(const int32_t *__restrict__ qc, const int32_t *__restrict__ kc
         float lb = inf;
         if (T < nk) {
             const int b0 = kc[2 * T], b1 = kc[2 * T + 1];
-            if (q_open || b1 - b0 + 1 > NPMAX) {
-                lb = -inf;
-            } else {
+            const float kball = kR[T];
 #pragma unroll
-                for (int q = 0; q < NPMAX; ++q) {
-                    if (a0 + q > a1) break;
-                    const float *dp = DP + int64_t(a0 + q) * K;
-                    for (int b = b0; b <= b1; ++b)
-                        lb = fminf(lb, __fsub_rd(__fsub_rd(dp[b], ra[q]), R[b]));
-                }
+            for (int q = 0; q < NPMAX; ++q) {
+                if (a0 + q > a1) break;
+                const float *dp = DP + int64_t(a0 + q) * K;
+                for (int b = b0; b <= b1; ++b)
+                    lb = fminf(lb, __fsub_rd(__fsub_rd(dp[b], ra[q]), kball >= 0.0f ? kball : R[b]));
             }
             visit = !(lb > tau);
             if (!visit) smin = fminf(smin, lb);
@@ -427,22 +508,27 @@ void order_cells(int K, const std::vector<int32_t> &tu, const std::vector<int32_
 }  // namespace
 
 int prune_pivots(int64_t n) {
-    int64_t K = n / 128;
-    if (K < 32) K = 32;
-    if (K > 8192) K = 8192;
+    int64_t K = n / 256;
+    if (K < 16) K = 16;
+    if (K > 4096) K = 4096;
     return int(K);
 }
+
+int prune_extra(int64_t n) { return prune_pivots(n) / 2; }
+
+int prune_pivots_max(int64_t n) { return prune_pivots(n) + 2 * prune_extra(n); }
 
 bool prune_supported(int64_t n, int d, int k, bool vec4) {
     return vec4 && d >= 4 && d <= 512 && n >= 4 * int64_t(k + 1) && n >= 4096;
 }
 
 size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk) {
-    const int64_t K = prune_pivots(n);
+    const int64_t K = prune_pivots_max(n);
     const int64_t Kpad = (K + KT - 1) / KT * KT;
     size_t b = 0;
     b += align256(size_t(K) * 4) + align256(size_t(K) * kh * 2) + align256(size_t(Kpad) * 4);
     b += align256(size_t(n) * 4) * 2 + align256(size_t(K + 1) * 4) * 2;        // keys, perm, cells
+    b += align256(size_t(n) * 4) * 2 + align256(size_t(K) * 4) + radix_sort_workspace(n);  // coverage
     b += radix_sort_workspace(n) + scan_workspace(K + 1) + 256;
     b += align256(size_t(n) * kh * 2) + align256(size_t(nk) * KT * 4);         // sorted operand
     b += align256(size_t(K) * 4) + align256(size_t(nq) * 4);                   // R, tau
@@ -450,6 +536,7 @@ size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk)
     b += align256(size_t(4 * K) * 4) + align256(size_t(K) * 4) * 5;             // order, tree
     b += boruvka_workspace(K);                                                 // pivot tree
     b += align256(size_t(nq) * 8) + align256(size_t(nk) * 8);                  // tile cells
+    b += align256(size_t(nq) * 4) + align256(size_t(nk) * 4);                  // tile balls
     b += align256(size_t(nq + 1) * 4) * 2 + scan_workspace(nq + 1) + 256;      // counts, offsets
     b += align256(size_t(nq) * nk * 4);                                        // lists (worst case)
     b += align256(size_t(nq) * 4) + align256(size_t(nq) * sizeof(TcTile));     // skip, table
@@ -458,10 +545,34 @@ size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk)
 }
 
 famst_status prune_pivot_operands(const Exec &ex, const __nv_bfloat16 *H, int kh, const float *ny,
-                                  int64_t n, int K, int32_t *piv, __nv_bfloat16 *Hp, float *nyp) {
-    const int Kpad = (K + KT - 1) / KT * KT;
+                                  int64_t n, int K, int Kpad, int32_t *piv, __nv_bfloat16 *Hp,
+                                  float *nyp) {
     FAMST_LAUNCH(ex, pivots_kernel, nblk(int64_t(Kpad) * 32, 256), 256, 0, H, kh, ny, n, K, Kpad,
-                 piv, Hp, nyp);
+                 nullptr, piv, Hp, nyp);
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+// Coverage: M points spread over those far from their current pivot
+// (approximate distances of the top-1 pass) become pivots K .. K + M - 1. A
+// group of points with no pivot of its own sits far from every pivot, so it
+// gains some; without them its points would widen foreign cells' balls.
+famst_status prune_augment(const Exec &ex, Arena &ar, const float *xn2, const float *s1, int64_t n,
+                           const __nv_bfloat16 *H, int kh, const float *ny, int M, int K,
+                           int32_t *piv, __nv_bfloat16 *Hp, float *nyp) {
+    const size_t mark = ar.off;
+    uint32_t *keys = ar.take<uint32_t>(size_t(n));
+    int32_t *vals = ar.take<int32_t>(size_t(n));
+    int32_t *rows = ar.take<int32_t>(size_t(M));
+    if (!keys || !vals || !rows) return FAMST_ERR_OOM;
+    FAMST_LAUNCH(ex, far_key_kernel, nblk(n, 256), 256, 0, xn2, s1, n, keys, vals);
+    famst_status st = radix_sort_pairs(ex, ar, keys, vals, n, 32);
+    if (st == FAMST_OK) {
+        FAMST_LAUNCH(ex, far_pick_kernel, 1, 256, 0, keys, vals, n, M, rows);
+        FAMST_LAUNCH(ex, pivots_kernel, nblk(int64_t(M) * 32, 256), 256, 0, H, kh, ny, n, M, M,
+                     rows, piv + K, Hp + size_t(K) * kh, nyp + K);
+    }
+    ar.off = mark;
+    if (st != FAMST_OK) return st;
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
@@ -488,6 +599,8 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     float *nw = ar.take<float>(size_t(K));
     int32_t *qc = ar.take<int32_t>(size_t(nq) * 2);
     int32_t *kc = ar.take<int32_t>(size_t(nk) * 2);
+    float *qR = ar.take<float>(size_t(nq));
+    float *kR = ar.take<float>(size_t(nk));
     int32_t *cnt = ar.take<int32_t>(size_t(nq + 1));
     int32_t *off = ar.take<int32_t>(size_t(nq + 1));
     int32_t *klist = ar.take<int32_t>(size_t(nq) * nk);
@@ -495,7 +608,8 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     TcTile *tab = ar.take<TcTile>(size_t(nq));
     int32_t *total = ar.take<int32_t>(1);
     if (!keys || !perm || !ccount || !cstart || !Hs || !nys || !R || !tauQ || !DP || !DPr || !ord ||
-        !tu || !tv || !tw || !nb || !nw || !qc || !kc || !cnt || !off || !klist || !skipQ || !tab ||
+        !tu || !tv || !tw || !nb || !nw || !qc || !kc || !qR || !kR || !cnt || !off || !klist ||
+        !skipQ || !tab ||
         !total)
         return FAMST_ERR_OOM;
     const float rho = fast_rho(d, 4);
@@ -593,20 +707,29 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
 #undef TAU
     // 5. lists
     FAMST_LAUNCH(ex, tile_cells_kernel, nblk(nq > nk ? nq : nk, 256), 256, 0, keys, n, nq, nk, qc,
-                 kc);
+                 kc, qR, kR);
+    if (fr == 1)
+        FAMST_LAUNCH(ex, tile_radius_kernel<1>, wgrid, 256, 0, X, d, n, perm, piv, order, qc, kc,
+                     rho, qR, kR);
+    else if (fr == 2)
+        FAMST_LAUNCH(ex, tile_radius_kernel<2>, wgrid, 256, 0, X, d, n, perm, piv, order, qc, kc,
+                     rho, qR, kR);
+    else
+        FAMST_LAUNCH(ex, tile_radius_kernel<4>, wgrid, 256, 0, X, d, n, perm, piv, order, qc, kc,
+                     rho, qR, kR);
     // visit unless LB > tau (1 + margin): the margin covers the canonical
     // rounding on both sides of the certificate's comparison
     const float margin = float(1.0 + 4.0 * (d + 4) * std::ldexp(1.0, -24) + std::ldexp(1.0, -20));
-    FAMST_LAUNCH(ex, tile_pairs_kernel<false>, unsigned(nq), 256, 0, qc, kc, nk, K, DPr, R, tauQ,
-                 margin, cnt, nullptr, nullptr, nullptr);
+    FAMST_LAUNCH(ex, tile_pairs_kernel<false>, unsigned(nq), 256, 0, qc, kc, qR, kR, nk, K, DPr, R,
+                 tauQ, margin, cnt, nullptr, nullptr, nullptr);
     {
         const size_t mark = ar.off;
         st = exclusive_scan_i32(ex, ar, cnt, off, nq + 1, total);
         ar.off = mark;
         if (st != FAMST_OK) return st;
     }
-    FAMST_LAUNCH(ex, tile_pairs_kernel<true>, unsigned(nq), 256, 0, qc, kc, nk, K, DPr, R, tauQ,
-                 margin, nullptr, off, klist, skipQ);
+    FAMST_LAUNCH(ex, tile_pairs_kernel<true>, unsigned(nq), 256, 0, qc, kc, qR, kR, nk, K, DPr, R,
+                 tauQ, margin, nullptr, off, klist, skipQ);
     FAMST_LAUNCH(ex, table_kernel, nblk(nq, 256), 256, 0, off, nq, nkb, n, tab);
     out->perm = perm;
     out->Hs = Hs;
