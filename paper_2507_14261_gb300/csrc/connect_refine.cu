@@ -101,6 +101,99 @@ __global__ void connect_kernel(const float *__restrict__ X, int d,
     }
 }
 
+// Filtered Algorithm 3 (rows 16-byte aligned, d % 4 == 0): the same draws,
+// but the warp first computes fast squared distances of all lambda^2 pairs
+// (grouped warp-wide sums, rows read contiguously) and runs the canonical
+// chain only for pairs whose lower bound is within the lambda-th smallest
+// upper bound (widened by 2^-20 for the rounding of sqrtf). At least lambda
+// pairs have p_canon <= that bound, so every pair of the exact top lambda
+// (w, s) survives, and the selection below sees the same winners.
+template <int PER, int G>
+__global__ void connect_filtered_kernel(const float *__restrict__ X, int d,
+                                        const int32_t *__restrict__ members,
+                                        const int32_t *__restrict__ comp_off, int64_t t,
+                                        int lambda, uint64_t seed, float rho,
+                                        int32_t *__restrict__ eu, int32_t *__restrict__ ev,
+                                        float *__restrict__ ew, int32_t *__restrict__ eci,
+                                        int32_t *__restrict__ ecj) {
+    const int lane = threadIdx.x & 31;
+    const int64_t npairs = t * (t - 1) / 2;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int L2 = lambda * lambda;
+    const uint2 key = make_uint2(uint32_t(seed), uint32_t(seed >> 32));
+    const float widen = 1.0f + 0x1p-20f;
+    for (int64_t pl = warp0; pl < npairs; pl += nwarps) {
+        int64_t i, j;
+        pair_of(pl, t, i, j);
+        const uint64_t p = uint64_t(i) * uint64_t(t) + uint64_t(j);
+        const int32_t oi = comp_off[i], oj = comp_off[j];
+        const uint64_t si = uint64_t(comp_off[i + 1] - oi), sj = uint64_t(comp_off[j + 1] - oj);
+        int32_t uu[PER], vv[PER];
+        float lo[PER];
+        uint64_t hk[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int s = lane + 32 * q;
+            uu[q] = -1;
+            vv[q] = -1;
+            if (s < L2) {
+                uint4 r = philox4x32_10(make_uint4(uint32_t(s), uint32_t(p), uint32_t(p >> 32), 0u),
+                                        key);
+                uu[q] = members[oi + int64_t((uint64_t(r.x) * si) >> 32)];
+                vv[q] = members[oj + int64_t((uint64_t(r.y) * sj) >> 32)];
+            }
+            const float pf = warp_pairsq32g<G, 4>(X, d, uu[q], vv[q], lane);
+            lo[q] = __fsub_rd(__fmul_rd(pf, 1.0f - rho), 1e-35f);
+            const float hi = __fadd_ru(__fmul_ru(pf, 1.0f + rho), 1e-35f);
+            hk[q] = s < L2 ? nb_key(hi, uint32_t(s)) : KEY_NONE;
+        }
+        // the lambda-th smallest upper bound
+        float H = 0.0f;
+        for (int r = 0; r < lambda; ++r) {
+            uint64_t mine = KEY_NONE;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) mine = hk[q] < mine ? hk[q] : mine;
+            const uint64_t best = warp_min_u64(mine);
+            H = key_w(best);
+#pragma unroll
+            for (int q = 0; q < PER; ++q)
+                if (hk[q] == best) hk[q] = KEY_NONE;
+        }
+        const float bound = __fmul_ru(H, widen);
+        uint64_t kk[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int s = lane + 32 * q;
+            kk[q] = KEY_NONE;
+            if (s < L2 && lo[q] <= bound)
+                kk[q] = nb_key(canon_dist<4>(X + int64_t(uu[q]) * d, X + int64_t(vv[q]) * d, d),
+                               uint32_t(s));
+        }
+        const int64_t ebase = pl * lambda;
+        for (int r = 0; r < lambda; ++r) {
+            uint64_t mine = KEY_NONE;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) mine = kk[q] < mine ? kk[q] : mine;
+            uint64_t best = warp_min_u64(mine);
+            int s = int(key_lo(best));
+            if ((s & 31) == lane) {
+                int qq = s >> 5;
+#pragma unroll
+                for (int q = 0; q < PER; ++q)
+                    if (q == qq) {
+                        kk[q] = KEY_NONE;
+                        eu[ebase + r] = uu[q];
+                        ev[ebase + r] = vv[q];
+                        ew[ebase + r] = key_w(best);
+                        eci[ebase + r] = int32_t(i);
+                        ecj[ebase + r] = int32_t(j);
+                    }
+            }
+        }
+    }
+}
+
 // Batched connect: pairs of every cloud in one index space. pp[b] (B+1,
 // device) = number of pairs of clouds before b, cbase[b] (B+1) = the first
 // global component index of cloud b; cloud b draws with key seed + b and the
@@ -295,6 +388,12 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
         const int ci = eci[e], cj = ecj[e];
         int changes = 0;
         unsigned evals = 0;
+        // The v-scan is a function of (v, u*) alone (C_i and C_j are disjoint,
+        // so the exclusion of u never bites, and its incumbent is w(u*, v)).
+        // When a sweep leaves v in place and the next one leaves u in place,
+        // the second v-scan repeats the first: its result is reused.
+        int mv_v = -1, mv_u = -1;
+        uint64_t mv_b = 0;
         for (; changes < max_iters; ++changes) {
             uint64_t bu, bv;
             int us, vs;
@@ -309,12 +408,17 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
             us = key_lo(bu) ? int(key_lo(bu)) - 1 : u;
             ws = key_w(bu);
             // v-loop: v' in G[v] ∩ C_j, v' != u, against the new u*
-            if constexpr (G > 0)
+            if (v == mv_v && us == mv_u)
+                bv = mv_b;
+            else if constexpr (G > 0)
                 bv = scan_side_filtered<G>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src,
                                            comp, lane, rho, evals);
             else
                 bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane,
                                     evals);
+            mv_v = v;
+            mv_u = us;
+            mv_b = bv;
             vs = key_lo(bv) ? int(key_lo(bv)) - 1 : v;
             ws = key_w(bv);
             if (us == u && vs == v) break;
@@ -403,10 +507,27 @@ famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
     if (t < 2) return FAMST_OK;
     int64_t npairs = t * (t - 1) / 2;
     int per = (lambda * lambda + 31) / 32;
+    // filtered variant for the common shapes (lambda <= 11, 32 <= d <= 256)
+    const int Gs = (vec4 && d >= 32) ? sq_group(d) : 0;
+    const int G = (per <= 4 && (Gs == 4 || Gs == 8 || Gs == 16)) ? Gs : 0;
     const int th = 256;
     int64_t want = (npairs * 32 + th - 1) / th;
     int64_t cap = int64_t(ex.num_sms) * 16;
     unsigned grid = unsigned(want < cap ? want : cap);
+    const float rho = fast_rho(d, 1);
+#define CONNECT_F(P, GG)                                                                      \
+    FAMST_LAUNCH(ex, (connect_filtered_kernel<P, GG>), grid, th, 0, X, d, members, comp_off, t, \
+                 lambda, seed, rho, eu, ev, ew, eci, ecj)
+    if (G > 0) {
+        if (per <= 1) {
+            if (G == 4) CONNECT_F(1, 4); else if (G == 8) CONNECT_F(1, 8); else CONNECT_F(1, 16);
+        } else if (per <= 2) {
+            if (G == 4) CONNECT_F(2, 4); else if (G == 8) CONNECT_F(2, 8); else CONNECT_F(2, 16);
+        } else {
+            if (G == 4) CONNECT_F(4, 4); else if (G == 8) CONNECT_F(4, 8); else CONNECT_F(4, 16);
+        }
+        return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    }
 #define CONNECT_CASE(P)                                                                       \
     if (per <= P) {                                                                           \
         if (vec4)                                                                             \
@@ -424,6 +545,7 @@ famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
     CONNECT_CASE(16)
     CONNECT_CASE(32)
 #undef CONNECT_CASE
+#undef CONNECT_F
     return FAMST_ERR_UNSUPPORTED;
 }
 

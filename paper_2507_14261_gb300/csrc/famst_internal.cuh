@@ -307,6 +307,46 @@ __device__ __forceinline__ float warp_sqdist32g(const float *__restrict__ X, int
     return cand >= 0 ? tot : 0.0f;
 }
 
+// Same layout for 32 independent pairs: lane l holds the pair (a[l], b[l])
+// (a < 0: none, result 0) and receives fl-sum of (X[a] - X[b])^2.
+template <int G, int V>
+__device__ __forceinline__ float warp_pairsq32g(const float *__restrict__ X, int d, int a, int b,
+                                                int lane) {
+    constexpr int R = 32 / G;
+    const int d4 = d >> 2, g = lane % G, h = lane / G;
+    float acc[G];
+#pragma unroll
+    for (int s = 0; s < G; ++s) {
+        const int ia = __shfl_sync(0xffffffffu, a, s * R + h);
+        const int ib = __shfl_sync(0xffffffffu, b, s * R + h);
+        const float4 *ra = reinterpret_cast<const float4 *>(X + int64_t(ia >= 0 ? ia : 0) * d);
+        const float4 *rb = reinterpret_cast<const float4 *>(X + int64_t(ia >= 0 ? ib : 0) * d);
+        unsigned long long a0 = 0ull, a1 = 0ull;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int q = g + G * v;
+            if (q < d4) {
+                const float4 x = __ldg(ra + q), y = __ldg(rb + q);
+                a0 = f2_sqacc(f2_sub(f2_pack(x.x, x.y), f2_pack(y.x, y.y)), a0);
+                a1 = f2_sqacc(f2_sub(f2_pack(x.z, x.w), f2_pack(y.z, y.w)), a1);
+            }
+        }
+        acc[s] = f2_hsum(f2_add(a0, a1));
+    }
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? acc[i] : acc[i + o];
+            const float keep = up ? acc[i + o] : acc[i];
+            acc[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+        }
+    }
+    const float tot = __shfl_sync(0xffffffffu, acc[0], (lane % R) * G + lane / R);
+    return a >= 0 ? tot : 0.0f;
+}
+
 // Lanes per row for the grouped sums with V = 4 float4 per lane (0: d too
 // large or not a multiple of 4).
 inline int sq_group(int d) {
