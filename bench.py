@@ -451,7 +451,8 @@ def main():
                       "boruvka_rounds": last["boruvka_rounds"], "W": last["W"],
                       "W64": last["W64"], "uncertified_rows": last["uncertified_rows"],
                       "knn_tile_fraction": last["knn_tile_fraction"],
-                      "refine_distance_evals": last["refine_distance_evals"]},
+                      "refine_distance_evals": last["refine_distance_evals"],
+                      "refine_canonical_evals": last["refine_canonical_evals"]},
         }
         print(json.dumps(line), flush=True)
     if pg is not None:

@@ -86,6 +86,7 @@ typedef struct famst_build_info {
     double  ms_knn, ms_components, ms_connect, ms_refine, ms_mst, ms_total;
     double  knn_tile_fraction; /* (query, key) tile pairs Phase 1 computed / all pairs */
     int64_t refine_distance_evals; /* candidate distances Algorithm 4 evaluated */
+    int64_t refine_canonical_evals; /* of which the exact FP32 chain decided */
 } famst_build_info;
 
 /* ------------------------------------------------------------ context */

@@ -317,7 +317,7 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
     const float *__restrict__ X, int d, int c, int fixed, int other, int want_comp, float w0,
     const int32_t *__restrict__ nbr, int k, const int32_t *__restrict__ rev_off,
     const int32_t *__restrict__ rev_src, const int32_t *__restrict__ comp, int lane, float rho,
-    unsigned &evals) {
+    unsigned &evals, unsigned &canon) {
     const float *xf = X + int64_t(fixed) * d;
     float4 fx[4];
     row_slices_g<G, 4>(xf, d >> 2, lane, fx);
@@ -345,6 +345,7 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
         const float wb = key_w(best);
         const float bound = fminf(__fmul_ru(mh, widen), __fmul_ru(__fmul_ru(wb, wb), widen));
         if (cand >= 0 && lo <= bound) {
+            ++canon;
             const float w = canon_dist<4>(X + int64_t(cand) * d, xf, d);
             const uint64_t key = (uint64_t(__float_as_uint(w)) << 32) | uint32_t(cand + 1);
             best = key < best ? key : best;
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
                               float rho, unsigned long long *__restrict__ evals_out) {
     if (m_dev) m = *m_dev < m ? *m_dev : m;  // device-side edge count, capped by capacity
     const int lane = threadIdx.x & 31;
-    unsigned long long evals_total = 0;   // distance evaluations of this lane
+    unsigned long long evals_total = 0, canon_total = 0;   // evaluations of this lane
     // Edges are handed out one at a time from a global counter, so the
     // edges in flight stay a narrow window of `order` (and their rows in L2)
     // even though edges need different numbers of sweeps.
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
         float wt = ew[e];
         const int ci = eci[e], cj = ecj[e];
         int changes = 0;
-        unsigned evals = 0;
+        unsigned evals = 0, canon = 0;
         // The v-scan is a function of (v, u*) alone (C_i and C_j are disjoint,
         // so the exclusion of u never bites, and its incumbent is w(u*, v)).
         // When a sweep leaves v in place and the next one leaves u in place,
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
             // u-loop: u' in G[u] ∩ C_i, u' != v, against v
             if constexpr (G > 0)
                 bu = scan_side_filtered<G>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp,
-                                           lane, rho, evals);
+                                           lane, rho, evals, canon);
             else
                 bu = scan_side<VEC>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp, lane,
                                     evals);
@@ -412,7 +413,7 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
                 bv = mv_b;
             else if constexpr (G > 0)
                 bv = scan_side_filtered<G>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src,
-                                           comp, lane, rho, evals);
+                                           comp, lane, rho, evals, canon);
             else
                 bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane,
                                     evals);
@@ -434,12 +435,18 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
             if (changes == max_iters) set_status(dstatus, STATUS_REFINE_CAP);
         }
         evals_total += evals;
+        canon_total += G > 0 ? canon : evals;
     }
-    if (evals_out) {
+    if (evals_out) {   // [0] candidate distances, [1] canonical chains among them
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1)
+        for (int o = 16; o >= 1; o >>= 1) {
             evals_total += __shfl_xor_sync(0xffffffffu, evals_total, o);
-        if (lane == 0) atomicAdd(evals_out, evals_total);
+            canon_total += __shfl_xor_sync(0xffffffffu, canon_total, o);
+        }
+        if (lane == 0) {
+            atomicAdd(evals_out, evals_total);
+            atomicAdd(evals_out + 1, canon_total);
+        }
     }
 }
 

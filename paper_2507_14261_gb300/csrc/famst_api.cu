@@ -325,10 +325,10 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     int32_t *eci = ar.take<int32_t>(size_t(m > 0 ? m : 1));
     int32_t *ecj = ar.take<int32_t>(size_t(m > 0 ? m : 1));
     int32_t *hist = ar.take<int32_t>(size_t(max_iters + 1));
-    unsigned long long *evals = ar.take<unsigned long long>(1);
+    unsigned long long *evals = ar.take<unsigned long long>(2);
     // the components kernels above used this slot; comp lives in slot 0
     int sweeps = 0;
-    unsigned long long evals_host = 0;
+    unsigned long long evals_host[2] = {0, 0};
     int64_t first_delta = 0;
     if (t > 1) {
         ST(member_lists(ex, ar, comp, n, t, members, comp_off));
@@ -340,7 +340,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         ST(reverse_csr(ex, ar, nbr, n, k, rev_off, rev_src));
         CK(cudaMemsetAsync(hist, 0, size_t(max_iters + 1) * 4, ctx->stream));
         if (!evals) return fail(ctx, FAMST_ERR_OOM, "workspace");
-        CK(cudaMemsetAsync(evals, 0, 8, ctx->stream));
+        CK(cudaMemsetAsync(evals, 0, 16, ctx->stream));
         ST(refine_edges(ex, ar, X, d, v4, nbr, k, rev_off, rev_src, comp, t, eu, evv, ew, eci, ecj, m,
                         max_iters, hist, evals));
         ev.mark(ctx->stream, 4);
@@ -350,7 +350,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         int32_t *hh = new (std::nothrow) int32_t[max_iters + 1];
         if (!hh) return fail(ctx, FAMST_ERR_OOM, "host");
         CK(cudaMemcpy(hh, hist, size_t(max_iters + 1) * 4, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(&evals_host, evals, 8, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(evals_host, evals, 16, cudaMemcpyDeviceToHost));
         for (int c = 0; c <= max_iters; ++c)
             if (hh[c]) sweeps = c + 1;
         first_delta = m - hh[0];
@@ -377,7 +377,8 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         info->refine_sweeps = sweeps;
         info->boruvka_rounds = rounds;
         info->first_delta = first_delta;
-        info->refine_distance_evals = int64_t(evals_host);
+        info->refine_distance_evals = int64_t(evals_host[0]);
+        info->refine_canonical_evals = int64_t(evals_host[1]);
         info->W = W[0];
         info->W64 = W[1];
     }

@@ -892,6 +892,18 @@ bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int 
     return r == CUDA_SUCCESS;
 }
 
+// keep the better of two top-1 results (the second with ids offset by k0)
+__global__ void top1_merge_kernel(const int32_t *__restrict__ c2, const float *__restrict__ s2,
+                                  int k0, int64_t n, int32_t *__restrict__ c,
+                                  float *__restrict__ s) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (c2[i] >= 0 && s2[i] < s[i]) {
+        c[i] = c2[i] + k0;
+        s[i] = s2[i];
+    }
+}
+
 struct TcPlan {
     int d_pad, nkb, kh, stages, kc;
     int64_t nq_tiles, nk_tiles;
@@ -931,7 +943,8 @@ size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prun
     size_t b = 0;
     if (prune) {
         const int64_t K = prune_pivots_max(n), Kpad = (K + BN - 1) / BN * BN;
-        b += align256(size_t(K) * 4) + align256(size_t(K) * p.kh * 2) + align256(size_t(Kpad) * 4);
+        b += align256(size_t(K) * 4) + align256(size_t(K) * p.kh * 2) +
+             align256(size_t(Kpad + BN) * 4) + align256(size_t(n) * 4) * 2;
         b += prune_workspace(n, d, p.kh, p.kc - 1, p.nq_tiles, p.nk_tiles);
     }
     b += align256(size_t(n) * p.kh * 2);                   // operand rows
@@ -986,29 +999,39 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         const int Kpadmax = (Kmax + BN - 1) / BN * BN;
         int32_t *piv = ar.take<int32_t>(size_t(Kmax));
         __nv_bfloat16 *Hp = ar.take<__nv_bfloat16>(size_t(Kmax) * p.kh);
-        float *nyp = ar.take<float>(size_t(Kpadmax));
+        float *nyp = ar.take<float>(size_t(Kpadmax + BN));   // +inf beyond the pivots
         if (!piv || !Hp || !nyp) return FAMST_ERR_OOM;
-        famst_status st = prune_pivot_operands(ex, H, p.kh, ny, n, K0, Kpadmax, piv, Hp, nyp);
+        famst_status st =
+            prune_pivot_operands(ex, H, p.kh, ny, n, K0, Kpadmax + BN, piv, Hp, nyp);
         if (st != FAMST_OK) return st;
         const TcPlan p1 = tc_plan(n, d, 1, false);
         if (set_smem_attr(knn_tc_kernel<1, false>, int(p1.smem), ex.stream) != cudaSuccess)
             return FAMST_ERR_CUDA;
-        auto assign = [&](int Kc) -> famst_status {
+        // top-1 over pivots [k0, k0 + kc) into (c_out, s_out), ids relative to k0
+        auto assign = [&](int k0, int kc, int32_t *c_out, float *s_out) -> famst_status {
             CUtensorMap mA1, mB1;
-            if (!make_map(&mA1, H, n, p.kh, BM) || !make_map(&mB1, Hp, Kc, p.kh, BN))
+            if (!make_map(&mA1, H, n, p.kh, BM) ||
+                !make_map(&mB1, Hp + size_t(k0) * p.kh, kc, p.kh, BN))
                 return FAMST_ERR_CUDA;
-            TcArgs a1{int(n), (Kc + BN - 1) / BN, p.nkb, 0, p1.stages, nyp, cand, splus,
+            TcArgs a1{int(n), (kc + BN - 1) / BN, p.nkb, 0, p1.stages, nyp + k0, c_out, s_out,
                       ex.dstatus, nullptr, nullptr, nullptr, 1};
             FAMST_LAUNCH(ex, (knn_tc_kernel<1, false>), unsigned(p.nq_tiles), TC_THREADS, p1.smem,
                          mA1, mB1, a1);
             return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
         };
         int K = K0;
-        st = assign(K);
+        st = assign(0, K, cand, splus);
+        // each coverage pass scores the points against the new pivots only
+        int32_t *c2 = ar.take<int32_t>(size_t(n));
+        float *s2 = ar.take<float>(size_t(n));
+        if (!c2 || !s2) return FAMST_ERR_OOM;
         for (int pass = 0; pass < 2 && st == FAMST_OK; ++pass) {
             st = prune_augment(ex, ar, xn2, splus, n, H, p.kh, ny, M, K, piv, Hp, nyp);
+            if (st == FAMST_OK) st = assign(K, M, c2, s2);
+            if (st == FAMST_OK)
+                FAMST_LAUNCH(ex, top1_merge_kernel, unsigned((n + 255) / 256), 256, 0, c2, s2, K,
+                             n, cand, splus);
             K += M;
-            if (st == FAMST_OK) st = assign(K);
         }
         if (st != FAMST_OK) return st;
         st = prune_partition(ex, ar, X, d, n, k, H, p.kh, ny, p.nkb, K, piv, cand, 1,

@@ -40,6 +40,7 @@ class BuildInfo(ctypes.Structure):
         ("ms_connect", ctypes.c_double), ("ms_refine", ctypes.c_double),
         ("ms_mst", ctypes.c_double), ("ms_total", ctypes.c_double),
         ("knn_tile_fraction", ctypes.c_double), ("refine_distance_evals", ctypes.c_int64),
+        ("refine_canonical_evals", ctypes.c_int64),
     ]
 
     def as_dict(self):
