@@ -31,10 +31,13 @@
  *    undefined but the context stays usable. Nothing aborts.
  *
  * Distances. Every distance the library computes, stores or compares is the
- * canonical FP32 Euclidean distance
- *     p = 0; for t = 0..d-1: delta = x[t] - y[t]; p = fmaf(delta, delta, p);
- *     w = sqrtf(p)        (all operations IEEE round-to-nearest)
- * It is symmetric bit for bit. Orders: neighbours of a row by (w, id);
+ * canonical FP32 Euclidean distance: 32 partial sums
+ *     p_l = 0; for t = l, l+32, l+64, ... < d: delta = x[t] - y[t];
+ *                                              p_l = fmaf(delta, delta, p_l)
+ * combined by the butterfly o = 16, 8, 4, 2, 1: p_l = p_l + p_(l xor o)
+ * (all l at once), then w = sqrtf(p_0); every operation IEEE
+ * round-to-nearest. It is the order a 32-lane warp evaluates naturally, and
+ * it is symmetric bit for bit. Orders: neighbours of a row by (w, id);
  * edges by (w, min id, max id). Weights of trees are summed in FP64.
  */
 #ifndef FAMST_H
@@ -62,10 +65,12 @@ typedef int32_t famst_status;
 
 /* Distance-tile precision for Phase 1 (famst_knn_graph, famst_build).
  * Every precision returns the exact kNN under the canonical distance:
- * reduced-precision tiles only choose candidates, which are re-ranked in
- * canonical FP32; a row whose candidate set cannot be certified from the
- * tile's error bound is recomputed by the FP32 tiles. */
-#define FAMST_PREC_FP32   0  /* SIMT FP32 tiles computing the canonical distance directly */
+ * the tiles only choose candidates, which are re-ranked on canonical
+ * distances; a row whose candidate set cannot be certified from the tile's
+ * error bound is recomputed by the FP32 tiles, and a row those cannot
+ * certify either (ties at the k-th distance) by an exact warp-per-row brute
+ * force on canonical distances. */
+#define FAMST_PREC_FP32   0  /* SIMT FP32 tiles (k + 8 candidates by a fast FP32 sum) */
 #define FAMST_PREC_BF16   1  /* tcgen05 BF16 tiles (x.y on tensor cores), FP32 re-rank */
 #define FAMST_PREC_BF16X3 2  /* tcgen05 BF16 hi/lo split, 3 products, FP32 re-rank */
 
@@ -86,7 +91,7 @@ typedef struct famst_build_info {
     double  ms_knn, ms_components, ms_connect, ms_refine, ms_mst, ms_total;
     double  knn_tile_fraction; /* (query, key) tile pairs Phase 1 computed / all pairs */
     int64_t refine_distance_evals; /* candidate distances Algorithm 4 evaluated */
-    int64_t refine_canonical_evals; /* of which the exact FP32 chain decided */
+    int64_t refine_canonical_evals; /* of which the canonical distance decided */
 } famst_build_info;
 
 /* ------------------------------------------------------------ context */

@@ -122,7 +122,8 @@ def threads_default() -> int:
 # ------------------------------------------------------------------ stages
 
 def dist32(a, b) -> float:
-    """Canonical FP32 Euclidean distance (sequential fmaf chain, sqrtf)."""
+    """Canonical FP32 Euclidean distance (32 fmaf partials t mod 32, xor
+    butterfly 16, 8, 4, 2, 1, sqrtf)."""
     a, b = _f32(a).ravel(), _f32(b).ravel()
     return float(_lib().or_dist32(a, b, a.size))
 

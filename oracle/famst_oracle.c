@@ -17,10 +17,15 @@
  *
  * Precision. The paper does not state one. Every decision (kNN order,
  * sample order, refinement comparisons, Kruskal order) is taken on the
- * canonical FP32 Euclidean distance
- *     p = 0;  for t = 0 .. d-1:  delta = x[t] - y[t];  p = fmaf(delta, delta, p)
- *     w = sqrtf(p)
- * (fmaf and sqrtf are correctly rounded; build with -ffp-contract=off).
+ * canonical FP32 Euclidean distance: 32 partial sums, partial l taking the
+ * coordinates t = l, l+32, l+64, ... < d in increasing order,
+ *     p_l = 0;  p_l = fmaf(delta_t, delta_t, p_l),  delta_t = x[t] - y[t]
+ * then combined pairwise by the butterfly o = 16, 8, 4, 2, 1:
+ *     p_l <- p_l + p_(l xor o)   (every l at once; lane 0's value is kept)
+ *     w = sqrtf(p_0)
+ * (fmaf, + and sqrtf are correctly rounded; build with -ffp-contract=off).
+ * This is the order a 32-lane warp evaluates naturally; it is symmetric in
+ * x and y bit for bit.
  * Sums of weights are taken in double. dist64() is the same distance in
  * double precision, used for the FP64 tree weight and the gradient.
  *
@@ -40,12 +45,17 @@
 
 float or_dist32(const float *a, const float *b, int d)
 {
-    float p = 0.0f;
-    for (int t = 0; t < d; ++t) {
+    float p[32], q[32];
+    for (int l = 0; l < 32; ++l) p[l] = 0.0f;
+    for (int t = 0; t < d; ++t) {        /* partial t mod 32, t increasing */
         float delta = a[t] - b[t];
-        p = fmaf(delta, delta, p);
+        p[t & 31] = fmaf(delta, delta, p[t & 31]);
     }
-    return sqrtf(p);
+    for (int o = 16; o >= 1; o >>= 1) {  /* butterfly, all partials at once */
+        for (int l = 0; l < 32; ++l) q[l] = p[l] + p[l ^ o];
+        for (int l = 0; l < 32; ++l) p[l] = q[l];
+    }
+    return sqrtf(p[0]);
 }
 
 double or_dist64(const float *a, const float *b, int d)

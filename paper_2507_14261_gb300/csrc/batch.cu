@@ -369,6 +369,8 @@ size_t batch_workspace(const BatchPlan &P) {
         add(size_t(N) * (P.tc_kc - 1) * 4);        // candidates
         add(size_t(N) * 4 * 2 + 256);              // splus, fail rows, count
     }
+    if (!P.f32t.empty())
+        add(size_t(N) * (P.k + 8) * 8 + size_t(N) * 4 + 512);  // FP32 candidates, fails
     add(size_t(N) * 4 * 3);                      // comp, members, keys
     add(size_t(N + 1) * 4);                      // comp_off
     add(size_t(B + 1) * 4 + size_t(B + 1) * 8 + 256);  // cbase, pp, counters
@@ -415,6 +417,14 @@ famst_status batch_bind(BatchPlan &P, char *base, size_t cap, cudaStream_t s) {
             !V.fail_count)
             return FAMST_ERR_OOM;
         if (!knn_tc_batched_maps(V.H, NP, int(D), P.x3, &P.mA, &P.mB)) return FAMST_ERR_CUDA;
+    }
+    if (!P.f32t.empty()) {
+        const int64_t kp = k + 8;
+        V.f32c = ar.take<int32_t>(size_t(N) * kp);
+        V.f32w = ar.take<float>(size_t(N) * kp);
+        V.f32fail = ar.take<int32_t>(size_t(N));
+        V.f32nfail = ar.take<int32_t>(1);
+        if (!V.f32c || !V.f32w || !V.f32fail || !V.f32nfail) return FAMST_ERR_OOM;
     }
     V.comp = ar.take<int32_t>(size_t(N));
     V.members = ar.take<int32_t>(size_t(N));
@@ -492,7 +502,9 @@ famst_status batch_enqueue(const Exec &ex, BatchPlan &P, char *base, size_t cap,
                            V.ny, V.xn2, V.mean, V.ymax, V.cand, V.splus, V.fail_rows, V.fail_count,
                            V.nbr, V.dist, &P.mA, &P.mB));
     if (!P.f32t.empty())
-        ST_(knn_fp32_batched(ex, V.Xc, int(D), k, V.f32t, int64_t(P.f32t.size()), V.nbr, V.dist));
+        ST_(knn_fp32_batched(ex, V.Xc, int(D), V.voff, B, V.cl, k, k + 8, V.f32t,
+                             int64_t(P.f32t.size()), V.f32c, V.f32w, V.f32fail, V.f32nfail, V.nbr,
+                             V.dist));
     // Alg. 2
     ST_(components_uf(ex, ar, V.nbr, N, k, V.comp, V.t_dev));
     FAMST_LAUNCH(ex, bt_cbase_kernel, 1, 256, 0, V.comp, V.voff, B, V.t_dev, V.cbase);

@@ -41,6 +41,8 @@ struct BatchDev {
     uint32_t *tkeys = nullptr;
     int32_t *tvals = nullptr;
     double *W = nullptr;
+    int32_t *f32c = nullptr, *f32fail = nullptr, *f32nfail = nullptr;  // FP32 clouds:
+    float *f32w = nullptr;                      // kp candidates per row, uncertified rows
     float *Xin = nullptr;                       // copy of the caller's clouds
     int32_t *out_u = nullptr, *out_v = nullptr; // per-cloud trees before the copy out
     float *out_w = nullptr;

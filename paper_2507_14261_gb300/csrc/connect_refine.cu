@@ -103,9 +103,10 @@ __global__ void connect_kernel(const float *__restrict__ X, int d,
 
 // Filtered Algorithm 3 (rows 16-byte aligned, d % 4 == 0): the same draws,
 // but the warp first computes fast squared distances of all lambda^2 pairs
-// (grouped warp-wide sums, rows read contiguously) and runs the canonical
-// chain only for pairs whose lower bound is within the lambda-th smallest
-// upper bound (widened by 2^-20 for the rounding of sqrtf). At least lambda
+// (grouped warp-wide sums, rows read contiguously) and evaluates the
+// canonical distance (the whole warp, lane l holding partial l) only for
+// pairs whose lower bound is within the lambda-th smallest upper bound
+// (widened by 2^-20 for the rounding of sqrtf). At least lambda
 // pairs have p_canon <= that bound, so every pair of the exact top lambda
 // (w, s) survives, and the selection below sees the same winners.
 template <int PER, int G>
@@ -164,11 +165,18 @@ __global__ void connect_filtered_kernel(const float *__restrict__ X, int d,
         uint64_t kk[PER];
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
-            const int s = lane + 32 * q;
             kk[q] = KEY_NONE;
-            if (s < L2 && lo[q] <= bound)
-                kk[q] = nb_key(canon_dist<4>(X + int64_t(uu[q]) * d, X + int64_t(vv[q]) * d, d),
-                               uint32_t(s));
+            // survivors: canonical distance by the whole warp, kept by their lane
+            unsigned sv = __ballot_sync(0xffffffffu, lane + 32 * q < L2 && lo[q] <= bound);
+            while (sv) {
+                const int sl = __ffs(sv) - 1;
+                sv &= sv - 1;
+                const int a = __shfl_sync(0xffffffffu, uu[q], sl);
+                const int b = __shfl_sync(0xffffffffu, vv[q], sl);
+                const float w = __fsqrt_rn(
+                    canon_p_warp(X + int64_t(a) * d, X + int64_t(b) * d, d, lane));
+                if (lane == sl) kk[q] = nb_key(w, uint32_t(sl + 32 * q));
+            }
         }
         const int64_t ebase = pl * lambda;
         for (int r = 0; r < lambda; ++r) {
@@ -304,8 +312,9 @@ __device__ __forceinline__ uint64_t scan_side(const float *__restrict__ X, int d
 // Filtered version (rows 16-byte aligned, d % 4 == 0, d <= 512): the warp
 // first computes fast squared distances of its 32 candidates with the
 // grouped warp-wide sums (every row read contiguously by G lanes), then
-// runs the canonical chain only for candidates the fast value cannot rule
-// out. The fast and the canonical sums add the same rounded terms
+// evaluates canonical distances (the whole warp per candidate, lane l
+// holding partial l) only for candidates the fast value cannot rule out.
+// The fast and the canonical sums add the same rounded terms
 // fl(x_t - y_t)^2 in different orders, so both lie within gamma_n of the
 // exact sum: p_canon / p_fast is within [1 - rho, 1 + rho]. A candidate
 // whose lower bound exceeds (a) the smallest upper bound in the round or
@@ -344,13 +353,17 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
         for (int o = 16; o >= 1; o >>= 1) mh = fminf(mh, __shfl_xor_sync(0xffffffffu, mh, o));
         const float wb = key_w(best);
         const float bound = fminf(__fmul_ru(mh, widen), __fmul_ru(__fmul_ru(wb, wb), widen));
-        if (cand >= 0 && lo <= bound) {
-            ++canon;
-            const float w = canon_dist<4>(X + int64_t(cand) * d, xf, d);
-            const uint64_t key = (uint64_t(__float_as_uint(w)) << 32) | uint32_t(cand + 1);
-            best = key < best ? key : best;
+        // survivors are decided on canonical distances, each by the whole warp
+        unsigned sv = __ballot_sync(0xffffffffu, cand >= 0 && lo <= bound);
+        if (lane == 0) canon += unsigned(__popc(sv));
+        while (sv) {
+            const int sl = __ffs(sv) - 1;
+            sv &= sv - 1;
+            const int c2 = __shfl_sync(0xffffffffu, cand, sl);
+            const float w = __fsqrt_rn(canon_p_warp(X + int64_t(c2) * d, xf, d, lane));
+            const uint64_t key = (uint64_t(__float_as_uint(w)) << 32) | uint32_t(c2 + 1);
+            best = key < best ? key : best;   // the same in every lane
         }
-        best = warp_min_u64(best);
     }
     return best;
 }
@@ -437,7 +450,7 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
         evals_total += evals;
         canon_total += G > 0 ? canon : evals;
     }
-    if (evals_out) {   // [0] candidate distances, [1] canonical chains among them
+    if (evals_out) {   // [0] candidate distances, [1] canonical evaluations among them
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
             evals_total += __shfl_xor_sync(0xffffffffu, evals_total, o);
@@ -452,7 +465,7 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
 
 // Launch of the refinement kernel in the variant the shape allows: the
 // filtered scan for 16-byte rows with 32 <= d <= 512, the per-lane
-// canonical chain otherwise. Persistent grid; edges are fetched from
+// canonical distance per lane otherwise. Persistent grid; edges are fetched from
 // *next_item (zeroed by the caller).
 famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, const int32_t *nbr,
                            int k, const int32_t *rev_off, const int32_t *rev_src,

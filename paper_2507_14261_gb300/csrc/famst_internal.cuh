@@ -69,35 +69,69 @@ static inline cudaError_t set_smem_attr(K *kernel, size_t bytes, cudaStream_t s)
 
 static constexpr uint64_t KEY_NONE = ~0ull;
 
-// Canonical FP32 distance: sequential fmaf chain over t = 0..d-1 and a
-// correctly rounded square root. VEC = 4 reads float4 (rows 16-byte
-// aligned, d % 4 == 0); the chain order is the same either way.
+// Canonical FP32 distance. 32 partial sums, partial l taking the
+// coordinates t = l, l+32, ... < d in increasing order (p_l = fmaf(delta_t,
+// delta_t, p_l), delta_t = x_t - y_t), combined by the butterfly o = 16, 8,
+// 4, 2, 1 (p_l <- p_l + p_(l xor o)), then a correctly rounded square root.
+// A warp evaluates it with lane l holding p_l (canon_p_warp); one thread
+// evaluates the identical value with the 32 partials in registers: the
+// butterfly's value at lane 0 is the binary tree q_l = p_l + p_(l+16),
+// r_l = q_l + q_(l+8), ... over l < 16, 8, 4, 2, 1 (addition commutes).
+// VEC = 4 reads float4 (rows 16-byte aligned, d % 4 == 0).
 template <int VEC>
 __device__ __forceinline__ float canon_p(const float *__restrict__ a,
                                          const float *__restrict__ b, int d) {
-    float p = 0.0f;
+    float p[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) p[l] = 0.0f;
     if constexpr (VEC == 4) {
         const float4 *a4 = reinterpret_cast<const float4 *>(a);
         const float4 *b4 = reinterpret_cast<const float4 *>(b);
-        int d4 = d >> 2;
-#pragma unroll 4
-        for (int q = 0; q < d4; ++q) {
-            float4 x = __ldg(a4 + q), y = __ldg(b4 + q);
-            float t0 = __fsub_rn(x.x, y.x);
-            p = __fmaf_rn(t0, t0, p);
-            float t1 = __fsub_rn(x.y, y.y);
-            p = __fmaf_rn(t1, t1, p);
-            float t2 = __fsub_rn(x.z, y.z);
-            p = __fmaf_rn(t2, t2, p);
-            float t3 = __fsub_rn(x.w, y.w);
-            p = __fmaf_rn(t3, t3, p);
+        const int d4 = d >> 2;
+        for (int q0 = 0; q0 < d4; q0 += 8) {   // 32 coordinates: one term per partial
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (q0 + i < d4) {
+                    const float4 x = __ldg(a4 + q0 + i), y = __ldg(b4 + q0 + i);
+                    const float t0 = __fsub_rn(x.x, y.x), t1 = __fsub_rn(x.y, y.y);
+                    const float t2 = __fsub_rn(x.z, y.z), t3 = __fsub_rn(x.w, y.w);
+                    p[4 * i + 0] = __fmaf_rn(t0, t0, p[4 * i + 0]);
+                    p[4 * i + 1] = __fmaf_rn(t1, t1, p[4 * i + 1]);
+                    p[4 * i + 2] = __fmaf_rn(t2, t2, p[4 * i + 2]);
+                    p[4 * i + 3] = __fmaf_rn(t3, t3, p[4 * i + 3]);
+                }
+            }
         }
     } else {
-        for (int t = 0; t < d; ++t) {
-            float t0 = __fsub_rn(__ldg(a + t), __ldg(b + t));
-            p = __fmaf_rn(t0, t0, p);
+        for (int t0 = 0; t0 < d; t0 += 32) {
+#pragma unroll
+            for (int l = 0; l < 32; ++l) {
+                if (t0 + l < d) {
+                    const float t = __fsub_rn(__ldg(a + t0 + l), __ldg(b + t0 + l));
+                    p[l] = __fmaf_rn(t, t, p[l]);
+                }
+            }
         }
     }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+#pragma unroll
+        for (int l = 0; l < o; ++l) p[l] = __fadd_rn(p[l], p[l + o]);
+    }
+    return p[0];
+}
+
+// The same value computed by a whole warp (every lane gets it): lane l
+// accumulates partial l over coalesced loads, then the xor butterfly.
+__device__ __forceinline__ float canon_p_warp(const float *__restrict__ a,
+                                              const float *__restrict__ b, int d, int lane) {
+    float p = 0.0f;
+    for (int t = lane; t < d; t += 32) {
+        const float x = __fsub_rn(__ldg(a + t), __ldg(b + t));
+        p = __fmaf_rn(x, x, p);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) p = __fadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
     return p;
 }
 
@@ -122,6 +156,20 @@ __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
     return (uint64_t(hi) << 32) | lo;
 }
 
+__device__ __forceinline__ uint64_t shfl_idx_u64(uint64_t v, int src) {
+    uint32_t lo = uint32_t(v), hi = uint32_t(v >> 32);
+    lo = __shfl_sync(0xffffffffu, lo, src);
+    hi = __shfl_sync(0xffffffffu, hi, src);
+    return (uint64_t(hi) << 32) | lo;
+}
+
+__device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v, int delta) {
+    uint32_t lo = uint32_t(v), hi = uint32_t(v >> 32);
+    lo = __shfl_up_sync(0xffffffffu, lo, delta);
+    hi = __shfl_up_sync(0xffffffffu, hi, delta);
+    return (uint64_t(hi) << 32) | lo;
+}
+
 __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) {
@@ -135,7 +183,7 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
 // Warp-cooperative squared distances for filters and bounds (never for a
 // stored weight). Rows are 16-byte aligned with d % 4 == 0; lane l holds
 // float4 columns l, l + 32, ..., FR of them (d <= 128 FR). Each term is
-// fl(y_t - x_t)^2 accumulated by fmaf as in the canonical chain, only in
+// fl(y_t - x_t)^2 accumulated by fmaf as in the canonical distance, only in
 // another order, so the result is within gamma_n of the exact sum of the
 // rounded differences, n = d + 4 FR + 5 roundings at most (the canonical
 // chain: gamma_d). fast_rho(d, FR) bounds both ratios p_canon / p_fast and
@@ -422,14 +470,24 @@ struct CloudDev {
     int use_tc;       // 1: rows come from the tensor tiles (re-rank them)
 };
 
-famst_status knn_fp32_batched(const Exec &ex, const float *Xp, int ld, int k, const F32Tile *tiles,
-                              int64_t nblocks, int32_t *nbr, float *dist);
+// Batched FP32 path: the tiles keep kp = k + 8 candidates per row (c, w,
+// N x kp), then canonical re-rank and certificate, then exact rows within
+// the cloud for rows it cannot certify (fails / nfail, N + 1 entries).
+famst_status knn_fp32_batched(const Exec &ex, const float *Xc, int ld, const long long *voff,
+                              int B, const CloudDev *cl, int k, int kp, const F32Tile *tiles,
+                              int64_t nblocks, int32_t *c, float *w, int32_t *fails,
+                              int32_t *nfail, int32_t *nbr, float *dist);
 
 // knn_tc.cu
 // Exact kNN through tcgen05 BF16 (x3 = hi/lo split) distance tiles, FP32
 // re-rank, certificate, FP32 recomputation of uncertified rows.
 bool knn_tc_supported(int64_t n, int d, int k, bool x3);
 size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prune = false);
+// Exact kNN of the listed rows of a batch of clouds (warp per row, canonical
+// distances within the row's cloud); rows / count on the device. k <= 64.
+famst_status fallback_rows_batched(const Exec &ex, const float *Xc, int ld, const long long *voff,
+                                   int B, const CloudDev *cl, int k, const int32_t *rows,
+                                   const int32_t *count, int32_t *nbr, float *dist);
 famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k, bool x3,
                     bool vec4, int32_t *nbr, float *dist, int32_t *pinned_host,
                     int64_t *uncertified, const int32_t *colcomp = nullptr, bool prune = false,

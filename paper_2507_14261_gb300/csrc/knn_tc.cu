@@ -611,7 +611,7 @@ struct CertConst {
 // One warp per row: canonical distances of the k' candidates, bitonic sort
 // of (w, id), top k, certificate. Row i's point is xi; candidate ids index
 // rows of X (row stride ld, chain length dc >= d: columns beyond d are zero
-// and leave the canonical chain unchanged). d is the true dimension used in
+// and leave the canonical distance unchanged). d is the true dimension used in
 // the error bounds. Returns whether the row was certified (then the k
 // results are written).
 template <int VEC, int KC>
@@ -763,7 +763,7 @@ __global__ void rerank_batched_kernel(const float *__restrict__ Xc, int ld, int6
 
 // Exact kNN of single rows by brute force within their cloud: one warp per
 // listed row (the count lives on the device); lane l scans keys l, l+32, ...
-// with the canonical chain and keeps its k best (w, id) in shared memory;
+// with canonical distances and keeps its k best (w, id) in shared memory;
 // the warp then merges the 32 sorted lists. k <= 64.
 constexpr int FB_WARPS = 2;  // 32 KB of static shared lists per block
 __global__ void fallback_rows_kernel(const float *__restrict__ Xc, int ld,
@@ -1178,6 +1178,14 @@ famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, i
                      k, cand, splus, xn2, ymax, nbr, dist, fail_rows, fail_count);
     FAMST_LAUNCH(ex, fallback_rows_kernel, unsigned(ex.num_sms) * 16, FB_WARPS * 32, 0, Xc, D, voff,
                  B, cl, k, fail_rows, fail_count, nbr, dist);
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+famst_status fallback_rows_batched(const Exec &ex, const float *Xc, int ld, const long long *voff,
+                                   int B, const CloudDev *cl, int k, const int32_t *rows,
+                                   const int32_t *count, int32_t *nbr, float *dist) {
+    FAMST_LAUNCH(ex, fallback_rows_kernel, unsigned(ex.num_sms) * 16, FB_WARPS * 32, 0, Xc, ld,
+                 voff, B, cl, k, rows, count, nbr, dist);
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 

@@ -6,9 +6,9 @@ import workloads
 
 
 def test_integer_coordinates_are_exact(orc):
-    # integer coordinates with |x| <= 100 and d <= 128: every partial sum is
-    # an integer below 2^24, so the FP32 chain is exact and w must be the
-    # correctly rounded square root of the exact integer.
+    # integer coordinates with |x| <= 100 and d <= 128: every partial and
+    # every butterfly sum is an integer below 2^24, so the FP32 sums are exact
+    # and w must be the correctly rounded square root of the exact integer.
     rng = np.random.default_rng(5)
     for d in (1, 3, 16, 17, 128):
         a = rng.integers(-100, 101, d).astype(np.float32)
@@ -16,6 +16,26 @@ def test_integer_coordinates_are_exact(orc):
         exact = int(((a.astype(np.int64) - b.astype(np.int64)) ** 2).sum())
         want = np.float32(np.sqrt(np.float64(exact)))  # double sqrt rounded once more is correctly rounded
         assert orc.dist32(a, b) == want
+
+
+def test_partial_sums_follow_lane_order(orc):
+    # d = 64, x = 1 on coordinates 0..31 and 2^-11 on 32..63, y = 0. With the
+    # partials t mod 32 every partial is 1 + 2^-22 and every butterfly sum is
+    # exact, so p = 32 + 2^-17 exactly; a single running sum over t would
+    # stay at 32 (each 2^-22 is below half an ulp of 32). w must be the
+    # correctly rounded sqrt of the exact sum, which differs from sqrtf(32).
+    a = np.concatenate([np.ones(32), np.full(32, 2.0 ** -11)]).astype(np.float32)
+    b = np.zeros(64, np.float32)
+    exact = np.float32(np.sqrt(np.float64(32.0) + 2.0 ** -17))
+    assert exact != np.float32(np.sqrt(32.0))
+    assert orc.dist32(a, b) == exact
+    # the same coordinates spread so that one partial holds all the small
+    # terms: 32 consecutive additions of 2^-22 to 1 + ... stay exact too
+    a2 = np.zeros(64 * 32, np.float32)
+    a2[0] = 1.0
+    a2[32::32] = 2.0 ** -11          # partial 0 only: 1 + 63 * 2^-22, exact
+    exact2 = np.float32(np.sqrt(np.float64(1.0) + 63 * 2.0 ** -22))
+    assert orc.dist32(a2, np.zeros_like(a2)) == exact2
 
 
 def test_distance_symmetric_bitwise(orc):
@@ -29,7 +49,7 @@ def test_distance_symmetric_bitwise(orc):
 
 def test_distance_within_fp32_error_bound(orc):
     # |w32 - w| <= (gamma_{d+1}/2 + u) w  with u = 2^-24 (rounding of the
-    # differences, the chain and the square root)
+    # differences, the partial chains and the butterfly, the square root)
     rng = np.random.default_rng(7)
     u = 2.0 ** -24
     for d in (1, 5, 64, 128, 784):
