@@ -321,15 +321,24 @@ __device__ __forceinline__ uint64_t scan_side(const float *__restrict__ X, int d
 // (b) the current best weight squared, both widened by 2^-20 for the
 // rounding of sqrtf, cannot be the argmin under (w, id); the others are
 // decided on canonical weights, so the result equals scan_side's.
-template <int G>
+// BF: the fast sums read the BF16 rows of hr (bounds in the distance domain
+// widened by hr's per-row error bounds, see h_bounds).
+template <int G, bool BF>
 __device__ __forceinline__ uint64_t scan_side_filtered(
     const float *__restrict__ X, int d, int c, int fixed, int other, int want_comp, float w0,
     const int32_t *__restrict__ nbr, int k, const int32_t *__restrict__ rev_off,
     const int32_t *__restrict__ rev_src, const int32_t *__restrict__ comp, int lane, float rho,
-    unsigned &evals, unsigned &canon) {
+    unsigned &evals, unsigned &canon, const __nv_bfloat16 *__restrict__ Hh, int hld,
+    const float *__restrict__ heb, const float *__restrict__ hm, float eps) {
     const float *xf = X + int64_t(fixed) * d;
     float4 fx[4];
-    row_slices_g<G, 4>(xf, d >> 2, lane, fx);
+    float ebx = 0.0f;
+    if constexpr (BF) {
+        row_slices_h<G>(xf, hm, d, lane, fx);
+        ebx = heb[fixed];
+    } else {
+        row_slices_g<G, 4>(xf, d >> 2, lane, fx);
+    }
     uint64_t best = uint64_t(__float_as_uint(w0)) << 32;
     const int r0 = rev_off[c], r1 = rev_off[c + 1];
     const int deg = k + (r1 - r0);
@@ -345,14 +354,26 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
         const unsigned live = __ballot_sync(0xffffffffu, cand >= 0);
         if (live == 0u) continue;
         if (lane == 0) evals += unsigned(__popc(live));
-        const float pf = warp_sqdist32g<G, 4>(X, d, fx, fixed, cand, lane);
-        const float lo = cand >= 0 ? __fsub_rd(__fmul_rd(pf, 1.0f - rho), 1e-35f) : inf;
-        const float hi = cand >= 0 ? __fadd_ru(__fmul_ru(pf, 1.0f + rho), 1e-35f) : inf;
-        float mh = hi;
+        float lo = inf, hi = inf, bound;
+        if constexpr (BF) {   // distance domain
+            const float pf = warp_sqdist32h<G>(Hh, hld, fx, fixed, cand, lane);
+            if (cand >= 0) h_bounds(pf, rho, __fadd_ru(ebx, heb[cand]), eps, lo, hi);
+            float mh = hi;
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) mh = fminf(mh, __shfl_xor_sync(0xffffffffu, mh, o));
-        const float wb = key_w(best);
-        const float bound = fminf(__fmul_ru(mh, widen), __fmul_ru(__fmul_ru(wb, wb), widen));
+            for (int o = 16; o >= 1; o >>= 1) mh = fminf(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+            bound = __fmul_ru(fminf(mh, key_w(best)), 1.0f + 0x1p-22f);
+        } else {              // squared domain
+            const float pf = warp_sqdist32g<G, 4>(X, d, fx, fixed, cand, lane);
+            if (cand >= 0) {
+                lo = __fsub_rd(__fmul_rd(pf, 1.0f - rho), 1e-35f);
+                hi = __fadd_ru(__fmul_ru(pf, 1.0f + rho), 1e-35f);
+            }
+            float mh = hi;
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) mh = fminf(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+            const float wb = key_w(best);
+            bound = fminf(__fmul_ru(mh, widen), __fmul_ru(__fmul_ru(wb, wb), widen));
+        }
         // survivors are decided on canonical distances, each by the whole warp
         unsigned sv = __ballot_sync(0xffffffffu, cand >= 0 && lo <= bound);
         if (lane == 0) canon += unsigned(__popc(sv));
@@ -372,7 +393,7 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
 // flight stay in L2), each to its own fixed point.
 // Four resident blocks per SM (64 registers): the scans are latency bound,
 // and occupancy buys more than the few spilled registers cost.
-template <int VEC, int G>
+template <int VEC, int G, bool BF>
 __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict__ X, int d,
                               const int32_t *__restrict__ nbr, int k,
                               const int32_t *__restrict__ rev_off,
@@ -384,7 +405,10 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
                               const int64_t *__restrict__ m_dev, int max_iters,
                               int32_t *__restrict__ change_hist,
                               unsigned long long *__restrict__ next_item, int *dstatus,
-                              float rho, unsigned long long *__restrict__ evals_out) {
+                              float rho, unsigned long long *__restrict__ evals_out,
+                              const __nv_bfloat16 *__restrict__ Hh, int hld,
+                              const float *__restrict__ heb, const float *__restrict__ hm,
+                              float eps) {
     if (m_dev) m = *m_dev < m ? *m_dev : m;  // device-side edge count, capped by capacity
     const int lane = threadIdx.x & 31;
     unsigned long long evals_total = 0, canon_total = 0;   // evaluations of this lane
@@ -414,8 +438,9 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
             float ws;
             // u-loop: u' in G[u] ∩ C_i, u' != v, against v
             if constexpr (G > 0)
-                bu = scan_side_filtered<G>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp,
-                                           lane, rho, evals, canon);
+                bu = scan_side_filtered<G, BF>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src,
+                                               comp, lane, rho, evals, canon, Hh, hld, heb, hm,
+                                               eps);
             else
                 bu = scan_side<VEC>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp, lane,
                                     evals);
@@ -425,8 +450,9 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
             if (v == mv_v && us == mv_u)
                 bv = mv_b;
             else if constexpr (G > 0)
-                bv = scan_side_filtered<G>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src,
-                                           comp, lane, rho, evals, canon);
+                bv = scan_side_filtered<G, BF>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src,
+                                               comp, lane, rho, evals, canon, Hh, hld, heb, hm,
+                                               eps);
             else
                 bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane,
                                     evals);
@@ -472,15 +498,22 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
                            const int32_t *comp, int32_t *eu, int32_t *ev, float *ew,
                            const int32_t *eci, const int32_t *ecj, const int32_t *order,
                            int64_t m, const int64_t *m_dev, int max_iters, int32_t *change_hist,
-                           unsigned long long *next_item, unsigned long long *evals) {
+                           unsigned long long *next_item, unsigned long long *evals,
+                           const HalfRows &hr) {
     const int th = 256;
     const int G = (vec4 && d >= 32) ? sq_group(d) : 0;
+    const bool bf = hr.h != nullptr && (G == 4 || G == 8 || G == 16);
+    const void *fn = bf ? (G == 4 ? (const void *)refine_kernel<4, 4, true>
+                           : G == 8 ? (const void *)refine_kernel<4, 8, true>
+                                    : (const void *)refine_kernel<4, 16, true>)
+                   : G == 2 ? (const void *)refine_kernel<4, 2, false>
+                   : G == 4 ? (const void *)refine_kernel<4, 4, false>
+                   : G == 8 ? (const void *)refine_kernel<4, 8, false>
+                   : G == 16 ? (const void *)refine_kernel<4, 16, false>
+                   : G == 32 ? (const void *)refine_kernel<4, 32, false>
+                   : vec4 ? (const void *)refine_kernel<4, 0, false>
+                          : (const void *)refine_kernel<1, 0, false>;
     // persistent grid: as many blocks as stay resident
-    const void *fns[6] = {(const void *)refine_kernel<4, 2>, (const void *)refine_kernel<4, 4>,
-                          (const void *)refine_kernel<4, 8>, (const void *)refine_kernel<4, 16>,
-                          (const void *)refine_kernel<4, 32>, (const void *)refine_kernel<4, 0>};
-    const void *fn = G == 2 ? fns[0] : G == 4 ? fns[1] : G == 8 ? fns[2] : G == 16 ? fns[3]
-                   : G == 32 ? fns[4] : (vec4 ? fns[5] : (const void *)refine_kernel<1, 0>);
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, th, 0) != cudaSuccess ||
         per_sm < 1)
@@ -490,22 +523,66 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
     unsigned grid = unsigned(want < cap ? want : cap);
     if (grid == 0) grid = 1;
     const float rho = fast_rho(d, 1);
-#define REFINE_LAUNCH(V, GG)                                                                   \
-    FAMST_LAUNCH(ex, (refine_kernel<V, GG>), grid, th, 0, X, d, nbr, k, rev_off, rev_src, comp,   \
-                 eu, ev, ew, eci, ecj, order, m, m_dev, max_iters, change_hist, next_item,     \
-                 ex.dstatus, rho, evals)
-    switch (G) {
-        case 2: REFINE_LAUNCH(4, 2); break;
-        case 4: REFINE_LAUNCH(4, 4); break;
-        case 8: REFINE_LAUNCH(4, 8); break;
-        case 16: REFINE_LAUNCH(4, 16); break;
-        case 32: REFINE_LAUNCH(4, 32); break;
-        default:
-            if (vec4) REFINE_LAUNCH(4, 0);
-            else REFINE_LAUNCH(1, 0);
+    // canonical distance vs the exact one, generously: (d + 16) u
+    const float eps = float((d + 16) * std::ldexp(1.0, -24) * 1.1);
+#define REFINE_LAUNCH(V, GG, B)                                                                  \
+    FAMST_LAUNCH(ex, (refine_kernel<V, GG, B>), grid, th, 0, X, d, nbr, k, rev_off, rev_src,     \
+                 comp, eu, ev, ew, eci, ecj, order, m, m_dev, max_iters, change_hist, next_item, \
+                 ex.dstatus, rho, evals, hr.h, hr.ld, hr.eb, hr.m, eps)
+    if (bf) {
+        if (G == 4) REFINE_LAUNCH(4, 4, true);
+        else if (G == 8) REFINE_LAUNCH(4, 8, true);
+        else REFINE_LAUNCH(4, 16, true);
+    } else {
+        switch (G) {
+            case 2: REFINE_LAUNCH(4, 2, false); break;
+            case 4: REFINE_LAUNCH(4, 4, false); break;
+            case 8: REFINE_LAUNCH(4, 8, false); break;
+            case 16: REFINE_LAUNCH(4, 16, false); break;
+            case 32: REFINE_LAUNCH(4, 32, false); break;
+            default:
+                if (vec4) REFINE_LAUNCH(4, 0, false);
+                else REFINE_LAUNCH(1, 0, false);
+        }
     }
 #undef REFINE_LAUNCH
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+// Centre m for the BF16 rows: the mean of up to 4096 evenly spaced rows (any
+// m is valid; the bounds use the actual fl(x - m)).
+__global__ void half_mean_kernel(const float *__restrict__ X, int64_t n, int d,
+                                 float *__restrict__ m) {
+    const int64_t S = n < 4096 ? n : 4096;
+    for (int t = threadIdx.x; t < d; t += blockDim.x) {
+        float s = 0.0f;
+        for (int64_t i = 0; i < S; ++i) s += __ldg(X + (i * n / S) * d + t);
+        m[t] = s / float(S);
+    }
+}
+
+// h = bf16(fl(x - m)), zero beyond d; eb >= (2^-9 + 2^-23) ||fl(x - m)||
+// (BF16 and centring rounding, each coordinate within that relative error of
+// x - m) with margins for the FP32 norm and a tiny absolute term for BF16
+// subnormals. One warp per row.
+__global__ void half_rows_kernel(const float *__restrict__ X, int64_t n, int d, int ld,
+                                 const float *__restrict__ m, __nv_bfloat16 *__restrict__ h,
+                                 float *__restrict__ eb) {
+    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    float acc = 0.0f;
+    for (int t = lane; t < ld; t += 32) {
+        const float x = t < d ? __fsub_rn(__ldg(X + r * d + t), __ldg(m + t)) : 0.0f;
+        h[r * ld + t] = __float2bfloat16_rn(x);
+        acc = __fmaf_ru(x, x, acc);
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) acc = __fadd_ru(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    if (lane == 0) {
+        const float nrm = __fmul_ru(__fsqrt_ru(acc), 1.0f + 0x1p-12f);
+        eb[r] = __fadd_ru(__fmul_ru(nrm, 0x1p-9f + 0x1p-21f), 1e-30f);
+    }
 }
 
 // tile key of an edge: its component pair's (ci / TT, cj / TT) cell
@@ -569,6 +646,28 @@ famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
     return FAMST_ERR_UNSUPPORTED;
 }
 
+size_t half_rows_workspace(int64_t n, int d) {
+    const int ld = (d + 7) / 8 * 8;
+    return align256(size_t(n) * ld * 2) + align256(size_t(n) * 4) + align256(size_t(d) * 4);
+}
+
+famst_status half_rows(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
+                       HalfRows *out) {
+    const int ld = (d + 7) / 8 * 8;
+    __nv_bfloat16 *h = ar.take<__nv_bfloat16>(size_t(n) * ld);
+    float *eb = ar.take<float>(size_t(n));
+    float *m = ar.take<float>(size_t(d));
+    if (!h || !eb || !m) return FAMST_ERR_OOM;
+    FAMST_LAUNCH(ex, half_mean_kernel, 1, 256, 0, X, n, d, m);
+    FAMST_LAUNCH(ex, half_rows_kernel, unsigned((n * 32 + 255) / 256), 256, 0, X, n, d, ld, m, h,
+                 eb);
+    out->h = h;
+    out->ld = ld;
+    out->eb = eb;
+    out->m = m;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
 size_t refine_workspace(int64_t m) {
     return align256(size_t(m) * 4) * 2 + 256 + radix_sort_workspace(m);
 }
@@ -578,7 +677,7 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
                           const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
                           int64_t m, int max_iters, int32_t *change_hist,
-                          unsigned long long *evals) {
+                          unsigned long long *evals, const HalfRows &hr) {
     if (m == 0) return FAMST_OK;
     // order: stable sort of the edges by component-pair tile
     constexpr int TT = 24;
@@ -595,7 +694,7 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
     famst_status st = radix_sort_pairs(ex, ar, keys, order, m, bits);
     if (st != FAMST_OK) return st;
     return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj, order,
-                         m, nullptr, max_iters, change_hist, next_item, evals);
+                         m, nullptr, max_iters, change_hist, next_item, evals, hr);
 }
 
 }  // namespace famst
@@ -615,7 +714,8 @@ famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, 
     if (!next_item) return FAMST_ERR_OOM;
     if (cudaMemsetAsync(next_item, 0, 8, ex.stream) != cudaSuccess) return FAMST_ERR_CUDA;
     return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj,
-                         nullptr, m_cap, m_dev, max_iters, change_hist, next_item, nullptr);
+                         nullptr, m_cap, m_dev, max_iters, change_hist, next_item, nullptr,
+                         HalfRows());
 }
 
 }  // namespace famst

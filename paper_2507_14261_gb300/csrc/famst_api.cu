@@ -315,7 +315,8 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
                   member_lists_workspace(n, t) + 5 * align256(size_t(m > 0 ? m : 1) * 4) +
                   align256(size_t(n + 1) * 4) + align256(size_t(n) * k * 4) +
                   reverse_csr_workspace(n, k) + align256(size_t(max_iters + 1) * 4) +
-                  refine_workspace(m) + boruvka_workspace(n) + tree_weight_workspace(n) + 4096;
+                  refine_workspace(m) + boruvka_workspace(n) + tree_weight_workspace(n) +
+                  half_rows_workspace(n, d) + 4096;
     ST(ensure_ws(ctx, 1, need, ar));
     int32_t *members = ar.take<int32_t>(size_t(n));
     int32_t *comp_off = ar.take<int32_t>(size_t(n + 1));
@@ -334,6 +335,10 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         ST(member_lists(ex, ar, comp, n, t, members, comp_off));
         ST(connect_edges(ex, X, d, v4, members, comp_off, t, lambda, seed, eu, evv, ew, eci, ecj));
         ev.mark(ctx->stream, 3);
+        // BF16 copies of the points for the Alg. 4 filter (half the bytes per
+        // candidate; exactness comes from the canonical survivors)
+        HalfRows hr;
+        if (v4 && d >= 32 && d <= 256) ST(half_rows(ex, ar, X, n, d, &hr));
         int32_t *rev_off = ar.take<int32_t>(size_t(n + 1));
         int32_t *rev_src = ar.take<int32_t>(size_t(n) * k);
         if (!rev_off || !rev_src || !hist) return fail(ctx, FAMST_ERR_OOM, "workspace");
@@ -342,7 +347,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         if (!evals) return fail(ctx, FAMST_ERR_OOM, "workspace");
         CK(cudaMemsetAsync(evals, 0, 16, ctx->stream));
         ST(refine_edges(ex, ar, X, d, v4, nbr, k, rev_off, rev_src, comp, t, eu, evv, ew, eci, ecj, m,
-                        max_iters, hist, evals));
+                        max_iters, hist, evals, hr));
         ev.mark(ctx->stream, 4);
         famst_status s = sync_status(ctx);
         if (s != FAMST_OK) return s;

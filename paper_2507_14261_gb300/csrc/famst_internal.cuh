@@ -395,6 +395,83 @@ __device__ __forceinline__ float warp_pairsq32g(const float *__restrict__ X, int
     return a >= 0 ? tot : 0.0f;
 }
 
+// BF16 filter rows: h = bf16(fl(x - m)) (row stride ld = d rounded up to 8,
+// zero beyond d) and eb >= ||bf16(fl(x - m)) - (x - m)|| per row, so for two
+// rows ||(h_y - h_x) - (y - x)|| <= eb_x + eb_y. Grouped like the FP32 sums:
+// G lanes per row, two uint4 (16 BF16 values) per lane, 16 G >= d; the
+// fixed point's slices fx hold fl(x - m) in FP32 for the same elements.
+__device__ __forceinline__ unsigned long long bf16x2_lo_hi(uint32_t w) {
+    return f2_pack(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+template <int G>
+__device__ __forceinline__ void row_slices_h(const float *__restrict__ x,
+                                             const float *__restrict__ m, int d, int lane,
+                                             float4 (&f)[4]) {
+    const int g = lane % G;
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+        const int e0 = 8 * (g + G * v);
+        float e[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            e[c] = e0 + c < d ? __fsub_rn(__ldg(x + e0 + c), __ldg(m + e0 + c)) : 0.0f;
+        f[2 * v] = make_float4(e[0], e[1], e[2], e[3]);
+        f[2 * v + 1] = make_float4(e[4], e[5], e[6], e[7]);
+    }
+}
+
+__device__ __forceinline__ unsigned long long sq8_h(uint4 y, const float4 &f0, const float4 &f1,
+                                                    unsigned long long a) {
+    a = f2_sqacc(f2_sub(bf16x2_lo_hi(y.x), f2_pack(f0.x, f0.y)), a);
+    a = f2_sqacc(f2_sub(bf16x2_lo_hi(y.y), f2_pack(f0.z, f0.w)), a);
+    a = f2_sqacc(f2_sub(bf16x2_lo_hi(y.z), f2_pack(f1.x, f1.y)), a);
+    a = f2_sqacc(f2_sub(bf16x2_lo_hi(y.w), f2_pack(f1.z, f1.w)), a);
+    return a;
+}
+
+template <int G>
+__device__ __forceinline__ float warp_sqdist32h(const __nv_bfloat16 *__restrict__ H, int ld,
+                                                const float4 (&fx)[4], int fixed, int cand,
+                                                int lane) {
+    constexpr int R = 32 / G;
+    const int nq = ld >> 3, g = lane % G, h = lane / G;
+    float acc[G];
+#pragma unroll
+    for (int s = 0; s < G; ++s) {
+        const int id = __shfl_sync(0xffffffffu, cand, s * R + h);
+        const uint4 *row = reinterpret_cast<const uint4 *>(H + int64_t(id >= 0 ? id : fixed) * ld);
+        unsigned long long a0 = 0ull, a1 = 0ull;
+        if (g < nq) a0 = sq8_h(__ldg(row + g), fx[0], fx[1], a0);
+        if (g + G < nq) a1 = sq8_h(__ldg(row + g + G), fx[2], fx[3], a1);
+        acc[s] = f2_hsum(f2_add(a0, a1));
+    }
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? acc[i] : acc[i + o];
+            const float keep = up ? acc[i + o] : acc[i];
+            acc[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+        }
+    }
+    const float tot = __shfl_sync(0xffffffffu, acc[0], (lane % R) * G + lane / R);
+    return cand >= 0 ? tot : 0.0f;
+}
+
+// Bounds on the canonical distance from a BF16 fast sum pf (FP32 sum of the
+// BF16 differences, within 1 +- rho of their exact sum), the rows' error
+// bounds E = eb_x + eb_y and the canonical error eps: directed rounding
+// keeps lo <= w_canon <= hi.
+__device__ __forceinline__ void h_bounds(float pf, float rho, float E, float eps, float &lo,
+                                         float &hi) {
+    const float slo = __fsqrt_rd(fmaxf(__fmul_rd(pf, 1.0f - rho), 0.0f));
+    const float shi = __fsqrt_ru(__fmul_ru(pf, 1.0f + rho));
+    lo = fmaxf(__fmul_rd(__fsub_rd(slo, E), 1.0f - eps), 0.0f);
+    hi = __fmul_ru(__fadd_ru(shi, E), 1.0f + eps);
+}
+
 // Lanes per row for the grouped sums with V = 4 float4 per lane (0: d too
 // large or not a multiple of 4).
 inline int sq_group(int d) {
@@ -559,6 +636,17 @@ famst_status reverse_csr(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t 
 size_t reverse_csr_workspace(int64_t n, int k);
 
 // connect_refine.cu
+// BF16 copies of the points for the Alg. 4 filter (see warp_sqdist32h);
+// h == nullptr: the filter reads the FP32 rows.
+struct HalfRows {
+    const __nv_bfloat16 *h = nullptr;
+    int ld = 0;
+    const float *eb = nullptr;   // per-row error bound
+    const float *m = nullptr;    // the centre m (d values)
+};
+size_t half_rows_workspace(int64_t n, int d);
+famst_status half_rows(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
+                       HalfRows *out);
 famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
                            const int32_t *members, const int32_t *comp_off, int64_t t,
                            int lambda, uint64_t seed, int32_t *eu, int32_t *ev, float *ew,
@@ -572,8 +660,8 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
                           const int32_t *nbr, int k, const int32_t *rev_off,
                           const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
-                          int64_t m, int max_iters, int32_t *change_hist,
-                          unsigned long long *evals = nullptr /*max_iters+1*/);
+                          int64_t m, int max_iters, int32_t *change_hist /*max_iters+1*/,
+                          unsigned long long *evals = nullptr, const HalfRows &hr = HalfRows());
 size_t refine_workspace(int64_t m);
 famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, bool vec4,
                               const int32_t *nbr, int k, const int32_t *rev_off,
