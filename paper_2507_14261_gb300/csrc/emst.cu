@@ -31,6 +31,7 @@ famst_status emst_exact(const Exec &ex, Arena &ar, const float *X, int64_t n, in
     BvState S;
     famst_status st = bv_state_init(ex, ar, n, &S);
     if (st != FAMST_OK) return st;
+    S.knn_exact = true;   // the first pass is the plain exact 1-NN
     int32_t *nbr1 = ar.take<int32_t>(size_t(n));
     float *dist1 = ar.take<float>(size_t(n));
     if (!nbr1 || !dist1) return FAMST_ERR_OOM;

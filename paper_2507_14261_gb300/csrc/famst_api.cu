@@ -368,7 +368,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     int64_t got = 0;
     int rounds = 0;
     ST(boruvka(ex, ar, n, nbr, dist, k, eu, evv, ew, m, MstOut{out.tu, out.tv, out.tw}, &got,
-               &rounds, ctx->pinned + PIN_MST));
+               &rounds, ctx->pinned + PIN_MST, true));
     if (got != n - 1) return fail(ctx, FAMST_ERR_DISCONNECTED, "candidate graph is not connected");
     ST(tree_weight(ex, ar, X, d, v4, out.tu, out.tv, out.tw, n - 1, ctx->dW));
     ev.mark(ctx->stream, 5);

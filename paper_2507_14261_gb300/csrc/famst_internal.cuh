@@ -678,6 +678,10 @@ struct MstOut {
 // Boruvka state for callers that drive the rounds themselves (exact EMST).
 struct BvState {
     int64_t n = 0;
+    int round = 0;   // rounds run so far
+    // the lists are the exact top-k by (w, id) (their first entry is every
+    // vertex's lightest edge): the first round needs no edge scan
+    bool knn_exact = false;
     unsigned long long *best1 = nullptr;
     unsigned int *best2 = nullptr;
     int32_t *comp = nullptr;   // component representative of every vertex
@@ -692,7 +696,7 @@ famst_status bv_round(const Exec &ex, Arena &ar, BvState &S, const int32_t *nbr,
 famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr,
                      const float *dist, int k, const int32_t *eu, const int32_t *ev,
                      const float *ew, int64_t m, MstOut out, int64_t *tree_edges,
-                     int *rounds, int32_t *pinned_host);
+                     int *rounds, int32_t *pinned_host, bool knn_exact = false);
 size_t boruvka_workspace(int64_t n);
 famst_status boruvka_dev(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr,
                          const float *dist, int k, const int32_t *eu, const int32_t *ev,

@@ -94,6 +94,26 @@ __global__ void bv_min2_kernel(EdgeSrc es, const int32_t *__restrict__ comp,
     }
 }
 
+// First round (every vertex its own component): a vertex's minimum incident
+// edge under (w, min, max) is its first kNN entry -- the list is the exact
+// top-k by (w, id), so no edge at v, kNN or inter-component, is lighter, and
+// at equal w the smallest id comes first. No edge scan is needed.
+__global__ void bv_first_kernel(const int32_t *__restrict__ nbr, const float *__restrict__ dist,
+                                int k, int64_t n, unsigned long long *__restrict__ best1,
+                                unsigned int *__restrict__ best2) {
+    const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    const int j = nbr[v * k];
+    if (j < 0) {
+        best1[v] = KEY_NONE;
+        best2[v] = 0xffffffffu;
+        return;
+    }
+    const int mn = int(v) < j ? int(v) : j, mx = int(v) < j ? j : int(v);
+    best1[v] = (uint64_t(__float_as_uint(dist[v * k])) << 32) | uint32_t(mn);
+    best2[v] = unsigned(mx);
+}
+
 __global__ void bv_hook_kernel(const int32_t *__restrict__ comp, int64_t n,
                                const unsigned long long *__restrict__ best1,
                                const unsigned int *__restrict__ best2, int32_t *__restrict__ newp,
@@ -406,11 +426,17 @@ famst_status bv_round(const Exec &ex, Arena &ar, BvState &S, const int32_t *nbr,
     unsigned ecap = unsigned(ex.num_sms) * 32;
     if (egrid > ecap) egrid = ecap;
     if (egrid == 0) egrid = 1;
-    if (cudaMemsetAsync(S.best1, 0xff, size_t(n) * 8, ex.stream) != cudaSuccess ||
-        cudaMemsetAsync(S.best2, 0xff, size_t(n) * 4, ex.stream) != cudaSuccess)
-        return FAMST_ERR_CUDA;
-    FAMST_LAUNCH(ex, bv_min1_kernel, egrid, th, 0, es, S.comp, S.best1, nullptr);
-    FAMST_LAUNCH(ex, bv_min2_kernel, egrid, th, 0, es, S.comp, S.best1, S.best2, nullptr);
+    if (S.round == 0 && S.knn_exact && k >= 1) {
+        FAMST_LAUNCH(ex, bv_first_kernel, blocks_for(n, th), th, 0, nbr, dist, k, n, S.best1,
+                     S.best2);
+    } else {
+        if (cudaMemsetAsync(S.best1, 0xff, size_t(n) * 8, ex.stream) != cudaSuccess ||
+            cudaMemsetAsync(S.best2, 0xff, size_t(n) * 4, ex.stream) != cudaSuccess)
+            return FAMST_ERR_CUDA;
+        FAMST_LAUNCH(ex, bv_min1_kernel, egrid, th, 0, es, S.comp, S.best1, nullptr);
+        FAMST_LAUNCH(ex, bv_min2_kernel, egrid, th, 0, es, S.comp, S.best1, S.best2, nullptr);
+    }
+    ++S.round;
     FAMST_LAUNCH(ex, bv_hook_kernel, blocks_for(n, th), th, 0, S.comp, n, S.best1, S.best2, S.newp,
                  S.flag, S.rmn, S.rmx, S.rw);
     FAMST_LAUNCH(ex, bv_jump_kernel, blocks_for(n, th), th, 0, S.comp, n, S.newp, ex.dstatus);
@@ -429,13 +455,15 @@ famst_status bv_round(const Exec &ex, Arena &ar, BvState &S, const int32_t *nbr,
 
 famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr, const float *dist,
                      int k, const int32_t *eu, const int32_t *ev, const float *ew, int64_t m,
-                     MstOut out, int64_t *tree_edges, int *rounds, int32_t *pinned_host) {
+                     MstOut out, int64_t *tree_edges, int *rounds, int32_t *pinned_host,
+                     bool knn_exact) {
     *tree_edges = 0;
     *rounds = 0;
     if (n <= 1) return FAMST_OK;
     BvState S;
     famst_status st = bv_state_init(ex, ar, n, &S);
     if (st != FAMST_OK) return st;
+    S.knn_exact = knn_exact;
     int64_t got = 0;
     for (int r = 0; r < 64 && got < n - 1; ++r) {
         st = bv_round(ex, ar, S, nbr, dist, k, eu, ev, ew, m, out, got, pinned_host);

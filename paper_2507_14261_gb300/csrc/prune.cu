@@ -637,6 +637,7 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
         const size_t mark = ar.off;
         BvState S;
         st = bv_state_init(ex, ar, K, &S);
+        S.knn_exact = true;   // nb / nw: each pivot's exact nearest under (DP, id)
         int64_t got = 0;
         for (int r = 0; r < 64 && got < K - 1 && st == FAMST_OK; ++r) {
             FAMST_LAUNCH(ex, pivot_nearest_kernel, nblk(int64_t(K) * 32, 256), 256, 0, DP, K,
