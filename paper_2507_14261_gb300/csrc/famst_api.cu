@@ -315,7 +315,8 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
                   member_lists_workspace(n, t) + 5 * align256(size_t(m > 0 ? m : 1) * 4) +
                   align256(size_t(n + 1) * 4) + align256(size_t(n) * k * 4) +
                   reverse_csr_workspace(n, k) + align256(size_t(max_iters + 1) * 4) +
-                  refine_workspace(m) + boruvka_workspace(n) + tree_weight_workspace(n) +
+                  refine_workspace(m) + boruvka_workspace(n, n * int64_t(k) + m) +
+                  tree_weight_workspace(n) +
                   half_rows_workspace(n, d) + 4096;
     ST(ensure_ws(ctx, 1, need, ar));
     int32_t *members = ar.take<int32_t>(size_t(n));
@@ -368,7 +369,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     int64_t got = 0;
     int rounds = 0;
     ST(boruvka(ex, ar, n, nbr, dist, k, eu, evv, ew, m, MstOut{out.tu, out.tv, out.tw}, &got,
-               &rounds, ctx->pinned + PIN_MST, true));
+               &rounds, ctx->pinned + PIN_MST, true, true));
     if (got != n - 1) return fail(ctx, FAMST_ERR_DISCONNECTED, "candidate graph is not connected");
     ST(tree_weight(ex, ar, X, d, v4, out.tu, out.tv, out.tw, n - 1, ctx->dW));
     ev.mark(ctx->stream, 5);

@@ -688,16 +688,24 @@ struct BvState {
     int32_t *newp = nullptr, *flag = nullptr, *pos = nullptr, *rmn = nullptr, *rmx = nullptr;
     float *rw = nullptr;
     int32_t *total = nullptr;
+    // compaction (ecap > 0): each scan also writes the edges it found between
+    // two components, a superset of the next round's; later rounds read that
+    // list (ping-pong, count on the device)
+    int64_t ecap = 0;
+    int cur = -1;   // list the next round reads; -1: the caller's edges
+    int32_t *cu[2] = {nullptr, nullptr}, *cv[2] = {nullptr, nullptr};
+    float *cw[2] = {nullptr, nullptr};
+    unsigned long long *ccount = nullptr;   // [2]
 };
-famst_status bv_state_init(const Exec &ex, Arena &ar, int64_t n, BvState *S);
+famst_status bv_state_init(const Exec &ex, Arena &ar, int64_t n, BvState *S, int64_t ecap = 0);
 famst_status bv_round(const Exec &ex, Arena &ar, BvState &S, const int32_t *nbr, const float *dist,
                       int k, const int32_t *eu, const int32_t *ev, const float *ew, int64_t m,
                       MstOut out, int64_t base, int32_t *added_host);
 famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr,
                      const float *dist, int k, const int32_t *eu, const int32_t *ev,
                      const float *ew, int64_t m, MstOut out, int64_t *tree_edges,
-                     int *rounds, int32_t *pinned_host, bool knn_exact = false);
-size_t boruvka_workspace(int64_t n);
+                     int *rounds, int32_t *pinned_host, bool knn_exact = false, bool compact = false);
+size_t boruvka_workspace(int64_t n, int64_t ecap = 0);
 famst_status boruvka_dev(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr,
                          const float *dist, int k, const int32_t *eu, const int32_t *ev,
                          const float *ew, int64_t m_cap, const int64_t *m_dev, MstOut out,

@@ -59,19 +59,41 @@ __global__ void bv_init_kernel(int32_t *comp, int64_t n) {
 }
 
 __global__ void bv_min1_kernel(EdgeSrc es, const int32_t *__restrict__ comp,
-                               unsigned long long *__restrict__ best1, const int *__restrict__ done) {
+                               unsigned long long *__restrict__ best1, const int *__restrict__ done,
+                               int32_t *__restrict__ ou = nullptr, int32_t *__restrict__ ov = nullptr,
+                               float *__restrict__ ow = nullptr,
+                               unsigned long long *__restrict__ ocount = nullptr) {
     if (done && *done) return;
     int64_t total = es.total();
+    const int lane = threadIdx.x & 31;
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
         int a, b;
         float w;
         es.get(e, a, b, w);
         int ca = comp[a], cb = comp[b];
-        if (ca == cb) continue;
-        unsigned long long key1 = (uint64_t(__float_as_uint(w)) << 32) | uint32_t(a < b ? a : b);
-        atomicMin(best1 + ca, key1);
-        atomicMin(best1 + cb, key1);
+        const bool inter = ca != cb;
+        if (inter) {
+            unsigned long long key1 = (uint64_t(__float_as_uint(w)) << 32) | uint32_t(a < b ? a : b);
+            atomicMin(best1 + ca, key1);
+            atomicMin(best1 + cb, key1);
+        }
+        if (ocount) {   // append the edges between components, one atomic per warp
+            const unsigned act = __activemask();
+            const unsigned bal = __ballot_sync(act, inter);
+            if (bal) {
+                const int leader = __ffs(act) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(ocount, (unsigned long long)__popc(bal));
+                base = __shfl_sync(act, base, leader);
+                if (inter) {
+                    const unsigned long long idx = base + __popc(bal & ((1u << lane) - 1u));
+                    ou[idx] = a;
+                    ov[idx] = b;
+                    ow[idx] = w;
+                }
+            }
+        }
     }
 }
 
@@ -332,8 +354,10 @@ inline unsigned blocks_for(int64_t count, int th) { return unsigned((count + th 
 
 }  // namespace
 
-size_t boruvka_workspace(int64_t n) {
-    return align256(size_t(n) * 8) + align256(size_t(n) * 4) * 8 + scan_workspace(n) + 256;
+size_t boruvka_workspace(int64_t n, int64_t ecap) {
+    size_t b = align256(size_t(n) * 8) + align256(size_t(n) * 4) * 8 + scan_workspace(n) + 256;
+    if (ecap > 0) b += align256(size_t(ecap) * 4) * 6 + 256;
+    return b;
 }
 
 // Boruvka with no host synchronisation: a fixed budget of rounds, the
@@ -392,8 +416,19 @@ famst_status boruvka_dev(const Exec &ex, Arena &ar, int64_t n, const int32_t *nb
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
-famst_status bv_state_init(const Exec &ex, Arena &ar, int64_t n, BvState *S) {
+famst_status bv_state_init(const Exec &ex, Arena &ar, int64_t n, BvState *S, int64_t ecap) {
     S->n = n;
+    if (ecap > 0) {
+        S->ecap = ecap;
+        for (int i = 0; i < 2; ++i) {
+            S->cu[i] = ar.take<int32_t>(size_t(ecap));
+            S->cv[i] = ar.take<int32_t>(size_t(ecap));
+            S->cw[i] = ar.take<float>(size_t(ecap));
+            if (!S->cu[i] || !S->cv[i] || !S->cw[i]) return FAMST_ERR_OOM;
+        }
+        S->ccount = ar.take<unsigned long long>(2);
+        if (!S->ccount) return FAMST_ERR_OOM;
+    }
     S->best1 = ar.take<unsigned long long>(size_t(n));
     S->best2 = ar.take<unsigned int>(size_t(n));
     S->comp = ar.take<int32_t>(size_t(n));
@@ -420,6 +455,9 @@ famst_status bv_round(const Exec &ex, Arena &ar, BvState &S, const int32_t *nbr,
                       MstOut out, int64_t base, int32_t *added_host) {
     const int64_t n = S.n;
     EdgeSrc es{nbr, dist, k, n * int64_t(k), eu, ev, ew, m, nullptr};
+    if (S.cur >= 0)   // the previous scan's edges between components
+        es = EdgeSrc{nullptr, nullptr, 1, 0, S.cu[S.cur], S.cv[S.cur], S.cw[S.cur], S.ecap,
+                      reinterpret_cast<const int64_t *>(S.ccount + S.cur)};
     const int th = 256;
     int64_t nedges = es.nk + es.m;
     unsigned egrid = blocks_for(nedges, th);
@@ -433,8 +471,19 @@ famst_status bv_round(const Exec &ex, Arena &ar, BvState &S, const int32_t *nbr,
         if (cudaMemsetAsync(S.best1, 0xff, size_t(n) * 8, ex.stream) != cudaSuccess ||
             cudaMemsetAsync(S.best2, 0xff, size_t(n) * 4, ex.stream) != cudaSuccess)
             return FAMST_ERR_CUDA;
-        FAMST_LAUNCH(ex, bv_min1_kernel, egrid, th, 0, es, S.comp, S.best1, nullptr);
-        FAMST_LAUNCH(ex, bv_min2_kernel, egrid, th, 0, es, S.comp, S.best1, S.best2, nullptr);
+        if (S.ecap > 0 && S.round >= 2) {   // early rounds keep most edges: no copy
+            const int nxt = S.cur == 0 ? 1 : 0;
+            if (cudaMemsetAsync(S.ccount + nxt, 0, 8, ex.stream) != cudaSuccess)
+                return FAMST_ERR_CUDA;
+            FAMST_LAUNCH(ex, bv_min1_kernel, egrid, th, 0, es, S.comp, S.best1, nullptr, S.cu[nxt],
+                         S.cv[nxt], S.cw[nxt], S.ccount + nxt);
+            FAMST_LAUNCH(ex, bv_min2_kernel, egrid, th, 0, es, S.comp, S.best1, S.best2, nullptr);
+            S.cur = nxt;
+        } else {
+            FAMST_LAUNCH(ex, bv_min1_kernel, egrid, th, 0, es, S.comp, S.best1, nullptr, nullptr,
+                         nullptr, nullptr, nullptr);
+            FAMST_LAUNCH(ex, bv_min2_kernel, egrid, th, 0, es, S.comp, S.best1, S.best2, nullptr);
+        }
     }
     ++S.round;
     FAMST_LAUNCH(ex, bv_hook_kernel, blocks_for(n, th), th, 0, S.comp, n, S.best1, S.best2, S.newp,
@@ -456,12 +505,12 @@ famst_status bv_round(const Exec &ex, Arena &ar, BvState &S, const int32_t *nbr,
 famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr, const float *dist,
                      int k, const int32_t *eu, const int32_t *ev, const float *ew, int64_t m,
                      MstOut out, int64_t *tree_edges, int *rounds, int32_t *pinned_host,
-                     bool knn_exact) {
+                     bool knn_exact, bool compact) {
     *tree_edges = 0;
     *rounds = 0;
     if (n <= 1) return FAMST_OK;
     BvState S;
-    famst_status st = bv_state_init(ex, ar, n, &S);
+    famst_status st = bv_state_init(ex, ar, n, &S, compact ? n * int64_t(k) + m : 0);
     if (st != FAMST_OK) return st;
     S.knn_exact = knn_exact;
     int64_t got = 0;
