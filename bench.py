@@ -137,9 +137,8 @@ def throughput(world: int, n: int, steps: int, seconds: float) -> float:
     return world * n * steps / seconds
 
 
-def kernel_source_hash(prec: str) -> str:
-    f = "knn_fp32.cu" if prec == "fp32" else "knn_tc.cu"
-    p = os.path.join(ROOT, "paper_2507_14261_gb300", "csrc", f)
+def source_hash(fname: str) -> str:
+    p = os.path.join(ROOT, "paper_2507_14261_gb300", "csrc", fname)
     try:
         with open(p, "rb") as fh:
             return hashlib.sha256(fh.read()).hexdigest()[:16]
@@ -147,22 +146,23 @@ def kernel_source_hash(prec: str) -> str:
         return ""
 
 
-def traffic_from_profile(workload: str, prec: str):
-    """DRAM bytes per launch of the distance kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    p = os.path.join(ROOT, "profiles", "knn_traffic.json")
+def traffic_from_profile(kernel: str, units: float):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary
+    (profiles/traffic.json: bytes per unit of work, measured on a smaller
+    case of the same recipe), if it was taken on the current kernel source;
+    else None. Units: candidate distances for the refinement kernel, visited
+    (query, key) pairs for the distance tiles."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             rec = json.load(f)
     except (OSError, ValueError):
         return None
     for r in rec.get("entries", []):
-        if r.get("prec") == prec and r.get("source_sha") == kernel_source_hash(prec):
-            per_unit = r.get("dram_bytes_per_query_row_per_key")
-            if per_unit is None:
-                continue
-            w = workloads.get(workload)
-            return float(per_unit) * w.n * w.n
+        if r.get("kernel") == kernel and r.get("source_sha") == source_hash(r.get("source", "")):
+            per_unit = r.get("dram_bytes_per_unit")
+            if per_unit is not None:
+                return float(per_unit) * units
     return None
 
 
@@ -409,9 +409,11 @@ def main():
     }
     dom = "refine" if ms_refine >= ms_knn else "knn"
     kd = kernels[dom]
+    traffic = (traffic_from_profile("refine_kernel", evals) if dom == "refine" else
+               traffic_from_profile("knn_tc_kernel", frac_tiles * nq * nk * 128 * 256))
     roofline = {"bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
                 "unit": kd["unit"], "frac": kd["achieved"] / kd["peak"],
-                "traffic": traffic_from_profile(w.name, args.prec) if dom == "knn" else None,
+                "traffic": traffic,
                 "kernel": kd["kernel"], "ms_per_launch": kd["ms"],
                 "peak_source": (pk["_source"] if kd["bound"] == "tensor" else
                                 "derived: 152 SMs x 128 FP32 lanes x max SM clock x 1.5 flop/instr")}

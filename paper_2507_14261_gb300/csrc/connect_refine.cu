@@ -549,11 +549,11 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
-// Centre m for the BF16 rows: the mean of up to 4096 evenly spaced rows (any
+// Centre m for the BF16 rows: the mean of up to 256 evenly spaced rows (any
 // m is valid; the bounds use the actual fl(x - m)).
 __global__ void half_mean_kernel(const float *__restrict__ X, int64_t n, int d,
                                  float *__restrict__ m) {
-    const int64_t S = n < 4096 ? n : 4096;
+    const int64_t S = n < 256 ? n : 256;
     for (int t = threadIdx.x; t < d; t += blockDim.x) {
         float s = 0.0f;
         for (int64_t i = 0; i < S; ++i) s += __ldg(X + (i * n / S) * d + t);
