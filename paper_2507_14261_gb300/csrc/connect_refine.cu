@@ -329,7 +329,7 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
     const int32_t *__restrict__ nbr, int k, const int32_t *__restrict__ rev_off,
     const int32_t *__restrict__ rev_src, const int32_t *__restrict__ comp, int lane, float rho,
     unsigned &evals, unsigned &canon, const __nv_bfloat16 *__restrict__ Hh, int hld,
-    const float *__restrict__ heb, const float *__restrict__ hm, float eps) {
+    const float *__restrict__ heb, const float *__restrict__ hm, float eps, bool check) {
     const float *xf = X + int64_t(fixed) * d;
     float4 fx[4];
     float ebx = 0.0f;
@@ -349,7 +349,9 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
         int cand = -1;
         if (idx < deg) {
             cand = idx < k ? nbr[int64_t(c) * k + idx] : rev_src[r0 + idx - k];
-            if (comp[cand] != want_comp || cand == other) cand = -1;  // G[c] ∩ C, u' != v
+            // G[c] ∩ C and u' != v: always true when comp labels the components
+            // of this graph (a build); checked for caller-supplied labels
+            if (check && (comp[cand] != want_comp || cand == other)) cand = -1;
         }
         const unsigned live = __ballot_sync(0xffffffffu, cand >= 0);
         if (live == 0u) continue;
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
                               float rho, unsigned long long *__restrict__ evals_out,
                               const __nv_bfloat16 *__restrict__ Hh, int hld,
                               const float *__restrict__ heb, const float *__restrict__ hm,
-                              float eps) {
+                              float eps, bool check) {
     if (m_dev) m = *m_dev < m ? *m_dev : m;  // device-side edge count, capped by capacity
     const int lane = threadIdx.x & 31;
     unsigned long long evals_total = 0, canon_total = 0;   // evaluations of this lane
@@ -440,7 +442,7 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
             if constexpr (G > 0)
                 bu = scan_side_filtered<G, BF>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src,
                                                comp, lane, rho, evals, canon, Hh, hld, heb, hm,
-                                               eps);
+                                               eps, check);
             else
                 bu = scan_side<VEC>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp, lane,
                                     evals);
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
             else if constexpr (G > 0)
                 bv = scan_side_filtered<G, BF>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src,
                                                comp, lane, rho, evals, canon, Hh, hld, heb, hm,
-                                               eps);
+                                               eps, check);
             else
                 bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane,
                                     evals);
@@ -499,7 +501,7 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
                            const int32_t *eci, const int32_t *ecj, const int32_t *order,
                            int64_t m, const int64_t *m_dev, int max_iters, int32_t *change_hist,
                            unsigned long long *next_item, unsigned long long *evals,
-                           const HalfRows &hr) {
+                           const HalfRows &hr, bool check) {
     const int th = 256;
     const int G = (vec4 && d >= 32) ? sq_group(d) : 0;
     const bool bf = hr.h != nullptr && (G == 4 || G == 8 || G == 16);
@@ -528,7 +530,7 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
 #define REFINE_LAUNCH(V, GG, B)                                                                  \
     FAMST_LAUNCH(ex, (refine_kernel<V, GG, B>), grid, th, 0, X, d, nbr, k, rev_off, rev_src,     \
                  comp, eu, ev, ew, eci, ecj, order, m, m_dev, max_iters, change_hist, next_item, \
-                 ex.dstatus, rho, evals, hr.h, hr.ld, hr.eb, hr.m, eps)
+                 ex.dstatus, rho, evals, hr.h, hr.ld, hr.eb, hr.m, eps, check)
     if (bf) {
         if (G == 4) REFINE_LAUNCH(4, 4, true);
         else if (G == 8) REFINE_LAUNCH(4, 8, true);
@@ -677,7 +679,7 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
                           const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
                           int64_t m, int max_iters, int32_t *change_hist,
-                          unsigned long long *evals, const HalfRows &hr) {
+                          unsigned long long *evals, const HalfRows &hr, bool check) {
     if (m == 0) return FAMST_OK;
     // order: stable sort of the edges by component-pair tile
     constexpr int TT = 24;
@@ -694,7 +696,7 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
     famst_status st = radix_sort_pairs(ex, ar, keys, order, m, bits);
     if (st != FAMST_OK) return st;
     return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj, order,
-                         m, nullptr, max_iters, change_hist, next_item, evals, hr);
+                         m, nullptr, max_iters, change_hist, next_item, evals, hr, check);
 }
 
 }  // namespace famst
@@ -715,7 +717,7 @@ famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, 
     if (cudaMemsetAsync(next_item, 0, 8, ex.stream) != cudaSuccess) return FAMST_ERR_CUDA;
     return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj,
                          nullptr, m_cap, m_dev, max_iters, change_hist, next_item, nullptr,
-                         HalfRows());
+                         HalfRows(), false);
 }
 
 }  // namespace famst

@@ -348,7 +348,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         if (!evals) return fail(ctx, FAMST_ERR_OOM, "workspace");
         CK(cudaMemsetAsync(evals, 0, 16, ctx->stream));
         ST(refine_edges(ex, ar, X, d, v4, nbr, k, rev_off, rev_src, comp, t, eu, evv, ew, eci, ecj, m,
-                        max_iters, hist, evals, hr));
+                        max_iters, hist, evals, hr, false));
         ev.mark(ctx->stream, 4);
         famst_status s = sync_status(ctx);
         if (s != FAMST_OK) return s;

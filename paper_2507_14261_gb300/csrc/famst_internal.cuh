@@ -412,12 +412,18 @@ __device__ __forceinline__ void row_slices_h(const float *__restrict__ x,
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
         const int e0 = 8 * (g + G * v);
-        float e[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-            e[c] = e0 + c < d ? __fsub_rn(__ldg(x + e0 + c), __ldg(m + e0 + c)) : 0.0f;
-        f[2 * v] = make_float4(e[0], e[1], e[2], e[3]);
-        f[2 * v + 1] = make_float4(e[4], e[5], e[6], e[7]);
+        for (int hh = 0; hh < 2; ++hh) {
+            const int e = e0 + 4 * hh;   // x and m rows are 16-byte aligned, d % 4 == 0
+            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (e < d) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(x + e));
+                const float4 b = __ldg(reinterpret_cast<const float4 *>(m + e));
+                r = make_float4(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z),
+                                __fsub_rn(a.w, b.w));
+            }
+            f[2 * v + hh] = r;
+        }
     }
 }
 
@@ -661,7 +667,8 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
                           const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
                           int64_t m, int max_iters, int32_t *change_hist /*max_iters+1*/,
-                          unsigned long long *evals = nullptr, const HalfRows &hr = HalfRows());
+                          unsigned long long *evals = nullptr, const HalfRows &hr = HalfRows(),
+                          bool check = true);
 size_t refine_workspace(int64_t m);
 famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, bool vec4,
                               const int32_t *nbr, int k, const int32_t *rev_off,
