@@ -587,6 +587,7 @@ struct PruneOut {
     int32_t *klist = nullptr;       // key tiles per query tile
     TcTile *tab = nullptr;          // per query tile: its range of klist
     float *skipQ = nullptr;         // per query tile
+    float *Xs = nullptr;            // the points in sorted order (FP32, n x d)
     int32_t *visited = nullptr;     // device: number of visited (query, key) tile pairs
     int64_t nq = 0, nk = 0;
 };
@@ -605,9 +606,7 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
                              const __nv_bfloat16 *H, int kh, const float *ny, int nkb, int K,
                              const int32_t *piv, const int32_t *acand, int akp,
                              int32_t *pinned_host, PruneOut *out);
-famst_status prune_scatter(const Exec &ex, const PruneOut &P, int64_t n, int kp,
-                           const int32_t *cand_s, const float *splus_s, int32_t *cand,
-                           float *splus, float *skip);
+
 
 }  // namespace famst
 #include <cuda.h>

@@ -621,7 +621,8 @@ __device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, 
                                            float skip, float xn2f, float ymf, double eps_dot,
                                            int lane,
                                            int32_t *__restrict__ nbr_row,
-                                           float *__restrict__ dist_row) {
+                                           float *__restrict__ dist_row,
+                                           const int32_t *__restrict__ idmap = nullptr) {
     constexpr int KP = KC - 1;
     uint64_t key[2];
 #pragma unroll
@@ -630,7 +631,9 @@ __device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, 
         key[h] = KEY_NONE;
         if (c < KP) {
             int j = cand_row[c];
-            if (j >= 0) key[h] = nb_key(canon_dist<VEC>(xi, X + int64_t(j) * ld, dc), uint32_t(j));
+            if (j >= 0)
+                key[h] = nb_key(canon_dist<VEC>(xi, X + int64_t(j) * ld, dc),
+                                uint32_t(idmap ? idmap[j] : j));
         }
     }
     // bitonic sort of 64 keys, element index = h*32 + lane
@@ -716,6 +719,32 @@ __global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int
     bool cert = rerank_row<VEC, KC>(X, d, d, d, X + i * d, k, cand + i * (KC - 1), splus[i], sk,
                                     xnorm2[i], __uint_as_float(*ymax_bits), cc.eps_dot, lane,
                                     nbr + i * k, dist + i * k);
+    if (!cert && lane == 0) fail_rows[atomicAdd(fail_count, 1)] = int32_t(i);
+}
+
+// Re-rank in the pruning's cell order: sorted row r is point i = perm[r];
+// candidate rows are read from the sorted copy Xs (a row's candidates are
+// mostly cell-mates, so they sit close together in memory), keyed and
+// written with their original ids.
+template <int VEC, int KC>
+__global__ void rerank_sorted_kernel(const float *__restrict__ Xs, int64_t n, int d, int k,
+                                     const int32_t *__restrict__ cand,
+                                     const float *__restrict__ splus,
+                                     const float *__restrict__ skipQ,
+                                     const int32_t *__restrict__ perm,
+                                     const float *__restrict__ xnorm2,
+                                     const unsigned *__restrict__ ymax_bits, CertConst cc,
+                                     int32_t *__restrict__ nbr, float *__restrict__ dist,
+                                     int32_t *__restrict__ fail_rows,
+                                     int32_t *__restrict__ fail_count) {
+    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const int64_t i = perm[r];
+    const bool cert = rerank_row<VEC, KC>(Xs, d, d, d, Xs + r * d, k, cand + r * (KC - 1),
+                                          splus[r], skipQ[r / BM], xnorm2[i],
+                                          __uint_as_float(*ymax_bits), cc.eps_dot, lane,
+                                          nbr + i * k, dist + i * k, perm);
     if (!cert && lane == 0) fail_rows[atomicAdd(fail_count, 1)] = int32_t(i);
 }
 
@@ -990,7 +1019,6 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     if (npad > n)
         FAMST_LAUNCH(ex, fill_inf_kernel, unsigned((npad - n + 255) / 256), 256, 0, ny, n, npad);
     const bool use_prune = prune && !colcomp && prune_supported(n, d, k, vec4);
-    float *skip = nullptr;
     PruneOut P;
     if (use_prune) {
         // pivot cells: top-1 pivot of every point on the tensor tiles (BF16),
@@ -1037,8 +1065,6 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         st = prune_partition(ex, ar, X, d, n, k, H, p.kh, ny, p.nkb, K, piv, cand, 1,
                              pinned_host + 2, &P);
         if (st != FAMST_OK) return st;
-        skip = ar.take<float>(size_t(n));
-        if (!skip) return FAMST_ERR_OOM;
     }
     // candidates of the tensor pass: directly in cand / splus, or (pruned)
     // in sorted order first
@@ -1081,10 +1107,6 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     }
 #undef TC_LAUNCH
     if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
-    if (use_prune) {
-        famst_status st = prune_scatter(ex, P, n, p.kc - 1, cand_t, splus_t, cand, splus, skip);
-        if (st != FAMST_OK) return st;
-    }
     // rerank + certificate
     const double u8 = 1.0 / 256.0;
     const double kprod = double(x3 ? 3 * p.d_pad : p.d_pad);
@@ -1095,8 +1117,15 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     cc.d_plus = double(d) + 4.0;
     const unsigned rgrid = unsigned((n * 32 + 255) / 256);
 #define RERANK(V, KCV)                                                                           \
-    FAMST_LAUNCH(ex, (rerank_kernel<V, KCV>), rgrid, 256, 0, X, n, d, k, cand, splus, skip, xn2, \
-                 ymax, cc, nbr, dist, fail_rows, fail_count)
+    do {                                                                                         \
+        if (use_prune)                                                                           \
+            FAMST_LAUNCH(ex, (rerank_sorted_kernel<V, KCV>), rgrid, 256, 0, P.Xs, n, d, k, cand_t, \
+                         splus_t, P.skipQ, P.perm, xn2, ymax, cc, nbr, dist, fail_rows,          \
+                         fail_count);                                                            \
+        else                                                                                     \
+            FAMST_LAUNCH(ex, (rerank_kernel<V, KCV>), rgrid, 256, 0, X, n, d, k, cand, splus,    \
+                         nullptr, xn2, ymax, cc, nbr, dist, fail_rows, fail_count);              \
+    } while (0)
     if (p.kc == 32) {
         if (vec4) RERANK(4, 32); else RERANK(1, 32);
     } else if (p.kc == 48) {

@@ -150,6 +150,23 @@ __global__ void gather_kernel(const __nv_bfloat16 *__restrict__ H, int kh,
     for (int q = lane; q < kh / 8; q += 32) dst[q] = src[q];
 }
 
+// FP32 rows in sorted order (for the re-rank), float4 when aligned
+__global__ void gather_f32_kernel(const float *__restrict__ X, int d,
+                                  const int32_t *__restrict__ perm, int64_t n,
+                                  float *__restrict__ Xs) {
+    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= n) return;
+    const float *src = X + int64_t(perm[r]) * d;
+    float *dst = Xs + r * d;
+    if ((d & 3) == 0 && ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Xs)) & 15) == 0) {
+        for (int q = lane; q < d / 4; q += 32)
+            reinterpret_cast<float4 *>(dst)[q] = __ldg(reinterpret_cast<const float4 *>(src) + q);
+    } else {
+        for (int t = lane; t < d; t += 32) dst[t] = __ldg(src + t);
+    }
+}
+
 // R_c: upper bound on the distance of every member of cell c to its pivot
 template <int FR>
 __global__ void radius_kernel(const float *__restrict__ X, int d, int64_t n,
@@ -427,27 +444,6 @@ __global__ void table_kernel(const int32_t *__restrict__ off, int64_t nq, int nk
     tab[q] = t;
 }
 
-// candidates, s+ and skip bound of sorted row r to original row perm[r],
-// candidate ids translated to original ids
-__global__ void scatter_kernel(const int32_t *__restrict__ perm, int64_t n, int kp,
-                               const int32_t *__restrict__ cand_s,
-                               const float *__restrict__ splus_s,
-                               const float *__restrict__ skipQ, int32_t *__restrict__ cand,
-                               float *__restrict__ splus, float *__restrict__ skip) {
-    const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (r >= n) return;
-    const int64_t i = perm[r];
-    for (int p = lane; p < kp; p += 32) {
-        const int j = cand_s[r * kp + p];
-        cand[i * kp + p] = j >= 0 ? perm[j] : -1;
-    }
-    if (lane == 0) {
-        splus[i] = splus_s[r];
-        skip[i] = skipQ[r / QT];
-    }
-}
-
 // Order of the cells. The minimum spanning tree of the pivots is cut at
 // edges longer than twice its median edge into groups (single linkage);
 // groups are laid out one after another, each by a depth-first walk over
@@ -540,7 +536,8 @@ size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk)
     b += align256(size_t(nq + 1) * 4) * 2 + scan_workspace(nq + 1) + 256;      // counts, offsets
     b += align256(size_t(nq) * nk * 4);                                        // lists (worst case)
     b += align256(size_t(nq) * 4) + align256(size_t(nq) * sizeof(TcTile));     // skip, table
-    b += align256(size_t(n) * kp * 4) + align256(size_t(n) * 4) * 2;           // sorted outputs
+    b += align256(size_t(n) * kp * 4) + align256(size_t(n) * 4);               // sorted outputs
+    b += align256(size_t(n) * d * 4);                                          // sorted points
     return b;
 }
 
@@ -607,6 +604,8 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     float *skipQ = ar.take<float>(size_t(nq));
     TcTile *tab = ar.take<TcTile>(size_t(nq));
     int32_t *total = ar.take<int32_t>(1);
+    float *Xs = ar.take<float>(size_t(n) * d);
+    if (!Xs) return FAMST_ERR_OOM;
     if (!keys || !perm || !ccount || !cstart || !Hs || !nys || !R || !tauQ || !DP || !DPr || !ord ||
         !tu || !tv || !tw || !nb || !nw || !qc || !kc || !qR || !kR || !cnt || !off || !klist ||
         !skipQ || !tab ||
@@ -683,6 +682,7 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     }
     FAMST_LAUNCH(ex, gather_kernel, nblk(nk * KT * 32, 256), 256, 0, H, kh, ny, perm, n, nk * KT,
                  Hs, nys);
+    FAMST_LAUNCH(ex, gather_f32_kernel, nblk(n * 32, 256), 256, 0, X, d, perm, n, Xs);
     FAMST_LAUNCH(ex, dp_gather_kernel, nblk(int64_t(K) * 32, 256), 256, 0, DP, K, order, DPr);
     // 4. balls and radii of interest
     const unsigned wgrid = nblk(n * 32, 256);
@@ -738,18 +738,12 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     out->klist = klist;
     out->tab = tab;
     out->skipQ = skipQ;
+    out->Xs = Xs;
     out->visited = total;
     out->nq = nq;
     out->nk = nk;
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
-famst_status prune_scatter(const Exec &ex, const PruneOut &P, int64_t n, int kp,
-                           const int32_t *cand_s, const float *splus_s, int32_t *cand,
-                           float *splus, float *skip) {
-    FAMST_LAUNCH(ex, scatter_kernel, nblk(n * 32, 256), 256, 0, P.perm, n, kp, cand_s, splus_s,
-                 P.skipQ, cand, splus, skip);
-    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
-}
 
 }  // namespace famst
