@@ -321,21 +321,31 @@ __device__ __forceinline__ uint64_t scan_side(const float *__restrict__ X, int d
 // (b) the current best weight squared, both widened by 2^-20 for the
 // rounding of sqrtf, cannot be the argmin under (w, id); the others are
 // decided on canonical weights, so the result equals scan_side's.
-// BF: the fast sums read the BF16 rows of hr (bounds in the distance domain
-// widened by hr's per-row error bounds, see h_bounds).
+// BF (G = NS, the BF16 row's 64-element segments): the fast value is
+// p~ = ||h_x||^2 + ||h_y||^2 - 2 h_x.h_y of the centred BF16 rows h, the dot
+// products on the tensor cores (warp_dot32_mma). |p~ - ||h_x - h_y||^2| <=
+// aerr (||h_x||^2 + ||h_y||^2) + 1e-35, and ||(h_y - h_x) - (y - x)|| <=
+// eb_x + eb_y, so in the distance domain sqrt(p~ -+ A) -+ (eb_x + eb_y),
+// widened by eps for the canonical sum's own error, bound w_canon; each
+// candidate's (eb, ||h||^2) comes from lst / rst, stored in list order.
 template <int G, bool BF>
 __device__ __forceinline__ uint64_t scan_side_filtered(
     const float *__restrict__ X, int d, int c, int fixed, int other, int want_comp, float w0,
     const int32_t *__restrict__ nbr, int k, const int32_t *__restrict__ rev_off,
     const int32_t *__restrict__ rev_src, const int32_t *__restrict__ comp, int lane, float rho,
     unsigned &evals, unsigned &canon, const __nv_bfloat16 *__restrict__ Hh, int hld,
-    const float *__restrict__ heb, const float *__restrict__ hm, float eps, bool check) {
+    const float *__restrict__ heb, const float *__restrict__ hn2,
+    const float2 *__restrict__ lst, const float2 *__restrict__ rst, float aerr, float eps,
+    bool check) {
     const float *xf = X + int64_t(fixed) * d;
-    float4 fx[4];
-    float ebx = 0.0f;
+    float4 fx[BF ? 1 : 4];
+    uint4 bx[BF ? G : 1];
+    float ebx = 0.0f, nx = 0.0f;
+    const int ns = hld >> 6;
     if constexpr (BF) {
-        row_slices_h<G>(xf, hm, d, lane, fx);
+        x_frag_mma<G>(Hh + int64_t(fixed) * hld, ns, lane, bx);
         ebx = heb[fixed];
+        nx = hn2[fixed];
     } else {
         row_slices_g<G, 4>(xf, d >> 2, lane, fx);
     }
@@ -347,8 +357,15 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
     for (int base = 0; base < deg; base += 32) {
         const int idx = base + lane;
         int cand = -1;
+        float2 en = make_float2(0.0f, 0.0f);
         if (idx < deg) {
-            cand = idx < k ? nbr[int64_t(c) * k + idx] : rev_src[r0 + idx - k];
+            if (idx < k) {
+                cand = nbr[int64_t(c) * k + idx];
+                if constexpr (BF) en = lst[int64_t(c) * k + idx];
+            } else {
+                cand = rev_src[r0 + idx - k];
+                if constexpr (BF) en = rst[r0 + idx - k];
+            }
             // G[c] ∩ C and u' != v: always true when comp labels the components
             // of this graph (a build); checked for caller-supplied labels
             if (check && (comp[cand] != want_comp || cand == other)) cand = -1;
@@ -358,8 +375,17 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
         if (lane == 0) evals += unsigned(__popc(live));
         float lo = inf, hi = inf, bound;
         if constexpr (BF) {   // distance domain
-            const float pf = warp_sqdist32h<G>(Hh, hld, fx, fixed, cand, lane);
-            if (cand >= 0) h_bounds(pf, rho, __fadd_ru(ebx, heb[cand]), eps, lo, hi);
+            const float dt = warp_dot32_mma<G>(Hh, hld, ns, bx, fixed, cand, lane);
+            if (cand >= 0) {
+                const float nn = __fadd_rn(nx, en.y);
+                const float pt = __fmaf_rn(-2.0f, dt, nn);
+                const float A = __fmaf_ru(nn, aerr, 1e-35f);
+                const float slo = __fsqrt_rd(fmaxf(__fsub_rd(pt, A), 0.0f));
+                const float shi = __fsqrt_ru(__fadd_ru(pt, A));
+                const float E = __fadd_ru(ebx, en.x);
+                lo = fmaxf(__fmul_rd(__fsub_rd(slo, E), 1.0f - eps), 0.0f);
+                hi = __fmul_ru(__fadd_ru(shi, E), 1.0f + eps);
+            }
             float mh = hi;
 #pragma unroll
             for (int o = 16; o >= 1; o >>= 1) mh = fminf(mh, __shfl_xor_sync(0xffffffffu, mh, o));
@@ -409,8 +435,9 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
                               unsigned long long *__restrict__ next_item, int *dstatus,
                               float rho, unsigned long long *__restrict__ evals_out,
                               const __nv_bfloat16 *__restrict__ Hh, int hld,
-                              const float *__restrict__ heb, const float *__restrict__ hm,
-                              float eps, bool check) {
+                              const float *__restrict__ heb, const float *__restrict__ hn2,
+                              const float2 *__restrict__ lst, const float2 *__restrict__ rst,
+                              float aerr, float eps, bool check) {
     if (m_dev) m = *m_dev < m ? *m_dev : m;  // device-side edge count, capped by capacity
     const int lane = threadIdx.x & 31;
     unsigned long long evals_total = 0, canon_total = 0;   // evaluations of this lane
@@ -441,8 +468,8 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
             // u-loop: u' in G[u] ∩ C_i, u' != v, against v
             if constexpr (G > 0)
                 bu = scan_side_filtered<G, BF>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src,
-                                               comp, lane, rho, evals, canon, Hh, hld, heb, hm,
-                                               eps, check);
+                                               comp, lane, rho, evals, canon, Hh, hld, heb, hn2,
+                                               lst, rst, aerr, eps, check);
             else
                 bu = scan_side<VEC>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp, lane,
                                     evals);
@@ -453,8 +480,8 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
                 bv = mv_b;
             else if constexpr (G > 0)
                 bv = scan_side_filtered<G, BF>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src,
-                                               comp, lane, rho, evals, canon, Hh, hld, heb, hm,
-                                               eps, check);
+                                               comp, lane, rho, evals, canon, Hh, hld, heb, hn2,
+                                               lst, rst, aerr, eps, check);
             else
                 bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane,
                                     evals);
@@ -504,10 +531,13 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
                            const HalfRows &hr, bool check) {
     const int th = 256;
     const int G = (vec4 && d >= 32) ? sq_group(d) : 0;
-    const bool bf = hr.h != nullptr && (G == 4 || G == 8 || G == 16);
-    const void *fn = bf ? (G == 4 ? (const void *)refine_kernel<4, 4, true>
-                           : G == 8 ? (const void *)refine_kernel<4, 8, true>
-                                    : (const void *)refine_kernel<4, 16, true>)
+    // BF16 filter on the tensor cores: ns = ld / 64 segments, d <= 256
+    const int nsk = hr.ld >> 6;
+    const int GB = nsk <= 1 ? 1 : (nsk <= 2 ? 2 : 4);
+    const bool bf = hr.h != nullptr && hr.lst != nullptr && nsk >= 1 && nsk <= 4;
+    const void *fn = bf ? (GB == 1 ? (const void *)refine_kernel<4, 1, true>
+                           : GB == 2 ? (const void *)refine_kernel<4, 2, true>
+                                     : (const void *)refine_kernel<4, 4, true>)
                    : G == 2 ? (const void *)refine_kernel<4, 2, false>
                    : G == 4 ? (const void *)refine_kernel<4, 4, false>
                    : G == 8 ? (const void *)refine_kernel<4, 8, false>
@@ -527,14 +557,23 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
     const float rho = fast_rho(d, 1);
     // canonical distance vs the exact one, generously: (d + 16) u
     const float eps = float((d + 16) * std::ldexp(1.0, -24) * 1.1);
+    // |p~ - ||h_x - h_y||^2| <= aerr (||h_x||^2 + ||h_y||^2) + 1e-35: the BF16
+    // products are exact in FP32; a 16-term block sum aligned to its largest
+    // exponent and cut to 24 bits loses at most 17 2^-23 of its absolute sum,
+    // which gives about ld 2^-23 (||h_x||^2 + ||h_y||^2) for 2 h_x.h_y. Taken
+    // 16 times over (20 kept bits would still be covered), plus the norms'
+    // and the two final roundings; 1e-35 covers products flushed below the
+    // FP32 normal range.
+    const float aerr = float(hr.ld * std::ldexp(1.0, -19) + std::ldexp(1.0, -20));
 #define REFINE_LAUNCH(V, GG, B)                                                                  \
     FAMST_LAUNCH(ex, (refine_kernel<V, GG, B>), grid, th, 0, X, d, nbr, k, rev_off, rev_src,     \
                  comp, eu, ev, ew, eci, ecj, order, m, m_dev, max_iters, change_hist, next_item, \
-                 ex.dstatus, rho, evals, hr.h, hr.ld, hr.eb, hr.m, eps, check)
+                 ex.dstatus, rho, evals, hr.h, hr.ld, hr.eb, hr.n2, hr.lst, hr.rst, aerr, eps,   \
+                 check)
     if (bf) {
-        if (G == 4) REFINE_LAUNCH(4, 4, true);
-        else if (G == 8) REFINE_LAUNCH(4, 8, true);
-        else REFINE_LAUNCH(4, 16, true);
+        if (GB == 1) REFINE_LAUNCH(4, 1, true);
+        else if (GB == 2) REFINE_LAUNCH(4, 2, true);
+        else REFINE_LAUNCH(4, 4, true);
     } else {
         switch (G) {
             case 2: REFINE_LAUNCH(4, 2, false); break;
@@ -569,21 +608,28 @@ __global__ void half_mean_kernel(const float *__restrict__ X, int64_t n, int d,
 // subnormals. One warp per row.
 __global__ void half_rows_kernel(const float *__restrict__ X, int64_t n, int d, int ld,
                                  const float *__restrict__ m, __nv_bfloat16 *__restrict__ h,
-                                 float *__restrict__ eb) {
+                                 float *__restrict__ eb, float *__restrict__ n2) {
     const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
-    float acc = 0.0f;
+    float acc = 0.0f, acch = 0.0f;
     for (int t = lane; t < ld; t += 32) {
         const float x = t < d ? __fsub_rn(__ldg(X + r * d + t), __ldg(m + t)) : 0.0f;
-        h[r * ld + t] = __float2bfloat16_rn(x);
+        const __nv_bfloat16 hb = __float2bfloat16_rn(x);
+        h[r * ld + t] = hb;
         acc = __fmaf_ru(x, x, acc);
+        const float hf = __bfloat162float(hb);
+        acch = __fmaf_rn(hf, hf, acch);
     }
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) acc = __fadd_ru(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+    for (int o = 16; o >= 1; o >>= 1) {
+        acc = __fadd_ru(acc, __shfl_xor_sync(0xffffffffu, acc, o));
+        acch = __fadd_rn(acch, __shfl_xor_sync(0xffffffffu, acch, o));
+    }
     if (lane == 0) {
         const float nrm = __fmul_ru(__fsqrt_ru(acc), 1.0f + 0x1p-12f);
         eb[r] = __fadd_ru(__fmul_ru(nrm, 0x1p-9f + 0x1p-21f), 1e-30f);
+        n2[r] = acch;   // within ld 2^-23 of ||h||^2
     }
 }
 
@@ -649,24 +695,52 @@ famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
 }
 
 size_t half_rows_workspace(int64_t n, int d) {
-    const int ld = (d + 7) / 8 * 8;
-    return align256(size_t(n) * ld * 2) + align256(size_t(n) * 4) + align256(size_t(d) * 4);
+    const int ld = (d + 63) / 64 * 64;
+    return align256(size_t(n) * ld * 2) + align256(size_t(n) * 4) * 2 + align256(size_t(d) * 4);
 }
 
 famst_status half_rows(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
                        HalfRows *out) {
-    const int ld = (d + 7) / 8 * 8;
+    const int ld = (d + 63) / 64 * 64;
     __nv_bfloat16 *h = ar.take<__nv_bfloat16>(size_t(n) * ld);
     float *eb = ar.take<float>(size_t(n));
+    float *n2 = ar.take<float>(size_t(n));
     float *m = ar.take<float>(size_t(d));
-    if (!h || !eb || !m) return FAMST_ERR_OOM;
+    if (!h || !eb || !n2 || !m) return FAMST_ERR_OOM;
     FAMST_LAUNCH(ex, half_mean_kernel, 1, 256, 0, X, n, d, m);
     FAMST_LAUNCH(ex, half_rows_kernel, unsigned((n * 32 + 255) / 256), 256, 0, X, n, d, ld, m, h,
-                 eb);
+                 eb, n2);
     out->h = h;
     out->ld = ld;
     out->eb = eb;
     out->m = m;
+    out->n2 = n2;
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+}
+
+__global__ void half_rows_lists_kernel(const float *__restrict__ eb, const float *__restrict__ n2,
+                                       const int32_t *__restrict__ idx, int64_t cnt,
+                                       float2 *__restrict__ out) {
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int32_t y = idx[i];
+    out[i] = make_float2(eb[y], n2[y]);
+}
+
+size_t half_rows_lists_workspace(int64_t n, int k) { return align256(size_t(n) * k * 8) * 2; }
+
+famst_status half_rows_lists(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t n, int k,
+                             const int32_t *rev_src, HalfRows *hr) {
+    if (!hr->h) return FAMST_OK;
+    const int64_t cnt = n * k;   // the reverse lists hold n k entries too
+    float2 *lst = ar.take<float2>(size_t(cnt));
+    float2 *rst = ar.take<float2>(size_t(cnt));
+    if (!lst || !rst) return FAMST_ERR_OOM;
+    const unsigned gr = unsigned((cnt + 255) / 256);
+    FAMST_LAUNCH(ex, half_rows_lists_kernel, gr, 256, 0, hr->eb, hr->n2, nbr, cnt, lst);
+    FAMST_LAUNCH(ex, half_rows_lists_kernel, gr, 256, 0, hr->eb, hr->n2, rev_src, cnt, rst);
+    hr->lst = lst;
+    hr->rst = rst;
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 

@@ -267,36 +267,6 @@ __device__ __forceinline__ float f2_hsum(unsigned long long a) {
     return __fadd_rn(lo, hi);
 }
 
-// Fast squared distance of global row y and row f (any address space, read
-// with plain loads), d % 4 == 0, both 16-byte aligned: eight independent
-// chains of fl(y_t - f_t)^2 (four packed accumulators), then a tree of
-// three adds -- at most d / 8 + 4 roundings on any path, inside the bound
-// fast_rho states for the warp-wide sums.
-__device__ __forceinline__ float row_sqdist_fast(const float *__restrict__ y, const float *f,
-                                                 int d) {
-    const float4 *y4 = reinterpret_cast<const float4 *>(y);
-    const float4 *f4 = reinterpret_cast<const float4 *>(f);
-    const int d4 = d >> 2;
-    unsigned long long a0 = 0ull, a1 = 0ull, a2 = 0ull, a3 = 0ull;
-    int q = 0;
-#pragma unroll 2
-    for (; q + 2 <= d4; q += 2) {
-        const float4 ya = __ldg(y4 + q), yb = __ldg(y4 + q + 1);
-        const float4 fa = f4[q], fb = f4[q + 1];
-        a0 = f2_sqacc(f2_sub(f2_pack(ya.x, ya.y), f2_pack(fa.x, fa.y)), a0);
-        a1 = f2_sqacc(f2_sub(f2_pack(ya.z, ya.w), f2_pack(fa.z, fa.w)), a1);
-        a2 = f2_sqacc(f2_sub(f2_pack(yb.x, yb.y), f2_pack(fb.x, fb.y)), a2);
-        a3 = f2_sqacc(f2_sub(f2_pack(yb.z, yb.w), f2_pack(fb.z, fb.w)), a3);
-    }
-    if (q < d4) {
-        const float4 ya = __ldg(y4 + q);
-        const float4 fa = f4[q];
-        a0 = f2_sqacc(f2_sub(f2_pack(ya.x, ya.y), f2_pack(fa.x, fa.y)), a0);
-        a1 = f2_sqacc(f2_sub(f2_pack(ya.z, ya.w), f2_pack(fa.z, fa.w)), a1);
-    }
-    return f2_hsum(f2_add(f2_add(a0, a1), f2_add(a2, a3)));
-}
-
 // Grouped warp-wide fast squared distances. Every candidate row is read by
 // a group of G lanes (float4 columns g, g + G, ..., V of them per lane,
 // G V 4 >= d), so 32 / G rows are read per load instruction, each
@@ -395,87 +365,76 @@ __device__ __forceinline__ float warp_pairsq32g(const float *__restrict__ X, int
     return a >= 0 ? tot : 0.0f;
 }
 
-// BF16 filter rows: h = bf16(fl(x - m)) (row stride ld = d rounded up to 8,
-// zero beyond d) and eb >= ||bf16(fl(x - m)) - (x - m)|| per row, so for two
-// rows ||(h_y - h_x) - (y - x)|| <= eb_x + eb_y. Grouped like the FP32 sums:
-// G lanes per row, two uint4 (16 BF16 values) per lane, 16 G >= d; the
-// fixed point's slices fx hold fl(x - m) in FP32 for the same elements.
-__device__ __forceinline__ unsigned long long bf16x2_lo_hi(uint32_t w) {
-    return f2_pack(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+// mma.sync m16n8k16 BF16 -> FP32 (D = A B + C), the warp-level tensor
+// instruction; used for 32-candidate dot products where a tcgen05 tile
+// would be mostly empty.
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint32_t a1,
+                                               uint32_t a2, uint32_t a3, uint32_t b0,
+                                               uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-template <int G>
-__device__ __forceinline__ void row_slices_h(const float *__restrict__ x,
-                                             const float *__restrict__ m, int d, int lane,
-                                             float4 (&f)[4]) {
-    const int g = lane % G;
+// Dot products h_j . h_x of the 32 lanes' candidate rows with one BF16 row
+// h_x (rows of stride ld, a multiple of 64, zero padded; ns = ld / 64 <= NS
+// segments of 64 elements). Four m16n8k16 tiles of 8 candidates each. Every
+// candidate takes two rows of A: the first and the second 32 elements of
+// each segment (rows 2 q and 2 q + 1 for candidate q < 4 of the tile, rows
+// 8 + 2 q and 9 + 2 q for candidate 4 + q), so the 8 lanes of two quads read
+// 128 contiguous bytes of one row per load; columns 0 and 1 of B hold the
+// matching halves of h_x, and candidate q's dot product is D[2q][0] +
+// D[2q + 1][1]. Inside a segment the k order is permuted: lane t of a quad
+// loads 8 consecutive elements and feeds them to two k-chunks, and h_x's
+// fragment (x_frag_mma, lanes 0-7) follows the same permutation, so every
+// product pairs equal elements. Lane j gets candidate j's dot product (0 for
+// cand < 0).
+template <int NS>
+__device__ __forceinline__ void x_frag_mma(const __nv_bfloat16 *__restrict__ hx, int ns, int lane,
+                                           uint4 (&bx)[NS]) {
 #pragma unroll
-    for (int v = 0; v < 2; ++v) {
-        const int e0 = 8 * (g + G * v);
+    for (int sg = 0; sg < NS; ++sg) {
+        bx[sg] = make_uint4(0u, 0u, 0u, 0u);
+        if (sg < ns && lane < 8)
+            bx[sg] = __ldg(reinterpret_cast<const uint4 *>(hx + 64 * sg + 8 * lane));
+    }
+}
+
+template <int NS>
+__device__ __forceinline__ float warp_dot32_mma(const __nv_bfloat16 *__restrict__ H, int ld,
+                                                int ns, const uint4 (&bx)[NS], int fixed,
+                                                int cand, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    const int half = g & 1, q = g >> 1;
+    float res = 0.0f;
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int e = e0 + 4 * hh;   // x and m rows are 16-byte aligned, d % 4 == 0
-            float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (e < d) {
-                const float4 a = __ldg(reinterpret_cast<const float4 *>(x + e));
-                const float4 b = __ldg(reinterpret_cast<const float4 *>(m + e));
-                r = make_float4(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z),
-                                __fsub_rn(a.w, b.w));
+    for (int T = 0; T < 4; ++T) {
+        const int ia = __shfl_sync(0xffffffffu, cand, 8 * T + q);
+        const int ib = __shfl_sync(0xffffffffu, cand, 8 * T + 4 + q);
+        const uint4 *ra = reinterpret_cast<const uint4 *>(
+            H + int64_t(ia >= 0 ? ia : fixed) * ld + 32 * half + 8 * t);
+        const uint4 *rb = reinterpret_cast<const uint4 *>(
+            H + int64_t(ib >= 0 ? ib : fixed) * ld + 32 * half + 8 * t);
+        float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int sg = 0; sg < NS; ++sg) {
+            if (sg < ns) {
+                const uint4 u = __ldg(ra + 8 * sg), v = __ldg(rb + 8 * sg);
+                mma_bf16_16816(c, u.x, v.x, u.y, v.y, bx[sg].x, bx[sg].y);
+                mma_bf16_16816(c, u.z, v.z, u.w, v.w, bx[sg].z, bx[sg].w);
             }
-            f[2 * v + hh] = r;
         }
+        // lane 8 q: D[2q][0] (c[0]) and D[8 + 2q][0] (c[2]); lane 8 q + 4:
+        // D[2q + 1][1] (c[1]) and D[9 + 2q][1] (c[3])
+        const float s0 = __fadd_rn(c[0], __shfl_xor_sync(0xffffffffu, c[1], 4));
+        const float s1 = __fadd_rn(c[2], __shfl_xor_sync(0xffffffffu, c[3], 4));
+        const float v0 = __shfl_sync(0xffffffffu, s0, 8 * (lane & 3));
+        const float v1 = __shfl_sync(0xffffffffu, s1, 8 * (lane & 3));
+        if ((lane >> 3) == T) res = (lane & 4) ? v1 : v0;
     }
-}
-
-__device__ __forceinline__ unsigned long long sq8_h(uint4 y, const float4 &f0, const float4 &f1,
-                                                    unsigned long long a) {
-    a = f2_sqacc(f2_sub(bf16x2_lo_hi(y.x), f2_pack(f0.x, f0.y)), a);
-    a = f2_sqacc(f2_sub(bf16x2_lo_hi(y.y), f2_pack(f0.z, f0.w)), a);
-    a = f2_sqacc(f2_sub(bf16x2_lo_hi(y.z), f2_pack(f1.x, f1.y)), a);
-    a = f2_sqacc(f2_sub(bf16x2_lo_hi(y.w), f2_pack(f1.z, f1.w)), a);
-    return a;
-}
-
-template <int G>
-__device__ __forceinline__ float warp_sqdist32h(const __nv_bfloat16 *__restrict__ H, int ld,
-                                                const float4 (&fx)[4], int fixed, int cand,
-                                                int lane) {
-    constexpr int R = 32 / G;
-    const int nq = ld >> 3, g = lane % G, h = lane / G;
-    float acc[G];
-#pragma unroll
-    for (int s = 0; s < G; ++s) {
-        const int id = __shfl_sync(0xffffffffu, cand, s * R + h);
-        const uint4 *row = reinterpret_cast<const uint4 *>(H + int64_t(id >= 0 ? id : fixed) * ld);
-        unsigned long long a0 = 0ull, a1 = 0ull;
-        if (g < nq) a0 = sq8_h(__ldg(row + g), fx[0], fx[1], a0);
-        if (g + G < nq) a1 = sq8_h(__ldg(row + g + G), fx[2], fx[3], a1);
-        acc[s] = f2_hsum(f2_add(a0, a1));
-    }
-#pragma unroll
-    for (int o = G / 2; o >= 1; o >>= 1) {
-        const bool up = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const float send = up ? acc[i] : acc[i + o];
-            const float keep = up ? acc[i + o] : acc[i];
-            acc[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
-        }
-    }
-    const float tot = __shfl_sync(0xffffffffu, acc[0], (lane % R) * G + lane / R);
-    return cand >= 0 ? tot : 0.0f;
-}
-
-// Bounds on the canonical distance from a BF16 fast sum pf (FP32 sum of the
-// BF16 differences, within 1 +- rho of their exact sum), the rows' error
-// bounds E = eb_x + eb_y and the canonical error eps: directed rounding
-// keeps lo <= w_canon <= hi.
-__device__ __forceinline__ void h_bounds(float pf, float rho, float E, float eps, float &lo,
-                                         float &hi) {
-    const float slo = __fsqrt_rd(fmaxf(__fmul_rd(pf, 1.0f - rho), 0.0f));
-    const float shi = __fsqrt_ru(__fmul_ru(pf, 1.0f + rho));
-    lo = fmaxf(__fmul_rd(__fsub_rd(slo, E), 1.0f - eps), 0.0f);
-    hi = __fmul_ru(__fadd_ru(shi, E), 1.0f + eps);
+    return cand >= 0 ? res : 0.0f;
 }
 
 // Lanes per row for the grouped sums with V = 4 float4 per lane (0: d too
@@ -641,17 +600,25 @@ famst_status reverse_csr(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t 
 size_t reverse_csr_workspace(int64_t n, int k);
 
 // connect_refine.cu
-// BF16 copies of the points for the Alg. 4 filter (see warp_sqdist32h);
+// BF16 copies of the points for the Alg. 4 filter (see warp_dot32_mma);
 // h == nullptr: the filter reads the FP32 rows.
 struct HalfRows {
     const __nv_bfloat16 *h = nullptr;
-    int ld = 0;
+    int ld = 0;                  // multiple of 64, zero beyond d
     const float *eb = nullptr;   // per-row error bound
     const float *m = nullptr;    // the centre m (d values)
+    const float *n2 = nullptr;   // per row: ||h||^2 (FP32 sum of the exact squares)
+    // (eb, n2) of the points of the kNN lists (n k entries, in nbr's order)
+    // and of the reverse lists (in rev_src's order): one coalesced load per
+    // 32 candidates instead of one scattered load per candidate
+    const float2 *lst = nullptr, *rst = nullptr;
 };
 size_t half_rows_workspace(int64_t n, int d);
 famst_status half_rows(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
                        HalfRows *out);
+size_t half_rows_lists_workspace(int64_t n, int k);
+famst_status half_rows_lists(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t n, int k,
+                             const int32_t *rev_src, HalfRows *hr);
 famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
                            const int32_t *members, const int32_t *comp_off, int64_t t,
                            int lambda, uint64_t seed, int32_t *eu, int32_t *ev, float *ew,
