@@ -219,16 +219,20 @@ struct TcArgs {
 
 template <int KC>
 __device__ __forceinline__ void list_insert(float (&ls)[KC], int (&lj)[KC], float s, int j) {
+    // (s, j) goes before the first entry greater than s; the entries from
+    // there on move one place up. Every slot is computed from the old
+    // ls[p - 1], ls[p] and s alone (no value carried from slot to slot), so
+    // the KC updates are independent instructions rather than one chain.
 #pragma unroll
-    for (int p = 0; p < KC; ++p) {
-        bool sw = s < ls[p];
-        float ts = ls[p];
-        int tj = lj[p];
-        ls[p] = sw ? s : ts;
-        lj[p] = sw ? j : tj;
-        s = sw ? ts : s;
-        j = sw ? tj : j;
+    for (int p = KC - 1; p >= 1; --p) {
+        const bool up = ls[p - 1] > s;   // the entry below moves here
+        const bool here = ls[p] > s;
+        ls[p] = up ? ls[p - 1] : (here ? s : ls[p]);
+        lj[p] = up ? lj[p - 1] : (here ? j : lj[p]);
     }
+    const bool here0 = ls[0] > s;
+    ls[0] = here0 ? s : ls[0];
+    lj[0] = here0 ? j : lj[0];
 }
 
 template <int KC, bool MASK>
