@@ -553,24 +553,40 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 // ------------------------------------------------------------- prep
 
 // per-block column sums (double) over a contiguous range of rows
+// (the rows in order, eight loads in flight per thread)
 __global__ void colsum_partial_kernel(const float *__restrict__ X, int64_t n, int d, int rows_per,
                                       double *__restrict__ part) {
     int64_t r0 = int64_t(blockIdx.x) * rows_per;
     int64_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
     for (int c = threadIdx.x; c < d; c += blockDim.x) {
         double s = 0.0;
-        for (int64_t r = r0; r < r1; ++r) s += double(X[r * d + c]);
+        int64_t r = r0;
+        for (; r + 8 <= r1; r += 8) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = __ldg(X + (r + q) * d + c);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s += double(v[q]);
+        }
+        for (; r < r1; ++r) s += double(__ldg(X + r * d + c));
         part[int64_t(blockIdx.x) * d + c] = s;
     }
 }
 
+// one block per column: strided partial sums, then a tree in shared memory
 __global__ void colsum_final_kernel(const double *__restrict__ part, int nb, int d, int64_t n,
                                     float *__restrict__ mean) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= d) return;
+    __shared__ double red[256];
+    const int c = blockIdx.x;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[int64_t(b) * d + c];
-    mean[c] = float(s / double(n));
+    for (int b = threadIdx.x; b < nb; b += 256) s += part[int64_t(b) * d + c];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o >= 1; o >>= 1) {
+        if (int(threadIdx.x) < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mean[c] = float(red[0] / double(n));
 }
 
 // One warp per row: centred row, BF16 hi (and lo) operand rows, FP32 norm.
@@ -1013,7 +1029,7 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         return FAMST_ERR_OOM;
     // prep: mean, centred BF16 operands, norms
     FAMST_LAUNCH(ex, colsum_partial_kernel, nb, 128, 0, X, n, d, rows_per, part);
-    FAMST_LAUNCH(ex, colsum_final_kernel, (d + 127) / 128, 128, 0, part, nb, d, n, mean);
+    FAMST_LAUNCH(ex, colsum_final_kernel, d, 256, 0, part, nb, d, n, mean);
     if (cudaMemsetAsync(ymax, 0, 4, ex.stream) != cudaSuccess ||
         cudaMemsetAsync(fail_count, 0, 4, ex.stream) != cudaSuccess)
         return FAMST_ERR_CUDA;

@@ -168,17 +168,17 @@ __global__ void gather_f32_kernel(const float *__restrict__ X, int d,
 }
 
 // R_c: upper bound on the distance of every member of cell c to its pivot
+// (members read from the sorted copy Xs, pivots from X)
 template <int FR>
-__global__ void radius_kernel(const float *__restrict__ X, int d, int64_t n,
-                              const int32_t *__restrict__ perm, const uint32_t *__restrict__ skey,
+__global__ void radius_kernel(const float *__restrict__ X, const float *__restrict__ Xs, int d,
+                              int64_t n, const uint32_t *__restrict__ skey,
                               const int32_t *__restrict__ piv, const int32_t *__restrict__ order,
                               float rho, unsigned *__restrict__ R_bits) {
     const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
     const int c = int(skey[r]);
-    const float s =
-        warp_sqdist1<FR>(X + int64_t(perm[r]) * d, X + int64_t(piv[order[c]]) * d, d, lane);
+    const float s = warp_sqdist1<FR>(Xs + r * d, X + int64_t(piv[order[c]]) * d, d, lane);
     if (lane == 0) {
         const float h = __fmul_ru(__fsqrt_ru(sq_hi(s, rho)), 1.0f + 0x1p-22f);
         atomicMax(R_bits + c, __float_as_uint(h));
@@ -189,8 +189,8 @@ __global__ void radius_kernel(const float *__restrict__ X, int d, int64_t n,
 // tile Q, from k other points next to each row in the sorted order, taken
 // inside the row's group of cells when the group holds k + 1 points
 template <int G>
-__global__ void tau_kernel(const float *__restrict__ X, int d, int64_t n, int k,
-                           const int32_t *__restrict__ perm, const uint32_t *__restrict__ skey,
+__global__ void tau_kernel(const float *__restrict__ Xs, int d, int64_t n, int k,
+                           const uint32_t *__restrict__ skey,
                            const int32_t *__restrict__ cstart, const int32_t *__restrict__ gfirst,
                            const int32_t *__restrict__ glast, float rho,
                            unsigned *__restrict__ tau_bits) {
@@ -209,15 +209,16 @@ __global__ void tau_kernel(const float *__restrict__ X, int d, int64_t n, int k,
     }
     int64_t w0 = r - k / 2;
     w0 = w0 < lo ? lo : (w0 > hi ? hi : w0);
-    const int self = int(perm[r]);
+    // rows of the sorted copy: the row itself and its k + 1 window neighbours
+    // sit next to each other in memory
     float4 fx[4];
-    row_slices_g<G, 4>(X + int64_t(self) * d, d >> 2, lane, fx);
+    row_slices_g<G, 4>(Xs + r * d, d >> 2, lane, fx);
     float t = 0.0f;
     for (int base = 0; base < k + 1; base += 32) {
         const int idx = base + lane;
         const int64_t pos = w0 + idx;
-        const int cand = (idx < k + 1 && pos != r) ? int(perm[pos]) : -1;
-        const float s = warp_sqdist32g<G, 4>(X, d, fx, self, cand, lane);
+        const int cand = (idx < k + 1 && pos != r) ? int(pos) : -1;
+        const float s = warp_sqdist32g<G, 4>(Xs, d, fx, int(r), cand, lane);
         if (cand >= 0) t = fmaxf(t, __fmul_ru(__fsqrt_ru(sq_hi(s, rho)), 1.0f + 0x1p-22f));
     }
 #pragma unroll
@@ -225,7 +226,8 @@ __global__ void tau_kernel(const float *__restrict__ X, int d, int64_t n, int k,
     if (lane == 0) atomicMax(tau_bits + r / QT, __float_as_uint(t));
 }
 
-// DP[a][b] <= |p_a - p_b|: warp per (a, 32 consecutive b)
+// DP[a][b] <= |p_a - p_b| for b >= a (the upper triangle; dp_mirror_kernel
+// copies it to the lower one): warp per (a, 32 consecutive b)
 template <int G>
 __global__ void pivot_dist_kernel(const float *__restrict__ X, int d, int K,
                                   const int32_t *__restrict__ piv, float rho,
@@ -235,26 +237,35 @@ __global__ void pivot_dist_kernel(const float *__restrict__ X, int d, int K,
     const int nbb = (K + 31) / 32;
     if (w >= int64_t(K) * nbb) return;
     const int a = int(w / nbb);
-    const int b = int(w % nbb) * 32 + lane;
+    const int bb = int(w % nbb);
+    if (bb * 32 + 31 < a) return;   // the whole block lies below the diagonal
+    const int b = bb * 32 + lane;
     const int pa = piv[a];
     float4 fx[4];
     row_slices_g<G, 4>(X + int64_t(pa) * d, d >> 2, lane, fx);
     const int cand = b < K ? piv[b] : -1;
     const float s = warp_sqdist32g<G, 4>(X, d, fx, pa, cand, lane);
-    if (b < K)
+    if (b < K && b >= a)
         DP[int64_t(a) * K + b] =
             a == b ? 0.0f : __fmul_rd(__fsqrt_rd(sq_lo(s, rho)), 1.0f - 0x1p-22f);
 }
 
-// DP[a][b] = DP[b][a] = the smaller of the two bounds (both are valid)
-__global__ void sym_kernel(float *__restrict__ DP, int K) {
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= int64_t(K) * K) return;
-    const int a = int(t / K), b = int(t % K);
-    if (b <= a) return;
-    const float v = fminf(DP[int64_t(a) * K + b], DP[int64_t(b) * K + a]);
-    DP[int64_t(a) * K + b] = v;
-    DP[int64_t(b) * K + a] = v;
+// DP[b][a] = DP[a][b] for b > a: 32 x 32 tiles of the upper triangle,
+// transposed through shared memory (coalesced on both sides)
+__global__ void dp_mirror_kernel(float *__restrict__ DP, int K) {
+    __shared__ float tile[32][33];
+    const int ta = blockIdx.y, tb = blockIdx.x;   // tile rows a, columns b
+    if (tb < ta) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8 threads
+    for (int r = ty; r < 32; r += 8) {
+        const int a = ta * 32 + r, b = tb * 32 + tx;
+        tile[r][tx] = (a < K && b < K) ? DP[int64_t(a) * K + b] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int b = tb * 32 + r, a = ta * 32 + tx;   // write row b, column a
+        if (a < K && b < K && b > a) DP[int64_t(b) * K + a] = tile[tx][r];
+    }
 }
 
 // Boruvka step on the complete pivot graph: nearest pivot of another
@@ -320,9 +331,8 @@ __global__ void tile_cells_kernel(const uint32_t *__restrict__ skey, int64_t n, 
 // Ball radius of every open tile: the largest distance (rounded up) of its
 // rows to its centre pivot, one warp per sorted row
 template <int FR>
-__global__ void tile_radius_kernel(const float *__restrict__ X, int d, int64_t n,
-                                   const int32_t *__restrict__ perm,
-                                   const int32_t *__restrict__ piv,
+__global__ void tile_radius_kernel(const float *__restrict__ X, const float *__restrict__ Xs,
+                                   int d, int64_t n, const int32_t *__restrict__ piv,
                                    const int32_t *__restrict__ order,
                                    const int32_t *__restrict__ qc, const int32_t *__restrict__ kc,
                                    float rho, float *__restrict__ qR, float *__restrict__ kR) {
@@ -330,7 +340,7 @@ __global__ void tile_radius_kernel(const float *__restrict__ X, int d, int64_t n
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
     const int64_t q = r / QT, t = r / KT;
-    const float *x = X + int64_t(perm[r]) * d;
+    const float *x = Xs + r * d;
     if (qR[q] > -1.0f) {
         const float s = warp_sqdist1<FR>(x, X + int64_t(piv[order[qc[2 * q]]]) * d, d, lane);
         if (lane == 0)
@@ -620,7 +630,7 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     const int64_t nbb = (K + 31) / 32;
     const int fr = d <= 128 ? 1 : (d <= 256 ? 2 : 4);
     const int G = sq_group(d);
-    // 1. pivot distances (lower bounds, symmetric)
+    // 1. pivot distances (lower bounds; computed once per unordered pair)
     const unsigned pgrid = nblk(int64_t(K) * nbb * 32, 256);
     switch (G) {
         case 2: FAMST_LAUNCH(ex, pivot_dist_kernel<2>, pgrid, 256, 0, X, d, K, piv, rho, DP); break;
@@ -629,7 +639,10 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
         case 16: FAMST_LAUNCH(ex, pivot_dist_kernel<16>, pgrid, 256, 0, X, d, K, piv, rho, DP); break;
         default: FAMST_LAUNCH(ex, pivot_dist_kernel<32>, pgrid, 256, 0, X, d, K, piv, rho, DP);
     }
-    FAMST_LAUNCH(ex, sym_kernel, nblk(int64_t(K) * K, 256), 256, 0, DP, K);
+    {
+        const unsigned nt = unsigned((K + 31) / 32);
+        FAMST_LAUNCH(ex, dp_mirror_kernel, dim3(nt, nt), dim3(32, 8), 0, DP, K);
+    }
     // 2. order of the cells: minimum spanning tree of the pivots (Boruvka)
     famst_status st;
     {
@@ -687,16 +700,16 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     // 4. balls and radii of interest
     const unsigned wgrid = nblk(n * 32, 256);
     if (fr == 1)
-        FAMST_LAUNCH(ex, radius_kernel<1>, wgrid, 256, 0, X, d, n, perm, keys, piv, order, rho,
+        FAMST_LAUNCH(ex, radius_kernel<1>, wgrid, 256, 0, X, Xs, d, n, keys, piv, order, rho,
                      reinterpret_cast<unsigned *>(R));
     else if (fr == 2)
-        FAMST_LAUNCH(ex, radius_kernel<2>, wgrid, 256, 0, X, d, n, perm, keys, piv, order, rho,
+        FAMST_LAUNCH(ex, radius_kernel<2>, wgrid, 256, 0, X, Xs, d, n, keys, piv, order, rho,
                      reinterpret_cast<unsigned *>(R));
     else
-        FAMST_LAUNCH(ex, radius_kernel<4>, wgrid, 256, 0, X, d, n, perm, keys, piv, order, rho,
+        FAMST_LAUNCH(ex, radius_kernel<4>, wgrid, 256, 0, X, Xs, d, n, keys, piv, order, rho,
                      reinterpret_cast<unsigned *>(R));
 #define TAU(GG)                                                                                  \
-    FAMST_LAUNCH(ex, tau_kernel<GG>, wgrid, 256, 0, X, d, n, k, perm, keys, cstart, gfirst, glast, \
+    FAMST_LAUNCH(ex, tau_kernel<GG>, wgrid, 256, 0, Xs, d, n, k, keys, cstart, gfirst, glast,     \
                  rho, reinterpret_cast<unsigned *>(tauQ))
     switch (G) {
         case 2: TAU(2); break;
@@ -710,13 +723,13 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     FAMST_LAUNCH(ex, tile_cells_kernel, nblk(nq > nk ? nq : nk, 256), 256, 0, keys, n, nq, nk, qc,
                  kc, qR, kR);
     if (fr == 1)
-        FAMST_LAUNCH(ex, tile_radius_kernel<1>, wgrid, 256, 0, X, d, n, perm, piv, order, qc, kc,
+        FAMST_LAUNCH(ex, tile_radius_kernel<1>, wgrid, 256, 0, X, Xs, d, n, piv, order, qc, kc,
                      rho, qR, kR);
     else if (fr == 2)
-        FAMST_LAUNCH(ex, tile_radius_kernel<2>, wgrid, 256, 0, X, d, n, perm, piv, order, qc, kc,
+        FAMST_LAUNCH(ex, tile_radius_kernel<2>, wgrid, 256, 0, X, Xs, d, n, piv, order, qc, kc,
                      rho, qR, kR);
     else
-        FAMST_LAUNCH(ex, tile_radius_kernel<4>, wgrid, 256, 0, X, d, n, perm, piv, order, qc, kc,
+        FAMST_LAUNCH(ex, tile_radius_kernel<4>, wgrid, 256, 0, X, Xs, d, n, piv, order, qc, kc,
                      rho, qR, kR);
     // visit unless LB > tau (1 + margin): the margin covers the canonical
     // rounding on both sides of the certificate's comparison
