@@ -58,34 +58,53 @@ __global__ void bv_init_kernel(int32_t *comp, int64_t n) {
     if (v < n) comp[v] = int32_t(v);
 }
 
+// Lanes of a warp whose edges end in the same component first take the
+// minimum of their keys (match + two 32-bit reductions: the weight bits,
+// then the smaller id among the lanes holding the minimum weight), and one
+// lane per component issues the atomic: in the late rounds, where few
+// components remain, millions of edges would otherwise hit the same few
+// addresses. The result is the same minimum.
+__device__ __forceinline__ void warp_min_to(unsigned long long *__restrict__ best, int c,
+                                            unsigned long long key, int lane) {
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const unsigned hi = unsigned(key >> 32), lo = unsigned(key);
+    const unsigned mhi = __reduce_min_sync(peers, hi);
+    const unsigned mlo = __reduce_min_sync(peers, hi == mhi ? lo : 0xffffffffu);
+    if (c >= 0 && lane == __ffs(peers) - 1)
+        atomicMin(best + c, (uint64_t(mhi) << 32) | mlo);
+}
+
 __global__ void bv_min1_kernel(EdgeSrc es, const int32_t *__restrict__ comp,
                                unsigned long long *__restrict__ best1, const int *__restrict__ done,
                                int32_t *__restrict__ ou = nullptr, int32_t *__restrict__ ov = nullptr,
                                float *__restrict__ ow = nullptr,
                                unsigned long long *__restrict__ ocount = nullptr) {
     if (done && *done) return;
-    int64_t total = es.total();
+    const int64_t total = es.total();
     const int lane = threadIdx.x & 31;
-    for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
-         e += int64_t(gridDim.x) * blockDim.x) {
-        int a, b;
-        float w;
-        es.get(e, a, b, w);
-        int ca = comp[a], cb = comp[b];
-        const bool inter = ca != cb;
-        if (inter) {
-            unsigned long long key1 = (uint64_t(__float_as_uint(w)) << 32) | uint32_t(a < b ? a : b);
-            atomicMin(best1 + ca, key1);
-            atomicMin(best1 + cb, key1);
+    // whole warps step together (the warp-wide reductions need every lane)
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t e0 = int64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31); e0 < total;
+         e0 += stride) {
+        const int64_t e = e0 + lane;
+        int a = 0, b = 0, ca = -1, cb = -1;
+        float w = 0.0f;
+        if (e < total) {
+            es.get(e, a, b, w);
+            ca = comp[a];
+            cb = comp[b];
         }
+        const bool inter = e < total && ca != cb;
+        const unsigned long long key1 =
+            (uint64_t(__float_as_uint(w)) << 32) | uint32_t(a < b ? a : b);
+        warp_min_to(best1, inter ? ca : -1, key1, lane);
+        warp_min_to(best1, inter ? cb : -1, key1, lane);
         if (ocount) {   // append the edges between components, one atomic per warp
-            const unsigned act = __activemask();
-            const unsigned bal = __ballot_sync(act, inter);
+            const unsigned bal = __ballot_sync(0xffffffffu, inter);
             if (bal) {
-                const int leader = __ffs(act) - 1;
                 unsigned long long base = 0;
-                if (lane == leader) base = atomicAdd(ocount, (unsigned long long)__popc(bal));
-                base = __shfl_sync(act, base, leader);
+                if (lane == 0) base = atomicAdd(ocount, (unsigned long long)__popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0);
                 if (inter) {
                     const unsigned long long idx = base + __popc(bal & ((1u << lane) - 1u));
                     ou[idx] = a;

@@ -213,11 +213,14 @@ __global__ void tau_kernel(const float *__restrict__ Xs, int d, int64_t n, int k
     // sit next to each other in memory
     float4 fx[4];
     row_slices_g<G, 4>(Xs + r * d, d >> 2, lane, fx);
+    // the window w0 .. w0 + k always holds r (w0 <= r <= w0 + k), so its
+    // other k positions are the candidates: candidate idx sits at w0 + idx,
+    // or one further on from r
     float t = 0.0f;
-    for (int base = 0; base < k + 1; base += 32) {
+    for (int base = 0; base < k; base += 32) {
         const int idx = base + lane;
-        const int64_t pos = w0 + idx;
-        const int cand = (idx < k + 1 && pos != r) ? int(pos) : -1;
+        const int64_t pos = w0 + idx + (w0 + idx >= r ? 1 : 0);
+        const int cand = idx < k ? int(pos) : -1;
         const float s = warp_sqdist32g<G, 4>(Xs, d, fx, int(r), cand, lane);
         if (cand >= 0) t = fmaxf(t, __fmul_ru(__fsqrt_ru(sq_hi(s, rho)), 1.0f + 0x1p-22f));
     }
