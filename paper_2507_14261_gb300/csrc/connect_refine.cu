@@ -110,7 +110,7 @@ __global__ void connect_kernel(const float *__restrict__ X, int d,
 // pairs have p_canon <= that bound, so every pair of the exact top lambda
 // (w, s) survives, and the selection below sees the same winners.
 template <int PER, int G>
-__global__ void connect_filtered_kernel(const float *__restrict__ X, int d,
+__global__ void __launch_bounds__(256, 4) connect_filtered_kernel(const float *__restrict__ X, int d,
                                         const int32_t *__restrict__ members,
                                         const int32_t *__restrict__ comp_off, int64_t t,
                                         int lambda, uint64_t seed, float rho,

@@ -747,7 +747,7 @@ __global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int
 // mostly cell-mates, so they sit close together in memory), keyed and
 // written with their original ids.
 template <int VEC, int KC>
-__global__ void rerank_sorted_kernel(const float *__restrict__ Xs, int64_t n, int d, int k,
+__global__ void __launch_bounds__(256, 5) rerank_sorted_kernel(const float *__restrict__ Xs, int64_t n, int d, int k,
                                      const int32_t *__restrict__ cand,
                                      const float *__restrict__ splus,
                                      const float *__restrict__ skipQ,
