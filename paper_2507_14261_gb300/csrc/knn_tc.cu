@@ -50,7 +50,7 @@ constexpr int BK = 64;           // K elements per stage (one 128-byte swizzle a
 constexpr int A_BLOCK = BM * BK * 2;   // 16 KB
 constexpr int B_BLOCK = BN * BK * 2;   // 32 KB
 constexpr int CAPB = 24;         // staged candidates per row (flush check every 16 columns)
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS_MAX = 64 + 32 * 8;   // producer, MMA issuer, up to 8 epilogue warps
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
 
 // ------------------------------------------------------------ PTX helpers
@@ -152,36 +152,25 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
             smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-        "[%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
-// Wait for this thread's tcgen05.ld results. The registers of the load
-// being waited for are tied to the wait as in/out operands, so no use of
-// them can be scheduled before it.
-__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld_wait16(uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
                    "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
-                   "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
-                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
-                   "+r"(r[30]), "+r"(r[31])
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
                  :
                  : "memory");
 }
-__device__ __forceinline__ void epilogue_bar() {  // the four epilogue warps
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+__device__ __forceinline__ void epilogue_bar(int nthreads) {  // the epilogue warps only
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
@@ -215,6 +204,8 @@ struct TcArgs {
     const int32_t *colcomp;  // MASK: component of every (padded) row; pairs in one component are skipped
     const int32_t *klist;    // non-null: CTA key tiles are klist[kt0 .. kt1) instead of kt0 .. kt1
     int cross;               // queries and keys are different sets: no self-exclusion
+    int epi;                 // epilogue warps: 8 (two per TMEM lane quarter, each on half
+                             // of the columns) or 4 (0 reads as 4)
 };
 
 template <int KC>
@@ -236,7 +227,7 @@ __device__ __forceinline__ void list_insert(float (&ls)[KC], int (&lj)[KC], floa
 }
 
 template <int KC, bool MASK>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(KC <= 2 * CAPB ? TC_THREADS_MAX : 64 + 32 * 4, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               TcArgs args) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -257,11 +248,15 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     const int nA = (args.x3 ? 2 : 1) * nkb;           // resident A blocks
     unsigned char *sA = base;
     unsigned char *sB = sA + size_t(nA) * A_BLOCK;
+    const int EPI = args.epi == 8 ? 8 : 4;
+    const int NH = EPI / 4;                           // column halves (1 or 2)
+    // staging [NH][CAPB][BM] scores and ids; with two halves, the second
+    // half's final list ([KC][BM], KC <= 2 CAPB) reuses it for the merge
     float *stg_s = reinterpret_cast<float *>(sB + size_t(args.stages) * B_BLOCK);
-    int *stg_j = reinterpret_cast<int *>(stg_s + CAPB * BM);
-    float *sny = reinterpret_cast<float *>(stg_j + CAPB * BM);   // [2][BN] key norms
-    int *scm = reinterpret_cast<int *>(sny + 2 * BN);            // [2][BN] key components (MASK)
-    uint64_t *bars = reinterpret_cast<uint64_t *>(scm + 2 * BN);
+    int *stg_j = reinterpret_cast<int *>(stg_s + NH * CAPB * BM);
+    volatile float *thr_sh = reinterpret_cast<volatile float *>(stg_j + NH * CAPB * BM);  // [2][BM]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(
+        reinterpret_cast<unsigned char *>(stg_j + NH * CAPB * BM) + 2 * BM * 4);
     uint64_t *full = bars;                       // [stages]
     uint64_t *empty = bars + args.stages;        // [stages]
     uint64_t *a_full = bars + 2 * args.stages;
@@ -283,7 +278,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         mbar_init(a_full, 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
+            mbar_init(&tempty[b], EPI);
         }
         mbar_init(mma_done, 1);
         *abort_flag = 0;
@@ -293,6 +288,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         tmem_alloc(tmem_slot, 512);
         tmem_relinquish();
     }
+    for (int x = threadIdx.x; x < 2 * BM; x += blockDim.x) thr_sh[x] = __int_as_float(0x7f800000);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -385,6 +381,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     } else {
         // ------------------------------------------------ epilogue
         const int quarter = warp & 3;               // TMEM lanes 32*quarter ..
+        const int half = (warp - 2) >> 2;           // columns [half * ncols, + ncols)
+        const int ncols = BN / NH;
+        const int col0 = half * ncols;
         const int row = quarter * 32 + lane;
         const int i = q0 + row;
         float ls[KC];
@@ -396,32 +395,33 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         }
         float thr = __int_as_float(0x7f800000);
         int cnt = 0;
-        float *my_s = stg_s + row;
-        int *my_j = stg_j + row;
+        float *my_s = stg_s + half * CAPB * BM + row;
+        int *my_j = stg_j + half * CAPB * BM + row;
+        // With two halves each list sees half the columns. A score at or above
+        // the other list's KC-th is not in the row's KC smallest (that list
+        // alone holds KC scores below it), so both filter with the smaller
+        // of the two thresholds.
+        auto partner_thr = [&]() {
+            return NH == 2 ? thr_sh[(1 - half) * BM + row] : __int_as_float(0x7f800000);
+        };
         auto flush = [&]() {
             const int mx = __reduce_max_sync(0xffffffffu, cnt);
+            const float pt = partner_thr();
             for (int q = 0; q < mx; ++q) {
                 if (q < cnt) {
                     float sv = my_s[q * BM];
                     int jv = my_j[q * BM];
-                    if ((args.cross || jv != i) && sv < ls[KC - 1]) list_insert<KC>(ls, lj, sv, jv);
+                    if ((args.cross || jv != i) && sv < fminf(ls[KC - 1], pt))
+                        list_insert<KC>(ls, lj, sv, jv);
                 }
             }
             cnt = 0;
-            thr = ls[KC - 1];
+            if (NH == 2) thr_sh[half * BM + row] = ls[KC - 1];
+            thr = fminf(ls[KC - 1], pt);
         };
         bool ok = true;
-        const int e_id = (warp - 2) * 32 + lane;   // 0..127 within the epilogue warps
-        const int kt_first = ntiles > 0 ? ktile(0) : 0;
-        float ny_next0 = __ldg(args.ny + size_t(kt_first) * BN + e_id);
-        float ny_next1 = __ldg(args.ny + size_t(kt_first) * BN + 128 + e_id);
-        int cm_next0 = 0, cm_next1 = 0, my_comp = 0;
-        if constexpr (MASK) {
-            cm_next0 = __ldg(args.colcomp + size_t(kt_first) * BN + e_id);
-            cm_next1 = __ldg(args.colcomp + size_t(kt_first) * BN + 128 + e_id);
-            my_comp = __ldg(args.colcomp + i);
-        }
-        int kt_cur = kt_first;
+        int my_comp = 0;
+        if constexpr (MASK) my_comp = __ldg(args.colcomp + i);
         for (int t = 0; t < ntiles; ++t) {
             const int b = t & 1, use = t >> 1;
             // every lane waits; the warp proceeds only if all lanes saw the phase
@@ -431,45 +431,34 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 break;
             }
             tc_fence_after();
-            const uint32_t tb = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * BN);
-            // key norms of this tile into shared memory (double buffered by b;
-            // the barrier of tile t-1 orders every read of buffer b from tile
-            // t-2 before these writes)
-            sny[b * BN + e_id] = ny_next0;
-            sny[b * BN + 128 + e_id] = ny_next1;
-            if constexpr (MASK) {
-                scm[b * BN + e_id] = cm_next0;
-                scm[b * BN + 128 + e_id] = cm_next1;
+            const uint32_t tb =
+                tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * BN + col0);
+            const int kt_this = ktile(t);
+            // key norms (and components) of this tile's columns straight from
+            // global memory: every lane reads the same addresses (L1 broadcast);
+            // the next tile's are prefetched into L1 meanwhile
+            const float *nyt = args.ny + size_t(kt_this) * BN + col0;
+            const int *cmt = MASK ? args.colcomp + size_t(kt_this) * BN + col0 : nullptr;
+            if (t + 1 < ntiles && lane < ncols / 32) {
+                const size_t nxt = size_t(ktile(t + 1)) * BN + col0 + 32 * lane;
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(args.ny + nxt));
+                if constexpr (MASK) asm volatile("prefetch.global.L1 [%0];" ::"l"(args.colcomp + nxt));
             }
-            const int kt_this = kt_cur;
-            if (t + 1 < ntiles) {   // the next tile's norms load under this tile's work
-                kt_cur = ktile(t + 1);
-                const float *g = args.ny + size_t(kt_cur) * BN;
-                ny_next0 = __ldg(g + e_id);
-                ny_next1 = __ldg(g + 128 + e_id);
-                if constexpr (MASK) {
-                    const int32_t *gc = args.colcomp + size_t(kt_cur) * BN;
-                    cm_next0 = __ldg(gc + e_id);
-                    cm_next1 = __ldg(gc + 128 + e_id);
-                }
-            }
-            epilogue_bar();
-            const float *nyt = sny + b * BN;
-            const int *cmt = scm + b * BN;
-            // Candidate staging for 32 columns. The divergent parts only touch
-            // this lane's stage; the warp-collective flush checks sit at
-            // warp-uniform points between the two 16-column halves.
-            auto process = [&](uint32_t(&v)[32], int ch) {
-                float mn0 = __int_as_float(0x7f800000), mn1 = mn0;
+            thr = fminf(thr, partner_thr());
+            // Candidate staging for 16 columns. The divergent part only touches
+            // this lane's stage; the warp-collective flush check sits at a
+            // warp-uniform point after it.
+            auto process = [&](uint32_t(&v)[16], int ch) {
+                float mn = __int_as_float(0x7f800000);
 #pragma unroll
-                for (int c4 = 0; c4 < 8; ++c4) {
-                    float4 nn = *reinterpret_cast<const float4 *>(nyt + ch * 32 + 4 * c4);
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const float4 nn = __ldg(reinterpret_cast<const float4 *>(nyt + ch * 16 + 4 * c4));
                     float s0 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 0]), nn.x);
                     float s1 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 1]), nn.y);
                     float s2 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 2]), nn.z);
                     float s3 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 3]), nn.w);
                     if constexpr (MASK) {  // same component: not a candidate
-                        const int4 cc = *reinterpret_cast<const int4 *>(cmt + ch * 32 + 4 * c4);
+                        const int4 cc = __ldg(reinterpret_cast<const int4 *>(cmt + ch * 16 + 4 * c4));
                         const float inf = __int_as_float(0x7f800000);
                         s0 = cc.x == my_comp ? inf : s0;
                         s1 = cc.y == my_comp ? inf : s1;
@@ -480,11 +469,10 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                     v[4 * c4 + 1] = __float_as_uint(s1);
                     v[4 * c4 + 2] = __float_as_uint(s2);
                     v[4 * c4 + 3] = __float_as_uint(s3);
-                    float m4 = fminf(fminf(s0, s1), fminf(s2, s3));
-                    if (c4 < 4) mn0 = fminf(mn0, m4); else mn1 = fminf(mn1, m4);
+                    mn = fminf(mn, fminf(fminf(s0, s1), fminf(s2, s3)));
                 }
-                const int j0 = kt_this * BN + ch * 32;
-                if (mn0 < thr) {
+                const int j0 = kt_this * BN + col0 + ch * 16;
+                if (mn < thr) {
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
                         float sc = __uint_as_float(v[c]);
@@ -495,35 +483,24 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         }
                     }
                 }
-                // at most 16 more per half: flush before a stage could overflow
-                if (__any_sync(0xffffffffu, cnt > CAPB - 16)) flush();
-                if (mn1 < thr) {
-#pragma unroll
-                    for (int c = 16; c < 32; ++c) {
-                        float sc = __uint_as_float(v[c]);
-                        if (sc < thr) {
-                            my_s[cnt * BM] = sc;
-                            my_j[cnt * BM] = j0 + c;
-                            ++cnt;
-                        }
-                    }
-                }
+                // at most 16 more per chunk: flush before a stage could overflow
                 if (__any_sync(0xffffffffu, cnt > CAPB - 16)) flush();
             };
-            // two register buffers: the load of chunk c+1 overlaps the
+            // two 16-column register buffers: the load of chunk c+1 overlaps the
             // processing of chunk c
-            uint32_t va[32], vb[32];
+            const int nch = ncols / 16;
+            uint32_t va[16], vb[16];
             __syncwarp();
-            tmem_ld32(tb, va);
+            tmem_ld16(tb, va);
 #pragma unroll 1
-            for (int ch = 0; ch < BN / 32; ch += 2) {
-                tmem_ld_wait(va);
+            for (int ch = 0; ch < nch; ch += 2) {
+                tmem_ld_wait16(va);
                 __syncwarp();
-                tmem_ld32(tb + (ch + 1) * 32, vb);
+                tmem_ld16(tb + (ch + 1) * 16, vb);
                 process(va, ch);
-                tmem_ld_wait(vb);
+                tmem_ld_wait16(vb);
                 __syncwarp();
-                if (ch + 2 < BN / 32) tmem_ld32(tb + (ch + 2) * 32, va);
+                if (ch + 2 < nch) tmem_ld16(tb + (ch + 2) * 16, va);
                 process(vb, ch + 1);
             }
             tc_fence_before();
@@ -531,7 +508,28 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             if (lane == 0) mbar_arrive(&tempty[b]);
         }
         flush();
-        if (ok && i < row_end) {
+        if (NH == 2) {
+            // merge: the second half's list goes through shared memory into the
+            // first half's (every epilogue warp reaches both barriers, on the
+            // error path too)
+            epilogue_bar(32 * EPI);
+            if (half == 1) {
+#pragma unroll
+                for (int p = 0; p < KC; ++p) {
+                    stg_s[p * BM + row] = ls[p];
+                    stg_j[p * BM + row] = lj[p];
+                }
+            }
+            epilogue_bar(32 * EPI);
+            if (half == 0) {
+                for (int p = 0; p < KC; ++p) {   // ascending: stop at the first that cannot enter
+                    const float sv = stg_s[p * BM + row];
+                    if (!(sv < ls[KC - 1])) break;
+                    list_insert<KC>(ls, lj, sv, stg_j[p * BM + row]);
+                }
+            }
+        }
+        if (ok && half == 0 && i < row_end) {
             if constexpr (KC == 1) {   // top-1 mode: the best key and its score
                 args.cand[i - shift] = lj[0] >= 0 ? lj[0] - shift : -1;
             } else {
@@ -954,12 +952,14 @@ __global__ void top1_merge_kernel(const int32_t *__restrict__ c2, const float *_
 }
 
 struct TcPlan {
-    int d_pad, nkb, kh, stages, kc;
+    int d_pad, nkb, kh, stages, kc, epi;
     int64_t nq_tiles, nk_tiles;
     size_t smem;
 };
 
-TcPlan tc_plan(int64_t n, int d, int k, bool x3) {
+// allow8: eight epilogue warps when the candidate lists fit the merge area
+// (KC <= 2 CAPB) and the larger staging area still leaves three B stages
+TcPlan tc_plan(int64_t n, int d, int k, bool x3, bool allow8 = true) {
     TcPlan p{};
     p.d_pad = (d + BK - 1) / BK * BK;
     p.nkb = p.d_pad / BK;
@@ -969,13 +969,20 @@ TcPlan tc_plan(int64_t n, int d, int k, bool x3) {
     p.kc = (k <= 21) ? 32 : (k <= 37 ? 48 : 64);
     p.nq_tiles = (n + BM - 1) / BM;
     p.nk_tiles = (n + BN - 1) / BN;
-    const size_t fixed = 1024 + size_t(x3 ? 2 : 1) * p.nkb * A_BLOCK + size_t(CAPB) * BM * 8 +
-                         4 * BN * 4 + 512;
     const size_t cap = 227 * 1024;
-    int st = cap > fixed ? int((cap - fixed) / B_BLOCK) : 0;
-    if (st > 6) st = 6;
-    p.stages = st;
-    p.smem = fixed + size_t(st) * B_BLOCK;
+    auto fixed_for = [&](int nh) {
+        return 1024 + size_t(x3 ? 2 : 1) * p.nkb * A_BLOCK + size_t(nh) * CAPB * BM * 8 +
+               2 * BM * 4 + 512;
+    };
+    auto stages_for = [&](size_t fixed) {
+        int st = cap > fixed ? int((cap - fixed) / B_BLOCK) : 0;
+        return st > 6 ? 6 : st;
+    };
+    const int st8 = stages_for(fixed_for(2));
+    p.epi = (allow8 && p.kc <= 2 * CAPB && st8 >= 3) ? 8 : 4;
+    const size_t fixed = fixed_for(p.epi / 4);
+    p.stages = stages_for(fixed);
+    p.smem = fixed + size_t(p.stages) * B_BLOCK;
     return p;
 }
 
@@ -993,7 +1000,7 @@ size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prun
     if (prune) {
         const int64_t K = prune_pivots_max(n), Kpad = (K + BN - 1) / BN * BN;
         b += align256(size_t(K) * 4) + align256(size_t(K) * p.kh * 2) +
-             align256(size_t(Kpad + BN) * 4) + align256(size_t(n) * 4) * 2;
+             align256(size_t(Kpad + BN) * 4) * 2 + align256(size_t(n) * 4) * 2;
         b += prune_workspace(n, d, p.kh, p.kc - 1, p.nq_tiles, p.nk_tiles);
     }
     b += align256(size_t(n) * p.kh * 2);                   // operand rows
@@ -1048,7 +1055,10 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         int32_t *piv = ar.take<int32_t>(size_t(Kmax));
         __nv_bfloat16 *Hp = ar.take<__nv_bfloat16>(size_t(Kmax) * p.kh);
         float *nyp = ar.take<float>(size_t(Kpadmax + BN));   // +inf beyond the pivots
-        if (!piv || !Hp || !nyp) return FAMST_ERR_OOM;
+        // the pass's norms copied to an aligned buffer: the tile kernel reads
+        // them as float4 from tile starts, and k0 need not be a multiple of 4
+        float *nya = ar.take<float>(size_t(Kpadmax + BN));
+        if (!piv || !Hp || !nyp || !nya) return FAMST_ERR_OOM;
         famst_status st =
             prune_pivot_operands(ex, H, p.kh, ny, n, K0, Kpadmax + BN, piv, Hp, nyp);
         if (st != FAMST_OK) return st;
@@ -1061,9 +1071,13 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
             if (!make_map(&mA1, H, n, p.kh, BM) ||
                 !make_map(&mB1, Hp + size_t(k0) * p.kh, kc, p.kh, BN))
                 return FAMST_ERR_CUDA;
-            TcArgs a1{int(n), (kc + BN - 1) / BN, p.nkb, 0, p1.stages, nyp + k0, c_out, s_out,
-                      ex.dstatus, nullptr, nullptr, nullptr, 1};
-            FAMST_LAUNCH(ex, (knn_tc_kernel<1, false>), unsigned(p.nq_tiles), TC_THREADS, p1.smem,
+            const int nkt = (kc + BN - 1) / BN;
+            if (cudaMemcpyAsync(nya, nyp + k0, size_t(nkt) * BN * 4, cudaMemcpyDeviceToDevice,
+                                ex.stream) != cudaSuccess)
+                return FAMST_ERR_CUDA;
+            TcArgs a1{int(n), nkt, p.nkb, 0, p1.stages, nya, c_out, s_out,
+                      ex.dstatus, nullptr, nullptr, nullptr, 1, p1.epi};
+            FAMST_LAUNCH(ex, (knn_tc_kernel<1, false>), unsigned(p.nq_tiles), 64 + 32 * p1.epi, p1.smem,
                          mA1, mB1, a1);
             return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
         };
@@ -1108,13 +1122,13 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     }
     TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, use_prune ? P.nys : ny, cand_t,
              splus_t, ex.dstatus, use_prune ? P.tab : nullptr, cpad,
-             use_prune ? P.klist : nullptr, 0};
+             use_prune ? P.klist : nullptr, 0, p.epi};
 #define TC_LAUNCH(KCV, M)                                                                        \
     do {                                                                                         \
         if (set_smem_attr(knn_tc_kernel<KCV, M>, int(p.smem), ex.stream) != cudaSuccess)         \
             return FAMST_ERR_CUDA;                                                               \
-        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, M>), unsigned(p.nq_tiles), TC_THREADS, p.smem, mA,  \
-                     mB, a);                                                                     \
+        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, M>), unsigned(p.nq_tiles), 64 + 32 * p.epi, p.smem, \
+                     mA, mB, a);                                                                 \
     } while (0)
     if (cpad) {
         if (p.kc == 32) TC_LAUNCH(32, true);
@@ -1177,7 +1191,7 @@ namespace famst {
 // largest cloud's K extent).
 bool knn_tc_batched_plan(int D, int k, bool x3, int *stages, size_t *smem, int *kc) {
     if (k + 1 > 64) return false;
-    TcPlan p = tc_plan(int64_t(1) << 20, D, k, x3);
+    TcPlan p = tc_plan(int64_t(1) << 20, D, k, x3, false);   // four epilogue warps
     if (p.stages < 2 || encode_fn() == nullptr) return false;
     *stages = p.stages;
     *smem = p.smem;
@@ -1202,13 +1216,13 @@ famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, i
     FAMST_LAUNCH(ex, tc_prep_batched_kernel, unsigned((NP * 32 + 255) / 256), 256, 0, Xc, D, NP,
                  roff, voff, B, cl, D, int(x3), mean, H, ny, xn2, ymax);
     if (nctas > 0) {
-        TcArgs a{0, 0, nkb, int(x3), stages, ny, cand, splus, ex.dstatus, tiles, nullptr, nullptr, 0};
+        TcArgs a{0, 0, nkb, int(x3), stages, ny, cand, splus, ex.dstatus, tiles, nullptr, nullptr, 0, 4};
 #define TCB_LAUNCH(KCV)                                                                          \
     do {                                                                                         \
         if (set_smem_attr(knn_tc_kernel<KCV, false>, \
                                  int(smem), ex.stream) != cudaSuccess)                                      \
             return FAMST_ERR_CUDA;                                                               \
-        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false>), unsigned(nctas), TC_THREADS, smem, *mA, *mB, a);   \
+        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false>), unsigned(nctas), 64 + 32 * 4, smem, *mA, *mB, a); \
     } while (0)
         if (kc == 32) TCB_LAUNCH(32);
         else if (kc == 48) TCB_LAUNCH(48);

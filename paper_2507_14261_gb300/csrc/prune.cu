@@ -358,8 +358,47 @@ __global__ void tile_radius_kernel(const float *__restrict__ X, const float *__r
     }
 }
 
+// Visit order inside every query tile's list: nearest key tiles first (by
+// the smallest pivot distance between their cells, then tile index), so the
+// candidate lists of the tile kernel fill with near points early and its
+// thresholds reject most keys of the later tiles. The set of tiles is the
+// same; lists longer than 1024 keep their ascending order.
+__global__ void __launch_bounds__(256) klist_sort_kernel(const int32_t *__restrict__ off,
+                                                         const float *__restrict__ kkey,
+                                                         int32_t *__restrict__ klist) {
+    __shared__ unsigned long long sk[1024];
+    const int Q = blockIdx.x;
+    const int s0 = off[Q], len = off[Q + 1] - s0;
+    if (len <= 1 || len > 1024) return;
+    int npow = 1;
+    while (npow < len) npow <<= 1;
+    // keys are distances >= 0: their bit patterns order like the values
+    for (int x = threadIdx.x; x < npow; x += blockDim.x)
+        sk[x] = x < len ? (uint64_t(__float_as_uint(kkey[s0 + x])) << 32) | uint32_t(klist[s0 + x])
+                        : ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= npow; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int x = threadIdx.x; x < npow; x += blockDim.x) {
+                const int y = x ^ stride;
+                if (y > x) {
+                    const bool asc = (x & size) == 0;
+                    const unsigned long long a = sk[x], b = sk[y];
+                    if ((a > b) == asc) {
+                        sk[x] = b;
+                        sk[y] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int x = threadIdx.x; x < len; x += blockDim.x) klist[s0 + x] = int32_t(uint32_t(sk[x]));
+}
+
 // Per query tile (one block): which key tiles to visit. FILL = false counts
-// them into cnt[Q]; FILL = true writes them, ascending, at klist + off[Q]
+// them into cnt[Q]; FILL = true writes them (ascending; klist_sort_kernel
+// then orders them nearest first) at klist + off[Q], with their sort keys,
 // and the smallest lower bound of the skipped tiles into skipQ[Q].
 template <bool FILL>
 __global__ void __launch_bounds__(256)
@@ -368,7 +407,7 @@ tile_pairs_kernel(const int32_t *__restrict__ qc, const int32_t *__restrict__ kc
                   int K, const float *__restrict__ DP, const float *__restrict__ R,
                   const float *__restrict__ tauQ, float margin, int32_t *__restrict__ cnt,
                   const int32_t *__restrict__ off, int32_t *__restrict__ klist,
-                  float *__restrict__ skipQ) {
+                  float *__restrict__ kkey, float *__restrict__ skipQ) {
     __shared__ int wsum[8];
     __shared__ float wmin[8];
     __shared__ int base_s;
@@ -388,7 +427,7 @@ tile_pairs_kernel(const int32_t *__restrict__ qc, const int32_t *__restrict__ kc
     for (int64_t c0 = 0; c0 < nk; c0 += 256) {
         const int64_t T = c0 + threadIdx.x;
         bool visit = false;
-        float lb = inf;
+        float lb = inf, dmin = inf;
         if (T < nk) {
             const int b0 = kc[2 * T], b1 = kc[2 * T + 1];
             const float kball = kR[T];
@@ -396,8 +435,10 @@ tile_pairs_kernel(const int32_t *__restrict__ qc, const int32_t *__restrict__ kc
             for (int q = 0; q < NPMAX; ++q) {
                 if (a0 + q > a1) break;
                 const float *dp = DP + int64_t(a0 + q) * K;
-                for (int b = b0; b <= b1; ++b)
+                for (int b = b0; b <= b1; ++b) {
                     lb = fminf(lb, __fsub_rd(__fsub_rd(dp[b], ra[q]), kball >= 0.0f ? kball : R[b]));
+                    dmin = fminf(dmin, dp[b]);
+                }
             }
             visit = !(lb > tau);
             if (!visit) smin = fminf(smin, lb);
@@ -408,7 +449,11 @@ tile_pairs_kernel(const int32_t *__restrict__ qc, const int32_t *__restrict__ kc
             __syncthreads();
             int pre = base_s;
             for (int w = 0; w < warp; ++w) pre += wsum[w];
-            if (visit) klist[off[Q] + pre + __popc(bal & ((1u << lane) - 1u))] = int32_t(T);
+            if (visit) {
+                const int at = off[Q] + pre + __popc(bal & ((1u << lane) - 1u));
+                klist[at] = int32_t(T);
+                kkey[at] = dmin;   // nearest pivot pair of the two tiles' cells
+            }
             __syncthreads();
             if (threadIdx.x == 0) {
                 int s = 0;
@@ -547,7 +592,7 @@ size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk)
     b += align256(size_t(nq) * 8) + align256(size_t(nk) * 8);                  // tile cells
     b += align256(size_t(nq) * 4) + align256(size_t(nk) * 4);                  // tile balls
     b += align256(size_t(nq + 1) * 4) * 2 + scan_workspace(nq + 1) + 256;      // counts, offsets
-    b += align256(size_t(nq) * nk * 4);                                        // lists (worst case)
+    b += align256(size_t(nq) * nk * 4) * 2;                                    // lists, keys (worst case)
     b += align256(size_t(nq) * 4) + align256(size_t(nq) * sizeof(TcTile));     // skip, table
     b += align256(size_t(n) * kp * 4) + align256(size_t(n) * 4);               // sorted outputs
     b += align256(size_t(n) * d * 4);                                          // sorted points
@@ -614,6 +659,7 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     int32_t *cnt = ar.take<int32_t>(size_t(nq + 1));
     int32_t *off = ar.take<int32_t>(size_t(nq + 1));
     int32_t *klist = ar.take<int32_t>(size_t(nq) * nk);
+    float *kkey = ar.take<float>(size_t(nq) * nk);
     float *skipQ = ar.take<float>(size_t(nq));
     TcTile *tab = ar.take<TcTile>(size_t(nq));
     int32_t *total = ar.take<int32_t>(1);
@@ -621,7 +667,7 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     if (!Xs) return FAMST_ERR_OOM;
     if (!keys || !perm || !ccount || !cstart || !Hs || !nys || !R || !tauQ || !DP || !DPr || !ord ||
         !tu || !tv || !tw || !nb || !nw || !qc || !kc || !qR || !kR || !cnt || !off || !klist ||
-        !skipQ || !tab ||
+        !kkey || !skipQ || !tab ||
         !total)
         return FAMST_ERR_OOM;
     const float rho = fast_rho(d, 4);
@@ -738,7 +784,7 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     // rounding on both sides of the certificate's comparison
     const float margin = float(1.0 + 4.0 * (d + 4) * std::ldexp(1.0, -24) + std::ldexp(1.0, -20));
     FAMST_LAUNCH(ex, tile_pairs_kernel<false>, unsigned(nq), 256, 0, qc, kc, qR, kR, nk, K, DPr, R,
-                 tauQ, margin, cnt, nullptr, nullptr, nullptr);
+                 tauQ, margin, cnt, nullptr, nullptr, nullptr, nullptr);
     {
         const size_t mark = ar.off;
         st = exclusive_scan_i32(ex, ar, cnt, off, nq + 1, total);
@@ -746,7 +792,8 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
         if (st != FAMST_OK) return st;
     }
     FAMST_LAUNCH(ex, tile_pairs_kernel<true>, unsigned(nq), 256, 0, qc, kc, qR, kR, nk, K, DPr, R,
-                 tauQ, margin, nullptr, off, klist, skipQ);
+                 tauQ, margin, nullptr, off, klist, kkey, skipQ);
+    FAMST_LAUNCH(ex, klist_sort_kernel, unsigned(nq), 256, 0, off, kkey, klist);
     FAMST_LAUNCH(ex, table_kernel, nblk(nq, 256), 256, 0, off, nq, nkb, n, tab);
     out->perm = perm;
     out->Hs = Hs;
