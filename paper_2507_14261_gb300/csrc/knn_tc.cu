@@ -592,26 +592,57 @@ __global__ void tc_prep_kernel(const float *__restrict__ X, int64_t n, int d, in
                                const float *__restrict__ mean, __nv_bfloat16 *__restrict__ H,
                                float *__restrict__ ny, float *__restrict__ xnorm,
                                unsigned *__restrict__ ymax_bits) {
-    int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (row >= n) return;
-    const int kh = (x3 ? 2 : 1) * d_pad;
-    __nv_bfloat16 *h = H + row * kh;
-    float acc = 0.0f;
-    for (int t = lane; t < d_pad; t += 32) {
-        float xc = t < d ? __fsub_rn(X[row * d + t], mean[t]) : 0.0f;
-        __nv_bfloat16 hi = __float2bfloat16_rn(xc);
-        h[t] = hi;
-        if (x3) h[d_pad + t] = __float2bfloat16_rn(__fsub_rn(xc, __bfloat162float(hi)));
-        acc = fmaf(xc, xc, acc);
-    }
+    __shared__ unsigned bmax;
+    if (threadIdx.x == 0) bmax = 0u;
+    __syncthreads();
+    const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row < n) {
+        const int kh = (x3 ? 2 : 1) * d_pad;
+        __nv_bfloat16 *h = H + row * kh;
+        const float *x = X + row * d;
+        float acc = 0.0f;
+        // four coordinates per lane per step (16-byte rows), else one
+        const bool v4 = (d & 3) == 0 && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+        if (v4) {
+            for (int t = 4 * lane; t < d_pad; t += 128) {
+                float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (t < d) {
+                    const float4 a = __ldg(reinterpret_cast<const float4 *>(x + t));
+                    const float4 m = __ldg(reinterpret_cast<const float4 *>(mean + t));
+                    xv = make_float4(__fsub_rn(a.x, m.x), __fsub_rn(a.y, m.y), __fsub_rn(a.z, m.z),
+                                     __fsub_rn(a.w, m.w));
+                }
+                const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+                __nv_bfloat16 hi[4], lo[4];
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-        ny[row] = acc;
-        xnorm[row] = acc;
-        atomicMax(ymax_bits, __float_as_uint(sqrtf(acc)));
+                for (int q = 0; q < 4; ++q) {
+                    hi[q] = __float2bfloat16_rn(xs[q]);
+                    lo[q] = __float2bfloat16_rn(__fsub_rn(xs[q], __bfloat162float(hi[q])));
+                    acc = fmaf(xs[q], xs[q], acc);
+                }
+                *reinterpret_cast<uint2 *>(h + t) = *reinterpret_cast<const uint2 *>(hi);
+                if (x3) *reinterpret_cast<uint2 *>(h + d_pad + t) = *reinterpret_cast<const uint2 *>(lo);
+            }
+        } else {
+            for (int t = lane; t < d_pad; t += 32) {
+                float xc = t < d ? __fsub_rn(x[t], mean[t]) : 0.0f;
+                __nv_bfloat16 hi = __float2bfloat16_rn(xc);
+                h[t] = hi;
+                if (x3) h[d_pad + t] = __float2bfloat16_rn(__fsub_rn(xc, __bfloat162float(hi)));
+                acc = fmaf(xc, xc, acc);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            ny[row] = acc;
+            xnorm[row] = acc;
+            atomicMax(&bmax, __float_as_uint(sqrtf(acc)));   // one global atomic per block
+        }
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && bmax != 0u) atomicMax(ymax_bits, bmax);
 }
 
 __global__ void fill_inf_kernel(float *p, int64_t from, int64_t to) {

@@ -258,9 +258,23 @@ __global__ void weight_partial_kernel(const float *__restrict__ X, int d,
         if (X) {
             const float *a = X + int64_t(tu[e]) * d, *b = X + int64_t(tv[e]) * d;
             double p = 0.0;
-            for (int t = 0; t < d; ++t) {
-                double dl = double(a[t]) - double(b[t]);
-                p = fma(dl, dl, p);
+            if constexpr (VEC == 4) {   // the same sum, 16-byte loads
+                const float4 *a4 = reinterpret_cast<const float4 *>(a);
+                const float4 *b4 = reinterpret_cast<const float4 *>(b);
+                for (int q = 0; q < d / 4; ++q) {
+                    const float4 x = __ldg(a4 + q), y = __ldg(b4 + q);
+                    const double d0 = double(x.x) - double(y.x), d1 = double(x.y) - double(y.y);
+                    const double d2 = double(x.z) - double(y.z), d3 = double(x.w) - double(y.w);
+                    p = fma(d0, d0, p);
+                    p = fma(d1, d1, p);
+                    p = fma(d2, d2, p);
+                    p = fma(d3, d3, p);
+                }
+            } else {
+                for (int t = 0; t < d; ++t) {
+                    double dl = double(a[t]) - double(b[t]);
+                    p = fma(dl, dl, p);
+                }
             }
             s64 += sqrt(p);
         }
