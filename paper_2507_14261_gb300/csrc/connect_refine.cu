@@ -602,17 +602,18 @@ __global__ void half_mean_kernel(const float *__restrict__ X, int64_t n, int d,
     }
 }
 
-// h = bf16(fl(x - m)), zero beyond d; eb >= (2^-9 + 2^-23) ||fl(x - m)||
-// (BF16 and centring rounding, each coordinate within that relative error of
-// x - m) with margins for the FP32 norm and a tiny absolute term for BF16
-// subnormals. One warp per row.
+// h = bf16(fl(x - m)), zero beyond d; eb >= ||h - (x - m)||: the BF16
+// rounding error of this row itself, ||h - fl(x - m)|| (each difference
+// exact, squares summed rounding up), plus the centring rounding (each
+// coordinate within 2^-24 of x - m), with margins for the square roots and
+// a tiny absolute term for BF16 subnormals. One warp per row; n2 = ||h||^2.
 __global__ void half_rows_kernel(const float *__restrict__ X, int64_t n, int d, int ld,
                                  const float *__restrict__ m, __nv_bfloat16 *__restrict__ h,
                                  float *__restrict__ eb, float *__restrict__ n2) {
     const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
-    float acc = 0.0f, acch = 0.0f;
+    float acc = 0.0f, acch = 0.0f, accr = 0.0f;
     for (int t = lane; t < ld; t += 32) {
         const float x = t < d ? __fsub_rn(__ldg(X + r * d + t), __ldg(m + t)) : 0.0f;
         const __nv_bfloat16 hb = __float2bfloat16_rn(x);
@@ -620,15 +621,19 @@ __global__ void half_rows_kernel(const float *__restrict__ X, int64_t n, int d, 
         acc = __fmaf_ru(x, x, acc);
         const float hf = __bfloat162float(hb);
         acch = __fmaf_rn(hf, hf, acch);
+        const float e = __fsub_rn(hf, x);   // exact: hf is x rounded to 8 bits
+        accr = __fmaf_ru(e, e, accr);
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
         acc = __fadd_ru(acc, __shfl_xor_sync(0xffffffffu, acc, o));
         acch = __fadd_rn(acch, __shfl_xor_sync(0xffffffffu, acch, o));
+        accr = __fadd_ru(accr, __shfl_xor_sync(0xffffffffu, accr, o));
     }
     if (lane == 0) {
         const float nrm = __fmul_ru(__fsqrt_ru(acc), 1.0f + 0x1p-12f);
-        eb[r] = __fadd_ru(__fmul_ru(nrm, 0x1p-9f + 0x1p-21f), 1e-30f);
+        const float rnd = __fmul_ru(__fsqrt_ru(accr), 1.0f + 0x1p-12f);
+        eb[r] = __fadd_ru(__fadd_ru(rnd, __fmul_ru(nrm, 0x1p-22f)), 1e-30f);
         n2[r] = acch;   // within ld 2^-23 of ||h||^2
     }
 }
