@@ -407,6 +407,27 @@ def main():
                    "achieved": 3.0 * w.d * evals / (ms_refine / 1e3) / 1e12, "peak": fp32_peak,
                    "unit": "TFLOP/s", "distance_evals": evals, "kernel": "refine_kernel"},
     }
+    # dW/dX of the tree weight (the tree held fixed), after the timed builds:
+    # per vertex its own row, its tree neighbours' rows and its gradient row
+    # ((n - 1) d 4 B x 4 algorithmic bytes), timed on the library's stream
+    gx = torch.empty_like(X)
+    ctx.mst_backward(X, tree.u, tree.v, 1.0, out=gx)
+    b0 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    reps = 5
+    b0.record(stream)
+    for _ in range(reps):
+        ctx.mst_backward(X, tree.u, tree.v, 1.0, out=gx)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    ms_bwd = b0.elapsed_time(b1) / reps
+    bwd_bytes = (w.n - 1) * w.d * 4 * 4
+    kernels["backward"] = {"bound": "hbm", "ms": ms_bwd,
+                           "achieved": bwd_bytes / (ms_bwd / 1e3) / 1e9,
+                           "peak": pk["hbm_gbs"], "unit": "GB/s",
+                           "frac": bwd_bytes / (ms_bwd / 1e3) / 1e9 / pk["hbm_gbs"],
+                           "kernel": "famst_mst_backward (edge lengths, incidence sort, per-vertex sums)"}
+    del gx
     dom = "refine" if ms_refine >= ms_knn else "knn"
     kd = kernels[dom]
     traffic = (traffic_from_profile("refine_kernel", evals) if dom == "refine" else

@@ -340,12 +340,24 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
     const float *xf = X + int64_t(fixed) * d;
     float4 fx[BF ? 1 : 4];
     uint4 bx[BF ? G : 1];
+    // BF with rows of at most two segments (d <= 128): the fixed point's FP32
+    // coordinates lane, lane + 32, ... stay in registers for the survivors'
+    // canonical distances (same terms, same order as canon_p_warp)
+    constexpr int XR = (BF && G <= 2) ? 2 * G : 1;
+    float xr[XR];
     float ebx = 0.0f, nx = 0.0f;
     const int ns = hld >> 6;
     if constexpr (BF) {
         x_frag_mma<G>(Hh + int64_t(fixed) * hld, ns, lane, bx);
         ebx = heb[fixed];
         nx = hn2[fixed];
+        if constexpr (G <= 2) {
+#pragma unroll
+            for (int q = 0; q < XR; ++q) {
+                const int t = lane + 32 * q;
+                xr[q] = t < d ? __ldg(xf + t) : 0.0f;
+            }
+        }
     } else {
         row_slices_g<G, 4>(xf, d >> 2, lane, fx);
     }
@@ -409,7 +421,27 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
             const int sl = __ffs(sv) - 1;
             sv &= sv - 1;
             const int c2 = __shfl_sync(0xffffffffu, cand, sl);
-            const float w = __fsqrt_rn(canon_p_warp(X + int64_t(c2) * d, xf, d, lane));
+            float p;
+            if constexpr (BF && G <= 2) {
+                const float *yr = X + int64_t(c2) * d;
+                float yv[XR];
+#pragma unroll
+                for (int q = 0; q < XR; ++q) {
+                    const int t = lane + 32 * q;
+                    yv[q] = t < d ? __ldg(yr + t) : 0.0f;
+                }
+                p = 0.0f;
+#pragma unroll
+                for (int q = 0; q < XR; ++q) {
+                    const float dl = __fsub_rn(yv[q], xr[q]);
+                    p = __fmaf_rn(dl, dl, p);
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) p = __fadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
+            } else {
+                p = canon_p_warp(X + int64_t(c2) * d, xf, d, lane);
+            }
+            const float w = __fsqrt_rn(p);
             const uint64_t key = (uint64_t(__float_as_uint(w)) << 32) | uint32_t(c2 + 1);
             best = key < best ? key : best;   // the same in every lane
         }
