@@ -379,8 +379,9 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
                 if constexpr (BF) en = rst[r0 + idx - k];
             }
             // G[c] ∩ C and u' != v: always true when comp labels the components
-            // of this graph (a build); checked for caller-supplied labels
-            if (check && (comp[cand] != want_comp || cand == other)) cand = -1;
+            // of this graph (a build, the only user of the BF scan); checked
+            // for caller-supplied labels
+            if (!BF && check && (comp[cand] != want_comp || cand == other)) cand = -1;
         }
         const unsigned live = __ballot_sync(0xffffffffu, cand >= 0);
         if (live == 0u) continue;
@@ -566,7 +567,8 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
     // BF16 filter on the tensor cores: ns = ld / 64 segments, d <= 256
     const int nsk = hr.ld >> 6;
     const int GB = nsk <= 1 ? 1 : (nsk <= 2 ? 2 : 4);
-    const bool bf = hr.h != nullptr && hr.lst != nullptr && nsk >= 1 && nsk <= 4;
+    // (builds only: the BF scan trusts comp to label this graph's components)
+    const bool bf = hr.h != nullptr && hr.lst != nullptr && !check && nsk >= 1 && nsk <= 4;
     const void *fn = bf ? (GB == 1 ? (const void *)refine_kernel<4, 1, true>
                            : GB == 2 ? (const void *)refine_kernel<4, 2, true>
                                      : (const void *)refine_kernel<4, 4, true>)
