@@ -10,7 +10,9 @@
 //
 // Refine: one warp per edge. A sweep of Algorithm 4 scans G[u] (kNN list
 // of u plus its reverse edges) for the u' minimising w(u', v) and then
-// G[v] against the new u. With the running best starting at the edge's
+// G[v] against the new u (candidates first through a fast filter with
+// rigorous bounds, the survivors decided on canonical distances). With the
+// running best starting at the edge's
 // own weight and a strict "<", the paper's ascending scan keeps the first
 // (smallest id) of equal minima and keeps the incumbent on ties; that is
 // an argmin under the key (w, 1 + id) with the incumbent keyed (w, 0), so
@@ -551,9 +553,10 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
     }
 }
 
-// Launch of the refinement kernel in the variant the shape allows: the
-// filtered scan for 16-byte rows with 32 <= d <= 512, the per-lane
-// canonical distance per lane otherwise. Persistent grid; edges are fetched from
+// Launch of the refinement kernel in the variant the shape allows: in a
+// build with BF16 rows (hr, d <= 256), the tensor-core filter; else the
+// FP32 grouped filter for 16-byte rows with 32 <= d <= 512, else the
+// canonical distance per lane. Persistent grid; edges are fetched from
 // *next_item (zeroed by the caller).
 famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, const int32_t *nbr,
                            int k, const int32_t *rev_off, const int32_t *rev_src,

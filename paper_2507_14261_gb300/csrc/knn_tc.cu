@@ -8,20 +8,23 @@
 // hi/lo split x' ~ xh + xl (xh.yh + xl.yh + xh.yl), whose error is
 // O(2^-16) instead of O(2^-8).
 //
-// Kernel (one CTA per 128 query rows, 192 threads):
+// Kernel (one CTA per 128 query rows, 64 + 32 E threads, E = 8 or 4):
 //   warp 0     TMA producer: the query tile's operand rows once (resident),
 //              then 256-key tiles, one 64-wide K block per ring stage;
 //   warp 1     allocates 512 TMEM columns (two 128 x 256 FP32
 //              accumulators) and one lane issues tcgen05.mma (M=128, N=256,
 //              K=16 per instruction) with SW128 K-major smem descriptors;
 //              tcgen05.commit frees ring stages and publishes accumulators;
-//   warps 2-5  epilogue: thread r owns query row r (TMEM lane r). It loads
-//              32 columns at a time with tcgen05.ld, forms s = ny_j - 2 acc,
-//              and stages the columns that beat its row's threshold in shared
-//              memory. When any lane's stage is nearly full the warp merges
-//              all stages into per-row sorted register lists of the KC
-//              smallest scores (lanes insert in parallel), then tightens the
-//              threshold to the KC-th score.
+//   warps 2..  E epilogue warps: thread r of a warp owns query row r of its
+//              TMEM lane quarter; with E = 8 two warps share a quarter, each
+//              on half of the columns. It loads 16 columns at a time with
+//              tcgen05.ld, forms s = ny_j - 2 acc (key norms read from L1),
+//              and stages the columns that beat its row's threshold in
+//              shared memory. When any lane's stage is nearly full the warp
+//              merges all stages into per-row sorted register lists of the
+//              KC smallest scores (lanes insert in parallel), then tightens
+//              the threshold to the KC-th score (the smaller of the two
+//              halves' when E = 8); the halves' lists merge at the end.
 // Nothing of the n x n score matrix leaves the SM. Every mbarrier wait is
 // bounded in time; on expiry the CTA sets an error bit, drains its own
 // copies and MMAs, frees its TMEM and returns.
