@@ -558,9 +558,11 @@ size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk)
 famst_status prune_pivot_operands(const Exec &ex, const __nv_bfloat16 *H, int kh, const float *ny,
                                   int64_t n, int K, int Kpad, int32_t *piv, __nv_bfloat16 *Hp,
                                   float *nyp);
+// me (host): how many of the M new pivot slots hold distinct far points
+// (the others repeat one point); only those need scoring
 famst_status prune_augment(const Exec &ex, Arena &ar, const float *xn2, const float *s1, int64_t n,
                            const __nv_bfloat16 *H, int kh, const float *ny, int M, int K,
-                           int32_t *piv, __nv_bfloat16 *Hp, float *nyp);
+                           int32_t *piv, __nv_bfloat16 *Hp, float *nyp, int *me);
 famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, int64_t n, int k,
                              const __nv_bfloat16 *H, int kh, const float *ny, int nkb, int K,
                              const int32_t *piv, const int32_t *acand, int akp,

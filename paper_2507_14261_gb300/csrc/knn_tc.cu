@@ -1109,6 +1109,8 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
             if (cudaMemcpyAsync(nya, nyp + k0, size_t(nkt) * BN * 4, cudaMemcpyDeviceToDevice,
                                 ex.stream) != cudaSuccess)
                 return FAMST_ERR_CUDA;
+            if (kc < nkt * BN)   // columns beyond the pass's pivots never win
+                FAMST_LAUNCH(ex, fill_inf_kernel, 1, 256, 0, nya, int64_t(kc), int64_t(nkt) * BN);
             TcArgs a1{int(n), nkt, p.nkb, 0, p1.stages, nya, c_out, s_out,
                       ex.dstatus, nullptr, nullptr, nullptr, 1, p1.epi};
             FAMST_LAUNCH(ex, (knn_tc_kernel<1, false>), unsigned(p.nq_tiles), 64 + 32 * p1.epi, p1.smem,
@@ -1122,11 +1124,15 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         float *s2 = ar.take<float>(size_t(n));
         if (!c2 || !s2) return FAMST_ERR_OOM;
         for (int pass = 0; pass < 2 && st == FAMST_OK; ++pass) {
-            st = prune_augment(ex, ar, xn2, splus, n, H, p.kh, ny, M, K, piv, Hp, nyp);
-            if (st == FAMST_OK) st = assign(K, M, c2, s2);
-            if (st == FAMST_OK)
-                FAMST_LAUNCH(ex, top1_merge_kernel, unsigned((n + 255) / 256), 256, 0, c2, s2, K,
-                             n, cand, splus);
+            int me = 0;
+            st = prune_augment(ex, ar, xn2, splus, n, H, p.kh, ny, M, K, piv, Hp, nyp, &me);
+            // only the distinct new pivots are scored (the repeats add no cell)
+            if (st == FAMST_OK && me > 0) {
+                st = assign(K, me, c2, s2);
+                if (st == FAMST_OK)
+                    FAMST_LAUNCH(ex, top1_merge_kernel, unsigned((n + 255) / 256), 256, 0, c2, s2,
+                                 K, n, cand, splus);
+            }
             K += M;
         }
         if (st != FAMST_OK) return st;

@@ -94,7 +94,8 @@ __global__ void far_key_kernel(const float *__restrict__ xn2, const float *__res
 // pick j takes sorted entry floor(j F / Me), so the picks spread evenly over
 // the far points instead of piling into the few most isolated groups.
 __global__ void far_pick_kernel(const uint32_t *__restrict__ keys, const int32_t *__restrict__ vals,
-                                int64_t n, int M, int32_t *__restrict__ rows) {
+                                int64_t n, int M, int32_t *__restrict__ rows,
+                                int32_t *__restrict__ me_out) {
     __shared__ long long F_s;
     if (threadIdx.x == 0) {
         const float med = __uint_as_float(~keys[n / 2]);
@@ -112,6 +113,7 @@ __global__ void far_pick_kernel(const uint32_t *__restrict__ keys, const int32_t
     // point nearest its pivot (a pivot itself), which adds no cell
     const int64_t F = F_s;
     const int64_t Me = F / 32 < M ? F / 32 : M;
+    if (threadIdx.x == 0) *me_out = int32_t(Me);
     for (int j = threadIdx.x; j < M; j += blockDim.x)
         rows[j] = j < Me ? vals[int64_t(j) * F / Me] : vals[n - 1];
 }
@@ -613,18 +615,25 @@ famst_status prune_pivot_operands(const Exec &ex, const __nv_bfloat16 *H, int kh
 // gains some; without them its points would widen foreign cells' balls.
 famst_status prune_augment(const Exec &ex, Arena &ar, const float *xn2, const float *s1, int64_t n,
                            const __nv_bfloat16 *H, int kh, const float *ny, int M, int K,
-                           int32_t *piv, __nv_bfloat16 *Hp, float *nyp) {
+                           int32_t *piv, __nv_bfloat16 *Hp, float *nyp, int *me) {
     const size_t mark = ar.off;
     uint32_t *keys = ar.take<uint32_t>(size_t(n));
     int32_t *vals = ar.take<int32_t>(size_t(n));
     int32_t *rows = ar.take<int32_t>(size_t(M));
-    if (!keys || !vals || !rows) return FAMST_ERR_OOM;
+    int32_t *me_dev = ar.take<int32_t>(1);
+    if (!keys || !vals || !rows || !me_dev) return FAMST_ERR_OOM;
     FAMST_LAUNCH(ex, far_key_kernel, nblk(n, 256), 256, 0, xn2, s1, n, keys, vals);
     famst_status st = radix_sort_pairs(ex, ar, keys, vals, n, 32);
     if (st == FAMST_OK) {
-        FAMST_LAUNCH(ex, far_pick_kernel, 1, 256, 0, keys, vals, n, M, rows);
+        FAMST_LAUNCH(ex, far_pick_kernel, 1, 256, 0, keys, vals, n, M, rows, me_dev);
         FAMST_LAUNCH(ex, pivots_kernel, nblk(int64_t(M) * 32, 256), 256, 0, H, kh, ny, n, M, M,
                      rows, piv + K, Hp + size_t(K) * kh, nyp + K);
+        // the number of distinct new pivots (the other slots repeat one point)
+        int32_t h = 0;
+        if (cudaMemcpyAsync(&h, me_dev, 4, cudaMemcpyDeviceToHost, ex.stream) != cudaSuccess ||
+            cudaStreamSynchronize(ex.stream) != cudaSuccess)
+            st = FAMST_ERR_CUDA;
+        *me = h;
     }
     ar.off = mark;
     if (st != FAMST_OK) return st;
