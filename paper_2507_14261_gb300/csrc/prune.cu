@@ -575,7 +575,11 @@ int prune_extra(int64_t n) { return prune_pivots(n) / 2; }
 int prune_pivots_max(int64_t n) { return prune_pivots(n) + 2 * prune_extra(n); }
 
 bool prune_supported(int64_t n, int d, int k, bool vec4) {
-    return vec4 && d >= 4 && d <= 512 && n >= 4 * int64_t(k + 1) && n >= 4096;
+    // the per-query-tile list offsets are int32: every (query tile, key tile)
+    // pair must be countable, whatever fraction is visited
+    const int64_t nq = (n + QT - 1) / QT, nk = (n + KT - 1) / KT;
+    return vec4 && d >= 4 && d <= 512 && n >= 4 * int64_t(k + 1) && n >= 4096 &&
+           nq * nk < (int64_t(1) << 31);
 }
 
 size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk) {
