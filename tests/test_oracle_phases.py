@@ -104,6 +104,82 @@ def test_random_edges_cross_and_are_lambda_shortest(orc):
     assert not (np.array_equal(E.u, E3.u) and np.array_equal(E.v, E3.v))
 
 
+def _draws_of_pair(orc, X, C, lam, seed, i, j):
+    """The lambda^2 samples of component pair (i, j) regenerated here from
+    the pinned Philox4x32-10 and the multiply-shift map of Alg. 3's reading
+    (counter (s, p_lo, p_hi, 0), key (seed_lo, seed_hi), p = i t + j),
+    as (w, s, u, v) tuples in draw order."""
+    t = C.t
+    p = i * t + j
+    key = [seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF]
+    mi = C.members[C.comp_off[i]:C.comp_off[i + 1]]
+    mj = C.members[C.comp_off[j]:C.comp_off[j + 1]]
+    out = []
+    for s in range(lam * lam):
+        r = orc.philox4x32_10([s, p & 0xFFFFFFFF, p >> 32, 0], key)
+        u = int(mi[(int(r[0]) * mi.size) >> 32])
+        v = int(mj[(int(r[1]) * mj.size) >> 32])
+        out.append((orc.dist32(X[u], X[v]), s, u, v))
+    return out
+
+
+def _check_pairs_keep_lambda_smallest(orc, X, C, E, lam, seed, pairs):
+    t = C.t
+    discriminating = 0
+    for i, j in pairs:
+        draws = _draws_of_pair(orc, X, C, lam, seed, i, j)
+        want = sorted(draws)[:lam]              # lambda smallest by (w, s)
+        rank = i * t - i * (i + 1) // 2 + (j - i - 1)
+        got = [(float(E.w[rank * lam + r]), int(E.u[rank * lam + r]), int(E.v[rank * lam + r]))
+               for r in range(lam)]
+        assert got == [(w, u, v) for (w, _, u, v) in want]
+        # a reading that kept the first lambda draws (sorted) would differ here
+        if sorted(draws[:lam]) != want:
+            discriminating += 1
+    return discriminating
+
+
+def test_random_edges_keep_lambda_smallest_of_lambda_sq_draws(orc):
+    # Alg. 3: of the lambda^2 draws of a pair, E keeps exactly the lambda
+    # smallest, ordered by (w, sample index)
+    X = workloads.blobs(900, 5, 9, (0.3, 0.6), 31)
+    nbr, _ = orc.knn(X, 4)
+    C = orc.components(orc.build_graph(nbr))
+    lam, seed = 4, 0x1234_5678_9ABC
+    E = orc.random_edges(X, C, lam, seed)
+    t = C.t
+    assert t >= 6
+    pairs = [(i, j) for i in range(t) for j in range(i + 1, t)][:12]
+    assert _check_pairs_keep_lambda_smallest(orc, X, C, E, lam, seed, pairs) >= 6
+
+
+def test_random_edges_ties_at_lambda_th_draw_break_by_sample_index(orc):
+    # integer lattice clusters: squared distances are integers, so draws of a
+    # pair tie often; the lambda-th and (lambda+1)-th smallest draws tie in w
+    # for some pair, and the kept one must be the one with the smaller s
+    rng = np.random.default_rng(5)
+    blocks = []
+    for c in range(4):
+        base = np.array([40 * c, 0, 0], np.float32)
+        g = np.stack(np.meshgrid(np.arange(4), np.arange(4), np.arange(2), indexing="ij"),
+                     -1).reshape(-1, 3).astype(np.float32)
+        blocks.append(base + g)
+    X = np.ascontiguousarray(np.concatenate(blocks)[rng.permutation(128)])
+    nbr, _ = orc.knn(X, 5)
+    C = orc.components(orc.build_graph(nbr))
+    assert C.t == 4
+    lam, seed = 3, 77
+    E = orc.random_edges(X, C, lam, seed)
+    pairs = [(i, j) for i in range(4) for j in range(i + 1, 4)]
+    _check_pairs_keep_lambda_smallest(orc, X, C, E, lam, seed, pairs)
+    tied = 0
+    for i, j in pairs:
+        srt = sorted(_draws_of_pair(orc, X, C, lam, seed, i, j))
+        if srt[lam - 1][0] == srt[lam][0]:
+            tied += 1
+    assert tied >= 1
+
+
 def test_sample_index_mapping_is_uniform(orc):
     # multiply-shift of Philox output over a component of size 7: chi-square
     sizes = 7
