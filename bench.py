@@ -166,27 +166,87 @@ def traffic_from_profile(kernel: str, units: float):
     return None
 
 
+def _oracle_knn_rate(X, k: int, threads: int, budget_s: float):
+    import oracle
+    n = X.shape[0]
+    probe = 4 * threads
+    oracle.knn(X, k, rows=(0, threads), threads=threads)  # warm the threads and caches
+    t0 = time.perf_counter()
+    oracle.knn(X, k, rows=(0, probe), threads=threads)
+    dt = time.perf_counter() - t0
+    S = int(max(probe, min(n, probe * budget_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.knn(X, k, rows=(0, S), threads=threads)
+    dt = time.perf_counter() - t0
+    return S, dt
+
+
 def cpu_baseline(X, k: int, budget_s: float = 15.0):
     """The oracle's brute-force kNN (Phase 1, the dominant cost of the
     oracle's build) on the first S query rows of the cloud, S sized to the
-    time budget; returns points/s and the sample description."""
+    time budget, on all host cores and on one thread; returns points/s and
+    the sample description."""
     import oracle
     oracle.build()
     n = X.shape[0]
     cores = os.cpu_count() or 1
-    probe = 4 * cores
-    oracle.knn(X, k, rows=(0, cores), threads=cores)  # warm the threads and caches
-    t0 = time.perf_counter()
-    oracle.knn(X, k, rows=(0, probe), threads=cores)
-    dt = time.perf_counter() - t0
-    S = int(max(probe, min(n, probe * budget_s / max(dt, 1e-6))))
-    t0 = time.perf_counter()
-    oracle.knn(X, k, rows=(0, S), threads=cores)
-    dt = time.perf_counter() - t0
+    S, dt = _oracle_knn_rate(X, k, cores, budget_s)
+    S1, dt1 = _oracle_knn_rate(X, k, 1, budget_s / 3)
     return {"value": S / dt, "unit": "points/s", "cores": cores, "kind": "oracle",
             "sample": f"oracle brute-force exact kNN of query rows 0..{S - 1} against all {n} "
                       f"points (Phase 1; the oracle's later phases cost <1% of it and are not "
-                      f"timed); {dt:.1f} s"}
+                      f"timed); {dt:.1f} s",
+            "single_thread": {"value": S1 / dt1, "unit": "points/s", "cores": 1,
+                              "sample": f"query rows 0..{S1 - 1}; {dt1:.1f} s"},
+            "cpu_model": _cpu_model()}
+
+
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def l2_copy_peak(device) -> dict:
+    """Measured L2 bandwidth: a plain copy between two 16 MB buffers (both
+    resident in the 129 MB L2), 64 copies per CUDA-graph replay so launch
+    gaps do not count, read + write bytes over CUDA-event time, best of 10
+    replays. The denominator for kernels that gather from L2."""
+    import torch
+    n = (16 << 20) // 4
+    a = torch.ones(n, dtype=torch.float32, device=device)
+    b = torch.empty_like(a)
+    reps = 64
+    s = torch.cuda.Stream(device)
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            b.copy_(a)
+    torch.cuda.synchronize(device)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        for _ in range(reps):
+            b.copy_(a)
+    g.replay()
+    torch.cuda.synchronize(device)
+    best = None
+    for _ in range(10):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        g.replay()
+        e1.record(s)
+        torch.cuda.synchronize(device)
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    gbs = 2.0 * a.numel() * 4 * reps / (best / 1e3) / 1e9
+    del g
+    return {"l2_gbs": gbs, "how": "torch copy 16 MB -> 16 MB, 64 per graph replay, best of 10"}
 
 
 def run_reference(args, world, rank):
@@ -229,6 +289,64 @@ def run_reference(args, world, rank):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def precision_compare(fam, torch) -> dict:
+    """Phase 1 of the 100k x 128 mixture (k = 16) by brute force in both
+    precisions: tcgen05 BF16 hi/lo tiles vs FP32 SIMT tiles, median of 3
+    after a warm-up, both exact (their graphs are compared)."""
+    w = workloads.get("blobs_100k")
+    X = torch.from_numpy(w.points()).cuda()
+    c = fam.Context(torch.cuda.current_device())
+    c.set_knn_pruning(False)
+    out = {"workload": "blobs_100k (100k x 128, k = 16), kNN stage, no tile pruning"}
+    graphs = {}
+    for prec in ("bf16x3", "fp32"):
+        c.knn_graph(X, w.k, prec)
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            nbr, dist = c.knn_graph(X, w.k, prec)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        graphs[prec] = (nbr, dist)
+        ms = statistics.median(ts)
+        out[prec] = {"ms": ms, "points_per_s": w.n / (ms / 1e3)}
+    out["identical_graphs"] = bool(torch.equal(graphs["bf16x3"][0], graphs["fp32"][0]) and
+                                   torch.equal(graphs["bf16x3"][1], graphs["fp32"][1]))
+    out["recall_at_k"] = 1.0 if out["identical_graphs"] else None
+    out["speedup_bf16x3_over_fp32"] = out["fp32"]["ms"] / out["bf16x3"]["ms"]
+    c.close()
+    return out
+
+
+def batch_sub(fam, torch, local: int, prec: str, steps: int = 5) -> dict:
+    clouds = workloads.batch_clouds()
+    off = np.zeros(len(clouds) + 1, np.int64)
+    for b, cl in enumerate(clouds):
+        off[b + 1] = off[b] + cl.shape[0]
+    dims = np.array([cl.shape[1] for cl in clouds], np.int32)
+    X = torch.from_numpy(np.concatenate([cl.ravel() for cl in clouds]).astype(np.float32)).cuda()
+    c = fam.Context(local)
+    k, lam = 16, 5
+    for _ in range(3):
+        c.build_batched(X, off, dims, k, lam, 1, prec)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        _, _, _, info = c.build_batched(X, off, dims, k, lam, 1, prec)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    c.close()
+    return {"points_per_s": int(off[-1]) * steps / dt, "ms_per_step": 1e3 * dt / steps,
+            "clouds": len(clouds), "points": int(off[-1]), "steps": steps,
+            "graph_replayed": info.graph_replayed, "graph_kernels": info.graph_kernels,
+            "tensor_clouds": info.tensor_clouds, "uncertified_rows": info.uncertified_rows,
+            "timing": "host wall clock around synchronised replays"}
 
 
 def run_batch(args, world, rank, local):
@@ -311,6 +429,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-quality", action="store_true",
                     help="skip the exact EMST (Eq. 1 relative error, after the timed region)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the precision comparison and the batch_256 sub-object")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -380,33 +500,64 @@ def main():
                "h2d_bytes_per_step": int(X_np.nbytes),
                "d2h_bytes_per_step": int((w.n - 1) * 12 + 8)}
 
-    # Roofline of the dominant kernel, timed by the library's CUDA events on
-    # its stream during the timed builds. Phase 1: the tensor tiles actually
-    # computed (2 d flops per query-key pair of a visited tile pair).
-    # Algorithm 4: every candidate distance it evaluated (3 d flops: d
-    # subtractions, d fused multiply-adds) against the FP32 pipe.
+    # Rooflines per kernel, each from that kernel's own CUDA-event time on
+    # the library's stream during the timed builds (famst_build_info).
     pk = peaks()
-    ms_knn = statistics.mean(i["ms_knn"] for i in infos)
-    ms_refine = statistics.mean(i["ms_refine"] for i in infos)
-    frac_tiles = statistics.mean(i["knn_tile_fraction"] for i in infos)
-    evals = statistics.mean(i["refine_distance_evals"] for i in infos)
-    fp32_peak = SMS * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 * 1.5 / 1e12
+    l2 = l2_copy_peak(X.device)
+    mean = lambda key: statistics.mean(i[key] for i in infos)  # noqa: E731
+    ms_tiles, ms_rerank = mean("ms_knn_tiles"), mean("ms_rerank")
+    ms_refk, ms_conk = mean("ms_refine_kernel"), mean("ms_connect_kernel")
+    frac_tiles = mean("knn_tile_fraction")
+    evals, canon = mean("refine_distance_evals"), mean("refine_canonical_evals")
     nq, nk = (w.n + 127) // 128, (w.n + 255) // 256
-    if args.prec == "fp32":
-        knn_flops, knn_peak, knn_bound = 3.0 * w.n * w.n * w.d, fp32_peak, "alu"
-    else:
-        knn_flops = 2.0 * nq * nk * 128 * 256 * w.d * frac_tiles
-        knn_peak, knn_bound = pk["bf16_tflops"], "tensor"
-    kernels = {
-        "knn": {"bound": knn_bound, "ms": ms_knn, "achieved": knn_flops / (ms_knn / 1e3) / 1e12,
-                "peak": knn_peak, "unit": "TFLOP/s", "tile_fraction": frac_tiles,
-                "kernel": "knn_fp32_kernel" if args.prec == "fp32" else "knn_tc_kernel",
-                "note": "stage time (prep, partition, tiles, re-rank) over the visited tiles' "
-                        "flops"},
-        "refine": {"bound": "alu", "ms": ms_refine,
-                   "achieved": 3.0 * w.d * evals / (ms_refine / 1e3) / 1e12, "peak": fp32_peak,
-                   "unit": "TFLOP/s", "distance_evals": evals, "kernel": "refine_kernel"},
-    }
+    kernels = {}
+    if args.prec != "fp32" and ms_tiles > 0:
+        # 2 d FLOP per (query, key) pair of every visited tile pair; BF16x3
+        # issues three products per pair, its own tensor ceiling is 1/3
+        pairs = nq * nk * 128 * 256 * frac_tiles
+        ach = 2.0 * w.d * pairs / (ms_tiles / 1e3) / 1e12
+        prods = 3 if args.prec == "bf16x3" else 1
+        kernels["knn_tiles"] = {
+            "bound": "tensor", "ms": ms_tiles, "achieved": ach, "peak": pk["bf16_tflops"],
+            "unit": "TFLOP/s", "frac": ach / pk["bf16_tflops"],
+            "frac_of_x3_ceiling": ach * prods / pk["bf16_tflops"],
+            "tile_fraction": frac_tiles, "kernel": "knn_tc_kernel",
+            "note": "visited tile pairs' 2 d FLOP per pair over the tile kernel's own time; "
+                    "peak = measured BF16 burst"}
+    kernels["knn_stage"] = {"ms": mean("ms_knn"),
+                            "note": "whole Phase 1: operand prep, pruning partition, tiles, "
+                                    "re-rank, fallback rows"}
+    if ms_rerank > 0:
+        # per query row: (KC - 1) candidate FP32 rows gathered (KC = 48 for k = 32)
+        kc = 32 if w.k <= 21 else (48 if w.k <= 37 else 64)
+        rb = w.n * (kc - 1) * w.d * 4.0 + w.n * w.k * 8.0
+        kernels["rerank"] = {"bound": "l2", "ms": ms_rerank,
+                             "achieved": rb / (ms_rerank / 1e3) / 1e9, "peak": l2["l2_gbs"],
+                             "unit": "GB/s", "frac": rb / (ms_rerank / 1e3) / 1e9 / l2["l2_gbs"],
+                             "kernel": "rerank_sorted_kernel",
+                             "note": "(KC - 1) FP32 candidate rows per query + nbr/dist out"}
+    if ms_refk > 0:
+        # per candidate distance: its BF16 row (2 d B) and its list entry (id
+        # 4 B + error bound and norm 8 B); per canonical survivor its FP32 row
+        rbytes = evals * (2.0 * w.d + 12.0) + canon * 4.0 * w.d
+        ach = rbytes / (ms_refk / 1e3) / 1e9
+        kernels["refine"] = {
+            "bound": "l2", "ms": ms_refk, "achieved": ach, "peak": l2["l2_gbs"], "unit": "GB/s",
+            "frac": ach / l2["l2_gbs"], "distance_evals": evals, "canonical_evals": canon,
+            "kernel": "refine_kernel",
+            "fp32_rows_equiv_gbs": evals * 4.0 * w.d / (ms_refk / 1e3) / 1e9,
+            "note": "bytes the filter needs per candidate (BF16 row + list entry) plus FP32 "
+                    "rows of canonical survivors, over the kernel's own time, against the "
+                    "measured L2 copy bandwidth; fp32_rows_equiv_gbs counts 4 d B per "
+                    "candidate as if every candidate read its FP32 row"}
+    if ms_conk > 0:
+        m_e = infos[-1]["m"]
+        cb = m_e / w.lam * (w.lam * w.lam) * 2.0 * w.d * 4.0
+        kernels["connect"] = {"bound": "l2", "ms": ms_conk,
+                              "achieved": cb / (ms_conk / 1e3) / 1e9, "peak": l2["l2_gbs"],
+                              "unit": "GB/s", "frac": cb / (ms_conk / 1e3) / 1e9 / l2["l2_gbs"],
+                              "kernel": "connect_filtered_kernel",
+                              "note": "lambda^2 draws x two FP32 rows per component pair"}
     # dW/dX of the tree weight (the tree held fixed), after the timed builds:
     # per vertex its own row, its tree neighbours' rows and its gradient row
     # ((n - 1) d 4 B x 4 algorithmic bytes), timed on the library's stream
@@ -428,16 +579,17 @@ def main():
                            "frac": bwd_bytes / (ms_bwd / 1e3) / 1e9 / pk["hbm_gbs"],
                            "kernel": "famst_mst_backward (edge lengths, incidence sort, per-vertex sums)"}
     del gx
-    dom = "refine" if ms_refine >= ms_knn else "knn"
+    # the dominant kernel of the build by its own time
+    cands = {kk: v for kk, v in kernels.items() if "bound" in v and kk != "backward"}
+    dom = max(cands, key=lambda kk: cands[kk]["ms"])
     kd = kernels[dom]
-    traffic = (traffic_from_profile("refine_kernel", evals) if dom == "refine" else
-               traffic_from_profile("knn_tc_kernel", frac_tiles * nq * nk * 128 * 256))
+    units = evals if dom == "refine" else frac_tiles * nq * nk * 128 * 256
+    traffic = traffic_from_profile(kd["kernel"], units)
     roofline = {"bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
-                "unit": kd["unit"], "frac": kd["achieved"] / kd["peak"],
-                "traffic": traffic,
+                "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic,
                 "kernel": kd["kernel"], "ms_per_launch": kd["ms"],
-                "peak_source": (pk["_source"] if kd["bound"] == "tensor" else
-                                "derived: 152 SMs x 128 FP32 lanes x max SM clock x 1.5 flop/instr")}
+                "peak_source": ("measured in this run: " + l2["how"]) if kd["bound"] == "l2"
+                else "MEASURED_PEAKS.json (" + pk["_source"] + ")"}
 
     # Eq. 1: relative error of the FAMST tree against the exact EMST, both
     # on the GPU, outside the timed region
@@ -450,6 +602,20 @@ def main():
                    "rel_err": (tree.W - T.W) / T.W if T.W > 0 else 0.0,
                    "exact": "GPU Boruvka over masked exact 1-NN passes",
                    "emst_rounds": rounds, "emst_s": time.perf_counter() - t0}
+
+    # Like-for-like precision comparison on the 100k x 128 mixture (k = 16):
+    # Phase 1 brute force (no tile pruning) with BF16 hi/lo tensor tiles
+    # against the FP32 SIMT tiles; both return the exact kNN graph (recall@k
+    # = 1.0, checked equal here), so only the distance arithmetic differs.
+    precision = None
+    if not args.no_extras and rank == 0:
+        precision = precision_compare(fam, torch)
+
+    # 256 clouds through the batched entry point (one CUDA-graph replay per
+    # step), after the timed region
+    batch = None
+    if not args.no_extras and rank == 0:
+        batch = batch_sub(fam, torch, local, args.prec)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -468,6 +634,7 @@ def main():
                        "l2": "inputs larger than L2 (X = %d MB)" % (X_np.nbytes >> 20)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "quality": quality, "kernels": kernels,
+            "l2_peak": l2, "precision_compare": precision, "batch_256": batch,
             "stages_ms": {k2: last[k2] for k2 in ("ms_knn", "ms_components", "ms_connect",
                                                   "ms_refine", "ms_mst", "ms_total")},
             "build": {"t": last["t"], "m": last["m"], "refine_sweeps": last["refine_sweeps"],
@@ -475,7 +642,8 @@ def main():
                       "W64": last["W64"], "uncertified_rows": last["uncertified_rows"],
                       "knn_tile_fraction": last["knn_tile_fraction"],
                       "refine_distance_evals": last["refine_distance_evals"],
-                      "refine_canonical_evals": last["refine_canonical_evals"]},
+                      "refine_canonical_evals": last["refine_canonical_evals"],
+                      "refine_filter": last["refine_filter"]},
         }
         print(json.dumps(line), flush=True)
     if pg is not None:

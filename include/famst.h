@@ -92,6 +92,17 @@ typedef struct famst_build_info {
     double  knn_tile_fraction; /* (query, key) tile pairs Phase 1 computed / all pairs */
     int64_t refine_distance_evals; /* candidate distances Algorithm 4 evaluated */
     int64_t refine_canonical_evals; /* of which the canonical distance decided */
+    int32_t refine_filter;    /* candidate filter of Algorithm 4's kernel: -1 no refinement
+                                 (t = 1), 0 none (canonical distance per candidate),
+                                 1 FP32 grouped sums, 2 BF16 dot products on the tensor
+                                 cores (mma.sync); survivors of a filter are decided on
+                                 canonical distances, so the result is the same */
+    int32_t reserved0;
+    /* CUDA-event milliseconds of single kernels (0 when the kernel did not
+     * run): the tcgen05 distance tiles of Phase 1's main pass, the
+     * canonical re-rank with its certificate, Algorithm 3's kernel and
+     * Algorithm 4's kernel */
+    double  ms_knn_tiles, ms_rerank, ms_connect_kernel, ms_refine_kernel;
 } famst_build_info;
 
 /* ------------------------------------------------------------ context */
@@ -109,6 +120,24 @@ famst_status famst_set_stream(famst_ctx *ctx, void *stream);
  * beyond an upper bound on its rows' k-th neighbour distance; the
  * certificate covers the skipped keys, so the kNN graph is unchanged. */
 famst_status famst_set_knn_pruning(famst_ctx *ctx, int32_t enable);
+/* *bytes (HOST) = device workspace a famst_build (or famst_build_host,
+ * whose device copies of X and the tree come on top) of this shape needs
+ * when its kNN graph has at most t_max components (Algorithm 2's t; the
+ * connect and refine workspace grows with lambda t (t - 1) / 2). The
+ * context grows its workspace to that size on first use (cudaMalloc) and
+ * keeps it; a caller that wants to allocate up front runs one build of the
+ * largest shape first. Depends on the context's pruning setting. Errors:
+ * INVALID_ARG (bad shape, 1 <= t_max <= n), UNSUPPORTED (as famst_build). */
+famst_status famst_workspace_query(famst_ctx *ctx, int64_t n, int32_t d, int32_t k,
+                                   int32_t lambda, int64_t t_max, int32_t prec,
+                                   int32_t max_iters, size_t *bytes);
+/* Iteration limit of the library's bounded loops: each find and hook loop
+ * of the union-find (Algorithm 2), the pointer jumping of every Boruvka
+ * round, and the number of Boruvka rounds (at most 64). A loop that reaches
+ * the limit makes the call return FAMST_ERR_TIMEOUT instead of a result; the
+ * context stays usable. 0 (the default) restores the built-in limits
+ * (2^22 steps, 64 rounds), which no valid input reaches. */
+famst_status famst_set_loop_limit(famst_ctx *ctx, int32_t limit);
 /* Static string naming a status code. */
 const char *famst_error_string(famst_status status);
 /* Detail of the last error on this context (static storage in ctx). */

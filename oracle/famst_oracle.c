@@ -247,10 +247,16 @@ int64_t or_random_edges(const float *X, int d, const int32_t *members,
                         int32_t *eci, int32_t *ecj)
 {
     int L2 = lambda * lambda;
-    sample_t *cand = (sample_t *)malloc(sizeof(sample_t) * (size_t)L2);
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-    int64_t m = 0;
+    /* pairs are drawn and selected independently of each other (Alg. 3), so
+     * the outer loop is spread over threads; pair (i, j) writes its lambda
+     * edges at its rank in the (i outer, j inner) order */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
     for (int64_t i = 0; i < t; ++i) {
+        sample_t *cand = (sample_t *)malloc(sizeof(sample_t) * (size_t)L2);
+        int64_t m = (i * t - i * (i + 1) / 2) * lambda;
         for (int64_t j = i + 1; j < t; ++j) {
             uint64_t p = (uint64_t)i * (uint64_t)t + (uint64_t)j;
             int64_t si = comp_off[i + 1] - comp_off[i];
@@ -276,9 +282,9 @@ int64_t or_random_edges(const float *X, int d, const int32_t *members,
                 ++m;
             }
         }
+        free(cand);
     }
-    free(cand);
-    return m;
+    return lambda * t * (t - 1) / 2;
 }
 
 /* --------------------------------------------------- Phase 3: Algorithm 4
@@ -298,6 +304,11 @@ int64_t or_refine_sweep(const float *X, int d, const int64_t *row_ptr,
                         unsigned char *changed)
 {
     int64_t delta = 0;
+    /* an edge's update reads only its own (u, v, d) and the fixed X, G and
+     * labels (Alg. 4), so edges are spread over threads */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 256) reduction(+:delta)
+#endif
     for (int64_t e = 0; e < m; ++e) {
         int32_t u = eu[e], v = ev[e];
         int32_t us = u, vs = v;

@@ -564,7 +564,7 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
                            const int32_t *eci, const int32_t *ecj, const int32_t *order,
                            int64_t m, const int64_t *m_dev, int max_iters, int32_t *change_hist,
                            unsigned long long *next_item, unsigned long long *evals,
-                           const HalfRows &hr, bool check) {
+                           const HalfRows &hr, bool check, int *variant) {
     const int th = 256;
     const int G = (vec4 && d >= 32) ? sq_group(d) : 0;
     // BF16 filter on the tensor cores: ns = ld / 64 segments, d <= 256
@@ -602,11 +602,13 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
     // and the two final roundings; 1e-35 covers products flushed below the
     // FP32 normal range.
     const float aerr = float(hr.ld * std::ldexp(1.0, -19) + std::ldexp(1.0, -20));
+    if (variant) *variant = bf ? REFINE_FILTER_BF16_MMA : G > 0 ? REFINE_FILTER_FP32 : REFINE_FILTER_NONE;
 #define REFINE_LAUNCH(V, GG, B)                                                                  \
     FAMST_LAUNCH(ex, (refine_kernel<V, GG, B>), grid, th, 0, X, d, nbr, k, rev_off, rev_src,     \
                  comp, eu, ev, ew, eci, ecj, order, m, m_dev, max_iters, change_hist, next_item, \
                  ex.dstatus, rho, evals, hr.h, hr.ld, hr.eb, hr.n2, hr.lst, hr.rst, aerr, eps,   \
                  check)
+    timer_mark(ex, TIMER_REFINE, false);
     if (bf) {
         if (GB == 1) REFINE_LAUNCH(4, 1, true);
         else if (GB == 2) REFINE_LAUNCH(4, 2, true);
@@ -623,6 +625,7 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
                 else REFINE_LAUNCH(1, 0, false);
         }
     }
+    timer_mark(ex, TIMER_REFINE, true);
 #undef REFINE_LAUNCH
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
@@ -706,6 +709,7 @@ famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
     FAMST_LAUNCH(ex, (connect_filtered_kernel<P, GG>), grid, th, 0, X, d, members, comp_off, t, \
                  lambda, seed, rho, eu, ev, ew, eci, ecj)
     if (G > 0) {
+        timer_mark(ex, TIMER_CONNECT, false);
         if (per <= 1) {
             if (G == 4) CONNECT_F(1, 4); else if (G == 8) CONNECT_F(1, 8); else CONNECT_F(1, 16);
         } else if (per <= 2) {
@@ -713,6 +717,7 @@ famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
         } else {
             if (G == 4) CONNECT_F(4, 4); else if (G == 8) CONNECT_F(4, 8); else CONNECT_F(4, 16);
         }
+        timer_mark(ex, TIMER_CONNECT, true);
         return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
     }
 #define CONNECT_CASE(P)                                                                       \
@@ -795,7 +800,8 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
                           const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
                           int64_t m, int max_iters, int32_t *change_hist,
-                          unsigned long long *evals, const HalfRows &hr, bool check) {
+                          unsigned long long *evals, const HalfRows &hr, bool check,
+                          int *variant) {
     if (m == 0) return FAMST_OK;
     // order: stable sort of the edges by component-pair tile
     constexpr int TT = 24;
@@ -812,7 +818,7 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
     famst_status st = radix_sort_pairs(ex, ar, keys, order, m, bits);
     if (st != FAMST_OK) return st;
     return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj, order,
-                         m, nullptr, max_iters, change_hist, next_item, evals, hr, check);
+                         m, nullptr, max_iters, change_hist, next_item, evals, hr, check, variant);
 }
 
 }  // namespace famst
@@ -833,7 +839,7 @@ famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, 
     if (cudaMemsetAsync(next_item, 0, 8, ex.stream) != cudaSuccess) return FAMST_ERR_CUDA;
     return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj,
                          nullptr, m_cap, m_dev, max_iters, change_hist, next_item, nullptr,
-                         HalfRows(), false);
+                         HalfRows(), false, nullptr);
 }
 
 }  // namespace famst

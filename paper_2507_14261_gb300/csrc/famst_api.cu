@@ -59,6 +59,9 @@ struct famst_ctx {
     int32_t *pinned = nullptr;    // 64 bytes of pinned host memory, slots PIN_*
     double *dW = nullptr;         // device: W, W64
     int prune = 1;                // Phase 1 tile pruning
+    int loop_limit = 0;           // bounded loops: 0 = defaults (famst_set_loop_limit)
+    KernelTimers timers;          // per-kernel events of a build with info
+    bool timers_made = false, timing = false;
     double tile_fraction = 1.0;   // of the last Phase 1
     char err[256] = {0};
 };
@@ -121,7 +124,38 @@ famst_status ensure_ws(famst_ctx *ctx, int slot, size_t bytes, Arena &ar) {
     return FAMST_OK;
 }
 
-Exec exec_of(famst_ctx *ctx) { return Exec{ctx->stream, &ctx->launches, ctx->num_sms, ctx->dstatus}; }
+Exec exec_of(famst_ctx *ctx) {
+    Exec e{ctx->stream, &ctx->launches, ctx->num_sms, ctx->dstatus};
+    e.loop_limit = ctx->loop_limit;
+    e.timers = ctx->timing ? &ctx->timers : nullptr;
+    return e;
+}
+
+// Per-kernel timers for one build (created on first use, kept by the context).
+struct TimingScope {
+    famst_ctx *ctx;
+    TimingScope(famst_ctx *c, bool on) : ctx(c) {
+        if (!on) return;
+        if (!ctx->timers_made) {
+            for (auto &e : ctx->timers.ev)
+                if (cudaEventCreate(&e) != cudaSuccess) return;
+            ctx->timers_made = true;
+        }
+        for (auto &u : ctx->timers.used) u = false;
+        ctx->timing = true;
+    }
+    double ms(int slot) const {
+        float f = 0.0f;
+        if (!ctx->timing || !ctx->timers.used[slot]) return 0.0;
+        if (cudaEventElapsedTime(&f, ctx->timers.ev[2 * slot], ctx->timers.ev[2 * slot + 1]) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 0.0;
+        }
+        return double(f);
+    }
+    ~TimingScope() { ctx->timing = false; }
+};
 
 __global__ void check_finite_kernel(const float *__restrict__ X, int64_t count, int *dstatus) {
     int bad = 0;
@@ -287,6 +321,22 @@ size_t knn_stage_ws(famst_ctx *ctx, int64_t n, int32_t d, int32_t k, int32_t pre
     return knn_fp32_workspace(n, d, k, n, ctx->num_sms);
 }
 
+// Workspace of Phases 2-3 + MST (slot 1) for m inter-component edges.
+size_t rest_ws(int64_t n, int32_t d, int32_t k, int64_t m, int64_t t, int32_t max_iters) {
+    return align256(size_t(n) * 4) + align256(size_t(n + 1) * 4) + member_lists_workspace(n, t) +
+           5 * align256(size_t(m > 0 ? m : 1) * 4) + align256(size_t(n + 1) * 4) +
+           align256(size_t(n) * k * 4) + reverse_csr_workspace(n, k) +
+           align256(size_t(max_iters + 1) * 4) + refine_workspace(m) +
+           boruvka_workspace(n, n * int64_t(k) + m) + tree_weight_workspace(n) +
+           half_rows_workspace(n, d) + half_rows_lists_workspace(n, k) + 4096;
+}
+
+// Workspace of Phase 1 inside a build (slot 0): nbr, dist, comp + the tiles.
+size_t build_knn_ws(famst_ctx *ctx, int64_t n, int32_t d, int32_t k, int32_t prec) {
+    return 2 * align256(size_t(n) * k * 4) + align256(size_t(n) * 4) +
+           knn_stage_ws(ctx, n, d, k, prec) + 4096;
+}
+
 // Phases 2-3 + MST on device data. nbr/dist come from Phase 1.
 struct BuildOut {
     int32_t *tu, *tv;
@@ -311,14 +361,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     const int64_t m = int64_t(lambda) * t * (t - 1) / 2;
     if (m >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "lambda*t*(t-1)/2 >= 2^31");
     // workspace for connect, refine and MST
-    size_t need = align256(size_t(n) * 4) + align256(size_t(n + 1) * 4) +
-                  member_lists_workspace(n, t) + 5 * align256(size_t(m > 0 ? m : 1) * 4) +
-                  align256(size_t(n + 1) * 4) + align256(size_t(n) * k * 4) +
-                  reverse_csr_workspace(n, k) + align256(size_t(max_iters + 1) * 4) +
-                  refine_workspace(m) + boruvka_workspace(n, n * int64_t(k) + m) +
-                  tree_weight_workspace(n) +
-                  half_rows_workspace(n, d) + half_rows_lists_workspace(n, k) + 4096;
-    ST(ensure_ws(ctx, 1, need, ar));
+    ST(ensure_ws(ctx, 1, rest_ws(n, d, k, m, t, max_iters), ar));
     int32_t *members = ar.take<int32_t>(size_t(n));
     int32_t *comp_off = ar.take<int32_t>(size_t(n + 1));
     int32_t *eu = ar.take<int32_t>(size_t(m > 0 ? m : 1));
@@ -329,7 +372,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     int32_t *hist = ar.take<int32_t>(size_t(max_iters + 1));
     unsigned long long *evals = ar.take<unsigned long long>(2);
     // the components kernels above used this slot; comp lives in slot 0
-    int sweeps = 0;
+    int sweeps = 0, filter = -1;
     unsigned long long evals_host[2] = {0, 0};
     int64_t first_delta = 0;
     if (t > 1) {
@@ -349,7 +392,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         if (!evals) return fail(ctx, FAMST_ERR_OOM, "workspace");
         CK(cudaMemsetAsync(evals, 0, 16, ctx->stream));
         ST(refine_edges(ex, ar, X, d, v4, nbr, k, rev_off, rev_src, comp, t, eu, evv, ew, eci, ecj, m,
-                        max_iters, hist, evals, hr, false));
+                        max_iters, hist, evals, hr, false, &filter));
         ev.mark(ctx->stream, 4);
         famst_status s = sync_status(ctx);
         if (s != FAMST_OK) return s;
@@ -386,6 +429,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         info->first_delta = first_delta;
         info->refine_distance_evals = int64_t(evals_host[0]);
         info->refine_canonical_evals = int64_t(evals_host[1]);
+        info->refine_filter = filter;
         info->W = W[0];
         info->W64 = W[1];
     }
@@ -406,14 +450,13 @@ famst_status build_impl(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     ST(check_knn_args(ctx, n, k));
     Events ev;
     ev.init(info != nullptr);
+    TimingScope tscope(ctx, info != nullptr);
     ev.mark(ctx->stream, 0);
     ST(reset_status(ctx));
     ST(check_points(ctx, X, n, d));
     ST(sync_status(ctx));
     Arena ar;
-    size_t need = 2 * align256(size_t(n) * k * 4) + align256(size_t(n) * 4) +
-                  knn_stage_ws(ctx, n, d, k, prec) + 4096;
-    ST(ensure_ws(ctx, 0, need, ar));
+    ST(ensure_ws(ctx, 0, build_knn_ws(ctx, n, d, k, prec), ar));
     int32_t *nbr = ar.take<int32_t>(size_t(n) * k);
     float *dist = ar.take<float>(size_t(n) * k);
     int32_t *comp = ar.take<int32_t>(size_t(n));
@@ -433,6 +476,10 @@ famst_status build_impl(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         info->ms_refine = ev.ms(3, 4);
         info->ms_mst = ev.ms(4, 5);
         info->ms_total = ev.ms(0, 5);
+        info->ms_knn_tiles = tscope.ms(TIMER_TILES);
+        info->ms_rerank = tscope.ms(TIMER_RERANK);
+        info->ms_connect_kernel = tscope.ms(TIMER_CONNECT);
+        info->ms_refine_kernel = tscope.ms(TIMER_REFINE);
     }
     return FAMST_OK;
 }
@@ -476,6 +523,8 @@ famst_status famst_destroy(famst_ctx *ctx) {
     if (ctx->dstatus) cudaFree(ctx->dstatus);
     if (ctx->dW) cudaFree(ctx->dW);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->timers_made)
+        for (auto &e : ctx->timers.ev) cudaEventDestroy(e);
     delete ctx;
     return FAMST_OK;
 }
@@ -484,6 +533,33 @@ famst_status famst_set_stream(famst_ctx *ctx, void *stream) {
     if (!ctx) return FAMST_ERR_INVALID_ARG;
     ctx->err[0] = 0;
     ctx->stream = static_cast<cudaStream_t>(stream);
+    return FAMST_OK;
+}
+
+famst_status famst_workspace_query(famst_ctx *ctx, int64_t n, int32_t d, int32_t k,
+                                   int32_t lambda, int64_t t_max, int32_t prec,
+                                   int32_t max_iters, size_t *bytes) {
+    if (!ctx || !bytes) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    *bytes = 0;
+    if (n < 1 || d < 1 || lambda < 1 || lambda > 32 || max_iters < 1 || prec < 0 || prec > 2 ||
+        t_max < 1 || t_max > n)
+        return fail(ctx, FAMST_ERR_INVALID_ARG, "bad shape");
+    if (n == 1) return FAMST_OK;
+    ST(check_knn_args(ctx, n, k));
+    const int64_t m = int64_t(lambda) * t_max * (t_max - 1) / 2;
+    if (m >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "lambda*t*(t-1)/2 >= 2^31");
+    // as ensure_ws rounds a slot: aligned, plus its 4 KB guard
+    *bytes = (align256(build_knn_ws(ctx, n, d, k, prec)) + 4096) +
+             (align256(rest_ws(n, d, k, m, t_max, max_iters)) + 4096);
+    return FAMST_OK;
+}
+
+famst_status famst_set_loop_limit(famst_ctx *ctx, int32_t limit) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (limit < 0) return fail(ctx, FAMST_ERR_INVALID_ARG, "need limit >= 0");
+    ctx->loop_limit = limit;
     return FAMST_OK;
 }
 

@@ -13,12 +13,30 @@ namespace famst {
 
 // Execution environment of one library call: the stream its work goes to
 // and the context's launch counter.
+// CUDA-event timers around single kernels of a build (the distance tiles,
+// the re-rank, Algorithm 3's and Algorithm 4's kernels), read back into the
+// build info after the call synchronises.
+enum : int { TIMER_TILES = 0, TIMER_RERANK = 1, TIMER_CONNECT = 2, TIMER_REFINE = 3, TIMER_N = 4 };
+struct KernelTimers {
+    cudaEvent_t ev[2 * TIMER_N] = {};
+    bool used[TIMER_N] = {};
+};
+
 struct Exec {
     cudaStream_t stream;
     unsigned long long *launches;
     int num_sms;
     int *dstatus;  // device status word (see STATUS_* below)
+    int loop_limit = 0;  // iteration limit of the bounded loops; 0 = their defaults
+    KernelTimers *timers = nullptr;  // optional
 };
+
+// Record the start / end event of timer `slot` on the call's stream.
+static inline void timer_mark(const Exec &ex, int slot, bool end) {
+    if (!ex.timers) return;
+    cudaEventRecord(ex.timers->ev[2 * slot + (end ? 1 : 0)], ex.stream);
+    if (end) ex.timers->used[slot] = true;
+}
 
 // Bits of the device status word. Kernels OR them in; the host reads the
 // word at the next synchronisation point.
@@ -636,7 +654,11 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
                           int64_t m, int max_iters, int32_t *change_hist /*max_iters+1*/,
                           unsigned long long *evals = nullptr, const HalfRows &hr = HalfRows(),
-                          bool check = true);
+                          bool check = true, int *variant = nullptr);
+// candidate filter of the refinement kernel that ran (build info)
+constexpr int REFINE_FILTER_NONE = 0;      // canonical distance per lane
+constexpr int REFINE_FILTER_FP32 = 1;      // FP32 grouped sums + canonical survivors
+constexpr int REFINE_FILTER_BF16_MMA = 2;  // BF16 dot products (mma.sync) + canonical survivors
 size_t refine_workspace(int64_t m);
 famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, bool vec4,
                               const int32_t *nbr, int k, const int32_t *rev_off,

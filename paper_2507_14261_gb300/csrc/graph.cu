@@ -167,18 +167,21 @@ __global__ void rs_scatter_kernel(const uint32_t *__restrict__ kin, const int32_
 
 constexpr int UF_LIMIT = 1 << 22;
 
-__device__ __forceinline__ int uf_find(int32_t *parent_, int v) {
-    // path splitting; parent[x] <= x always holds. Volatile: other threads
-    // hook and compress concurrently, every read must see memory.
+// Root of v. Path splitting; parent[x] <= x always holds. Volatile: other
+// threads hook and compress concurrently, every read must see memory. At
+// most `limit` steps: a find cut short raises STATUS_LOOP_LIMIT (the call
+// then fails with FAMST_ERR_TIMEOUT) and returns an ancestor of v.
+__device__ __forceinline__ int uf_find(int32_t *parent_, int v, int limit, int *dstatus) {
     volatile int32_t *parent = parent_;
     int p = parent[v];
     int guard = 0;
-    while (p != v && guard++ < UF_LIMIT) {
+    while (p != v && guard++ < limit) {
         int g = parent[p];
         if (g != p) parent[v] = g;  // benign race: any ancestor is valid
         v = p;
         p = g;
     }
+    if (p != v) set_status(dstatus, STATUS_LOOP_LIMIT);
     return v;
 }
 
@@ -188,18 +191,19 @@ __global__ void uf_init_kernel(int32_t *parent, int64_t n) {
 }
 
 __global__ void uf_hook_kernel(const int32_t *__restrict__ nbr, int64_t nk, int k,
-                               int32_t *parent, int *dstatus) {
+                               int32_t *parent, int limit, int *dstatus) {
     int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (e >= nk) return;
     int a = int(e / k), b = nbr[e];
-    int ra = uf_find(parent, a), rb = uf_find(parent, b);
-    for (int it = 0; it < UF_LIMIT; ++it) {
+    int ra = uf_find(parent, a, limit, dstatus), rb = uf_find(parent, b, limit, dstatus);
+    for (int it = 0; it < limit; ++it) {
         if (ra == rb) return;
         int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
         int old = atomicCAS(&parent[hi], hi, lo);
         if (old == hi) return;
         // hi was hooked meanwhile: continue from its new parent
-        if (ra > rb) ra = uf_find(parent, old); else rb = uf_find(parent, old);
+        if (ra > rb) ra = uf_find(parent, old, limit, dstatus);
+        else rb = uf_find(parent, old, limit, dstatus);
     }
     set_status(dstatus, STATUS_LOOP_LIMIT);
 }
@@ -207,10 +211,10 @@ __global__ void uf_hook_kernel(const int32_t *__restrict__ nbr, int64_t nk, int 
 // Roots go to a separate array: a concurrent find may still rewrite
 // parent[v] with a non-root ancestor after this thread stored the root.
 __global__ void uf_flatten_kernel(int32_t *parent, int64_t n, int32_t *root,
-                                  int32_t *is_root) {
+                                  int32_t *is_root, int limit, int *dstatus) {
     int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (v >= n) return;
-    int r = uf_find(parent, int(v));
+    int r = uf_find(parent, int(v), limit, dstatus);
     root[v] = r;
     is_root[v] = (r == v) ? 1 : 0;
 }
@@ -328,12 +332,14 @@ famst_status components_uf(const Exec &ex, Arena &ar, const int32_t *nbr, int64_
     int32_t *root = ar.take<int32_t>(size_t(n));
     if (!parent || !flag || !rank || !root) return FAMST_ERR_OOM;
     const int th = 256;
+    const int lim = ex.loop_limit > 0 ? ex.loop_limit : UF_LIMIT;
     int64_t nk = n * k;
     FAMST_LAUNCH(ex, uf_init_kernel, blocks_for(n, th), th, 0, parent, n);
     if (nk > 0)
-        FAMST_LAUNCH(ex, uf_hook_kernel, blocks_for(nk, th), th, 0, nbr, nk, k, parent,
+        FAMST_LAUNCH(ex, uf_hook_kernel, blocks_for(nk, th), th, 0, nbr, nk, k, parent, lim,
                      ex.dstatus);
-    FAMST_LAUNCH(ex, uf_flatten_kernel, blocks_for(n, th), th, 0, parent, n, root, flag);
+    FAMST_LAUNCH(ex, uf_flatten_kernel, blocks_for(n, th), th, 0, parent, n, root, flag, lim,
+                 ex.dstatus);
     famst_status st = exclusive_scan_i32(ex, ar, flag, rank, n, t_dev);
     if (st != FAMST_OK) return st;
     FAMST_LAUNCH(ex, uf_label_kernel, blocks_for(n, th), th, 0, root, rank, n, comp);

@@ -1170,6 +1170,7 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, M>), unsigned(p.nq_tiles), 64 + 32 * p.epi, p.smem, \
                      mA, mB, a);                                                                 \
     } while (0)
+    timer_mark(ex, TIMER_TILES, false);
     if (cpad) {
         if (p.kc == 32) TC_LAUNCH(32, true);
         else if (p.kc == 48) TC_LAUNCH(48, true);
@@ -1179,6 +1180,7 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         else if (p.kc == 48) TC_LAUNCH(48, false);
         else TC_LAUNCH(64, false);
     }
+    timer_mark(ex, TIMER_TILES, true);
 #undef TC_LAUNCH
     if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
     // rerank + certificate
@@ -1200,6 +1202,7 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
             FAMST_LAUNCH(ex, (rerank_kernel<V, KCV>), rgrid, 256, 0, X, n, d, k, cand, splus,    \
                          nullptr, xn2, ymax, cc, nbr, dist, fail_rows, fail_count);              \
     } while (0)
+    timer_mark(ex, TIMER_RERANK, false);
     if (p.kc == 32) {
         if (vec4) RERANK(4, 32); else RERANK(1, 32);
     } else if (p.kc == 48) {
@@ -1207,6 +1210,7 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     } else {
         if (vec4) RERANK(4, 64); else RERANK(1, 64);
     }
+    timer_mark(ex, TIMER_RERANK, true);
 #undef RERANK
     if (cudaMemcpyAsync(pinned_host, fail_count, 4, cudaMemcpyDeviceToHost, ex.stream) != cudaSuccess ||
         (use_prune && cudaMemcpyAsync(pinned_host + 1, P.visited, 4, cudaMemcpyDeviceToHost,

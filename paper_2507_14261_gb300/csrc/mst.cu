@@ -186,12 +186,12 @@ __global__ void bv_hook_kernel(const int32_t *__restrict__ comp, int64_t n,
 }
 
 __global__ void bv_jump_kernel(const int32_t *__restrict__ comp, int64_t n, int32_t *newp_,
-                               int *dstatus) {
+                               int limit, int *dstatus) {
     int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (c >= n || comp[c] != c) return;
     volatile int32_t *newp = newp_;
     int guard = 0;
-    while (guard++ < JUMP_LIMIT) {
+    while (guard++ < limit) {
         int p = newp[c];
         int g = newp[p];
         if (g == p) return;
@@ -436,7 +436,8 @@ famst_status boruvka_dev(const Exec &ex, Arena &ar, int64_t n, const int32_t *nb
         FAMST_LAUNCH(ex, bv_hook_kernel, blocks_for(n, th), th, 0, comp, n, best1, best2, newp,
                      flag, rmn, rmx, rw);
         FAMST_LAUNCH(ex, bv_gate_kernel, blocks_for(n, th), th, 0, done, flag, n);
-        FAMST_LAUNCH(ex, bv_jump_kernel, blocks_for(n, th), th, 0, comp, n, newp, ex.dstatus);
+        FAMST_LAUNCH(ex, bv_jump_kernel, blocks_for(n, th), th, 0, comp, n, newp,
+                     ex.loop_limit > 0 ? ex.loop_limit : JUMP_LIMIT, ex.dstatus);
         FAMST_LAUNCH(ex, bv_relabel_kernel, blocks_for(n, th), th, 0, comp, n, newp);
         size_t mark = ar.off;
         famst_status st = exclusive_scan_i32(ex, ar, flag, pos, n, added);
@@ -521,7 +522,8 @@ famst_status bv_round(const Exec &ex, Arena &ar, BvState &S, const int32_t *nbr,
     ++S.round;
     FAMST_LAUNCH(ex, bv_hook_kernel, blocks_for(n, th), th, 0, S.comp, n, S.best1, S.best2, S.newp,
                  S.flag, S.rmn, S.rmx, S.rw);
-    FAMST_LAUNCH(ex, bv_jump_kernel, blocks_for(n, th), th, 0, S.comp, n, S.newp, ex.dstatus);
+    FAMST_LAUNCH(ex, bv_jump_kernel, blocks_for(n, th), th, 0, S.comp, n, S.newp,
+                 ex.loop_limit > 0 ? ex.loop_limit : JUMP_LIMIT, ex.dstatus);
     FAMST_LAUNCH(ex, bv_relabel_kernel, blocks_for(n, th), th, 0, S.comp, n, S.newp);
     size_t mark = ar.off;  // the scan's scratch is reused by every round
     famst_status st = exclusive_scan_i32(ex, ar, S.flag, S.pos, n, S.total);
@@ -547,15 +549,21 @@ famst_status boruvka(const Exec &ex, Arena &ar, int64_t n, const int32_t *nbr, c
     if (st != FAMST_OK) return st;
     S.knn_exact = knn_exact;
     int64_t got = 0;
-    for (int r = 0; r < 64 && got < n - 1; ++r) {
+    // at least half the components disappear every round that adds edges:
+    // 64 rounds cover any n; the context's loop limit can lower the budget
+    const int budget = ex.loop_limit > 0 && ex.loop_limit < 64 ? ex.loop_limit : 64;
+    int32_t added = 0;
+    for (int r = 0; r < budget && got < n - 1; ++r) {
         st = bv_round(ex, ar, S, nbr, dist, k, eu, ev, ew, m, out, got, pinned_host);
         if (st != FAMST_OK) return st;
         *rounds = r + 1;
-        int32_t added = *pinned_host;
+        added = *pinned_host;
         if (added == 0) break;
         got += added;
     }
     *tree_edges = got;
+    // the budget ran out while rounds still added edges: not a disconnected graph
+    if (got < n - 1 && added > 0) return FAMST_ERR_TIMEOUT;
     return FAMST_OK;
 }
 

@@ -40,7 +40,10 @@ class BuildInfo(ctypes.Structure):
         ("ms_connect", ctypes.c_double), ("ms_refine", ctypes.c_double),
         ("ms_mst", ctypes.c_double), ("ms_total", ctypes.c_double),
         ("knn_tile_fraction", ctypes.c_double), ("refine_distance_evals", ctypes.c_int64),
-        ("refine_canonical_evals", ctypes.c_int64),
+        ("refine_canonical_evals", ctypes.c_int64), ("refine_filter", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32), ("ms_knn_tiles", ctypes.c_double),
+        ("ms_rerank", ctypes.c_double), ("ms_connect_kernel", ctypes.c_double),
+        ("ms_refine_kernel", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -74,6 +77,9 @@ _SIGS = {
     "famst_destroy": (_I32, [_P]),
     "famst_set_stream": (_I32, [_P, _P]),
     "famst_set_knn_pruning": (_I32, [_P, _I32]),
+    "famst_set_loop_limit": (_I32, [_P, _I32]),
+    "famst_workspace_query": (_I32, [_P, _I64, _I32, _I32, _I32, _I64, _I32, _I32,
+                                     ctypes.POINTER(ctypes.c_size_t)]),
     "famst_error_string": (ctypes.c_char_p, [_I32]),
     "famst_last_error": (ctypes.c_char_p, [_P]),
     "famst_launch_count": (ctypes.c_uint64, [_P]),
@@ -172,6 +178,21 @@ class Context:
     @property
     def workspace_bytes(self) -> int:
         return int(lib().famst_workspace_bytes(self._h))
+
+    def set_loop_limit(self, limit: int):
+        """Iteration limit of the union-find and Boruvka loops (0 = defaults);
+        a loop that reaches it makes the call raise FAMST_ERR_TIMEOUT."""
+        self._check(lib().famst_set_loop_limit(self._h, int(limit)), "famst_set_loop_limit")
+
+    def workspace_query(self, n: int, d: int, k: int, lam: int, t_max: int,
+                        prec: str = "fp32", max_iters: int = 10000) -> int:
+        """Device workspace bytes a build of this shape needs (at most t_max
+        components in its kNN graph)."""
+        b = ctypes.c_size_t(0)
+        self._check(lib().famst_workspace_query(self._h, n, d, k, lam, t_max, PREC[prec],
+                                                max_iters, ctypes.byref(b)),
+                    "famst_workspace_query")
+        return int(b.value)
 
     def set_knn_pruning(self, enable: bool):
         """Phase 1 tile pruning on (default) or off; the kNN graph is exact

@@ -266,3 +266,56 @@ def test_refine_iteration_cap(orc, ctx, fam):
     with pytest.raises(fam.FamstError) as e:
         ctx.refine(Xd, nbr, comp, E2, max_iters=sweeps - 1)
     assert e.value.name == "FAMST_ERR_NO_CONVERGENCE"
+
+
+def test_loop_limit_reports_timeout_and_context_recovers(orc, ctx, fam):
+    # evenly spaced collinear points with k = 2: the kNN graph is one long
+    # path, so the union-find trees are deep and Boruvka needs many rounds; a
+    # limit of one step / one round must end each call with
+    # FAMST_ERR_TIMEOUT (a status the bounded loops raise, no fault), and the
+    # context must work after
+    n = 3000
+    X = np.zeros((n, 4), np.float32)
+    X[:, 0] = np.random.default_rng(3).permutation(n)   # unit spacing, shuffled ids
+    Xd = _dev(X)
+    nbr, dist = ctx.knn_graph(Xd, 2)
+    comp_ref, t_ref = ctx.components(nbr)
+    assert t_ref == 1
+    try:
+        ctx.set_loop_limit(1)
+        with pytest.raises(fam.FamstError) as e:
+            ctx.components(nbr)
+        assert e.value.name == "FAMST_ERR_TIMEOUT"
+        with pytest.raises(fam.FamstError) as e:
+            ctx.mst(n, nbr, dist, None)
+        assert e.value.name == "FAMST_ERR_TIMEOUT"
+        with pytest.raises(fam.FamstError) as e:
+            ctx.build(Xd, 2, 2, 1)
+        assert e.value.name == "FAMST_ERR_TIMEOUT"
+    finally:
+        ctx.set_loop_limit(0)
+    comp, t = ctx.components(nbr)
+    assert t == 1 and torch.equal(comp, comp_ref)
+    tu, tv, tw, W = ctx.mst(n, nbr, dist, None)
+    T = orc.kruskal(n, nbr.cpu().numpy(), dist.cpu().numpy(), None)
+    assert _tree_keys(tw.cpu(), tu.cpu(), tv.cpu()) == _tree_keys(T.w, T.u, T.v)
+    assert W == n - 1
+
+
+def test_workspace_query_matches_a_build(fam):
+    # a fresh context grows its workspace to exactly what the query reports
+    # (plus the quarter of slack each slot is allocated with)
+    w = workloads.get("blobs_100k")
+    X = w.points(20_000)
+    c = fam.Context(0)
+    try:
+        tree, info = c.build(_dev(X), w.k, w.lam, 1, "bf16x3")
+        q = c.workspace_query(X.shape[0], X.shape[1], w.k, w.lam, info.t, "bf16x3")
+        held = c.workspace_bytes
+        assert q <= held <= q + q // 4 + 16
+        # more components can only need more
+        assert c.workspace_query(X.shape[0], X.shape[1], w.k, w.lam, 4 * info.t, "bf16x3") > q
+        with pytest.raises(fam.FamstError):
+            c.workspace_query(X.shape[0], X.shape[1], w.k, w.lam, 0, "bf16x3")
+    finally:
+        c.close()
