@@ -232,15 +232,17 @@ def l2_copy_peak(device) -> dict:
     with torch.cuda.graph(g, stream=s):
         for _ in range(reps):
             b.copy_(a)
-    g.replay()
+    with torch.cuda.stream(s):
+        g.replay()
     torch.cuda.synchronize(device)
     best = None
     for _ in range(10):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        g.replay()
-        e1.record(s)
+        with torch.cuda.stream(s):   # replay() launches on the current stream
+            e0.record(s)
+            g.replay()
+            e1.record(s)
         torch.cuda.synchronize(device)
         ms = e0.elapsed_time(e1)
         best = ms if best is None else min(best, ms)

@@ -328,7 +328,7 @@ size_t rest_ws(int64_t n, int32_t d, int32_t k, int64_t m, int64_t t, int32_t ma
            align256(size_t(n) * k * 4) + reverse_csr_workspace(n, k) +
            align256(size_t(max_iters + 1) * 4) + refine_workspace(m) +
            boruvka_workspace(n, n * int64_t(k) + m) + tree_weight_workspace(n) +
-           half_rows_workspace(n, d) + half_rows_lists_workspace(n, k) + 4096;
+           half_rows_workspace(n, d) + glists_workspace(n, k) + 4096;
 }
 
 // Workspace of Phase 1 inside a build (slot 0): nbr, dist, comp + the tiles.
@@ -387,7 +387,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         int32_t *rev_src = ar.take<int32_t>(size_t(n) * k);
         if (!rev_off || !rev_src || !hist) return fail(ctx, FAMST_ERR_OOM, "workspace");
         ST(reverse_csr(ex, ar, nbr, n, k, rev_off, rev_src));
-        ST(half_rows_lists(ex, ar, nbr, n, k, rev_src, &hr));
+        ST(refine_glists(ex, ar, nbr, n, k, rev_off, rev_src, &hr));
         CK(cudaMemsetAsync(hist, 0, size_t(max_iters + 1) * 4, ctx->stream));
         if (!evals) return fail(ctx, FAMST_ERR_OOM, "workspace");
         CK(cudaMemsetAsync(evals, 0, 16, ctx->stream));

@@ -622,6 +622,15 @@ size_t reverse_csr_workspace(int64_t n, int k);
 // connect_refine.cu
 // BF16 copies of the points for the Alg. 4 filter (see warp_dot32_mma);
 // h == nullptr: the filter reads the FP32 rows.
+// G[c] of every vertex as one deduplicated list (the kNN list of c, then
+// the reverse entries not already in it): entries off[c] .. off[c+1]-1 hold
+// the neighbour's id and (eb, ||h||^2) of its BF16 row.
+struct GLists {
+    const int32_t *off = nullptr;
+    const int32_t *id = nullptr;
+    const float2 *en = nullptr;
+};
+
 struct HalfRows {
     const __nv_bfloat16 *h = nullptr;
     int ld = 0;                  // multiple of 64, zero beyond d
@@ -632,6 +641,7 @@ struct HalfRows {
     // and of the reverse lists (in rev_src's order): one coalesced load per
     // 32 candidates instead of one scattered load per candidate
     const float2 *lst = nullptr, *rst = nullptr;
+    GLists g;   // deduplicated G lists for the staged refinement scans
 };
 size_t half_rows_workspace(int64_t n, int d);
 famst_status half_rows(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
@@ -639,6 +649,16 @@ famst_status half_rows(const Exec &ex, Arena &ar, const float *X, int64_t n, int
 size_t half_rows_lists_workspace(int64_t n, int k);
 famst_status half_rows_lists(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t n, int k,
                              const int32_t *rev_src, HalfRows *hr);
+// refine_bulk.cu: deduplicated G lists and the refinement kernel whose
+// candidate rows are staged in shared memory by bulk copies
+size_t glists_workspace(int64_t n, int k);
+famst_status refine_glists(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t n, int k,
+                           const int32_t *rev_off, const int32_t *rev_src, HalfRows *hr);
+bool refine_bulk_supported(const HalfRows &hr);
+famst_status launch_refine_bulk(const Exec &ex, const float *X, int d, const HalfRows &hr,
+                                int32_t *eu, int32_t *ev, float *ew, const int32_t *order,
+                                int64_t m, int max_iters, int32_t *change_hist,
+                                unsigned long long *next_item, unsigned long long *evals);
 famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
                            const int32_t *members, const int32_t *comp_off, int64_t t,
                            int lambda, uint64_t seed, int32_t *eu, int32_t *ev, float *ew,

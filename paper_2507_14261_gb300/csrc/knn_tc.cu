@@ -43,6 +43,7 @@
 #include <cmath>
 
 #include "famst_internal.cuh"
+#include "mbarrier.cuh"
 
 namespace famst {
 namespace {
@@ -54,41 +55,9 @@ constexpr int A_BLOCK = BM * BK * 2;   // 16 KB
 constexpr int B_BLOCK = BN * BK * 2;   // 32 KB
 constexpr int CAPB = 24;         // staged candidates per row (flush check every 16 columns)
 constexpr int TC_THREADS_MAX = 64 + 32 * 8;   // producer, MMA issuer, up to 8 epilogue warps
-constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
 
 // ------------------------------------------------------------ PTX helpers
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
 // Bounded wait for the phase of parity `parity` to complete. Returns false
 // if the CTA aborted or the time limit expired (then it raises the abort).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
@@ -103,12 +72,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
             set_status(status, STATUS_LOOP_LIMIT);
             return false;
         }
-    }
-}
-// Bounded wait that ignores the abort flag (used to drain in-flight work).
-__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity) {
-    uint64_t t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity) && globaltimer() - t0 < WAIT_NS) {
     }
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x,
