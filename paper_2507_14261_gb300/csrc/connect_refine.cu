@@ -565,11 +565,6 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
                            int64_t m, const int64_t *m_dev, int max_iters, int32_t *change_hist,
                            unsigned long long *next_item, unsigned long long *evals,
                            const HalfRows &hr, bool check, int *variant) {
-    if (!check && !m_dev && refine_bulk_supported(hr)) {   // builds: staged BF16 rows
-        if (variant) *variant = REFINE_FILTER_BF16_MMA;
-        return launch_refine_bulk(ex, X, d, hr, eu, ev, ew, order, m, max_iters, change_hist,
-                                  next_item, evals);
-    }
     const int th = 256;
     const int G = (vec4 && d >= 32) ? sq_group(d) : 0;
     // BF16 filter on the tensor cores: ns = ld / 64 segments, d <= 256

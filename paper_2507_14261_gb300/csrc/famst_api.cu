@@ -69,7 +69,7 @@ struct famst_ctx {
 namespace {
 
 // slots of the pinned host words: status word, component count, MST counter
-constexpr int PIN_STATUS = 0, PIN_T = 4, PIN_MST = 8, PIN_KNN = 12;
+constexpr int PIN_STATUS = 0, PIN_T = 4, PIN_MST = 8, PIN_KNN = 12, PIN_REF = 14;
 
 // Record the first error of a call (the innermost, most specific one).
 famst_status fail(famst_ctx *c, famst_status s, const char *msg) {
@@ -328,7 +328,8 @@ size_t rest_ws(int64_t n, int32_t d, int32_t k, int64_t m, int64_t t, int32_t ma
            align256(size_t(n) * k * 4) + reverse_csr_workspace(n, k) +
            align256(size_t(max_iters + 1) * 4) + refine_workspace(m) +
            boruvka_workspace(n, n * int64_t(k) + m) + tree_weight_workspace(n) +
-           half_rows_workspace(n, d) + glists_workspace(n, k) + 4096;
+           half_rows_workspace(n, d) + glists_workspace(n, k) + refine_build_workspace(n, m) +
+           4096;
 }
 
 // Workspace of Phase 1 inside a build (slot 0): nbr, dist, comp + the tiles.
@@ -391,8 +392,14 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         CK(cudaMemsetAsync(hist, 0, size_t(max_iters + 1) * 4, ctx->stream));
         if (!evals) return fail(ctx, FAMST_ERR_OOM, "workspace");
         CK(cudaMemsetAsync(evals, 0, 16, ctx->stream));
-        ST(refine_edges(ex, ar, X, d, v4, nbr, k, rev_off, rev_src, comp, t, eu, evv, ew, eci, ecj, m,
-                        max_iters, hist, evals, hr, false, &filter));
+        if (refine_staged_supported(hr)) {   // BF16 rows staged in shared memory
+            filter = REFINE_FILTER_BF16_MMA;
+            ST(refine_build(ex, ar, X, d, hr, members, n, eu, evv, ew, nullptr, m, max_iters, hist,
+                            evals, ctx->pinned + PIN_REF));
+        } else {
+            ST(refine_edges(ex, ar, X, d, v4, nbr, k, rev_off, rev_src, comp, t, eu, evv, ew, eci,
+                            ecj, m, max_iters, hist, evals, hr, false, &filter));
+        }
         ev.mark(ctx->stream, 4);
         famst_status s = sync_status(ctx);
         if (s != FAMST_OK) return s;

@@ -649,16 +649,22 @@ famst_status half_rows(const Exec &ex, Arena &ar, const float *X, int64_t n, int
 size_t half_rows_lists_workspace(int64_t n, int k);
 famst_status half_rows_lists(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t n, int k,
                              const int32_t *rev_src, HalfRows *hr);
-// refine_bulk.cu: deduplicated G lists and the refinement kernel whose
-// candidate rows are staged in shared memory by bulk copies
+// refine_staged.cu: deduplicated G lists; Algorithm 4 inside a build with
+// candidate rows staged in shared memory (sweep-synchronous grouped scans,
+// then per-edge fixed points for the last active edges)
 size_t glists_workspace(int64_t n, int k);
 famst_status refine_glists(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t n, int k,
                            const int32_t *rev_off, const int32_t *rev_src, HalfRows *hr);
-bool refine_bulk_supported(const HalfRows &hr);
-famst_status launch_refine_bulk(const Exec &ex, const float *X, int d, const HalfRows &hr,
-                                int32_t *eu, int32_t *ev, float *ew, const int32_t *order,
-                                int64_t m, int max_iters, int32_t *change_hist,
-                                unsigned long long *next_item, unsigned long long *evals);
+bool refine_staged_supported(const HalfRows &hr);
+famst_status launch_refine_staged(const Exec &ex, const float *X, int d, const HalfRows &hr,
+                                  int32_t *eu, int32_t *ev, float *ew, const int32_t *order,
+                                  int64_t m, int max_iters, int32_t *change_hist,
+                                  unsigned long long *next_item, unsigned long long *evals);
+size_t refine_build_workspace(int64_t n, int64_t m);
+famst_status refine_build(const Exec &ex, Arena &ar, const float *X, int d, const HalfRows &hr,
+                          const int32_t *members, int64_t n, int32_t *eu, int32_t *ev, float *ew,
+                          const int32_t *order, int64_t m, int max_iters, int32_t *change_hist,
+                          unsigned long long *evals, int32_t *pinned_host);
 famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
                            const int32_t *members, const int32_t *comp_off, int64_t t,
                            int lambda, uint64_t seed, int32_t *eu, int32_t *ev, float *ew,
