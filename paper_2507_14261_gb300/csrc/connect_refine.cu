@@ -323,46 +323,15 @@ __device__ __forceinline__ uint64_t scan_side(const float *__restrict__ X, int d
 // (b) the current best weight squared, both widened by 2^-20 for the
 // rounding of sqrtf, cannot be the argmin under (w, id); the others are
 // decided on canonical weights, so the result equals scan_side's.
-// BF (G = NS, the BF16 row's 64-element segments): the fast value is
-// p~ = ||h_x||^2 + ||h_y||^2 - 2 h_x.h_y of the centred BF16 rows h, the dot
-// products on the tensor cores (warp_dot32_mma). |p~ - ||h_x - h_y||^2| <=
-// aerr (||h_x||^2 + ||h_y||^2) + 1e-35, and ||(h_y - h_x) - (y - x)|| <=
-// eb_x + eb_y, so in the distance domain sqrt(p~ -+ A) -+ (eb_x + eb_y),
-// widened by eps for the canonical sum's own error, bound w_canon; each
-// candidate's (eb, ||h||^2) comes from lst / rst, stored in list order.
-template <int G, bool BF>
+template <int G>
 __device__ __forceinline__ uint64_t scan_side_filtered(
     const float *__restrict__ X, int d, int c, int fixed, int other, int want_comp, float w0,
     const int32_t *__restrict__ nbr, int k, const int32_t *__restrict__ rev_off,
     const int32_t *__restrict__ rev_src, const int32_t *__restrict__ comp, int lane, float rho,
-    unsigned &evals, unsigned &canon, const __nv_bfloat16 *__restrict__ Hh, int hld,
-    const float *__restrict__ heb, const float *__restrict__ hn2,
-    const float2 *__restrict__ lst, const float2 *__restrict__ rst, float aerr, float eps,
-    bool check) {
+    unsigned &evals, unsigned &canon, bool check) {
     const float *xf = X + int64_t(fixed) * d;
-    float4 fx[BF ? 1 : 4];
-    uint4 bx[BF ? G : 1];
-    // BF with rows of at most two segments (d <= 128): the fixed point's FP32
-    // coordinates lane, lane + 32, ... stay in registers for the survivors'
-    // canonical distances (same terms, same order as canon_p_warp)
-    constexpr int XR = (BF && G <= 2) ? 2 * G : 1;
-    float xr[XR];
-    float ebx = 0.0f, nx = 0.0f;
-    const int ns = hld >> 6;
-    if constexpr (BF) {
-        x_frag_mma<G>(Hh + int64_t(fixed) * hld, ns, lane, bx);
-        ebx = heb[fixed];
-        nx = hn2[fixed];
-        if constexpr (G <= 2) {
-#pragma unroll
-            for (int q = 0; q < XR; ++q) {
-                const int t = lane + 32 * q;
-                xr[q] = t < d ? __ldg(xf + t) : 0.0f;
-            }
-        }
-    } else {
-        row_slices_g<G, 4>(xf, d >> 2, lane, fx);
-    }
+    float4 fx[4];
+    row_slices_g<G, 4>(xf, d >> 2, lane, fx);
     uint64_t best = uint64_t(__float_as_uint(w0)) << 32;
     const int r0 = rev_off[c], r1 = rev_off[c + 1];
     const int deg = k + (r1 - r0);
@@ -371,52 +340,25 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
     for (int base = 0; base < deg; base += 32) {
         const int idx = base + lane;
         int cand = -1;
-        float2 en = make_float2(0.0f, 0.0f);
         if (idx < deg) {
-            if (idx < k) {
-                cand = nbr[int64_t(c) * k + idx];
-                if constexpr (BF) en = lst[int64_t(c) * k + idx];
-            } else {
-                cand = rev_src[r0 + idx - k];
-                if constexpr (BF) en = rst[r0 + idx - k];
-            }
-            // G[c] ∩ C and u' != v: always true when comp labels the components
-            // of this graph (a build, the only user of the BF scan); checked
-            // for caller-supplied labels
-            if (!BF && check && (comp[cand] != want_comp || cand == other)) cand = -1;
+            cand = idx < k ? nbr[int64_t(c) * k + idx] : rev_src[r0 + idx - k];
+            // G[c] ∩ C and u' != v (checked for caller-supplied labels)
+            if (check && (comp[cand] != want_comp || cand == other)) cand = -1;
         }
         const unsigned live = __ballot_sync(0xffffffffu, cand >= 0);
         if (live == 0u) continue;
         if (lane == 0) evals += unsigned(__popc(live));
-        float lo = inf, hi = inf, bound;
-        if constexpr (BF) {   // distance domain
-            const float dt = warp_dot32_mma<G>(Hh, hld, ns, bx, fixed, cand, lane);
-            if (cand >= 0) {
-                const float nn = __fadd_rn(nx, en.y);
-                const float pt = __fmaf_rn(-2.0f, dt, nn);
-                const float A = __fmaf_ru(nn, aerr, 1e-35f);
-                const float slo = __fsqrt_rd(fmaxf(__fsub_rd(pt, A), 0.0f));
-                const float shi = __fsqrt_ru(__fadd_ru(pt, A));
-                const float E = __fadd_ru(ebx, en.x);
-                lo = fmaxf(__fmul_rd(__fsub_rd(slo, E), 1.0f - eps), 0.0f);
-                hi = __fmul_ru(__fadd_ru(shi, E), 1.0f + eps);
-            }
-            float mh = hi;
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) mh = fminf(mh, __shfl_xor_sync(0xffffffffu, mh, o));
-            bound = __fmul_ru(fminf(mh, key_w(best)), 1.0f + 0x1p-22f);
-        } else {              // squared domain
-            const float pf = warp_sqdist32g<G, 4>(X, d, fx, fixed, cand, lane);
-            if (cand >= 0) {
-                lo = __fsub_rd(__fmul_rd(pf, 1.0f - rho), 1e-35f);
-                hi = __fadd_ru(__fmul_ru(pf, 1.0f + rho), 1e-35f);
-            }
-            float mh = hi;
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) mh = fminf(mh, __shfl_xor_sync(0xffffffffu, mh, o));
-            const float wb = key_w(best);
-            bound = fminf(__fmul_ru(mh, widen), __fmul_ru(__fmul_ru(wb, wb), widen));
+        float lo = inf, hi = inf;
+        const float pf = warp_sqdist32g<G, 4>(X, d, fx, fixed, cand, lane);
+        if (cand >= 0) {
+            lo = __fsub_rd(__fmul_rd(pf, 1.0f - rho), 1e-35f);
+            hi = __fadd_ru(__fmul_ru(pf, 1.0f + rho), 1e-35f);
         }
+        float mh = hi;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) mh = fminf(mh, __shfl_xor_sync(0xffffffffu, mh, o));
+        const float wb = key_w(best);
+        const float bound = fminf(__fmul_ru(mh, widen), __fmul_ru(__fmul_ru(wb, wb), widen));
         // survivors are decided on canonical distances, each by the whole warp
         unsigned sv = __ballot_sync(0xffffffffu, cand >= 0 && lo <= bound);
         if (lane == 0) canon += unsigned(__popc(sv));
@@ -424,27 +366,7 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
             const int sl = __ffs(sv) - 1;
             sv &= sv - 1;
             const int c2 = __shfl_sync(0xffffffffu, cand, sl);
-            float p;
-            if constexpr (BF && G <= 2) {
-                const float *yr = X + int64_t(c2) * d;
-                float yv[XR];
-#pragma unroll
-                for (int q = 0; q < XR; ++q) {
-                    const int t = lane + 32 * q;
-                    yv[q] = t < d ? __ldg(yr + t) : 0.0f;
-                }
-                p = 0.0f;
-#pragma unroll
-                for (int q = 0; q < XR; ++q) {
-                    const float dl = __fsub_rn(yv[q], xr[q]);
-                    p = __fmaf_rn(dl, dl, p);
-                }
-#pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) p = __fadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
-            } else {
-                p = canon_p_warp(X + int64_t(c2) * d, xf, d, lane);
-            }
-            const float w = __fsqrt_rn(p);
+            const float w = __fsqrt_rn(canon_p_warp(X + int64_t(c2) * d, xf, d, lane));
             const uint64_t key = (uint64_t(__float_as_uint(w)) << 32) | uint32_t(c2 + 1);
             best = key < best ? key : best;   // the same in every lane
         }
@@ -456,7 +378,7 @@ __device__ __forceinline__ uint64_t scan_side_filtered(
 // flight stay in L2), each to its own fixed point.
 // Four resident blocks per SM (64 registers): the scans are latency bound,
 // and occupancy buys more than the few spilled registers cost.
-template <int VEC, int G, bool BF>
+template <int VEC, int G>
 __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict__ X, int d,
                               const int32_t *__restrict__ nbr, int k,
                               const int32_t *__restrict__ rev_off,
@@ -468,11 +390,7 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
                               const int64_t *__restrict__ m_dev, int max_iters,
                               int32_t *__restrict__ change_hist,
                               unsigned long long *__restrict__ next_item, int *dstatus,
-                              float rho, unsigned long long *__restrict__ evals_out,
-                              const __nv_bfloat16 *__restrict__ Hh, int hld,
-                              const float *__restrict__ heb, const float *__restrict__ hn2,
-                              const float2 *__restrict__ lst, const float2 *__restrict__ rst,
-                              float aerr, float eps, bool check) {
+                              float rho, unsigned long long *__restrict__ evals_out, bool check) {
     if (m_dev) m = *m_dev < m ? *m_dev : m;  // device-side edge count, capped by capacity
     const int lane = threadIdx.x & 31;
     unsigned long long evals_total = 0, canon_total = 0;   // evaluations of this lane
@@ -502,9 +420,8 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
             float ws;
             // u-loop: u' in G[u] ∩ C_i, u' != v, against v
             if constexpr (G > 0)
-                bu = scan_side_filtered<G, BF>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src,
-                                               comp, lane, rho, evals, canon, Hh, hld, heb, hn2,
-                                               lst, rst, aerr, eps, check);
+                bu = scan_side_filtered<G>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp,
+                                           lane, rho, evals, canon, check);
             else
                 bu = scan_side<VEC>(X, d, u, v, v, ci, wt, nbr, k, rev_off, rev_src, comp, lane,
                                     evals);
@@ -514,9 +431,8 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
             if (v == mv_v && us == mv_u)
                 bv = mv_b;
             else if constexpr (G > 0)
-                bv = scan_side_filtered<G, BF>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src,
-                                               comp, lane, rho, evals, canon, Hh, hld, heb, hn2,
-                                               lst, rst, aerr, eps, check);
+                bv = scan_side_filtered<G>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp,
+                                           lane, rho, evals, canon, check);
             else
                 bv = scan_side<VEC>(X, d, v, us, u, cj, ws, nbr, k, rev_off, rev_src, comp, lane,
                                     evals);
@@ -553,35 +469,27 @@ __global__ void __launch_bounds__(256, 4) refine_kernel(const float *__restrict_
     }
 }
 
-// Launch of the refinement kernel in the variant the shape allows: in a
-// build with BF16 rows (hr, d <= 256), the tensor-core filter; else the
-// FP32 grouped filter for 16-byte rows with 32 <= d <= 512, else the
-// canonical distance per lane. Persistent grid; edges are fetched from
+// Launch of the refinement kernel in the variant the shape allows: the FP32
+// grouped filter for 16-byte rows with 32 <= d <= 512, else the canonical
+// distance per lane. (Builds with BF16 rows use refine_build, which stages
+// rows in shared memory.) Persistent grid; edges are fetched from
 // *next_item (zeroed by the caller).
 famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, const int32_t *nbr,
                            int k, const int32_t *rev_off, const int32_t *rev_src,
                            const int32_t *comp, int32_t *eu, int32_t *ev, float *ew,
                            const int32_t *eci, const int32_t *ecj, const int32_t *order,
                            int64_t m, const int64_t *m_dev, int max_iters, int32_t *change_hist,
-                           unsigned long long *next_item, unsigned long long *evals,
-                           const HalfRows &hr, bool check, int *variant) {
+                           unsigned long long *next_item, unsigned long long *evals, bool check,
+                           int *variant) {
     const int th = 256;
     const int G = (vec4 && d >= 32) ? sq_group(d) : 0;
-    // BF16 filter on the tensor cores: ns = ld / 64 segments, d <= 256
-    const int nsk = hr.ld >> 6;
-    const int GB = nsk <= 1 ? 1 : (nsk <= 2 ? 2 : 4);
-    // (builds only: the BF scan trusts comp to label this graph's components)
-    const bool bf = hr.h != nullptr && hr.lst != nullptr && !check && nsk >= 1 && nsk <= 4;
-    const void *fn = bf ? (GB == 1 ? (const void *)refine_kernel<4, 1, true>
-                           : GB == 2 ? (const void *)refine_kernel<4, 2, true>
-                                     : (const void *)refine_kernel<4, 4, true>)
-                   : G == 2 ? (const void *)refine_kernel<4, 2, false>
-                   : G == 4 ? (const void *)refine_kernel<4, 4, false>
-                   : G == 8 ? (const void *)refine_kernel<4, 8, false>
-                   : G == 16 ? (const void *)refine_kernel<4, 16, false>
-                   : G == 32 ? (const void *)refine_kernel<4, 32, false>
-                   : vec4 ? (const void *)refine_kernel<4, 0, false>
-                          : (const void *)refine_kernel<1, 0, false>;
+    const void *fn = G == 2 ? (const void *)refine_kernel<4, 2>
+                   : G == 4 ? (const void *)refine_kernel<4, 4>
+                   : G == 8 ? (const void *)refine_kernel<4, 8>
+                   : G == 16 ? (const void *)refine_kernel<4, 16>
+                   : G == 32 ? (const void *)refine_kernel<4, 32>
+                   : vec4 ? (const void *)refine_kernel<4, 0>
+                          : (const void *)refine_kernel<1, 0>;
     // persistent grid: as many blocks as stay resident
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, th, 0) != cudaSuccess ||
@@ -592,38 +500,21 @@ famst_status launch_refine(const Exec &ex, const float *X, int d, bool vec4, con
     unsigned grid = unsigned(want < cap ? want : cap);
     if (grid == 0) grid = 1;
     const float rho = fast_rho(d, 1);
-    // canonical distance vs the exact one, generously: (d + 16) u
-    const float eps = float((d + 16) * std::ldexp(1.0, -24) * 1.1);
-    // |p~ - ||h_x - h_y||^2| <= aerr (||h_x||^2 + ||h_y||^2) + 1e-35: the BF16
-    // products are exact in FP32; a 16-term block sum aligned to its largest
-    // exponent and cut to 24 bits loses at most 17 2^-23 of its absolute sum,
-    // which gives about ld 2^-23 (||h_x||^2 + ||h_y||^2) for 2 h_x.h_y. Taken
-    // 16 times over (20 kept bits would still be covered), plus the norms'
-    // and the two final roundings; 1e-35 covers products flushed below the
-    // FP32 normal range.
-    const float aerr = float(hr.ld * std::ldexp(1.0, -19) + std::ldexp(1.0, -20));
-    if (variant) *variant = bf ? REFINE_FILTER_BF16_MMA : G > 0 ? REFINE_FILTER_FP32 : REFINE_FILTER_NONE;
-#define REFINE_LAUNCH(V, GG, B)                                                                  \
-    FAMST_LAUNCH(ex, (refine_kernel<V, GG, B>), grid, th, 0, X, d, nbr, k, rev_off, rev_src,     \
-                 comp, eu, ev, ew, eci, ecj, order, m, m_dev, max_iters, change_hist, next_item, \
-                 ex.dstatus, rho, evals, hr.h, hr.ld, hr.eb, hr.n2, hr.lst, hr.rst, aerr, eps,   \
-                 check)
+    if (variant) *variant = G > 0 ? REFINE_FILTER_FP32 : REFINE_FILTER_NONE;
+#define REFINE_LAUNCH(V, GG)                                                                     \
+    FAMST_LAUNCH(ex, (refine_kernel<V, GG>), grid, th, 0, X, d, nbr, k, rev_off, rev_src, comp, \
+                 eu, ev, ew, eci, ecj, order, m, m_dev, max_iters, change_hist, next_item,       \
+                 ex.dstatus, rho, evals, check)
     timer_mark(ex, TIMER_REFINE, false);
-    if (bf) {
-        if (GB == 1) REFINE_LAUNCH(4, 1, true);
-        else if (GB == 2) REFINE_LAUNCH(4, 2, true);
-        else REFINE_LAUNCH(4, 4, true);
-    } else {
-        switch (G) {
-            case 2: REFINE_LAUNCH(4, 2, false); break;
-            case 4: REFINE_LAUNCH(4, 4, false); break;
-            case 8: REFINE_LAUNCH(4, 8, false); break;
-            case 16: REFINE_LAUNCH(4, 16, false); break;
-            case 32: REFINE_LAUNCH(4, 32, false); break;
-            default:
-                if (vec4) REFINE_LAUNCH(4, 0, false);
-                else REFINE_LAUNCH(1, 0, false);
-        }
+    switch (G) {
+        case 2: REFINE_LAUNCH(4, 2); break;
+        case 4: REFINE_LAUNCH(4, 4); break;
+        case 8: REFINE_LAUNCH(4, 8); break;
+        case 16: REFINE_LAUNCH(4, 16); break;
+        case 32: REFINE_LAUNCH(4, 32); break;
+        default:
+            if (vec4) REFINE_LAUNCH(4, 0);
+            else REFINE_LAUNCH(1, 0);
     }
     timer_mark(ex, TIMER_REFINE, true);
 #undef REFINE_LAUNCH
@@ -765,32 +656,6 @@ famst_status half_rows(const Exec &ex, Arena &ar, const float *X, int64_t n, int
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
-__global__ void half_rows_lists_kernel(const float *__restrict__ eb, const float *__restrict__ n2,
-                                       const int32_t *__restrict__ idx, int64_t cnt,
-                                       float2 *__restrict__ out) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= cnt) return;
-    const int32_t y = idx[i];
-    out[i] = make_float2(eb[y], n2[y]);
-}
-
-size_t half_rows_lists_workspace(int64_t n, int k) { return align256(size_t(n) * k * 8) * 2; }
-
-famst_status half_rows_lists(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t n, int k,
-                             const int32_t *rev_src, HalfRows *hr) {
-    if (!hr->h) return FAMST_OK;
-    const int64_t cnt = n * k;   // the reverse lists hold n k entries too
-    float2 *lst = ar.take<float2>(size_t(cnt));
-    float2 *rst = ar.take<float2>(size_t(cnt));
-    if (!lst || !rst) return FAMST_ERR_OOM;
-    const unsigned gr = unsigned((cnt + 255) / 256);
-    FAMST_LAUNCH(ex, half_rows_lists_kernel, gr, 256, 0, hr->eb, hr->n2, nbr, cnt, lst);
-    FAMST_LAUNCH(ex, half_rows_lists_kernel, gr, 256, 0, hr->eb, hr->n2, rev_src, cnt, rst);
-    hr->lst = lst;
-    hr->rst = rst;
-    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
-}
-
 size_t refine_workspace(int64_t m) {
     return align256(size_t(m) * 4) * 2 + 256 + radix_sort_workspace(m);
 }
@@ -800,8 +665,7 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
                           const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
                           int64_t m, int max_iters, int32_t *change_hist,
-                          unsigned long long *evals, const HalfRows &hr, bool check,
-                          int *variant) {
+                          unsigned long long *evals, bool check, int *variant) {
     if (m == 0) return FAMST_OK;
     // order: stable sort of the edges by component-pair tile
     constexpr int TT = 24;
@@ -818,7 +682,7 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
     famst_status st = radix_sort_pairs(ex, ar, keys, order, m, bits);
     if (st != FAMST_OK) return st;
     return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj, order,
-                         m, nullptr, max_iters, change_hist, next_item, evals, hr, check, variant);
+                         m, nullptr, max_iters, change_hist, next_item, evals, check, variant);
 }
 
 }  // namespace famst
@@ -839,7 +703,7 @@ famst_status refine_edges_dev(const Exec &ex, Arena &ar, const float *X, int d, 
     if (cudaMemsetAsync(next_item, 0, 8, ex.stream) != cudaSuccess) return FAMST_ERR_CUDA;
     return launch_refine(ex, X, d, vec4, nbr, k, rev_off, rev_src, comp, eu, ev, ew, eci, ecj,
                          nullptr, m_cap, m_dev, max_iters, change_hist, next_item, nullptr,
-                         HalfRows(), false, nullptr);
+                         false, nullptr);
 }
 
 }  // namespace famst

@@ -398,7 +398,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
                             evals, ctx->pinned + PIN_REF));
         } else {
             ST(refine_edges(ex, ar, X, d, v4, nbr, k, rev_off, rev_src, comp, t, eu, evv, ew, eci,
-                            ecj, m, max_iters, hist, evals, hr, false, &filter));
+                            ecj, m, max_iters, hist, evals, false, &filter));
         }
         ev.mark(ctx->stream, 4);
         famst_status s = sync_status(ctx);

@@ -396,65 +396,6 @@ __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], uint32_t a0, uint3
         : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// Dot products h_j . h_x of the 32 lanes' candidate rows with one BF16 row
-// h_x (rows of stride ld, a multiple of 64, zero padded; ns = ld / 64 <= NS
-// segments of 64 elements). Four m16n8k16 tiles of 8 candidates each. Every
-// candidate takes two rows of A: the first and the second 32 elements of
-// each segment (rows 2 q and 2 q + 1 for candidate q < 4 of the tile, rows
-// 8 + 2 q and 9 + 2 q for candidate 4 + q), so the 8 lanes of two quads read
-// 128 contiguous bytes of one row per load; columns 0 and 1 of B hold the
-// matching halves of h_x, and candidate q's dot product is D[2q][0] +
-// D[2q + 1][1]. Inside a segment the k order is permuted: lane t of a quad
-// loads 8 consecutive elements and feeds them to two k-chunks, and h_x's
-// fragment (x_frag_mma, lanes 0-7) follows the same permutation, so every
-// product pairs equal elements. Lane j gets candidate j's dot product (0 for
-// cand < 0).
-template <int NS>
-__device__ __forceinline__ void x_frag_mma(const __nv_bfloat16 *__restrict__ hx, int ns, int lane,
-                                           uint4 (&bx)[NS]) {
-#pragma unroll
-    for (int sg = 0; sg < NS; ++sg) {
-        bx[sg] = make_uint4(0u, 0u, 0u, 0u);
-        if (sg < ns && lane < 8)
-            bx[sg] = __ldg(reinterpret_cast<const uint4 *>(hx + 64 * sg + 8 * lane));
-    }
-}
-
-template <int NS>
-__device__ __forceinline__ float warp_dot32_mma(const __nv_bfloat16 *__restrict__ H, int ld,
-                                                int ns, const uint4 (&bx)[NS], int fixed,
-                                                int cand, int lane) {
-    const int g = lane >> 2, t = lane & 3;
-    const int half = g & 1, q = g >> 1;
-    float res = 0.0f;
-#pragma unroll
-    for (int T = 0; T < 4; ++T) {
-        const int ia = __shfl_sync(0xffffffffu, cand, 8 * T + q);
-        const int ib = __shfl_sync(0xffffffffu, cand, 8 * T + 4 + q);
-        const uint4 *ra = reinterpret_cast<const uint4 *>(
-            H + int64_t(ia >= 0 ? ia : fixed) * ld + 32 * half + 8 * t);
-        const uint4 *rb = reinterpret_cast<const uint4 *>(
-            H + int64_t(ib >= 0 ? ib : fixed) * ld + 32 * half + 8 * t);
-        float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int sg = 0; sg < NS; ++sg) {
-            if (sg < ns) {
-                const uint4 u = __ldg(ra + 8 * sg), v = __ldg(rb + 8 * sg);
-                mma_bf16_16816(c, u.x, v.x, u.y, v.y, bx[sg].x, bx[sg].y);
-                mma_bf16_16816(c, u.z, v.z, u.w, v.w, bx[sg].z, bx[sg].w);
-            }
-        }
-        // lane 8 q: D[2q][0] (c[0]) and D[8 + 2q][0] (c[2]); lane 8 q + 4:
-        // D[2q + 1][1] (c[1]) and D[9 + 2q][1] (c[3])
-        const float s0 = __fadd_rn(c[0], __shfl_xor_sync(0xffffffffu, c[1], 4));
-        const float s1 = __fadd_rn(c[2], __shfl_xor_sync(0xffffffffu, c[3], 4));
-        const float v0 = __shfl_sync(0xffffffffu, s0, 8 * (lane & 3));
-        const float v1 = __shfl_sync(0xffffffffu, s1, 8 * (lane & 3));
-        if ((lane >> 3) == T) res = (lane & 4) ? v1 : v0;
-    }
-    return cand >= 0 ? res : 0.0f;
-}
-
 // Lanes per row for the grouped sums with V = 4 float4 per lane (0: d too
 // large or not a multiple of 4).
 inline int sq_group(int d) {
@@ -637,18 +578,11 @@ struct HalfRows {
     const float *eb = nullptr;   // per-row error bound
     const float *m = nullptr;    // the centre m (d values)
     const float *n2 = nullptr;   // per row: ||h||^2 (FP32 sum of the exact squares)
-    // (eb, n2) of the points of the kNN lists (n k entries, in nbr's order)
-    // and of the reverse lists (in rev_src's order): one coalesced load per
-    // 32 candidates instead of one scattered load per candidate
-    const float2 *lst = nullptr, *rst = nullptr;
     GLists g;   // deduplicated G lists for the staged refinement scans
 };
 size_t half_rows_workspace(int64_t n, int d);
 famst_status half_rows(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
                        HalfRows *out);
-size_t half_rows_lists_workspace(int64_t n, int k);
-famst_status half_rows_lists(const Exec &ex, Arena &ar, const int32_t *nbr, int64_t n, int k,
-                             const int32_t *rev_src, HalfRows *hr);
 // refine_staged.cu: deduplicated G lists; Algorithm 4 inside a build with
 // candidate rows staged in shared memory (sweep-synchronous grouped scans,
 // then per-edge fixed points for the last active edges)
@@ -679,8 +613,8 @@ famst_status refine_edges(const Exec &ex, Arena &ar, const float *X, int d, bool
                           const int32_t *rev_src, const int32_t *comp, int64_t t, int32_t *eu,
                           int32_t *ev, float *ew, const int32_t *eci, const int32_t *ecj,
                           int64_t m, int max_iters, int32_t *change_hist /*max_iters+1*/,
-                          unsigned long long *evals = nullptr, const HalfRows &hr = HalfRows(),
-                          bool check = true, int *variant = nullptr);
+                          unsigned long long *evals = nullptr, bool check = true,
+                          int *variant = nullptr);
 // candidate filter of the refinement kernel that ran (build info)
 constexpr int REFINE_FILTER_NONE = 0;      // canonical distance per lane
 constexpr int REFINE_FILTER_FP32 = 1;      // FP32 grouped sums + canonical survivors

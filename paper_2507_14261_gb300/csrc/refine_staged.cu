@@ -385,33 +385,77 @@ __global__ void bsp_count_kernel(const int32_t *__restrict__ list, const int32_t
     slot[e] = atomicAdd(&cnt[c], 1);
 }
 
-// the scans sorted by scanned vertex; each scan's best starts at its incumbent
+// The scans sorted by scanned vertex, one record per sorted position:
+// (edge, fixed point, its eb, its ||h||^2), and the best key starting at the
+// edge's incumbent (w, 0).
 __global__ void bsp_scatter_kernel(const int32_t *__restrict__ list, const int32_t *__restrict__ nt,
                                    int side, const int32_t *__restrict__ eu,
                                    const int32_t *__restrict__ ev, const float *__restrict__ ew,
+                                   const float *__restrict__ heb, const float *__restrict__ hn2,
                                    const int32_t *__restrict__ bstart,
-                                   const int32_t *__restrict__ slot, int32_t *__restrict__ tasks,
+                                   const int32_t *__restrict__ slot, int4 *__restrict__ rec,
                                    unsigned long long *__restrict__ best) {
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= *nt) return;
     const int32_t e = list[i];
     const int32_t c = side ? ev[e] : eu[e];
-    tasks[bstart[c] + slot[e]] = e;
-    best[e] = uint64_t(__float_as_uint(ew[e])) << 32;
+    const int32_t fx = side ? eu[e] : ev[e];
+    const int64_t pos = int64_t(bstart[c]) + slot[e];
+    rec[pos] = make_int4(e, fx, __float_as_int(heb[fx]), __float_as_int(hn2[fx]));
+    best[pos] = uint64_t(__float_as_uint(ew[e])) << 32;
 }
 
-// One warp per scanned vertex c (visited in component order): G[c]'s rows
-// are staged once per round of 32 and scored against the fixed points of
-// all scans of c, eight per mma; each scan's best key is kept in best[e].
+// Up to four canonical distances (X rows fx[j], c2[j]) computed together,
+// each keyed (w, 1 + c2) into sbest[tj] when smaller; warp-uniform inputs.
+template <int XR>
+__device__ __forceinline__ void canon_batch(const float *__restrict__ X, int d, int nq,
+                                            const int (&fx)[4], const int (&c2)[4],
+                                            const int (&tj)[4], unsigned long long *sbest,
+                                            int lane) {
+    if constexpr (XR > 0) {
+        float xa[4][XR], xb[4][XR];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < XR; ++q) {
+                const int t = lane + 32 * q;
+                const bool ok = j < nq && t < d;
+                xa[j][q] = ok ? __ldg(X + int64_t(fx[j]) * d + t) : 0.0f;
+                xb[j][q] = ok ? __ldg(X + int64_t(c2[j]) * d + t) : 0.0f;
+            }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (j >= nq) break;
+            float p = 0.0f;
+#pragma unroll
+            for (int q = 0; q < XR; ++q) {
+                const float dl = __fsub_rn(xb[j][q], xa[j][q]);
+                p = __fmaf_rn(dl, dl, p);
+            }
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) p = __fadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
+            const uint64_t key = cand_key(__fsqrt_rn(p), c2[j]);
+            if (lane == 0 && key < sbest[tj[j]]) sbest[tj[j]] = key;
+        }
+    } else {
+        for (int j = 0; j < nq; ++j) {
+            const uint64_t key = cand_key(canon_w<0>(X, d, fx[j], c2[j], lane), c2[j]);
+            if (lane == 0 && key < sbest[tj[j]]) sbest[tj[j]] = key;
+        }
+    }
+    __syncwarp();
+}
+
+// One warp per scanned vertex c (visited in component order, 32 vertices
+// looked up per step): G[c]'s rows are staged once per round of 32 and
+// scored against the fixed points of all scans of c, eight per mma; the
+// best key of the scan at sorted position i is kept in best[i].
 template <int NKS, int XR, int MINB>
 __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
     refine_group_kernel(const float *__restrict__ X, int d, GLists g,
-                        const __nv_bfloat16 *__restrict__ H, const float *__restrict__ heb,
-                        const float *__restrict__ hn2, const int32_t *__restrict__ members,
+                        const __nv_bfloat16 *__restrict__ H, const int32_t *__restrict__ members,
                         int64_t n, const int32_t *__restrict__ bstart,
-                        const int32_t *__restrict__ tasks, int side,
-                        const int32_t *__restrict__ eu, const int32_t *__restrict__ ev,
-                        unsigned long long *__restrict__ best,
+                        const int4 *__restrict__ rec, unsigned long long *__restrict__ best,
                         unsigned long long *__restrict__ evals_out, float aerr, float eps) {
     using S = Stage<NKS>;
     extern __shared__ __align__(128) char smem[];
@@ -426,109 +470,149 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
     const float inf = __int_as_float(0x7f800000);
     const int g4 = lane >> 2, t4 = lane & 3;   // mma fragment row group / column pair
     unsigned long long evals = 0, canon = 0;
+    // warp w visits the members at w, w + W, w + 2W, ... (W warps in all),
+    // so the warps work on neighbouring members, i.e. a few components at a
+    // time; the next 32 of its vertices are looked up together
     const int64_t nw = int64_t(gridDim.x) * S::WARPS;
-    for (int64_t p = int64_t(blockIdx.x) * S::WARPS + warp; p < n; p += nw) {
-        const int c = members[p];
-        const int t0 = bstart[c], t1 = bstart[c + 1];
-        if (t0 == t1) continue;
-        const int base = g.off[c], deg = g.off[c + 1] - base;
-        for (int r0 = 0; r0 < deg; r0 += 32) {
-            const int idx = r0 + lane;
-            const bool valid = idx < deg;
-            int cand = -1;
-            float2 en = make_float2(inf, 0.0f);
-            if (valid) {
-                cand = __ldg(g.id + base + idx);
-                en = __ldg(g.en + base + idx);
+    const int64_t w0 = int64_t(blockIdx.x) * S::WARPS + warp;
+    for (int64_t p0 = w0; p0 < n; p0 += 32 * nw) {
+        int cl = 0, tl0 = 0, tl1 = 0, gl0 = 0, gl1 = 0;
+        const int64_t pl = p0 + int64_t(lane) * nw;
+        if (pl < n) {
+            cl = members[pl];
+            tl0 = bstart[cl];
+            tl1 = bstart[cl + 1];
+            if (tl1 > tl0) {
+                gl0 = g.off[cl];
+                gl1 = g.off[cl + 1];
             }
-            const int nv = __popc(__ballot_sync(0xffffffffu, valid));
-            s_en[lane] = en;
-            s_id[lane] = cand;
-            stage_rows<NKS>(H, cand, sbuf, lane);
-            for (int tb = t0; tb < t1; tb += 8) {
-                const int ntb = t1 - tb < 8 ? t1 - tb : 8;
-                if (lane < ntb) {
-                    const int32_t e = tasks[tb + lane];
-                    const int32_t fx = side ? eu[e] : ev[e];
-                    s_task[lane] = make_float4(__int_as_float(fx), __ldg(heb + fx),
-                                               __ldg(hn2 + fx), 0.0f);
-                    s_best[lane] = best[e];
+        }
+        unsigned busy = __ballot_sync(0xffffffffu, tl1 > tl0);
+        while (busy) {
+            const int src = __ffs(busy) - 1;
+            busy &= busy - 1;
+            const int t0 = __shfl_sync(0xffffffffu, tl0, src);
+            const int t1 = __shfl_sync(0xffffffffu, tl1, src);
+            const int base = __shfl_sync(0xffffffffu, gl0, src);
+            const int deg = __shfl_sync(0xffffffffu, gl1, src) - base;
+            for (int r0 = 0; r0 < deg; r0 += 32) {
+                const int idx = r0 + lane;
+                const bool valid = idx < deg;
+                int cand = -1;
+                float2 en = make_float2(inf, 0.0f);
+                if (valid) {
+                    cand = __ldg(g.id + base + idx);
+                    en = __ldg(g.en + base + idx);
                 }
-                __syncwarp();
-                // B column j = the fixed row of task slot j (lane 4 j + t
-                // carries k pairs (2t, 2t+1) and (8+2t, 9+2t) of each k step)
-                uint32_t b0[NKS], b1[NKS];
-                {
-                    const bool has = g4 < ntb;
-                    const __nv_bfloat16 *hf =
-                        H + int64_t(has ? __float_as_int(s_task[g4].x) : 0) * S::LD;
-#pragma unroll
-                    for (int ks = 0; ks < NKS; ++ks) {
-                        b0[ks] = has ? ldg_u32(hf + 16 * ks + 2 * t4) : 0u;
-                        b1[ks] = has ? ldg_u32(hf + 16 * ks + 8 + 2 * t4) : 0u;
+                const int nv = __popc(__ballot_sync(0xffffffffu, valid));
+                s_en[lane] = en;
+                s_id[lane] = cand;
+                stage_rows<NKS>(H, cand, sbuf, lane);
+                for (int tb = t0; tb < t1; tb += 8) {
+                    const int ntb = t1 - tb < 8 ? t1 - tb : 8;
+                    if (lane < ntb) {
+                        const int4 r = rec[tb + lane];
+                        s_task[lane] = make_float4(__int_as_float(r.y), __int_as_float(r.z),
+                                                   __int_as_float(r.w), 0.0f);
+                        s_best[lane] = best[tb + lane];
                     }
-                }
-                float acc[2][4];
-                round_dots<NKS>(sbuf, b0, b1, lane, acc);
-                // this lane holds the pairs (candidate 16 T + g4 + 8 (e2 >> 1),
-                // task 2 t4 + (e2 & 1)) in acc[T][e2]
-                float lo[2][4];
-                float mh0 = inf, mh1 = inf;
+                    __syncwarp();
+                    // B column j = the fixed row of task slot j (lane 4 j + t
+                    // carries k pairs (2t, 2t+1) and (8+2t, 9+2t) of each k step)
+                    uint32_t b0[NKS], b1[NKS];
+                    {
+                        const bool has = g4 < ntb;
+                        const __nv_bfloat16 *hf =
+                            H + int64_t(has ? __float_as_int(s_task[g4].x) : 0) * S::LD;
 #pragma unroll
-                for (int T = 0; T < 2; ++T)
-#pragma unroll
-                    for (int e2 = 0; e2 < 4; ++e2) {
-                        const int ci = 16 * T + g4 + 8 * (e2 >> 1), tj = 2 * t4 + (e2 & 1);
-                        float hi = inf;
-                        lo[T][e2] = inf;
-                        if (ci < nv && tj < ntb) {
-                            const float2 ce = s_en[ci];
-                            const float4 ts = s_task[tj];
-                            dist_bounds(acc[T][e2], ts.z, ce.y, ts.y, ce.x, aerr, eps, lo[T][e2],
-                                        hi);
-                        }
-                        if (e2 & 1) mh1 = fminf(mh1, hi);
-                        else mh0 = fminf(mh0, hi);
-                    }
-                // per task: the smallest upper bound over all candidates (the
-                // lanes with the same t4)
-#pragma unroll
-                for (int o = 4; o <= 16; o <<= 1) {
-                    mh0 = fminf(mh0, __shfl_xor_sync(0xffffffffu, mh0, o));
-                    mh1 = fminf(mh1, __shfl_xor_sync(0xffffffffu, mh1, o));
-                }
-                float bnd[2];
-                bnd[0] = 2 * t4 < ntb
-                             ? __fmul_ru(fminf(mh0, key_w(s_best[2 * t4])), 1.0f + 0x1p-22f)
-                             : -inf;
-                bnd[1] = 2 * t4 + 1 < ntb
-                             ? __fmul_ru(fminf(mh1, key_w(s_best[2 * t4 + 1])), 1.0f + 0x1p-22f)
-                             : -inf;
-                if (lane == 0) evals += (unsigned long long)(nv) * ntb;
-                __syncwarp();
-                // survivors, decided on canonical distances by the whole warp
-#pragma unroll
-                for (int T = 0; T < 2; ++T)
-#pragma unroll
-                    for (int e2 = 0; e2 < 4; ++e2) {
-                        unsigned sv = __ballot_sync(0xffffffffu, lo[T][e2] <= bnd[e2 & 1]);
-                        if (lane == 0) canon += __popc(sv);
-                        while (sv) {
-                            const int sl = __ffs(sv) - 1;
-                            sv &= sv - 1;
-                            const int ci = 16 * T + (sl >> 2) + 8 * (e2 >> 1);
-                            const int tj = 2 * (sl & 3) + (e2 & 1);
-                            const int c2 = s_id[ci];
-                            const int fx = __float_as_int(s_task[tj].x);
-                            const uint64_t key = cand_key(canon_w<XR>(X, d, fx, c2, lane), c2);
-                            if (lane == 0 && key < s_best[tj]) s_best[tj] = key;
-                            __syncwarp();
+                        for (int ks = 0; ks < NKS; ++ks) {
+                            b0[ks] = has ? ldg_u32(hf + 16 * ks + 2 * t4) : 0u;
+                            b1[ks] = has ? ldg_u32(hf + 16 * ks + 8 + 2 * t4) : 0u;
                         }
                     }
-                if (lane < ntb) best[tasks[tb + lane]] = s_best[lane];
-                __syncwarp();
+                    float acc[2][4];
+                    round_dots<NKS>(sbuf, b0, b1, lane, acc);
+                    // this lane holds the pairs (candidate 16 T + g4 + 8 (e2 >> 1),
+                    // task 2 t4 + (e2 & 1)) in acc[T][e2]
+                    float lo[2][4];
+                    float mh0 = inf, mh1 = inf;
+#pragma unroll
+                    for (int T = 0; T < 2; ++T)
+#pragma unroll
+                        for (int e2 = 0; e2 < 4; ++e2) {
+                            const int ci = 16 * T + g4 + 8 * (e2 >> 1), tj = 2 * t4 + (e2 & 1);
+                            float hi = inf;
+                            lo[T][e2] = inf;
+                            if (ci < nv && tj < ntb) {
+                                const float2 ce = s_en[ci];
+                                const float4 ts = s_task[tj];
+                                dist_bounds(acc[T][e2], ts.z, ce.y, ts.y, ce.x, aerr, eps,
+                                            lo[T][e2], hi);
+                            }
+                            if (e2 & 1) mh1 = fminf(mh1, hi);
+                            else mh0 = fminf(mh0, hi);
+                        }
+                    // per task: the smallest upper bound over all candidates
+                    // (the lanes with the same t4)
+#pragma unroll
+                    for (int o = 4; o <= 16; o <<= 1) {
+                        mh0 = fminf(mh0, __shfl_xor_sync(0xffffffffu, mh0, o));
+                        mh1 = fminf(mh1, __shfl_xor_sync(0xffffffffu, mh1, o));
+                    }
+                    const float bnd0 =
+                        2 * t4 < ntb
+                            ? __fmul_ru(fminf(mh0, key_w(s_best[2 * t4])), 1.0f + 0x1p-22f)
+                            : -inf;
+                    const float bnd1 =
+                        2 * t4 + 1 < ntb
+                            ? __fmul_ru(fminf(mh1, key_w(s_best[2 * t4 + 1])), 1.0f + 0x1p-22f)
+                            : -inf;
+                    if (lane == 0) evals += (unsigned long long)(nv) * ntb;
+                    __syncwarp();
+                    // survivors, decided on canonical distances by the whole
+                    // warp, up to four at a time; bit 4 T + e2 of `my` marks a
+                    // surviving pair of this lane (one copy of the batch code).
+                    unsigned my = 0;
+#pragma unroll
+                    for (int T = 0; T < 2; ++T)
+#pragma unroll
+                        for (int e2 = 0; e2 < 4; ++e2)
+                            if (lo[T][e2] <= ((e2 & 1) ? bnd1 : bnd0)) my |= 1u << (4 * T + e2);
+                    {
+                        int cnt = __popc(my);
+#pragma unroll
+                        for (int o = 16; o >= 1; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+                        if (lane == 0) canon += unsigned(cnt);
+                    }
+#pragma unroll 1
+                    while (true) {
+                        int qf[4], qc[4], qt[4], nq = 0;
+#pragma unroll 1
+                        while (nq < 4) {
+                            const unsigned any = __ballot_sync(0xffffffffu, my != 0u);
+                            if (!any) break;
+                            const int sl = __ffs(any) - 1;
+                            const int bit = __ffs(__shfl_sync(0xffffffffu, my, sl)) - 1;
+                            if (lane == sl) my &= my - 1u;
+                            const int ci = 16 * (bit >> 2) + (sl >> 2) + 8 * ((bit & 3) >> 1);
+                            const int tj = 2 * (sl & 3) + (bit & 1);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if (j == nq) {
+                                    qc[j] = s_id[ci];
+                                    qf[j] = __float_as_int(s_task[tj].x);
+                                    qt[j] = tj;
+                                }
+                            ++nq;
+                        }
+                        if (nq == 0) break;
+                        canon_batch<XR>(X, d, nq, qf, qc, qt, s_best, lane);
+                    }
+                    if (lane < ntb) best[tb + lane] = s_best[lane];
+                    __syncwarp();
+                }
+                __syncwarp();   // the rows stay until every task block is done
             }
-            __syncwarp();   // the rows stay until every task block is done
         }
     }
     if (evals_out && lane == 0) {
@@ -542,6 +626,8 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
 // previous one); the others go on to the v-scans.
 __global__ void bsp_finish_u_kernel(const int32_t *__restrict__ list, const int32_t *__restrict__ nt,
                                     int32_t *__restrict__ eu, float *__restrict__ ew,
+                                    const int32_t *__restrict__ bstart,
+                                    const int32_t *__restrict__ slot,
                                     const unsigned long long *__restrict__ best,
                                     const uint8_t *__restrict__ vstable, uint8_t *__restrict__ uchg,
                                     int32_t *__restrict__ listB, int32_t *__restrict__ nB,
@@ -549,7 +635,7 @@ __global__ void bsp_finish_u_kernel(const int32_t *__restrict__ list, const int3
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= *nt) return;
     const int32_t e = list[i];
-    const unsigned long long b = best[e];
+    const unsigned long long b = best[int64_t(bstart[eu[e]]) + slot[e]];
     const bool moved = key_lo(b) != 0;
     if (moved) eu[e] = int32_t(key_lo(b)) - 1;
     ew[e] = key_w(b);
@@ -564,6 +650,8 @@ __global__ void bsp_finish_u_kernel(const int32_t *__restrict__ list, const int3
 // After the v-scans: move v; changed edges stay active for the next sweep.
 __global__ void bsp_finish_v_kernel(const int32_t *__restrict__ listB, const int32_t *__restrict__ nB,
                                     int32_t *__restrict__ ev, float *__restrict__ ew,
+                                    const int32_t *__restrict__ bstart,
+                                    const int32_t *__restrict__ slot,
                                     const unsigned long long *__restrict__ best,
                                     uint8_t *__restrict__ vstable, const uint8_t *__restrict__ uchg,
                                     int32_t *__restrict__ next, int32_t *__restrict__ nnext,
@@ -571,7 +659,7 @@ __global__ void bsp_finish_v_kernel(const int32_t *__restrict__ listB, const int
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= *nB) return;
     const int32_t e = listB[i];
-    const unsigned long long b = best[e];
+    const unsigned long long b = best[int64_t(bstart[ev[e]]) + slot[e]];
     const bool moved = key_lo(b) != 0;
     if (moved) ev[e] = int32_t(key_lo(b)) - 1;
     ew[e] = key_w(b);
@@ -632,31 +720,26 @@ famst_status launch_staged_t(const Exec &ex, const float *X, int d, const HalfRo
 template <int NKS, int XR, int MINB>
 famst_status launch_group_t(const Exec &ex, const float *X, int d, const HalfRows &hr,
                             const int32_t *members, int64_t n, const int32_t *bstart,
-                            const int32_t *tasks, int side, const int32_t *eu, const int32_t *ev,
-                            unsigned long long *best, unsigned long long *evals) {
+                            const int4 *rec, unsigned long long *best, unsigned long long *evals) {
     using S = Stage<NKS>;
     unsigned grid;
     auto *fn = refine_group_kernel<NKS, XR, MINB>;
     famst_status st =
         occupancy_grid(ex, fn, S::WARPS * 32, S::SMEM, (n + S::WARPS - 1) / S::WARPS, &grid);
     if (st != FAMST_OK) return st;
-    FAMST_LAUNCH(ex, fn, grid, S::WARPS * 32, S::SMEM, X, d, hr.g, hr.h, hr.eb, hr.n2, members, n,
-                 bstart, tasks, side, eu, ev, best, evals, refine_aerr<NKS>(), refine_eps(d));
+    FAMST_LAUNCH(ex, fn, grid, S::WARPS * 32, S::SMEM, X, d, hr.g, hr.h, members, n, bstart, rec,
+                 best, evals, refine_aerr<NKS>(), refine_eps(d));
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 famst_status launch_group(const Exec &ex, const float *X, int d, const HalfRows &hr,
                           const int32_t *members, int64_t n, const int32_t *bstart,
-                          const int32_t *tasks, int side, const int32_t *eu, const int32_t *ev,
-                          unsigned long long *best, unsigned long long *evals) {
+                          const int4 *rec, unsigned long long *best, unsigned long long *evals) {
     if (hr.ld == 64)
-        return launch_group_t<4, 2, 4>(ex, X, d, hr, members, n, bstart, tasks, side, eu, ev,
-                                       best, evals);
+        return launch_group_t<4, 2, 4>(ex, X, d, hr, members, n, bstart, rec, best, evals);
     if (hr.ld == 128)
-        return launch_group_t<8, 4, 3>(ex, X, d, hr, members, n, bstart, tasks, side, eu, ev,
-                                       best, evals);
-    return launch_group_t<16, 0, 2>(ex, X, d, hr, members, n, bstart, tasks, side, eu, ev, best,
-                                    evals);
+        return launch_group_t<8, 4, 3>(ex, X, d, hr, members, n, bstart, rec, best, evals);
+    return launch_group_t<16, 0, 2>(ex, X, d, hr, members, n, bstart, rec, best, evals);
 }
 
 }  // namespace
@@ -703,8 +786,9 @@ famst_status launch_refine_staged(const Exec &ex, const float *X, int d, const H
 }
 
 size_t refine_build_workspace(int64_t n, int64_t m) {
-    return 2 * align256(size_t(n + 1) * 4) + scan_workspace(n + 1) + 4 * align256(size_t(m) * 4) +
-           align256(size_t(m) * 8) + 2 * align256(size_t(m)) + align256(64);
+    return 2 * align256(size_t(n + 1) * 4) + scan_workspace(n + 1) + 3 * align256(size_t(m) * 4) +
+           align256(size_t(m) * 16) + align256(size_t(m) * 8) + 2 * align256(size_t(m)) +
+           align256(64);
 }
 
 // Algorithm 4 repeated until no edge changes (Algorithm 1), inside a build:
@@ -720,14 +804,14 @@ famst_status refine_build(const Exec &ex, Arena &ar, const float *X, int d, cons
     int32_t *cnt = ar.take<int32_t>(size_t(n + 1));
     int32_t *bstart = ar.take<int32_t>(size_t(n + 1));
     int32_t *slot = ar.take<int32_t>(size_t(m));
-    int32_t *tasks = ar.take<int32_t>(size_t(m));
+    int4 *rec = ar.take<int4>(size_t(m));
     int32_t *listA = ar.take<int32_t>(size_t(m));
     int32_t *listB = ar.take<int32_t>(size_t(m));
     unsigned long long *best = ar.take<unsigned long long>(size_t(m));
     uint8_t *vstable = ar.take<uint8_t>(size_t(m));
     uint8_t *uchg = ar.take<uint8_t>(size_t(m));
     int32_t *counts = ar.take<int32_t>(16);   // [0] |list A|, [1] |list B|, [2] next; [8..9] cursor
-    if (!cnt || !bstart || !slot || !tasks || !listA || !listB || !best || !vstable || !uchg ||
+    if (!cnt || !bstart || !slot || !rec || !listA || !listB || !best || !vstable || !uchg ||
         !counts)
         return FAMST_ERR_OOM;
     unsigned long long *next_item = reinterpret_cast<unsigned long long *>(counts + 8);
@@ -743,9 +827,9 @@ famst_status refine_build(const Exec &ex, Arena &ar, const float *X, int d, cons
         famst_status st = exclusive_scan_i32(ex, ar, cnt, bstart, n + 1, nullptr);
         ar.off = mark;
         if (st != FAMST_OK) return st;
-        FAMST_LAUNCH(ex, bsp_scatter_kernel, blocks(nmax), th, 0, list, nt, side, eu, ev, ew,
-                     bstart, slot, tasks, best);
-        return launch_group(ex, X, d, hr, members, n, bstart, tasks, side, eu, ev, best, evals);
+        FAMST_LAUNCH(ex, bsp_scatter_kernel, blocks(nmax), th, 0, list, nt, side, eu, ev, ew, hr.eb,
+                     hr.n2, bstart, slot, rec, best);
+        return launch_group(ex, X, d, hr, members, n, bstart, rec, best, evals);
     };
     timer_mark(ex, TIMER_REFINE, false);
     FAMST_LAUNCH(ex, bsp_iota_kernel, blocks(m), th, 0, listA, m);
@@ -762,13 +846,13 @@ famst_status refine_build(const Exec &ex, Arena &ar, const float *X, int d, cons
             return FAMST_ERR_CUDA;
         famst_status st = phase(listA, counts, active, 0);
         if (st != FAMST_OK) return st;
-        FAMST_LAUNCH(ex, bsp_finish_u_kernel, blocks(active), th, 0, listA, counts, eu, ew, best,
-                     vstable, uchg, listB, counts + 1, change_hist, sweep);
+        FAMST_LAUNCH(ex, bsp_finish_u_kernel, blocks(active), th, 0, listA, counts, eu, ew, bstart,
+                     slot, best, vstable, uchg, listB, counts + 1, change_hist, sweep);
         st = phase(listB, counts + 1, active, 1);
         if (st != FAMST_OK) return st;
         // listA receives the edges still active (count in counts[2])
         FAMST_LAUNCH(ex, bsp_finish_v_kernel, blocks(active), th, 0, listB, counts + 1, ev, ew,
-                     best, vstable, uchg, listA, counts + 2, change_hist, sweep);
+                     bstart, slot, best, vstable, uchg, listA, counts + 2, change_hist, sweep);
         if (cudaMemcpyAsync(pinned_host + 1, counts + 2, 4, cudaMemcpyDeviceToHost, ex.stream) !=
                 cudaSuccess ||
             cudaStreamSynchronize(ex.stream) != cudaSuccess)
