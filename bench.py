@@ -539,19 +539,24 @@ def main():
                              "kernel": "rerank_sorted_kernel",
                              "note": "(KC - 1) FP32 candidate rows per query + nbr/dist out"}
     if ms_refk > 0:
-        # per candidate distance: its BF16 row (2 d B) and its list entry (id
-        # 4 B + error bound and norm 8 B); per canonical survivor its FP32 row
-        rbytes = evals * (2.0 * w.d + 12.0) + canon * 4.0 * w.d
+        # bytes Algorithm 4's kernels read: every staged candidate BF16 row
+        # (2 ld B) with its list entry (id, eb, ||h||^2: 12 B), every fixed
+        # point's BF16 row with its scan record (2 ld + 24 B), and two FP32 rows
+        # per canonical evaluation (2 x 4 d B)
+        ld = (w.d + 63) // 64 * 64
+        staged, fixed = mean("refine_rows_staged"), mean("refine_fixed_rows")
+        rbytes = staged * (2.0 * ld + 12.0) + fixed * (2.0 * ld + 24.0) + canon * 8.0 * w.d
         ach = rbytes / (ms_refk / 1e3) / 1e9
         kernels["refine"] = {
             "bound": "l2", "ms": ms_refk, "achieved": ach, "peak": l2["l2_gbs"], "unit": "GB/s",
             "frac": ach / l2["l2_gbs"], "distance_evals": evals, "canonical_evals": canon,
-            "kernel": "refine_kernel",
-            "fp32_rows_equiv_gbs": evals * 4.0 * w.d / (ms_refk / 1e3) / 1e9,
-            "note": "bytes the filter needs per candidate (BF16 row + list entry) plus FP32 "
-                    "rows of canonical survivors, over the kernel's own time, against the "
-                    "measured L2 copy bandwidth; fp32_rows_equiv_gbs counts 4 d B per "
-                    "candidate as if every candidate read its FP32 row"}
+            "rows_staged": staged, "fixed_rows": fixed,
+            "pairs_per_s": evals / (ms_refk / 1e3),
+            "kernel": "refine_group_kernel + refine_staged_kernel",
+            "note": "bytes the kernels read (staged candidate rows once per scanned vertex and "
+                    "round, fixed rows, canonical survivors' FP32 rows) over the kernels' own "
+                    "time, against the measured L2 copy bandwidth; the kernels are latency "
+                    "bound (see profiles/), so the fraction is well below 1"}
     if ms_conk > 0:
         m_e = infos[-1]["m"]
         cb = m_e / w.lam * (w.lam * w.lam) * 2.0 * w.d * 4.0
@@ -586,7 +591,8 @@ def main():
     dom = max(cands, key=lambda kk: cands[kk]["ms"])
     kd = kernels[dom]
     units = evals if dom == "refine" else frac_tiles * nq * nk * 128 * 256
-    traffic = traffic_from_profile(kd["kernel"], units)
+    traffic = traffic_from_profile("refine_group_kernel" if dom == "refine" else kd["kernel"],
+                                   units)
     roofline = {"bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
                 "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic,
                 "kernel": kd["kernel"], "ms_per_launch": kd["ms"],

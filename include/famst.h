@@ -103,6 +103,10 @@ typedef struct famst_build_info {
      * canonical re-rank with its certificate, Algorithm 3's kernel and
      * Algorithm 4's kernel */
     double  ms_knn_tiles, ms_rerank, ms_connect_kernel, ms_refine_kernel;
+    /* rows Algorithm 4's kernels read (filter 2 only, 0 otherwise): candidate
+     * BF16 rows staged in shared memory, and rows of fixed points (one per
+     * scan); each canonical evaluation reads two FP32 rows */
+    int64_t refine_rows_staged, refine_fixed_rows;
 } famst_build_info;
 
 /* ------------------------------------------------------------ context */

@@ -371,10 +371,10 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     int32_t *eci = ar.take<int32_t>(size_t(m > 0 ? m : 1));
     int32_t *ecj = ar.take<int32_t>(size_t(m > 0 ? m : 1));
     int32_t *hist = ar.take<int32_t>(size_t(max_iters + 1));
-    unsigned long long *evals = ar.take<unsigned long long>(2);
+    unsigned long long *evals = ar.take<unsigned long long>(4);
     // the components kernels above used this slot; comp lives in slot 0
     int sweeps = 0, filter = -1;
-    unsigned long long evals_host[2] = {0, 0};
+    unsigned long long evals_host[4] = {0, 0, 0, 0};
     int64_t first_delta = 0;
     if (t > 1) {
         ST(member_lists(ex, ar, comp, n, t, members, comp_off));
@@ -391,7 +391,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         ST(refine_glists(ex, ar, nbr, n, k, rev_off, rev_src, &hr));
         CK(cudaMemsetAsync(hist, 0, size_t(max_iters + 1) * 4, ctx->stream));
         if (!evals) return fail(ctx, FAMST_ERR_OOM, "workspace");
-        CK(cudaMemsetAsync(evals, 0, 16, ctx->stream));
+        CK(cudaMemsetAsync(evals, 0, 32, ctx->stream));
         if (refine_staged_supported(hr)) {   // BF16 rows staged in shared memory
             filter = REFINE_FILTER_BF16_MMA;
             ST(refine_build(ex, ar, X, d, hr, members, n, eu, evv, ew, nullptr, m, max_iters, hist,
@@ -407,7 +407,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         int32_t *hh = new (std::nothrow) int32_t[max_iters + 1];
         if (!hh) return fail(ctx, FAMST_ERR_OOM, "host");
         CK(cudaMemcpy(hh, hist, size_t(max_iters + 1) * 4, cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(evals_host, evals, 16, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(evals_host, evals, 32, cudaMemcpyDeviceToHost));
         for (int c = 0; c <= max_iters; ++c)
             if (hh[c]) sweeps = c + 1;
         first_delta = m - hh[0];
@@ -437,6 +437,8 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         info->refine_distance_evals = int64_t(evals_host[0]);
         info->refine_canonical_evals = int64_t(evals_host[1]);
         info->refine_filter = filter;
+        info->refine_rows_staged = int64_t(evals_host[2]);
+        info->refine_fixed_rows = int64_t(evals_host[3]);
         info->W = W[0];
         info->W64 = W[1];
     }

@@ -263,7 +263,7 @@ __device__ __forceinline__ uint64_t scan_staged(
             en = __ldg(g.en + base + idx);
         }
         const unsigned vm = __ballot_sync(0xffffffffu, valid);
-        if (lane == 0) evals += unsigned(__popc(vm));
+        if (lane == 0) evals += unsigned(__popc(vm));   // every candidate is staged once
         stage_rows<NKS>(H, cand, sbuf, lane);
         float acc[2][4];
         round_dots<NKS>(sbuf, b0, b1, lane, acc);
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
     extern __shared__ __align__(128) char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t sbuf = smem_addr(smem + warp * S::WARP_BYTES);
-    unsigned long long evals_total = 0, canon_total = 0;
+    unsigned long long evals_total = 0, canon_total = 0, scans_total = 0;
     while (true) {
         unsigned long long w0 = 0;
         if (lane == 0) w0 = atomicAdd(next_item, 1ull);
@@ -330,15 +330,18 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
             // u-loop: u' in G[u] against v
             const uint64_t bu = scan_staged<NKS, XR>(X, d, u, v, wt, g, H, heb, hn2, sbuf, lane,
                                                      aerr, eps, evals, canon);
+            ++scans_total;
             const int us = key_lo(bu) ? int(key_lo(bu)) - 1 : u;
             float ws = key_w(bu);
             // v-loop: v' in G[v] against the new u*
             uint64_t bv;
             if (v == mv_v && us == mv_u)
                 bv = mv_b;
-            else
+            else {
                 bv = scan_staged<NKS, XR>(X, d, v, us, ws, g, H, heb, hn2, sbuf, lane, aerr, eps,
                                           evals, canon);
+                ++scans_total;
+            }
             mv_v = v;
             mv_u = us;
             mv_b = bv;
@@ -359,9 +362,11 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
         evals_total += evals;
         canon_total += canon;
     }
-    if (evals_out && lane == 0) {   // [0] candidate distances, [1] canonical evaluations
+    if (evals_out && lane == 0) {   // pairs, canonical evaluations, rows staged, fixed rows read
         atomicAdd(evals_out, evals_total);
         atomicAdd(evals_out + 1, canon_total);
+        atomicAdd(evals_out + 2, evals_total);
+        atomicAdd(evals_out + 3, scans_total);
     }
 }
 
@@ -469,7 +474,7 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
         reinterpret_cast<unsigned long long *>(wb + S::ROWS_BYTES + 512);    // 8 best keys
     const float inf = __int_as_float(0x7f800000);
     const int g4 = lane >> 2, t4 = lane & 3;   // mma fragment row group / column pair
-    unsigned long long evals = 0, canon = 0;
+    unsigned long long evals = 0, canon = 0, staged = 0, fixed_rows = 0;
     // warp w visits the members at w, w + W, w + 2W, ... (W warps in all),
     // so the warps work on neighbouring members, i.e. a few components at a
     // time; the next 32 of its vertices are looked up together
@@ -508,8 +513,10 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
                 s_en[lane] = en;
                 s_id[lane] = cand;
                 stage_rows<NKS>(H, cand, sbuf, lane);
+                staged += unsigned(nv);
                 for (int tb = t0; tb < t1; tb += 8) {
                     const int ntb = t1 - tb < 8 ? t1 - tb : 8;
+                    fixed_rows += unsigned(ntb);
                     if (lane < ntb) {
                         const int4 r = rec[tb + lane];
                         s_task[lane] = make_float4(__int_as_float(r.y), __int_as_float(r.z),
@@ -615,9 +622,11 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
             }
         }
     }
-    if (evals_out && lane == 0) {
+    if (evals_out && lane == 0) {   // pairs, canonical evaluations, rows staged, fixed rows read
         atomicAdd(evals_out, evals);
         atomicAdd(evals_out + 1, canon);
+        atomicAdd(evals_out + 2, staged);
+        atomicAdd(evals_out + 3, fixed_rows);
     }
 }
 

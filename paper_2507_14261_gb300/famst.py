@@ -43,7 +43,8 @@ class BuildInfo(ctypes.Structure):
         ("refine_canonical_evals", ctypes.c_int64), ("refine_filter", ctypes.c_int32),
         ("reserved0", ctypes.c_int32), ("ms_knn_tiles", ctypes.c_double),
         ("ms_rerank", ctypes.c_double), ("ms_connect_kernel", ctypes.c_double),
-        ("ms_refine_kernel", ctypes.c_double),
+        ("ms_refine_kernel", ctypes.c_double), ("refine_rows_staged", ctypes.c_int64),
+        ("refine_fixed_rows", ctypes.c_int64),
     ]
 
     def as_dict(self):
