@@ -351,6 +351,61 @@ def batch_sub(fam, torch, local: int, prec: str, steps: int = 5) -> dict:
             "timing": "host wall clock around synchronised replays"}
 
 
+def run_sweep(args, world, rank, local):
+    """The shape of the paper's k / lambda study (Sec. 5: relative error and
+    time against k and lambda) on the synthetic stand-ins for its data: the
+    2,000 x 16 and 100,000 x 128 Gaussian mixtures. For every (k, lambda) one
+    JSON line: build time (median of 3 after a warm-up, CUDA events),
+    W, Eq. 1's relative error against the exact EMST of the same cloud (GPU
+    Boruvka over exact masked 1-NN passes; at 2,000 points also checked
+    against the oracle's Prim), t, |E| and the refinement sweeps."""
+    import torch
+    import paper_2507_14261_gb300 as fam
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    ctx = fam.Context(local)
+    ks = [int(x) for x in args.sweep_k.split(",")]
+    lams = [int(x) for x in args.sweep_lambda.split(",")]
+    for name in args.sweep_workloads.split(","):
+        w = workloads.get(name)
+        X_np = w.points()
+        X = torch.from_numpy(X_np).cuda()
+        T, _ = ctx.emst_exact(X, args.prec)
+        W_exact = T.W
+        prim = None
+        if w.n <= 5000:
+            import oracle
+            oracle.build()
+            prim = oracle.prim_exact(X_np).W
+        for k in ks:
+            for lam in lams:
+                if k > w.n - 1:
+                    continue
+                ctx.build(X, k, lam, 1, args.prec)
+                ts, info = [], None
+                for _ in range(3):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    tree, info = ctx.build(X, k, lam, 1, args.prec)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = statistics.median(ts)
+                line = {"sweep": "k_lambda", "workload": name, "n": w.n, "d": w.d, "k": k,
+                        "lambda": lam, "prec": args.prec, "ms": ms,
+                        "points_per_s": w.n / (ms / 1e3), "W": tree.W, "W_exact": W_exact,
+                        "rel_err": (tree.W - W_exact) / W_exact, "t": info.t, "m": info.m,
+                        "refine_sweeps": info.refine_sweeps,
+                        "ms_stages": {"knn": info.ms_knn, "connect": info.ms_connect,
+                                      "refine": info.ms_refine, "mst": info.ms_mst}}
+                if prim is not None:
+                    line["W_exact_oracle_prim"] = prim
+                print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batch(args, world, rank, local):
     """256 clouds (n_b ~ U{500..20000}, d_b in {3, 32, 128}, 5-20 clusters,
     k=16, lambda=5) per step through famst_build_batched: one captured CUDA
@@ -431,6 +486,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-quality", action="store_true",
                     help="skip the exact EMST (Eq. 1 relative error, after the timed region)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="k / lambda study on the 2k x 16 and 100k x 128 mixtures (JSON lines)")
+    ap.add_argument("--sweep-k", default="5,10,16,20,32")
+    ap.add_argument("--sweep-lambda", default="1,2,5,10")
+    ap.add_argument("--sweep-workloads", default="blobs_small,blobs_100k")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the precision comparison and the batch_256 sub-object")
     args = ap.parse_args()
@@ -445,6 +505,8 @@ def main():
 
     if args.workload == "batch_256":
         return run_batch(args, world, rank, local)
+    if args.sweep:
+        return run_sweep(args, world, rank, local)
     torch.cuda.set_device(local)
     pg = None
     if world > 1:
