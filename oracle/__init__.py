@@ -87,6 +87,9 @@ def _lib():
                                           c.c_int, c.c_uint64, _i32p, _i32p, _f32p,
                                           _i32p, _i32p]
             L.or_random_edges.restype = c.c_int64
+            L.or_nearest_edges.argtypes = [_f32p, c.c_int, _i32p, _i64p, c.c_int64, c.c_int,
+                                           _i32p, _i32p, _f32p, _i32p, _i32p]
+            L.or_nearest_edges.restype = c.c_int64
             L.or_refine_sweep.argtypes = [_f32p, c.c_int, _i64p, _i32p, _i32p,
                                           c.c_int64, _i32p, _i32p, _f32p, _i32p,
                                           _i32p, _u8p]
@@ -254,6 +257,20 @@ def random_edges(X, C: Components, lam: int, seed: int) -> Edges:
     return Edges(*(a[:m].copy() for a in out))
 
 
+def nearest_edges(X, C: Components, lam: int) -> Edges:
+    """The lambda nearest pairs (u in C_i, v in C_j) of every component pair
+    under the order (w, min id, max id): the nearest-pair variant of Alg. 3."""
+    X = _f32(X)
+    n, d = X.shape
+    t = C.t
+    m = lam * t * (t - 1) // 2
+    out = [np.empty(max(1, m), dt) for dt in
+           (np.int32, np.int32, np.float32, np.int32, np.int32)]
+    got = _lib().or_nearest_edges(X, d, C.members, C.comp_off, t, lam, *out)
+    assert got == m
+    return Edges(*(a[:m].copy() for a in out))
+
+
 def refine_sweep(X, G: Graph, C: Components, E: Edges, changed=None) -> int:
     """One sweep of Alg. 4 over E, in place; returns |Delta|."""
     X = _f32(X)
@@ -363,9 +380,12 @@ class FamstResult:
 
 
 def famst(X, k: int, lam: int, seed: int, knn_graph=None,
-          max_iters: int = 10000, threads: int | None = None) -> FamstResult:
+          max_iters: int = 10000, threads: int | None = None,
+          connect: str = "random") -> FamstResult:
     """Algorithm 1. ``knn_graph`` = (nbr, dist) replaces the exact kNN stage
-    (used to run the later stages on another implementation's graph)."""
+    (used to run the later stages on another implementation's graph);
+    ``connect`` = "random" (Alg. 3) or "nearest" (the lambda nearest pairs
+    of every component pair)."""
     X = _f32(X)
     n = X.shape[0]
     if knn_graph is None:
@@ -374,7 +394,7 @@ def famst(X, k: int, lam: int, seed: int, knn_graph=None,
         nbr, dist = _i32(knn_graph[0]), _f32(knn_graph[1])
     G = build_graph(nbr)
     C = components(G)
-    E0 = random_edges(X, C, lam, seed)
+    E0 = nearest_edges(X, C, lam) if connect == "nearest" else random_edges(X, C, lam, seed)
     E = E0.copy()
     deltas, changes = refine(X, G, C, E, max_iters=max_iters)
     tree = kruskal(n, nbr, dist, E)

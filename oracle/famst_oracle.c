@@ -287,6 +287,69 @@ int64_t or_random_edges(const float *X, int d, const int32_t *members,
     return lambda * t * (t - 1) / 2;
 }
 
+/* ------------------------- Phase 2b variant: the lambda nearest pairs
+ * The variant of Algorithm 3 that joins components by their nearest
+ * pairs instead of random samples ("the lambda nearest cross-component
+ * edges"): for every component pair i < j (i outer, j inner), all
+ * |C_i| |C_j| pairs (u in C_i, v in C_j) are compared by the canonical
+ * distance and the lambda smallest under the edge order (w, min(u,v),
+ * max(u,v)) are kept, ascending. Edge e = (pair rank) * lambda + r holds
+ * (u, v, w, i, j); a pair with fewer than lambda vertex pairs cannot occur
+ * (every component has at least k + 1 >= 2 members) but is padded with
+ * (-1, -1, +inf) all the same. Returns |E| = lambda t (t - 1) / 2. */
+typedef struct { float w; int32_t a; int32_t b; int32_t u; int32_t v; } pairkey_t;
+
+static int pair_less(const pairkey_t *x, const pairkey_t *y)
+{
+    if (x->w != y->w) return x->w < y->w;
+    if (x->a != y->a) return x->a < y->a;
+    return x->b < y->b;
+}
+
+int64_t or_nearest_edges(const float *X, int d, const int32_t *members,
+                         const int64_t *comp_off, int64_t t, int lambda,
+                         int32_t *eu, int32_t *ev, float *ew, int32_t *eci,
+                         int32_t *ecj)
+{
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < t; ++i) {
+        pairkey_t *best = (pairkey_t *)malloc(sizeof(pairkey_t) * (size_t)lambda);
+        for (int64_t j = i + 1; j < t; ++j) {
+            int have = 0;
+            for (int64_t a = comp_off[i]; a < comp_off[i + 1]; ++a) {
+                for (int64_t b = comp_off[j]; b < comp_off[j + 1]; ++b) {
+                    pairkey_t c;
+                    c.u = members[a];
+                    c.v = members[b];
+                    c.w = or_dist32(X + (int64_t)c.u * d, X + (int64_t)c.v * d, d);
+                    c.a = c.u < c.v ? c.u : c.v;
+                    c.b = c.u < c.v ? c.v : c.u;
+                    if (have == lambda && !pair_less(&c, &best[lambda - 1])) continue;
+                    int pos = have < lambda ? have : lambda - 1;   /* sorted insertion */
+                    while (pos > 0 && pair_less(&c, &best[pos - 1])) {
+                        best[pos] = best[pos - 1];
+                        --pos;
+                    }
+                    best[pos] = c;
+                    if (have < lambda) ++have;
+                }
+            }
+            int64_t base = (i * t - i * (i + 1) / 2 + (j - i - 1)) * lambda;
+            for (int r = 0; r < lambda; ++r) {
+                eu[base + r] = r < have ? best[r].u : -1;
+                ev[base + r] = r < have ? best[r].v : -1;
+                ew[base + r] = r < have ? best[r].w : INFINITY;
+                eci[base + r] = (int32_t)i;
+                ecj[base + r] = (int32_t)j;
+            }
+        }
+        free(best);
+    }
+    return lambda * t * (t - 1) / 2;
+}
+
 /* --------------------------------------------------- Phase 3: Algorithm 4
  * One refinement sweep over E, in place (edges do not depend on each
  * other). For edge (u, v, d) of pair (C_i, C_j):

@@ -268,3 +268,57 @@ def test_refine_result_is_local_minimum(orc):
             assert not orc.dist32(X[up], X[v]) < w
         for vp in G.neighbours(v):
             assert not orc.dist32(X[u], X[vp]) < w
+
+
+# --------------------------------- Alg. 3 variant: the lambda nearest pairs
+
+def test_nearest_pairs_hand_worked_1d(orc):
+    g = json.load(open(os.path.join(GOLDEN, "nearest_pairs_1d.json")))
+    X = np.array(g["x"], dtype=np.float32)[:, None]
+    nbr, _ = orc.knn(X, g["k"])
+    C = orc.components(orc.build_graph(nbr))
+    assert [C.members[C.comp_off[c]:C.comp_off[c + 1]].tolist() for c in range(C.t)] == \
+        g["components"]
+    lam = g["lambda"]
+    E = orc.nearest_edges(X, C, lam)
+    assert [[int(u), int(v), float(w)] for u, v, w in zip(E.u, E.v, E.w)] == \
+        [[a, b, float(w)] for a, b, w in g["kept"]]
+    Eall = orc.nearest_edges(X, C, 9)   # lambda = |C_0| |C_1|: every pair, sorted
+    assert [[int(u), int(v), float(w)] for u, v, w in zip(Eall.u, Eall.v, Eall.w)] == \
+        [[a, b, float(w)] for a, b, w in g["all_cross_pairs_sorted"]]
+
+
+def test_nearest_pairs_against_float64_cdist(orc):
+    sp = pytest.importorskip("scipy.spatial")
+    X = workloads.blobs(700, 7, 7, (0.3, 0.8), 17)
+    nbr, _ = orc.knn(X, 4)
+    C = orc.components(orc.build_graph(nbr))
+    lam = 6
+    E = orc.nearest_edges(X, C, lam)
+    t = C.t
+    assert t >= 7 and len(E) == lam * t * (t - 1) // 2
+    X64 = X.astype(np.float64)
+    r = 0
+    for i in range(t):
+        mi = C.members[C.comp_off[i]:C.comp_off[i + 1]]
+        for j in range(i + 1, t):
+            mj = C.members[C.comp_off[j]:C.comp_off[j + 1]]
+            D = sp.distance.cdist(X64[mi], X64[mj])
+            sel = slice(r * lam, (r + 1) * lam)
+            u, v, w = E.u[sel], E.v[sel], E.w[sel]
+            assert np.all(C.comp[u] == i) and np.all(C.comp[v] == j)
+            assert np.all(E.ci[sel] == i) and np.all(E.cj[sel] == j)
+            # the first kept pair is the closest pair of the two components
+            assert abs(float(w[0]) - D.min()) <= 1e-5 * D.min()
+            # every dropped pair is at least as far as the last kept one
+            kept = set(zip(u.tolist(), v.tolist()))
+            pos = {int(x): a for a, x in enumerate(mi)}
+            qos = {int(x): b for b, x in enumerate(mj)}
+            flat = np.sort(D, axis=None)
+            assert abs(float(w[-1]) - flat[lam - 1]) <= 1e-5 * flat[lam - 1]
+            for a, b in kept:
+                assert abs(D[pos[a], qos[b]] - orc.dist32(X[a], X[b])) <= 1e-5 * D[pos[a], qos[b]]
+            # ascending under (w, min id, max id), no pair twice
+            keys = [(float(ww), min(a, b), max(a, b)) for a, b, ww in zip(u, v, w)]
+            assert keys == sorted(keys) and len(set(keys)) == lam
+            r += 1
