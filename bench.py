@@ -687,6 +687,27 @@ def main():
     if not args.no_extras and rank == 0:
         batch = batch_sub(fam, torch, local, args.prec)
 
+    # The nearest-pair connect (the lambda nearest cross pairs of every
+    # component pair instead of Algorithm 3's samples) on the same cloud,
+    # once, after the timed region: W and Eq. 1's error against Algorithm 3's
+    nearest = None
+    if not args.no_extras and rank == 0:
+        c2 = fam.Context(local)
+        c2.set_connect_mode("nearest")
+        tree_n, info_n = c2.build(X, w.k, w.lam, 1, args.prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tree_n, info_n = c2.build(X, w.k, w.lam, 1, args.prec)
+        torch.cuda.synchronize()
+        nearest = {"W": tree_n.W, "W_random_alg3": tree.W,
+                   "ms_build": 1e3 * (time.perf_counter() - t0), "ms_connect": info_n.ms_connect,
+                   "ms_refine": info_n.ms_refine, "refine_sweeps": info_n.refine_sweeps,
+                   "timing": "one build after a warm-up, host wall clock"}
+        if quality is not None and quality["W_exact"] > 0:
+            nearest["rel_err"] = (tree_n.W - quality["W_exact"]) / quality["W_exact"]
+            nearest["rel_err_random_alg3"] = quality["rel_err"]
+        c2.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(X_np, w.k)
@@ -705,6 +726,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "quality": quality, "kernels": kernels,
             "l2_peak": l2, "precision_compare": precision, "batch_256": batch,
+            "connect_nearest": nearest,
             "stages_ms": {k2: last[k2] for k2 in ("ms_knn", "ms_components", "ms_connect",
                                                   "ms_refine", "ms_mst", "ms_total")},
             "build": {"t": last["t"], "m": last["m"], "refine_sweeps": last["refine_sweeps"],

@@ -135,6 +135,12 @@ famst_status famst_set_knn_pruning(famst_ctx *ctx, int32_t enable);
 famst_status famst_workspace_query(famst_ctx *ctx, int64_t n, int32_t d, int32_t k,
                                    int32_t lambda, int64_t t_max, int32_t prec,
                                    int32_t max_iters, size_t *bytes);
+/* Connect step of famst_build / famst_build_host: FAMST_CONNECT_RANDOM
+ * (Algorithm 3, the default) or FAMST_CONNECT_NEAREST (famst_connect_nearest;
+ * the rest of Algorithm 1 is unchanged). */
+#define FAMST_CONNECT_RANDOM  0
+#define FAMST_CONNECT_NEAREST 1
+famst_status famst_set_connect_mode(famst_ctx *ctx, int32_t mode);
 /* Iteration limit of the library's bounded loops: each find and hook loop
  * of the union-find (Algorithm 2), the pointer jumping of every Boruvka
  * round, and the number of Boruvka rounds (at most 64). A loop that reaches
@@ -185,6 +191,22 @@ famst_status famst_connect(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
                            const int32_t *comp, int64_t t, int32_t lambda, uint64_t seed,
                            int32_t *eu, int32_t *ev, float *ew, int32_t *eci, int32_t *ecj,
                            int64_t capacity, int64_t *m_out);
+
+/* ------------------------------- Phase 2b variant: the nearest pairs
+ * The variant of Algorithm 3 that joins components by their nearest pairs
+ * ("the lambda nearest cross-component edges", Sec. 3 on joining the
+ * components): for every component pair i < j (i outer, j inner), the
+ * lambda pairs (u in C_i, v in C_j) with the smallest canonical distance
+ * under the order (w, min id, max id), ascending, over all |C_i| |C_j|
+ * pairs. A pair with fewer than lambda cross pairs repeats its farthest
+ * pair. Same arguments, layout and errors as famst_connect (no seed);
+ * 1 <= d <= 256 (UNSUPPORTED beyond). The work is all cross pairs (about
+ * n^2 / 2 distance evaluations on the tensor cores, filtered by rigorous
+ * bounds and decided on canonical distances). Synchronises. */
+famst_status famst_connect_nearest(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                                   const int32_t *comp, int64_t t, int32_t lambda,
+                                   int32_t *eu, int32_t *ev, float *ew, int32_t *eci,
+                                   int32_t *ecj, int64_t capacity, int64_t *m_out);
 
 /* ------------------------------------------------- Phase 3: Algorithm 4
  * Repeat the refinement sweep of Algorithm 4 over the m edges in place

@@ -294,9 +294,9 @@ int64_t or_random_edges(const float *X, int d, const int32_t *members,
  * |C_i| |C_j| pairs (u in C_i, v in C_j) are compared by the canonical
  * distance and the lambda smallest under the edge order (w, min(u,v),
  * max(u,v)) are kept, ascending. Edge e = (pair rank) * lambda + r holds
- * (u, v, w, i, j); a pair with fewer than lambda vertex pairs cannot occur
- * (every component has at least k + 1 >= 2 members) but is padded with
- * (-1, -1, +inf) all the same. Returns |E| = lambda t (t - 1) / 2. */
+ * (u, v, w, i, j). A component pair with fewer than lambda cross pairs
+ * repeats its farthest pair in the remaining slots (duplicate edges change
+ * neither the refinement nor Kruskal). Returns |E| = lambda t (t - 1) / 2. */
 typedef struct { float w; int32_t a; int32_t b; int32_t u; int32_t v; } pairkey_t;
 
 static int pair_less(const pairkey_t *x, const pairkey_t *y)
@@ -338,9 +338,10 @@ int64_t or_nearest_edges(const float *X, int d, const int32_t *members,
             }
             int64_t base = (i * t - i * (i + 1) / 2 + (j - i - 1)) * lambda;
             for (int r = 0; r < lambda; ++r) {
-                eu[base + r] = r < have ? best[r].u : -1;
-                ev[base + r] = r < have ? best[r].v : -1;
-                ew[base + r] = r < have ? best[r].w : INFINITY;
+                const pairkey_t *c = &best[r < have ? r : have - 1];
+                eu[base + r] = c->u;
+                ev[base + r] = c->v;
+                ew[base + r] = c->w;
                 eci[base + r] = (int32_t)i;
                 ecj[base + r] = (int32_t)j;
             }

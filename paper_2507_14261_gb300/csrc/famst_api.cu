@@ -60,6 +60,7 @@ struct famst_ctx {
     double *dW = nullptr;         // device: W, W64
     int prune = 1;                // Phase 1 tile pruning
     int loop_limit = 0;           // bounded loops: 0 = defaults (famst_set_loop_limit)
+    int connect_mode = FAMST_CONNECT_RANDOM;
     KernelTimers timers;          // per-kernel events of a build with info
     bool timers_made = false, timing = false;
     double tile_fraction = 1.0;   // of the last Phase 1
@@ -322,8 +323,9 @@ size_t knn_stage_ws(famst_ctx *ctx, int64_t n, int32_t d, int32_t k, int32_t pre
 }
 
 // Workspace of Phases 2-3 + MST (slot 1) for m inter-component edges.
-size_t rest_ws(int64_t n, int32_t d, int32_t k, int64_t m, int64_t t, int32_t max_iters) {
-    return align256(size_t(n) * 4) + align256(size_t(n + 1) * 4) + member_lists_workspace(n, t) +
+size_t rest_ws(int64_t n, int32_t d, int32_t k, int64_t m, int64_t t, int32_t max_iters,
+               int lambda_nearest = 0) {
+    return (lambda_nearest > 0 ? connect_nearest_workspace(n, t, lambda_nearest) : 0) + align256(size_t(n) * 4) + align256(size_t(n + 1) * 4) + member_lists_workspace(n, t) +
            5 * align256(size_t(m > 0 ? m : 1) * 4) + align256(size_t(n + 1) * 4) +
            align256(size_t(n) * k * 4) + reverse_csr_workspace(n, k) +
            align256(size_t(max_iters + 1) * 4) + refine_workspace(m) +
@@ -362,7 +364,10 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     const int64_t m = int64_t(lambda) * t * (t - 1) / 2;
     if (m >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "lambda*t*(t-1)/2 >= 2^31");
     // workspace for connect, refine and MST
-    ST(ensure_ws(ctx, 1, rest_ws(n, d, k, m, t, max_iters), ar));
+    ST(ensure_ws(ctx, 1,
+                 rest_ws(n, d, k, m, t, max_iters,
+                         ctx->connect_mode == FAMST_CONNECT_NEAREST ? lambda : 0),
+                 ar));
     int32_t *members = ar.take<int32_t>(size_t(n));
     int32_t *comp_off = ar.take<int32_t>(size_t(n + 1));
     int32_t *eu = ar.take<int32_t>(size_t(m > 0 ? m : 1));
@@ -378,12 +383,28 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     int64_t first_delta = 0;
     if (t > 1) {
         ST(member_lists(ex, ar, comp, n, t, members, comp_off));
-        ST(connect_edges(ex, X, d, v4, members, comp_off, t, lambda, seed, eu, evv, ew, eci, ecj));
-        ev.mark(ctx->stream, 3);
         // BF16 copies of the points for the Alg. 4 filter (half the bytes per
-        // candidate; exactness comes from the canonical survivors)
+        // candidate; exactness comes from the canonical survivors) and for the
+        // nearest-pair connect
         HalfRows hr;
-        if (v4 && d >= 32 && d <= 256) ST(half_rows(ex, ar, X, n, d, &hr));
+        const bool nearest = ctx->connect_mode == FAMST_CONNECT_NEAREST;
+        if ((v4 && d >= 32 && d <= 256) || nearest) ST(half_rows(ex, ar, X, n, d, &hr));
+        if (nearest) {
+            if (d > 256) return fail(ctx, FAMST_ERR_UNSUPPORTED, "the nearest-pair connect needs d <= 256");
+            std::vector<int32_t> off_h(size_t(t + 1));
+            CK(cudaMemcpyAsync(off_h.data(), comp_off, size_t(t + 1) * 4, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            const size_t mark = ar.off;   // the lists are scratch of this step
+            ST(connect_nearest(ex, ar, X, d, hr, members, comp_off, off_h.data(), t, lambda, eu,
+                               evv, ew, eci, ecj, nullptr));
+            ar.off = mark;
+        } else {
+            ST(connect_edges(ex, X, d, v4, members, comp_off, t, lambda, seed, eu, evv, ew, eci,
+                             ecj));
+        }
+        ev.mark(ctx->stream, 3);
+        if (!(v4 && d >= 32 && d <= 256)) hr = HalfRows();   // the refinement filter needs them
         int32_t *rev_off = ar.take<int32_t>(size_t(n + 1));
         int32_t *rev_src = ar.take<int32_t>(size_t(n) * k);
         if (!rev_off || !rev_src || !hist) return fail(ctx, FAMST_ERR_OOM, "workspace");
@@ -560,7 +581,18 @@ famst_status famst_workspace_query(famst_ctx *ctx, int64_t n, int32_t d, int32_t
     if (m >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "lambda*t*(t-1)/2 >= 2^31");
     // as ensure_ws rounds a slot: aligned, plus its 4 KB guard
     *bytes = (align256(build_knn_ws(ctx, n, d, k, prec)) + 4096) +
-             (align256(rest_ws(n, d, k, m, t_max, max_iters)) + 4096);
+             (align256(rest_ws(n, d, k, m, t_max, max_iters,
+                               ctx->connect_mode == FAMST_CONNECT_NEAREST ? lambda : 0)) +
+              4096);
+    return FAMST_OK;
+}
+
+famst_status famst_set_connect_mode(famst_ctx *ctx, int32_t mode) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (mode != FAMST_CONNECT_RANDOM && mode != FAMST_CONNECT_NEAREST)
+        return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown connect mode");
+    ctx->connect_mode = mode;
     return FAMST_OK;
 }
 
@@ -675,6 +707,47 @@ famst_status famst_connect(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
     ST(sync_status(ctx));
     ST(connect_edges(ex, X, d, vec4_ok(X, d), members, comp_off, t, lambda, seed, eu, ev, ew, eci,
                      ecj));
+    return sync_status(ctx);
+}
+
+famst_status famst_connect_nearest(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                                   const int32_t *comp, int64_t t, int32_t lambda,
+                                   int32_t *eu, int32_t *ev, float *ew, int32_t *eci,
+                                   int32_t *ecj, int64_t capacity, int64_t *m_out) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!comp || !m_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL argument");
+    if (lambda < 1 || lambda > 32) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= lambda <= 32");
+    if (t < 1 || t > n) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= t <= n");
+    if (d > 256) return fail(ctx, FAMST_ERR_UNSUPPORTED, "the nearest-pair connect needs d <= 256");
+    const int64_t m = int64_t(lambda) * t * (t - 1) / 2;
+    *m_out = m;
+    if (m >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "lambda*t*(t-1)/2 >= 2^31");
+    if (capacity < m) return fail(ctx, FAMST_ERR_CAPACITY, "edge arrays shorter than lambda*t*(t-1)/2");
+    if (m > 0 && (!eu || !ev || !ew || !eci || !ecj)) return fail(ctx, FAMST_ERR_INVALID_ARG, "NULL edge array");
+    CK(cudaSetDevice(ctx->device));
+    ST(reset_status(ctx));
+    ST(check_points(ctx, X, n, d));
+    Exec ex = exec_of(ctx);
+    FAMST_LAUNCH(ex, check_ids_kernel, grid_cap(ctx, n, 256), 256, 0, comp, n, t, 0, ctx->dstatus);
+    ST(sync_status(ctx));
+    if (m == 0) return FAMST_OK;
+    Arena ar;
+    ST(ensure_ws(ctx, 1, align256(size_t(n) * 4) + align256(size_t(n + 1) * 4) +
+                             member_lists_workspace(n, t) + half_rows_workspace(n, d) +
+                             connect_nearest_workspace(n, t, lambda), ar));
+    int32_t *members = ar.take<int32_t>(size_t(n));
+    int32_t *comp_off = ar.take<int32_t>(size_t(n + 1));
+    CK(cudaMemsetAsync(comp_off, 0xff, size_t(n + 1) * 4, ctx->stream));
+    ST(member_lists(ex, ar, comp, n, t, members, comp_off));
+    FAMST_LAUNCH(ex, check_off_kernel, unsigned((t + 255) / 256), 256, 0, comp_off, t, ctx->dstatus);
+    ST(sync_status(ctx));
+    std::vector<int32_t> off_h(size_t(t + 1));
+    CK(cudaMemcpy(off_h.data(), comp_off, size_t(t + 1) * 4, cudaMemcpyDeviceToHost));
+    HalfRows hr;
+    ST(half_rows(ex, ar, X, n, d, &hr));
+    ST(connect_nearest(ex, ar, X, d, hr, members, comp_off, off_h.data(), t, lambda, eu, ev, ew,
+                       eci, ecj, nullptr));
     return sync_status(ctx);
 }
 

@@ -599,6 +599,13 @@ famst_status refine_build(const Exec &ex, Arena &ar, const float *X, int d, cons
                           const int32_t *members, int64_t n, int32_t *eu, int32_t *ev, float *ew,
                           const int32_t *order, int64_t m, int max_iters, int32_t *change_hist,
                           unsigned long long *evals, int32_t *pinned_host);
+// connect_nearest.cu: the lambda nearest pairs of every component pair
+size_t connect_nearest_workspace(int64_t n, int64_t t, int lambda);
+famst_status connect_nearest(const Exec &ex, Arena &ar, const float *X, int d,
+                             const HalfRows &hr, const int32_t *members,
+                             const int32_t *comp_off, const int32_t *comp_off_host, int64_t t,
+                             int lambda, int32_t *eu, int32_t *ev, float *ew, int32_t *eci,
+                             int32_t *ecj, unsigned long long *stats);
 famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
                            const int32_t *members, const int32_t *comp_off, int64_t t,
                            int lambda, uint64_t seed, int32_t *eu, int32_t *ev, float *ew,

@@ -79,6 +79,9 @@ _SIGS = {
     "famst_set_stream": (_I32, [_P, _P]),
     "famst_set_knn_pruning": (_I32, [_P, _I32]),
     "famst_set_loop_limit": (_I32, [_P, _I32]),
+    "famst_set_connect_mode": (_I32, [_P, _I32]),
+    "famst_connect_nearest": (_I32, [_P, _P, _I64, _I32, _P, _I64, _I32, _P, _P, _P, _P, _P,
+                                     _I64, _PI64]),
     "famst_workspace_query": (_I32, [_P, _I64, _I32, _I32, _I32, _I64, _I32, _I32,
                                      ctypes.POINTER(ctypes.c_size_t)]),
     "famst_error_string": (ctypes.c_char_p, [_I32]),
@@ -240,6 +243,32 @@ class Context:
             raise FamstError(st, f"capacity {cap} < required {mo.value}")
         self._check(st, "famst_connect")
         return E.slice(int(mo.value))
+
+    def connect_nearest(self, X, comp, t: int, lam: int, capacity: int | None = None):
+        """famst_connect_nearest: the lambda nearest pairs of every component
+        pair (order (w, min id, max id)), in famst_connect's layout."""
+        _need(X, torch.float32, "X")
+        _need(comp, torch.int32, "comp")
+        n, d = X.shape
+        m = lam * t * (t - 1) // 2
+        cap = m if capacity is None else capacity
+        dev = X.device
+        E = Edges(*(torch.empty(max(cap, 1), dtype=dt, device=dev) for dt in
+                    (torch.int32, torch.int32, torch.float32, torch.int32, torch.int32)))
+        mo = ctypes.c_int64(0)
+        self._stream()
+        st = lib().famst_connect_nearest(self._h, _ptr(X), n, d, _ptr(comp), t, lam, _ptr(E.u),
+                                         _ptr(E.v), _ptr(E.w), _ptr(E.ci), _ptr(E.cj), cap,
+                                         ctypes.byref(mo))
+        if st == -2:
+            raise FamstError(st, f"capacity {cap} < required {mo.value}")
+        self._check(st, "famst_connect_nearest")
+        return E.slice(int(mo.value))
+
+    def set_connect_mode(self, mode: str):
+        """Connect step of builds: "random" (Algorithm 3) or "nearest"."""
+        code = {"random": 0, "nearest": 1}[mode]
+        self._check(lib().famst_set_connect_mode(self._h, code), "famst_set_connect_mode")
 
     def refine(self, X, nbr, comp, E: "Edges", max_iters: int = 10000):
         _need(X, torch.float32, "X")

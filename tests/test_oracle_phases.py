@@ -322,3 +322,14 @@ def test_nearest_pairs_against_float64_cdist(orc):
             keys = [(float(ww), min(a, b), max(a, b)) for a, b, ww in zip(u, v, w)]
             assert keys == sorted(keys) and len(set(keys)) == lam
             r += 1
+
+
+def test_nearest_pairs_fewer_pairs_than_lambda_repeat_the_farthest(orc):
+    g = json.load(open(os.path.join(GOLDEN, "nearest_pairs_1d.json")))
+    X = np.array(g["x"], dtype=np.float32)[:, None]
+    nbr, _ = orc.knn(X, g["k"])
+    C = orc.components(orc.build_graph(nbr))
+    E = orc.nearest_edges(X, C, 12)   # 9 cross pairs only
+    got = [[int(u), int(v), float(w)] for u, v, w in zip(E.u, E.v, E.w)]
+    want = [[a, b, float(w)] for a, b, w in g["all_cross_pairs_sorted"]]
+    assert got == want + [want[-1]] * 3
