@@ -250,12 +250,16 @@ __global__ void __launch_bounds__(NP_WARPS * 32)
                     thr = fminf(thr, kth);
                 }
                 const float bound = __fmul_ru(thr, 1.0f + 0x1p-22f);
+                // survivors among the valid pairs only (the bound is +inf while a
+                // step has fewer than lambda pairs)
                 unsigned my = 0;
 #pragma unroll
                 for (int T = 0; T < 2; ++T)
 #pragma unroll
-                    for (int e2 = 0; e2 < 4; ++e2)
-                        if (lo[T][e2] <= bound) my |= 1u << (4 * T + e2);
+                    for (int e2 = 0; e2 < 4; ++e2) {
+                        const int ui = 16 * T + g4 + 8 * (e2 >> 1), vj = 2 * t4 + (e2 & 1);
+                        if (ui < nu && vj < nvb && lo[T][e2] <= bound) my |= 1u << (4 * T + e2);
+                    }
                 {
                     int cnt = __popc(my);
 #pragma unroll

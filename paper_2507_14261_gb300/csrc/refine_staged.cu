@@ -466,7 +466,9 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
                     for (int T = 0; T < 2; ++T)
 #pragma unroll
                         for (int e2 = 0; e2 < 4; ++e2)
-                            if (lo[T][e2] <= ((e2 & 1) ? bnd1 : bnd0)) my |= 1u << (4 * T + e2);
+                            if (16 * T + g4 + 8 * (e2 >> 1) < nv && 2 * t4 + (e2 & 1) < ntb &&
+                                lo[T][e2] <= ((e2 & 1) ? bnd1 : bnd0))
+                                my |= 1u << (4 * T + e2);
                     {
                         int cnt = __popc(my);
 #pragma unroll
