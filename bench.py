@@ -293,35 +293,81 @@ def run_reference(args, world, rank):
     return 0
 
 
-def precision_compare(fam, torch) -> dict:
-    """Phase 1 of the 100k x 128 mixture (k = 16) by brute force in both
-    precisions: tcgen05 BF16 hi/lo tiles vs FP32 SIMT tiles, median of 3
-    after a warm-up, both exact (their graphs are compared)."""
+def _knn_ms(c, X, k, prec, torch, reps=3):
+    c.knn_graph(X, k, prec)
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        nbr, dist = c.knn_graph(X, k, prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts), nbr, dist
+
+
+def precision_compare(fam, torch, bf16_peak=None) -> dict:
+    """Phase 1 of the 100k x 128 mixture (k = 16) by brute force in every
+    tile precision: tcgen05 BF16 hi/lo, BF16, E4M3 (kind::f8f6f4) and the
+    FP32 SIMT tiles, median of 3 after a warm-up. All return the exact kNN
+    graph (compared here); the precisions differ in tile time and in how
+    many rows their error bound leaves to the FP32 recomputation (read from
+    one build's statistics)."""
     w = workloads.get("blobs_100k")
     X = torch.from_numpy(w.points()).cuda()
     c = fam.Context(torch.cuda.current_device())
     c.set_knn_pruning(False)
     out = {"workload": "blobs_100k (100k x 128, k = 16), kNN stage, no tile pruning"}
     graphs = {}
-    for prec in ("bf16x3", "fp32"):
-        c.knn_graph(X, w.k, prec)
-        ts = []
-        for _ in range(3):
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            nbr, dist = c.knn_graph(X, w.k, prec)
-            e1.record()
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
+    for prec in ("bf16x3", "bf16", "fp8", "fp32"):
+        ms, nbr, dist = _knn_ms(c, X, w.k, prec, torch)
         graphs[prec] = (nbr, dist)
-        ms = statistics.median(ts)
-        out[prec] = {"ms": ms, "points_per_s": w.n / (ms / 1e3)}
-    out["identical_graphs"] = bool(torch.equal(graphs["bf16x3"][0], graphs["fp32"][0]) and
-                                   torch.equal(graphs["bf16x3"][1], graphs["fp32"][1]))
+        _, info = c.build(X, w.k, w.lam, 1, prec)
+        out[prec] = {"ms": ms, "points_per_s": w.n / (ms / 1e3),
+                     "uncertified_rows": info.uncertified_rows,
+                     "ms_tiles": info.ms_knn_tiles, "ms_rerank": info.ms_rerank}
+        if prec != "fp32" and bf16_peak:
+            kel = 128 if prec == "fp8" else 64
+            d_pad = -(-w.d // kel) * kel
+            nt = -(-w.n // 128)
+            # every tile pair of the padded square; 2 d_pad FLOP per pair
+            # (BF16 hi/lo issues three products: 'issued_frac')
+            flops = 2.0 * (nt * 128) ** 2 * d_pad
+            peak = bf16_peak * (2.0 if prec == "fp8" else 1.0)
+            out[prec]["tiles_tflops"] = flops / (info.ms_knn_tiles / 1e3) / 1e12
+            out[prec]["tiles_frac"] = out[prec]["tiles_tflops"] / peak
+            out[prec]["issued_frac"] = out[prec]["tiles_frac"] * (3 if prec == "bf16x3" else 1)
+            out[prec]["tiles_peak"] = ("measured bf16 x 2 (nominal fp8:bf16 ratio)"
+                                       if prec == "fp8" else "measured bf16")
+    ref = graphs["fp32"]
+    out["identical_graphs"] = bool(all(torch.equal(g[0], ref[0]) and torch.equal(g[1], ref[1])
+                                       for g in graphs.values()))
     out["recall_at_k"] = 1.0 if out["identical_graphs"] else None
     out["speedup_bf16x3_over_fp32"] = out["fp32"]["ms"] / out["bf16x3"]["ms"]
+    out["speedup_fp8_over_bf16x3"] = out["bf16x3"]["ms"] / out["fp8"]["ms"]
+    c.close()
+    return out
+
+
+def fp8_on_workload(fam, torch, X, w, prec, tree_ref) -> dict:
+    """One build of the timed workload with E4M3 tiles (no tile pruning)
+    after a warm-up, against the timed precision's tree: the same tree, its
+    kNN-stage time and the rows its error bound could not certify."""
+    c = fam.Context(torch.cuda.current_device())
+    c.build(X, w.k, w.lam, 1, "fp8")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tree, info = c.build(X, w.k, w.lam, 1, "fp8")
+    torch.cuda.synchronize()
+    out = {"ms_build": 1e3 * (time.perf_counter() - t0), "ms_knn": info.ms_knn,
+           "ms_tiles": info.ms_knn_tiles, "uncertified_rows": info.uncertified_rows,
+           "uncertified_frac": info.uncertified_rows / w.n,
+           "same_tree_as": prec,
+           "same_tree": bool(torch.equal(tree.u, tree_ref.u) and torch.equal(tree.v, tree_ref.v)
+                             and torch.equal(tree.w, tree_ref.w)),
+           "timing": "one build after a warm-up, host wall clock; stage times by CUDA events"}
     c.close()
     return out
 
@@ -677,9 +723,10 @@ def main():
     # Phase 1 brute force (no tile pruning) with BF16 hi/lo tensor tiles
     # against the FP32 SIMT tiles; both return the exact kNN graph (recall@k
     # = 1.0, checked equal here), so only the distance arithmetic differs.
-    precision = None
+    precision = fp8 = None
     if not args.no_extras and rank == 0:
-        precision = precision_compare(fam, torch)
+        precision = precision_compare(fam, torch, pk.get("bf16_tflops"))
+        fp8 = fp8_on_workload(fam, torch, X, w, args.prec, tree)
 
     # 256 clouds through the batched entry point (one CUDA-graph replay per
     # step), after the timed region
@@ -726,7 +773,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "quality": quality, "kernels": kernels,
             "l2_peak": l2, "precision_compare": precision, "batch_256": batch,
-            "connect_nearest": nearest,
+            "connect_nearest": nearest, "fp8_tiles": fp8,
             "stages_ms": {k2: last[k2] for k2 in ("ms_knn", "ms_components", "ms_connect",
                                                   "ms_refine", "ms_mst", "ms_total")},
             "build": {"t": last["t"], "m": last["m"], "refine_sweeps": last["refine_sweeps"],

@@ -73,6 +73,13 @@ typedef int32_t famst_status;
 #define FAMST_PREC_FP32   0  /* SIMT FP32 tiles (k + 8 candidates by a fast FP32 sum) */
 #define FAMST_PREC_BF16   1  /* tcgen05 BF16 tiles (x.y on tensor cores), FP32 re-rank */
 #define FAMST_PREC_BF16X3 2  /* tcgen05 BF16 hi/lo split, 3 products, FP32 re-rank */
+/* tcgen05 E4M3 tiles (kind::f8f6f4), each centred row scaled by a power of
+ * two to the E4M3 range, FP32 re-rank. famst_knn_graph and famst_build
+ * only (famst_emst_exact and famst_build_batched return UNSUPPORTED); no
+ * tile pruning. Its error bound is ~2^-4 relative, so on clouds whose k-th
+ * and (k+8)-th neighbour distances are closer than that most rows fall back
+ * to the FP32 tiles: the result stays exact, the time does not. */
+#define FAMST_PREC_FP8    3
 
 typedef struct famst_ctx famst_ctx;
 

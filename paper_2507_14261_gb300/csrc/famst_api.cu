@@ -299,13 +299,13 @@ famst_status knn_stage(famst_ctx *ctx, Arena &ar, const float *X, int64_t n, int
     Exec ex = exec_of(ctx);
     *uncert = 0;
     if (prec != FAMST_PREC_FP32) {
-        const bool x3 = prec == FAMST_PREC_BF16X3;
-        if (knn_tc_supported(n, d, k, x3)) {
+        const bool x3 = prec == FAMST_PREC_BF16X3, f8 = prec == FAMST_PREC_FP8;
+        if (knn_tc_supported(n, d, k, x3, f8)) {
             int64_t visited = 0;
             ctx->tile_fraction = 1.0;
             famst_status st = knn_tc(ex, ar, X, n, d, k, x3, vec4_ok(X, d), nbr, dist,
-                                     ctx->pinned + PIN_KNN, uncert, nullptr, ctx->prune != 0,
-                                     &visited);
+                                     ctx->pinned + PIN_KNN, uncert, nullptr,
+                                     ctx->prune != 0 && !f8, &visited, f8);
             const double all = double((n + 127) / 128) * double((n + 255) / 256);
             if (st == FAMST_OK) ctx->tile_fraction = double(visited) / all;
             return st;
@@ -316,9 +316,10 @@ famst_status knn_stage(famst_ctx *ctx, Arena &ar, const float *X, int64_t n, int
 }
 
 size_t knn_stage_ws(famst_ctx *ctx, int64_t n, int32_t d, int32_t k, int32_t prec) {
-    if (prec != FAMST_PREC_FP32 && knn_tc_supported(n, d, k, prec == FAMST_PREC_BF16X3))
+    const bool f8 = prec == FAMST_PREC_FP8;
+    if (prec != FAMST_PREC_FP32 && knn_tc_supported(n, d, k, prec == FAMST_PREC_BF16X3, f8))
         return knn_tc_workspace(n, d, k, prec == FAMST_PREC_BF16X3, ctx->num_sms,
-                                ctx->prune != 0 && prune_supported(n, d, k, true));
+                                !f8 && ctx->prune != 0 && prune_supported(n, d, k, true), f8);
     return knn_fp32_workspace(n, d, k, n, ctx->num_sms);
 }
 
@@ -471,7 +472,7 @@ famst_status build_impl(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
                         BuildOut out, double *W_out, famst_build_info *info) {
     if (lambda < 1 || lambda > 32) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= lambda <= 32");
     if (max_iters < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "need max_iters >= 1");
-    if (prec < 0 || prec > 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown precision");
+    if (prec < 0 || prec > 3) return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown precision");
     if (info) memset(info, 0, sizeof(*info));
     if (n == 1) {
         if (W_out) *W_out = 0.0;
@@ -572,7 +573,7 @@ famst_status famst_workspace_query(famst_ctx *ctx, int64_t n, int32_t d, int32_t
     if (!ctx || !bytes) return FAMST_ERR_INVALID_ARG;
     ctx->err[0] = 0;
     *bytes = 0;
-    if (n < 1 || d < 1 || lambda < 1 || lambda > 32 || max_iters < 1 || prec < 0 || prec > 2 ||
+    if (n < 1 || d < 1 || lambda < 1 || lambda > 32 || max_iters < 1 || prec < 0 || prec > 3 ||
         t_max < 1 || t_max > n)
         return fail(ctx, FAMST_ERR_INVALID_ARG, "bad shape");
     if (n == 1) return FAMST_OK;
@@ -640,7 +641,7 @@ famst_status famst_knn_graph(famst_ctx *ctx, const float *X, int64_t n, int32_t 
     if (!ctx) return FAMST_ERR_INVALID_ARG;
     ctx->err[0] = 0;
     if (!nbr || !dist) return fail(ctx, FAMST_ERR_INVALID_ARG, "nbr/dist NULL");
-    if (prec < 0 || prec > 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown precision");
+    if (prec < 0 || prec > 3) return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown precision");
     if (n < 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "need n >= 2");
     ST(check_knn_args(ctx, n, k));
     CK(cudaSetDevice(ctx->device));
@@ -868,6 +869,7 @@ famst_status famst_emst_exact(famst_ctx *ctx, const float *X, int64_t n, int32_t
     if (!ctx) return FAMST_ERR_INVALID_ARG;
     ctx->err[0] = 0;
     if (!W_out) return fail(ctx, FAMST_ERR_INVALID_ARG, "W_out NULL");
+    if (prec == FAMST_PREC_FP8) return fail(ctx, FAMST_ERR_UNSUPPORTED, "FP8 tiles: kNN graph and build only");
     if (prec < 0 || prec > 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown precision");
     if (n < 1 || n >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= n < 2^31");
     *W_out = 0.0;
@@ -1014,6 +1016,7 @@ famst_status famst_build_batched(famst_ctx *ctx, const float *X, const int64_t *
     if (!X || !offsets || !dims || B < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "bad batch");
     if (lambda < 1 || lambda > 32) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= lambda <= 32");
     if (max_iters < 1) return fail(ctx, FAMST_ERR_INVALID_ARG, "need max_iters >= 1");
+    if (prec == FAMST_PREC_FP8) return fail(ctx, FAMST_ERR_UNSUPPORTED, "FP8 tiles: kNN graph and build only");
     if (prec < 0 || prec > 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown precision");
     if (k < 1 || k > 64) return fail(ctx, FAMST_ERR_UNSUPPORTED, "batched builds need 1 <= k <= 64");
     if (offsets[0] != 0) return fail(ctx, FAMST_ERR_INVALID_ARG, "offsets[0] must be 0");

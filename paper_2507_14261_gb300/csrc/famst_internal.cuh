@@ -482,8 +482,9 @@ famst_status knn_fp32_batched(const Exec &ex, const float *Xc, int ld, const lon
 // knn_tc.cu
 // Exact kNN through tcgen05 BF16 (x3 = hi/lo split) distance tiles, FP32
 // re-rank, certificate, FP32 recomputation of uncertified rows.
-bool knn_tc_supported(int64_t n, int d, int k, bool x3);
-size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prune = false);
+bool knn_tc_supported(int64_t n, int d, int k, bool x3, bool f8 = false);
+size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prune = false,
+                        bool f8 = false);
 // Exact kNN of the listed rows of a batch of clouds (warp per row, canonical
 // distances within the row's cloud); rows / count on the device. k <= 64.
 famst_status fallback_rows_batched(const Exec &ex, const float *Xc, int ld, const long long *voff,
@@ -492,7 +493,7 @@ famst_status fallback_rows_batched(const Exec &ex, const float *Xc, int ld, cons
 famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k, bool x3,
                     bool vec4, int32_t *nbr, float *dist, int32_t *pinned_host,
                     int64_t *uncertified, const int32_t *colcomp = nullptr, bool prune = false,
-                    int64_t *tiles_visited = nullptr);
+                    int64_t *tiles_visited = nullptr, bool f8 = false);
 
 // prune.cu
 // Tile pruning of Phase 1: locality partition (pivot cells), ball bounds,

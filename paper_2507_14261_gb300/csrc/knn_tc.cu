@@ -37,6 +37,7 @@
 // FP32 SIMT tiles, so the output equals the exact brute-force kNN.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -151,9 +152,25 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 // Instruction descriptor, kind::f16: D F32, A/B BF16, both K-major.
-constexpr uint32_t idesc_bf16(int M, int N) {
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) |
            (uint32_t(M >> 4) << 24);
+}
+
+// Instruction descriptor, kind::f8f6f4: D F32, A/B E4M3 (format 0), both K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f8f6f4 (E4M3 inputs, FP32 accumulate;
+// K = 32 per instruction, 32 bytes of each K-major row as for kind::f16)
+__device__ __forceinline__ void umma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 
 struct TcArgs {
@@ -172,6 +189,8 @@ struct TcArgs {
     int cross;               // queries and keys are different sets: no self-exclusion
     int epi;                 // epilogue warps: 8 (two per TMEM lane quarter, each on half
                              // of the columns) or 4 (0 reads as 4)
+    const float *rscale;     // FP8 operands: per-row scale s (x' ~ s q), query and key rows
+                             // alike (keys padded with 1 to nk_tiles * BN entries)
 };
 
 template <int KC>
@@ -192,7 +211,7 @@ __device__ __forceinline__ void list_insert(float (&ls)[KC], int (&lj)[KC], floa
     lj[0] = here0 ? j : lj[0];
 }
 
-template <int KC, bool MASK>
+template <int KC, bool MASK, bool F8 = false>
 __global__ void __launch_bounds__(KC <= 2 * CAPB ? TC_THREADS_MAX : 64 + 32 * 4, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               TcArgs args) {
@@ -272,7 +291,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             // block args.nkb + kb of the operand rows)
             for (int a = 0; a < nA; ++a) {
                 const int col = a < nkb ? a : args.nkb + (a - nkb);
-                tma_load_2d(sA + size_t(a) * A_BLOCK, &tmA, a_full, col * BK, q0);
+                tma_load_2d(sA + size_t(a) * A_BLOCK, &tmA, a_full, col * (F8 ? 2 * BK : BK), q0);
             }
             int it = 0;
             bool ok = true;
@@ -286,7 +305,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 // x3 order per key tile: hi_0, lo_0, hi_1, lo_1, ...
                 const int col = args.x3 ? ((blk & 1) ? args.nkb + (blk >> 1) : (blk >> 1)) : blk;
                 mbar_expect_tx(&full[s], B_BLOCK);
-                tma_load_2d(sB + size_t(s) * B_BLOCK, &tmB, &full[s], col * BK, t * BN);
+                tma_load_2d(sB + size_t(s) * B_BLOCK, &tmB, &full[s], col * (F8 ? 2 * BK : BK),
+                            t * BN);
             }
             // drain: every issued copy must land before the CTA leaves
             mbar_drain(a_full, 0);
@@ -299,7 +319,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t IDESC = idesc_bf16(BM, BN);
+            constexpr uint32_t IDESC = F8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
             bool ok = mbar_wait(a_full, 0, abort_flag, args.status);
             tc_fence_after();
             int it = 0;
@@ -330,8 +350,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         const uint32_t asm_ = smem_u32(sA + size_t(ablk) * A_BLOCK);
 #pragma unroll
                         for (int kk = 0; kk < BK / 16; ++kk) {
-                            umma_f16(d_tmem, sdesc_sw128(asm_ + kk * 32), sdesc_sw128(bsm + kk * 32),
-                                     IDESC, acc);
+                            if constexpr (F8)
+                                umma_f8(d_tmem, sdesc_sw128(asm_ + kk * 32),
+                                        sdesc_sw128(bsm + kk * 32), IDESC, acc);
+                            else
+                                umma_f16(d_tmem, sdesc_sw128(asm_ + kk * 32),
+                                         sdesc_sw128(bsm + kk * 32), IDESC, acc);
                             acc = 1;
                         }
                     }
@@ -388,6 +412,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         bool ok = true;
         int my_comp = 0;
         if constexpr (MASK) my_comp = __ldg(args.colcomp + i);
+        // FP8: acc = q_i . q_j, so x'_i . x'_j ~ s_i s_j acc
+        float m2s = -2.0f;
+        if constexpr (F8) m2s = -2.0f * (i < args.n ? __ldg(args.rscale + i) : 1.0f);
         for (int t = 0; t < ntiles; ++t) {
             const int b = t & 1, use = t >> 1;
             // every lane waits; the warp proceeds only if all lanes saw the phase
@@ -419,10 +446,16 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4) {
                     const float4 nn = __ldg(reinterpret_cast<const float4 *>(nyt + ch * 16 + 4 * c4));
-                    float s0 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 0]), nn.x);
-                    float s1 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 1]), nn.y);
-                    float s2 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 2]), nn.z);
-                    float s3 = fmaf(-2.0f, __uint_as_float(v[4 * c4 + 3]), nn.w);
+                    float4 cs = make_float4(m2s, m2s, m2s, m2s);
+                    if constexpr (F8) {   // per-key scales, same layout as the norms
+                        const float4 sk = __ldg(reinterpret_cast<const float4 *>(
+                            args.rscale + (nyt - args.ny) + ch * 16 + 4 * c4));
+                        cs = make_float4(m2s * sk.x, m2s * sk.y, m2s * sk.z, m2s * sk.w);
+                    }
+                    float s0 = fmaf(cs.x, __uint_as_float(v[4 * c4 + 0]), nn.x);
+                    float s1 = fmaf(cs.y, __uint_as_float(v[4 * c4 + 1]), nn.y);
+                    float s2 = fmaf(cs.z, __uint_as_float(v[4 * c4 + 2]), nn.z);
+                    float s3 = fmaf(cs.w, __uint_as_float(v[4 * c4 + 3]), nn.w);
                     if constexpr (MASK) {  // same component: not a candidate
                         const int4 cc = __ldg(reinterpret_cast<const int4 *>(cmt + ch * 16 + 4 * c4));
                         const float inf = __int_as_float(0x7f800000);
@@ -609,6 +642,64 @@ __global__ void tc_prep_kernel(const float *__restrict__ X, int64_t n, int d, in
     }
     __syncthreads();
     if (threadIdx.x == 0 && bmax != 0u) atomicMax(ymax_bits, bmax);
+}
+
+// One warp per row, FP8 operands: centred row x' = fl(x - mean), scale
+// s = 2^e with e the smallest integer such that max |x'| <= 448 s (the
+// largest finite E4M3), q = e4m3(x' / s) rounded to nearest (the division by
+// a power of two is exact), FP32 norm ||x'||^2 as for the BF16 operands.
+// Rows of d_pad bytes, zero beyond d.
+__global__ void tc_prep_f8_kernel(const float *__restrict__ X, int64_t n, int d, int d_pad,
+                                  const float *__restrict__ mean, uint8_t *__restrict__ Q,
+                                  float *__restrict__ rscale, float *__restrict__ ny,
+                                  float *__restrict__ xnorm, unsigned *__restrict__ ymax_bits) {
+    __shared__ unsigned bmax;
+    if (threadIdx.x == 0) bmax = 0u;
+    __syncthreads();
+    const int64_t row = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row < n) {
+        const float *x = X + row * d;
+        float amax = 0.0f, acc = 0.0f;
+        for (int t = lane; t < d; t += 32) {
+            const float xc = __fsub_rn(__ldg(x + t), __ldg(mean + t));
+            amax = fmaxf(amax, fabsf(xc));
+            acc = fmaf(xc, xc, acc);
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        }
+        // smallest e with amax <= 448 2^e (so 2^e < 2 amax / 448), kept to
+        // normal FP32 scales; the quotient's rounding is corrected by the
+        // exact comparisons with 448 2^e
+        int e = 0;
+        if (amax > 0.0f) {
+            frexpf(amax / 448.0f, &e);   // amax / 448 = f 2^e, 0.5 <= f < 1
+            while (e > -126 && ldexpf(448.0f, e - 1) >= amax) e -= 1;
+            while (e < 127 && ldexpf(448.0f, e) < amax) e += 1;
+        }
+        const float sc = ldexpf(1.0f, e);
+        uint8_t *q = Q + row * d_pad;
+        for (int t = lane; t < d_pad; t += 32) {
+            const float xc = t < d ? __fsub_rn(__ldg(x + t), __ldg(mean + t)) : 0.0f;
+            q[t] = uint8_t(__nv_cvt_float_to_fp8(ldexpf(xc, -e), __NV_SATFINITE, __NV_E4M3));
+        }
+        if (lane == 0) {
+            rscale[row] = sc;
+            ny[row] = acc;
+            xnorm[row] = acc;
+            atomicMax(&bmax, __float_as_uint(sqrtf(acc)));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && bmax != 0u) atomicMax(ymax_bits, bmax);
+}
+
+__global__ void fill_value_kernel(float *p, int64_t from, int64_t to, float v) {
+    int64_t i = from + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < to) p[i] = v;
 }
 
 __global__ void fill_inf_kernel(float *p, int64_t from, int64_t to) {
@@ -923,14 +1014,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int box_rows) {
+// 2-D map over row-major operand rows of `cols` elements: BF16 (boxes of 64
+// elements) or, with f8, bytes (boxes of 128); 128 bytes per box row either way
+bool make_map(CUtensorMap *m, const void *base, int64_t rows, int64_t cols, int box_rows,
+              bool f8 = false) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t gdim[2] = {cuuint64_t(cols), cuuint64_t(rows)};
-    cuuint64_t gstride[1] = {cuuint64_t(cols) * 2};
-    cuuint32_t box[2] = {cuuint32_t(BK), cuuint32_t(box_rows)};
+    cuuint64_t gstride[1] = {cuuint64_t(cols) * (f8 ? 1 : 2)};
+    cuuint32_t box[2] = {cuuint32_t(f8 ? 2 * BK : BK), cuuint32_t(box_rows)};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), gdim, gstride,
+    CUresult r = fn(m, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                    const_cast<void *>(base), gdim, gstride,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -956,10 +1051,12 @@ struct TcPlan {
 
 // allow8: eight epilogue warps when the candidate lists fit the merge area
 // (KC <= 2 CAPB) and the larger staging area still leaves three B stages
-TcPlan tc_plan(int64_t n, int d, int k, bool x3, bool allow8 = true) {
+// f8: E4M3 operand rows, 128 elements (128 bytes) per K block
+TcPlan tc_plan(int64_t n, int d, int k, bool x3, bool allow8 = true, bool f8 = false) {
     TcPlan p{};
-    p.d_pad = (d + BK - 1) / BK * BK;
-    p.nkb = p.d_pad / BK;
+    const int kel = f8 ? 2 * BK : BK;   // elements per 128-byte K block
+    p.d_pad = (d + kel - 1) / kel * kel;
+    p.nkb = p.d_pad / kel;
     p.kh = (x3 ? 2 : 1) * p.d_pad;
     // keep at least ~10 candidates beyond k so that the certificate has a
     // gap to work with: k <= 21 -> 31 candidates, k <= 37 -> 47, k <= 63 -> 63
@@ -985,14 +1082,15 @@ TcPlan tc_plan(int64_t n, int d, int k, bool x3, bool allow8 = true) {
 
 }  // namespace
 
-bool knn_tc_supported(int64_t n, int d, int k, bool x3) {
+bool knn_tc_supported(int64_t n, int d, int k, bool x3, bool f8) {
     if (k + 1 > 64 || n < 2) return false;
-    TcPlan p = tc_plan(n, d, k, x3);
+    TcPlan p = tc_plan(n, d, k, x3 && !f8, true, f8);
     return p.stages >= 2 && encode_fn() != nullptr;
 }
 
-size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prune) {
-    TcPlan p = tc_plan(n, d, k, x3);
+size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prune, bool f8) {
+    TcPlan p = tc_plan(n, d, k, x3 && !f8, true, f8);
+    if (f8) prune = false;
     size_t b = 0;
     if (prune) {
         const int64_t K = prune_pivots_max(n), Kpad = (K + BN - 1) / BN * BN;
@@ -1000,7 +1098,8 @@ size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prun
              align256(size_t(Kpad + BN) * 4) * 2 + align256(size_t(n) * 4) * 2;
         b += prune_workspace(n, d, p.kh, p.kc - 1, p.nq_tiles, p.nk_tiles);
     }
-    b += align256(size_t(n) * p.kh * 2);                   // operand rows
+    b += align256(size_t(n) * p.kh * (f8 ? 1 : 2));        // operand rows
+    if (f8) b += align256(size_t(p.nk_tiles) * BN * 4);    // per-row scales
     b += align256(size_t(p.nk_tiles) * BN * 4) * 2;        // ny, components (padded)
     b += align256(size_t(n) * 4);                          // xnorm2
     b += align256(size_t(d) * 4) + 256;                    // mean, ymax
@@ -1014,10 +1113,19 @@ size_t knn_tc_workspace(int64_t n, int d, int k, bool x3, int num_sms, bool prun
 famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k, bool x3,
                     bool vec4, int32_t *nbr, float *dist, int32_t *pinned_host,
                     int64_t *uncertified, const int32_t *colcomp, bool prune,
-                    int64_t *tiles_visited) {
-    TcPlan p = tc_plan(n, d, k, x3);
+                    int64_t *tiles_visited, bool f8) {
+    if (f8) {   // single E4M3 products, no tile pruning, no component mask
+        x3 = false;
+        prune = false;
+        if (colcomp) return FAMST_ERR_UNSUPPORTED;
+    }
+    TcPlan p = tc_plan(n, d, k, x3, true, f8);
     if (p.stages < 2 || k + 1 > 64) return FAMST_ERR_UNSUPPORTED;
-    __nv_bfloat16 *H = ar.take<__nv_bfloat16>(size_t(n) * p.kh);
+    // operand rows: BF16 (kh elements) or E4M3 bytes (kh bytes) with per-row scales
+    __nv_bfloat16 *H = f8 ? nullptr : ar.take<__nv_bfloat16>(size_t(n) * p.kh);
+    uint8_t *Q = f8 ? ar.take<uint8_t>(size_t(n) * p.kh) : nullptr;
+    float *rscale = f8 ? ar.take<float>(size_t(p.nk_tiles) * BN) : nullptr;
+    if (f8 && (!Q || !rscale)) return FAMST_ERR_OOM;
     float *ny = ar.take<float>(size_t(p.nk_tiles) * BN);
     float *xn2 = ar.take<float>(size_t(n));
     float *mean = ar.take<float>(size_t(d));
@@ -1029,7 +1137,8 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     float *splus = ar.take<float>(size_t(n));
     int32_t *fail_rows = ar.take<int32_t>(size_t(n));
     int32_t *fail_count = ar.take<int32_t>(1);
-    if (!H || !ny || !xn2 || !mean || !ymax || !part || !cand || !splus || !fail_rows || !fail_count)
+    if ((!f8 && !H) || !ny || !xn2 || !mean || !ymax || !part || !cand || !splus || !fail_rows ||
+        !fail_count)
         return FAMST_ERR_OOM;
     // prep: mean, centred BF16 operands, norms
     FAMST_LAUNCH(ex, colsum_partial_kernel, nb, 128, 0, X, n, d, rows_per, part);
@@ -1037,9 +1146,17 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     if (cudaMemsetAsync(ymax, 0, 4, ex.stream) != cudaSuccess ||
         cudaMemsetAsync(fail_count, 0, 4, ex.stream) != cudaSuccess)
         return FAMST_ERR_CUDA;
-    FAMST_LAUNCH(ex, tc_prep_kernel, unsigned((n * 32 + 255) / 256), 256, 0, X, n, d, p.d_pad,
-                 int(x3), mean, H, ny, xn2, ymax);
     const int64_t npad = p.nk_tiles * BN;
+    if (f8) {
+        FAMST_LAUNCH(ex, tc_prep_f8_kernel, unsigned((n * 32 + 255) / 256), 256, 0, X, n, d,
+                     p.d_pad, mean, Q, rscale, ny, xn2, ymax);
+        if (npad > n)
+            FAMST_LAUNCH(ex, fill_value_kernel, unsigned((npad - n + 255) / 256), 256, 0, rscale,
+                         n, npad, 1.0f);
+    } else {
+        FAMST_LAUNCH(ex, tc_prep_kernel, unsigned((n * 32 + 255) / 256), 256, 0, X, n, d, p.d_pad,
+                     int(x3), mean, H, ny, xn2, ymax);
+    }
     if (npad > n)
         FAMST_LAUNCH(ex, fill_inf_kernel, unsigned((npad - n + 255) / 256), 256, 0, ny, n, npad);
     const bool use_prune = prune && !colcomp && prune_supported(n, d, k, vec4);
@@ -1112,9 +1229,11 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         splus_t = ar.take<float>(size_t(n));
         if (!cand_t || !splus_t) return FAMST_ERR_OOM;
     }
-    const __nv_bfloat16 *Hop = use_prune ? P.Hs : H;
+    const void *Hop = f8 ? static_cast<const void *>(Q)
+                         : static_cast<const void *>(use_prune ? P.Hs : H);
     CUtensorMap mA, mB;
-    if (!make_map(&mA, Hop, n, p.kh, BM) || !make_map(&mB, Hop, n, p.kh, BN)) return FAMST_ERR_CUDA;
+    if (!make_map(&mA, Hop, n, p.kh, BM, f8) || !make_map(&mB, Hop, n, p.kh, BN, f8))
+        return FAMST_ERR_CUDA;
     int32_t *cpad = nullptr;   // components over the padded rows (-1 beyond n)
     if (colcomp) {
         cpad = ar.take<int32_t>(size_t(npad));
@@ -1125,7 +1244,7 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     }
     TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, use_prune ? P.nys : ny, cand_t,
              splus_t, ex.dstatus, use_prune ? P.tab : nullptr, cpad,
-             use_prune ? P.klist : nullptr, 0, p.epi};
+             use_prune ? P.klist : nullptr, 0, p.epi, rscale};
 #define TC_LAUNCH(KCV, M)                                                                        \
     do {                                                                                         \
         if (set_smem_attr(knn_tc_kernel<KCV, M>, int(p.smem), ex.stream) != cudaSuccess)         \
@@ -1133,8 +1252,19 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, M>), unsigned(p.nq_tiles), 64 + 32 * p.epi, p.smem, \
                      mA, mB, a);                                                                 \
     } while (0)
+#define TC_LAUNCH_F8(KCV)                                                                           \
+    do {                                                                                            \
+        if (set_smem_attr(knn_tc_kernel<KCV, false, true>, int(p.smem), ex.stream) != cudaSuccess)  \
+            return FAMST_ERR_CUDA;                                                                  \
+        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false, true>), unsigned(p.nq_tiles), 64 + 32 * p.epi,  \
+                     p.smem, mA, mB, a);                                                            \
+    } while (0)
     timer_mark(ex, TIMER_TILES, false);
-    if (cpad) {
+    if (f8) {
+        if (p.kc == 32) TC_LAUNCH_F8(32);
+        else if (p.kc == 48) TC_LAUNCH_F8(48);
+        else TC_LAUNCH_F8(64);
+    } else if (cpad) {
         if (p.kc == 32) TC_LAUNCH(32, true);
         else if (p.kc == 48) TC_LAUNCH(48, true);
         else TC_LAUNCH(64, true);
@@ -1145,6 +1275,7 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     }
     timer_mark(ex, TIMER_TILES, true);
 #undef TC_LAUNCH
+#undef TC_LAUNCH_F8
     if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
     // rerank + certificate
     const double u8 = 1.0 / 256.0;
@@ -1153,6 +1284,19 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     cc.eps_dot = (x3 ? (3.0 * u8 * u8 + 3.0 * u8 * u8 * u8 + u8 * u8 * u8 * u8)
                      : (2.0 * u8 + u8 * u8)) +
                  kprod * std::ldexp(1.0, -22) * (1.0 + 4.0 * u8);
+    if (f8) {
+        // E4M3 with the row's scale: a normal element is within u = 2^-4 of
+        // x'_t (relative); an element below the normal range within 2^-10 s,
+        // and s <= 2 max|x'| / 448, so over the row those add at most
+        // sqrt(d) 2^-10 (2 / 448) ||x'|| per side. Products of E4M3 values
+        // are exact in FP32; the accumulation term is as for BF16.
+        // With |x^_t - x'_t| <= u|x'_t| + c ||x'|| (c = 2^-10 2/448) on both
+        // sides, |x^.y^ - x'.y'| <= ((2u + u^2) + 2 sqrt(d)(1 + u) c + d c^2)
+        // ||x'|| ||y'||.
+        const double u4 = 1.0 / 16.0, c8 = 2.0 / 448.0 / 1024.0, dp = double(p.d_pad);
+        cc.eps_dot = 2.0 * u4 + u4 * u4 + 2.0 * std::sqrt(dp) * (1.0 + u4) * c8 + dp * c8 * c8 +
+                     kprod * std::ldexp(1.0, -22) * (1.0 + 4.0 * u4);
+    }
     cc.d_plus = double(d) + 4.0;
     const unsigned rgrid = unsigned((n * 32 + 255) / 256);
 #define RERANK(V, KCV)                                                                           \

@@ -21,7 +21,7 @@ ERRORS = {
     -4: "FAMST_ERR_TIMEOUT", -5: "FAMST_ERR_CUDA", -6: "FAMST_ERR_OOM",
     -7: "FAMST_ERR_UNSUPPORTED", -8: "FAMST_ERR_NONFINITE", -9: "FAMST_ERR_DISCONNECTED",
 }
-PREC = {"fp32": 0, "bf16": 1, "bf16x3": 2}
+PREC = {"fp32": 0, "bf16": 1, "bf16x3": 2, "fp8": 3}
 
 
 class FamstError(RuntimeError):

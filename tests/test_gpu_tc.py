@@ -1,4 +1,4 @@
-"""Parity of the tcgen05 (BF16 / BF16 hi-lo x3) distance path with the
+"""Parity of the tcgen05 (BF16 / BF16 hi-lo x3 / E4M3) distance path with the
 oracle's exact kNN: candidates from reduced-precision tiles, canonical FP32
 re-rank, certificate, FP32 recomputation of uncertified rows -- the output
 must equal the brute-force kNN bit for bit, at any precision."""
@@ -43,7 +43,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "fp8"])
 @pytest.mark.parametrize("name,make,k", CASES, ids=[c[0] for c in CASES])
 def test_tensor_knn_is_exact(orc, ctx, prec, name, make, k):
     X = make()
@@ -66,7 +66,48 @@ def test_build_matches_fp32_path(ctx):
     X = workloads.get("blobs_100k").points(5000)
     Xd = _dev(X)
     t32, i32 = ctx.build(Xd, 16, 5, 3, "fp32")
-    for prec in ("bf16x3", "bf16"):
+    for prec in ("bf16x3", "bf16", "fp8"):
         t, i = ctx.build(Xd, 16, 5, 3, prec)
         assert torch.equal(t.u, t32.u) and torch.equal(t.v, t32.v) and torch.equal(t.w, t32.w)
         assert t.W == t32.W
+
+
+def _separated_groups(groups, size, d, seed):
+    # groups of `size` points (spread 0.01) whose centres are >= 10 apart:
+    # for k < size the k-th neighbour lies in the point's own group and every
+    # point outside it is ~1000x farther, a gap far above E4M3's 2^-4 error
+    rng = np.random.default_rng(seed)
+    c = 10.0 * np.eye(groups, d) if groups <= d else 10.0 * rng.standard_normal((groups, d))
+    X = np.repeat(c, size, axis=0) + 0.01 * rng.standard_normal((groups * size, d))
+    return np.ascontiguousarray(X[rng.permutation(len(X))], dtype=np.float32)
+
+
+def test_fp8_certifies_separated_groups(orc, ctx):
+    X = _separated_groups(128, 24, 128, 21)
+    tree, info = ctx.build(_dev(X), 10, 3, 1, "fp8")
+    assert info.uncertified_rows <= X.shape[0] // 100
+    nbr, dist = ctx.knn_graph(_dev(X), 10, "fp8")
+    rn, rd = orc.knn(X, 10)
+    assert np.array_equal(nbr.cpu().numpy(), rn) and np.array_equal(dist.cpu().numpy(), rd)
+
+
+def test_fp8_scales_span_magnitudes(orc, ctx):
+    # rows from 1e-6 to 1e6 in norm: each row's power-of-two scale keeps its
+    # E4M3 codes in range, and the exact result does not depend on it
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((1500, 40)) * np.exp(rng.uniform(-14, 14, (1500, 1)))
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    nbr, dist = ctx.knn_graph(_dev(X), 7, "fp8")
+    rn, rd = orc.knn(X, 7)
+    assert np.array_equal(nbr.cpu().numpy(), rn) and np.array_equal(dist.cpu().numpy(), rd)
+
+
+def test_fp8_only_where_supported(ctx):
+    import paper_2507_14261_gb300 as P
+    X = _dev(workloads.blobs(500, 16, 4, (1, 1), 3))
+    with pytest.raises(P.FamstError) as e:
+        ctx.emst_exact(X, "fp8")
+    assert e.value.name == "FAMST_ERR_UNSUPPORTED"
+    with pytest.raises(P.FamstError) as e:
+        ctx.build_batched(X.reshape(-1), [0, 500], [16], 5, 3, 1, "fp8")
+    assert e.value.name == "FAMST_ERR_UNSUPPORTED"
