@@ -350,9 +350,11 @@ famst_status famst_emst_exact(famst_ctx *ctx, const float *X, int64_t n, int32_t
  * int32 plus small tables), present on every GPU that loads this library
  * until the process exits. n > FAMST_NOALLOC_MAX_N returns
  * FAMST_ERR_UNSUPPORTED; 1 <= k <= n-1 and n*k < 2^31 are required.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream
- * capture. Every call on a device shares the array and leaves its contents
+ * Every call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, which allocates nothing; nothing is cached, so
+ * calls stay valid after cudaDeviceReset). The first call in a context may
+ * load the module, so make it before any stream capture. Every call on a
+ * device shares the array and leaves its contents
  * behind (each call initialises what it reads); calls whose work overlaps
  * on the GPU race on it, so serialise them (one stream, or events). */
 #define FAMST_NOALLOC_MAX_N (1 << 20)

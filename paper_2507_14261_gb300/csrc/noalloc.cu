@@ -14,7 +14,6 @@
 // work overlaps on the GPU race on the array.
 #include <cuda_runtime.h>
 
-#include <mutex>
 
 #include "famst_internal.cuh"
 
@@ -169,21 +168,13 @@ __global__ void na_label_kernel(int64_t n, const int32_t *__restrict__ scratch,
     if (v == 0) *t_out = scratch[OFF_WORDS] ? -1 : scratch[OFF_WORDS + 1];
 }
 
-std::mutex g_na_mutex;
-int32_t *g_na_addr[128] = {};
-
-// Device address of the scratch array on the current device, looked up once.
+// Device address of the scratch array in the current context. Looked up on
+// every call (the lookup allocates nothing): a cached address would dangle
+// after cudaDeviceReset, which unloads the module with the context.
 famst_status na_scratch(int32_t **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return FAMST_ERR_CUDA;
-    std::lock_guard<std::mutex> lk(g_na_mutex);
-    if (!g_na_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
-            return FAMST_ERR_CUDA;
-        g_na_addr[dev] = static_cast<int32_t *>(p);
-    }
-    *out = g_na_addr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return FAMST_ERR_CUDA;
+    *out = static_cast<int32_t *>(p);
     return FAMST_OK;
 }
 
