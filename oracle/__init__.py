@@ -83,6 +83,10 @@ def _lib():
             L.or_components.restype = c.c_int64
             L.or_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
             L.or_philox4x32_10.restype = None
+            L.or_nndescent.argtypes = [_f32p, c.c_int64, c.c_int, c.c_int, c.c_int, c.c_int,
+                                       c.c_double, c.c_uint64, c.c_void_p, _i32p, _f32p,
+                                       _i64p, _i64p]
+            L.or_nndescent.restype = c.c_int
             L.or_random_edges.argtypes = [_f32p, c.c_int, _i32p, _i64p, c.c_int64,
                                           c.c_int, c.c_uint64, _i32p, _i32p, _f32p,
                                           _i32p, _i32p]
@@ -149,6 +153,53 @@ def knn(X, k: int, rows=None, threads: int | None = None):
     _lib().or_knn(X, n, d, k, r0, r1, nbr, dist,
                   threads if threads is not None else threads_default())
     return nbr, dist
+
+
+@dataclass
+class NNDescent:
+    nbr: np.ndarray       # n x k ids, (w, id) ascending per row
+    dist: np.ndarray      # n x k canonical distances
+    iters: int            # iterations run
+    updates: np.ndarray   # c of every iteration run
+    pairs: np.ndarray     # pairs evaluated by the joins of every iteration
+
+
+def nndescent(X, k: int, S: int, max_iters: int, delta: float, seed: int,
+              init=None) -> NNDescent:
+    """NN-Descent (Dong, Charikar and Li, 2011), the algorithm behind the
+    paper's Phase 1 library, with set-defined steps (see ``or_nndescent``):
+    lists of k, samples of S per class over both directions with Philox
+    priorities, local joins, k smallest of each list and its proposals;
+    stop when an iteration changes fewer than delta n k entries (or none)."""
+    X = _f32(X)
+    n, d = X.shape
+    if not (1 <= k <= n - 1 and 1 <= S and max_iters >= 0):
+        raise ValueError("need 1 <= k <= n-1, S >= 1, max_iters >= 0")
+    ip = None
+    if init is not None:
+        init = _i32(init).reshape(n, k)
+        if (init < 0).any() or (init >= n).any() or (init == np.arange(n)[:, None]).any():
+            raise ValueError("init ids must be in [0, n) and not the row itself")
+        if any(len(set(r)) != k for r in init.tolist()):
+            raise ValueError("init rows must hold k distinct ids")
+        ip = init.ctypes.data_as(ctypes.c_void_p)
+    nbr = np.empty((n, k), np.int32)
+    dist = np.empty((n, k), np.float32)
+    upd = np.zeros(max(max_iters, 1), np.int64)
+    prs = np.zeros(max(max_iters, 1), np.int64)
+    it = _lib().or_nndescent(X, n, d, k, S, max_iters, float(delta), seed & (2**64 - 1), ip,
+                             nbr, dist, upd, prs)
+    return NNDescent(nbr, dist, int(it), upd[:it].copy(), prs[:it].copy())
+
+
+def recall(nbr, exact_nbr) -> float:
+    """Fraction of the exact kNN ids that a graph's rows hold (recall@k)."""
+    nbr, exact_nbr = np.asarray(nbr), np.asarray(exact_nbr)
+    n, k = exact_nbr.shape
+    hit = 0
+    for a, b in zip(nbr, exact_nbr):
+        hit += len(np.intersect1d(a, b, assume_unique=True))
+    return hit / (n * k)
 
 
 def knn_rows(X, k: int, rows, threads: int | None = None):
@@ -381,14 +432,18 @@ class FamstResult:
 
 def famst(X, k: int, lam: int, seed: int, knn_graph=None,
           max_iters: int = 10000, threads: int | None = None,
-          connect: str = "random") -> FamstResult:
+          connect: str = "random", nnd: dict | None = None) -> FamstResult:
     """Algorithm 1. ``knn_graph`` = (nbr, dist) replaces the exact kNN stage
     (used to run the later stages on another implementation's graph);
     ``connect`` = "random" (Alg. 3) or "nearest" (the lambda nearest pairs
-    of every component pair)."""
+    of every component pair); ``nnd`` = dict(S=, max_iters=, delta=) takes
+    Phase 1 by NN-Descent with the build's seed."""
     X = _f32(X)
     n = X.shape[0]
-    if knn_graph is None:
+    if knn_graph is None and nnd is not None:
+        r = nndescent(X, k, nnd["S"], nnd["max_iters"], nnd["delta"], seed)
+        nbr, dist = r.nbr, r.dist
+    elif knn_graph is None:
         nbr, dist = knn(X, k, threads=threads)
     else:
         nbr, dist = _i32(knn_graph[0]), _f32(knn_graph[1])

@@ -223,6 +223,236 @@ static int64_t pick(uint32_t r, int64_t size)
     return (int64_t)(((uint64_t)r * (uint64_t)size) >> 32);
 }
 
+/* ------------------------------------ Phase 1 alternative: NN-Descent
+ * GetANNs by NN-Descent (Dong, Charikar and Li, WWW 2011), the algorithm of
+ * the library the paper uses for its Phase 1 (Sec. 2 and Sec. 3). Every step
+ * is defined on sets, so the result does not depend on the order in which
+ * the comparisons are made; draws come from Philox4x32-10 with the key
+ * (seed_lo, seed_hi):
+ *
+ * Lists. B[v] holds k distinct ids u != v with (w(v,u), u) ascending and a
+ *   flag "new" per entry.
+ * Start. Without a given graph, B[v] takes the first k distinct ids among
+ *   the draws r = 0 .. 8k-1, u = pick(r0, n-1) (u += 1 when u >= v) with
+ *   (r0, ., ., .) = Philox(counter = (v, r, 0, 1)); if fewer than k are
+ *   distinct, the smallest unused ids fill the list. Every entry is new.
+ * One iteration (it = 0, 1, ...), on the lists as the iteration finds them:
+ *   1. For every v and each class (new, old): the candidates are the ids
+ *      u of B[v] of that class and the ids u whose list B[u] holds v with
+ *      that class; each candidate has the priority
+ *      pr(v,u) = r0 of Philox(counter = (v, u, it, 2)), and the S candidates
+ *      smallest in (pr, u) form new[v] (resp. old[v]): the sample of rate
+ *      S / k of the paper, taken jointly over both directions.
+ *   2. Every entry u of B[v] that is new and in new[v] becomes old.
+ *   3. Local join: for every v, each pair of distinct ids {a, b} with a, b
+ *      in new[v], or a in new[v] and b in old[v], proposes b to B[a] and a
+ *      to B[b] with w(a, b).
+ *   4. B[a] becomes the k smallest distinct (w, id) of B[a] and every
+ *      proposal to a; an entry that came from a proposal is new.
+ *   c = the number of entries in all lists that were not there before.
+ * The iterations stop after the first one with c = 0 or c < delta n k, or
+ * after max_iters. Returns the number of iterations run; updates[it] = c and
+ * pairs[it] = the pairs {a, b} (a != b) its joins evaluated, counted once
+ * per v and per set they came from: C(|new[v]|, 2) + |new[v] x old[v]|
+ * less the pairs with a = b. */
+typedef struct { float w; int32_t id; uint8_t flag; } nnd_ent;
+enum { NND_NEW = 1, NND_INSERTED = 2 };
+typedef struct { uint32_t pr; int32_t u; } nnd_cand;
+
+static uint32_t nnd_draw(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                         const uint32_t key[2])
+{
+    uint32_t ctr[4] = {c0, c1, c2, c3}, r[4];
+    or_philox4x32_10(ctr, key, r);
+    return r[0];
+}
+
+static int cmp_nnd_cand(const void *a, const void *b)
+{
+    const nnd_cand *x = (const nnd_cand *)a, *y = (const nnd_cand *)b;
+    if (x->pr != y->pr) return x->pr < y->pr ? -1 : 1;
+    return (x->u > y->u) - (x->u < y->u);
+}
+
+/* insert (w, id) into the sorted list L of k entries if it is among the k
+ * smallest and not already there */
+static void nnd_insert(nnd_ent *L, int k, float w, int32_t id)
+{
+    if (!nb_less(w, id, L[k - 1].w, L[k - 1].id)) return;
+    for (int r = 0; r < k; ++r)
+        if (L[r].id == id) return;
+    int pos = k - 1;
+    while (pos > 0 && nb_less(w, id, L[pos - 1].w, L[pos - 1].id)) {
+        L[pos] = L[pos - 1];
+        --pos;
+    }
+    L[pos].w = w;
+    L[pos].id = id;
+    L[pos].flag = NND_NEW | NND_INSERTED;
+}
+
+int or_nndescent(const float *X, int64_t n, int d, int k, int S, int max_iters,
+                 double delta, uint64_t seed, const int32_t *init,
+                 int32_t *nbr, float *dist, int64_t *updates, int64_t *pairs)
+{
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    nnd_ent *B = (nnd_ent *)malloc(sizeof(nnd_ent) * (size_t)(n * k));
+    /* start */
+    for (int64_t v = 0; v < n; ++v) {
+        nnd_ent *L = B + v * k;
+        int have = 0;
+        if (init) {
+            for (int r = 0; r < k; ++r) L[r].id = init[v * k + r];
+            have = k;
+        }
+        for (int r = 0; r < 8 * k && have < k; ++r) {
+            int64_t u = pick(nnd_draw((uint32_t)v, (uint32_t)r, 0u, 1u, key), n - 1);
+            if (u >= v) ++u;
+            int dup = 0;
+            for (int q = 0; q < have; ++q) dup |= L[q].id == (int32_t)u;
+            if (!dup) L[have++].id = (int32_t)u;
+        }
+        for (int64_t u = 0; u < n && have < k; ++u) {
+            int dup = u == v;
+            for (int q = 0; q < have; ++q) dup |= L[q].id == (int32_t)u;
+            if (!dup) L[have++].id = (int32_t)u;
+        }
+        for (int r = 0; r < k; ++r) {
+            L[r].w = or_dist32(X + v * d, X + (int64_t)L[r].id * d, d);
+            L[r].flag = NND_NEW;
+        }
+        for (int r = 1; r < k; ++r) {   /* insertion sort by (w, id) */
+            nnd_ent e = L[r];
+            int q = r;
+            while (q > 0 && nb_less(e.w, e.id, L[q - 1].w, L[q - 1].id)) {
+                L[q] = L[q - 1];
+                --q;
+            }
+            L[q] = e;
+        }
+    }
+    int32_t *samp = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * n * S));
+    int32_t *scnt = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * n));
+    int64_t *roff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * (n + 1)));
+    int32_t *rsrc = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n * k));
+    nnd_cand *cbuf = (nnd_cand *)malloc(sizeof(nnd_cand) * (size_t)(n * k + k));
+    float *wbuf = (float *)malloc(sizeof(float) * (size_t)(1024 * ((int64_t)S * (3 * S - 1) / 2)));
+    int it = 0;
+    while (it < max_iters) {
+        /* step 1: reverse entries of each class, by counting */
+        for (int cls = 0; cls < 2; ++cls) {
+            int64_t *off = roff + cls * (n + 1);
+            for (int64_t v = 0; v <= n; ++v) off[v] = 0;
+            for (int64_t e = 0; e < n * k; ++e)
+                if (((B[e].flag & NND_NEW) != 0) == (cls == 0)) off[B[e].id + 1] += 1;
+            for (int64_t v = 0; v < n; ++v) off[v + 1] += off[v];
+        }
+        for (int cls = 0; cls < 2; ++cls) {
+            const int64_t *off = roff + cls * (n + 1);
+            int64_t *fill = (int64_t *)calloc((size_t)n, sizeof(int64_t));
+            for (int64_t e = 0; e < n * k; ++e) {
+                if (((B[e].flag & NND_NEW) != 0) != (cls == 0)) continue;
+                int32_t v = B[e].id;
+                rsrc[off[v] + fill[v]++] = (int32_t)(e / k);
+            }
+            free(fill);
+            for (int64_t v = 0; v < n; ++v) {
+                int m = 0;
+                for (int r = 0; r < k; ++r) {
+                    const nnd_ent *x = B + v * k + r;
+                    if (((x->flag & NND_NEW) != 0) == (cls == 0)) cbuf[m++].u = x->id;
+                }
+                for (int64_t q = off[v]; q < off[v + 1]; ++q) cbuf[m++].u = rsrc[q];
+                for (int q = 0; q < m; ++q)
+                    cbuf[q].pr = nnd_draw((uint32_t)v, (uint32_t)cbuf[q].u, (uint32_t)it, 2u, key);
+                qsort(cbuf, (size_t)m, sizeof(nnd_cand), cmp_nnd_cand);
+                int c = 0;
+                for (int q = 0; q < m && c < S; ++q) {
+                    if (q > 0 && cbuf[q].u == cbuf[q - 1].u) continue;   /* both directions */
+                    samp[(cls * n + v) * S + c++] = cbuf[q].u;
+                }
+                scnt[cls * n + v] = c;
+            }
+        }
+        /* step 2 */
+        for (int64_t v = 0; v < n; ++v) {
+            const int32_t *nv = samp + v * S;
+            for (int r = 0; r < k; ++r) {
+                nnd_ent *x = B + v * k + r;
+                if (!(x->flag & NND_NEW)) continue;
+                for (int q = 0; q < scnt[v]; ++q)
+                    if (nv[q] == x->id) x->flag = 0;
+            }
+        }
+        /* steps 3 and 4: the lists are updated as proposals arrive, which
+         * gives the k smallest of the union whatever the order; the
+         * distances of a block of joins are computed first, spread over
+         * threads (they do not depend on the lists) */
+        const int64_t VB = 1024, PP = (int64_t)S * (3 * S - 1) / 2;
+        int64_t joined = 0;
+        for (int64_t v0 = 0; v0 < n; v0 += VB) {
+            const int64_t v1 = v0 + VB < n ? v0 + VB : n;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+            for (int64_t v = v0; v < v1; ++v) {
+                const int32_t *nv = samp + v * S, *ov = samp + (n + v) * S;
+                const int nn = scnt[v], no = scnt[n + v];
+                float *wv = wbuf + (v - v0) * PP;
+                int64_t q = 0;
+                for (int i = 0; i < nn; ++i) {
+                    const float *xa = X + (int64_t)nv[i] * d;
+                    for (int j = i + 1; j < nn; ++j)
+                        wv[q++] = or_dist32(xa, X + (int64_t)nv[j] * d, d);
+                    for (int j = 0; j < no; ++j)
+                        wv[q++] = or_dist32(xa, X + (int64_t)ov[j] * d, d);
+                }
+            }
+            for (int64_t v = v0; v < v1; ++v) {
+                const int32_t *nv = samp + v * S, *ov = samp + (n + v) * S;
+                const int nn = scnt[v], no = scnt[n + v];
+                const float *wv = wbuf + (v - v0) * PP;
+                int64_t q = 0;
+                for (int i = 0; i < nn; ++i) {
+                    const int32_t a = nv[i];
+                    for (int j = i + 1; j < nn; ++j, ++q) {
+                        ++joined;
+                        nnd_insert(B + (int64_t)a * k, k, wv[q], nv[j]);
+                        nnd_insert(B + (int64_t)nv[j] * k, k, wv[q], a);
+                    }
+                    for (int j = 0; j < no; ++j, ++q) {
+                        if (ov[j] == a) continue;   /* a in both samples */
+                        ++joined;
+                        nnd_insert(B + (int64_t)a * k, k, wv[q], ov[j]);
+                        nnd_insert(B + (int64_t)ov[j] * k, k, wv[q], a);
+                    }
+                }
+            }
+        }
+        int64_t c = 0;
+        for (int64_t e = 0; e < n * k; ++e) {
+            c += (B[e].flag & NND_INSERTED) != 0;
+            B[e].flag &= (uint8_t)~NND_INSERTED;
+        }
+        if (updates) updates[it] = c;
+        if (pairs) pairs[it] = joined;
+        ++it;
+        if (c == 0 || (double)c < delta * (double)n * (double)k) break;
+    }
+    for (int64_t e = 0; e < n * k; ++e) {
+        nbr[e] = B[e].id;
+        dist[e] = B[e].w;
+    }
+    free(B);
+    free(samp);
+    free(scnt);
+    free(roff);
+    free(rsrc);
+    free(cbuf);
+    free(wbuf);
+    return it;
+}
+
 typedef struct { float w; int32_t s; int32_t u; int32_t v; } sample_t;
 
 static int cmp_sample(const void *a, const void *b)
