@@ -372,6 +372,43 @@ def fp8_on_workload(fam, torch, X, w, prec, tree_ref) -> dict:
     return out
 
 
+def nndescent_sub(fam, torch, X, w, prec, quality, S=None, iters=10, delta=0.001) -> dict:
+    """NN-Descent as Phase 1 on the timed cloud: famst_knn_nndescent timed
+    by CUDA events after a warm-up, recall@k against the exact tiles'
+    graph, join pairs per iteration, and one build with it as Phase 1."""
+    c = fam.Context(torch.cuda.current_device())
+    S = min(w.k, 32) if S is None else S
+    exact_nbr, _ = c.knn_graph(X, w.k, prec)
+    c.knn_nndescent(X, w.k, S, iters, delta, 1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    nbr, dist, it, upd, prs = c.knn_nndescent(X, w.k, S, iters, delta, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    hit = 0
+    for r0 in range(0, w.n, 65536):   # recall@k in slices (bounded memory)
+        a, b = nbr[r0:r0 + 65536], exact_nbr[r0:r0 + 65536]
+        hit += int((a.unsqueeze(2) == b.unsqueeze(1)).any(2).sum().item())
+    out = {"S": S, "max_iters": iters, "delta": delta, "ms": ms, "iters": it,
+           "updates": upd.tolist(), "join_pairs": prs.tolist(),
+           "recall_at_k": hit / (w.n * w.k),
+           "points_per_s": w.n / (ms / 1e3),
+           "timing": "CUDA events around famst_knn_nndescent after a warm-up"}
+    c.set_knn_method("nndescent", S, iters, delta)
+    tree, info = c.build(X, w.k, w.lam, 1, prec)
+    out["build"] = {"W": tree.W, "ms_knn": info.ms_knn, "ms_total": info.ms_total,
+                    "t": info.t, "refine_sweeps": info.refine_sweeps,
+                    "knn_iters": info.knn_iters}
+    if quality is not None and quality["W_exact"] > 0:
+        out["build"]["rel_err"] = (tree.W - quality["W_exact"]) / quality["W_exact"]
+        out["build"]["rel_err_exact_knn"] = quality["rel_err"]
+    c.close()
+    return out
+
+
 def batch_sub(fam, torch, local: int, prec: str, steps: int = 5) -> dict:
     clouds = workloads.batch_clouds()
     off = np.zeros(len(clouds) + 1, np.int64)
@@ -755,6 +792,13 @@ def main():
             nearest["rel_err_random_alg3"] = quality["rel_err"]
         c2.close()
 
+    # Phase 1 by NN-Descent (the paper's own Phase 1 method) on the same
+    # cloud, after the timed region: its time, iterations and recall@k
+    # against the exact graph, and a whole build on it (W, Eq. 1's error)
+    nndescent = None
+    if not args.no_extras and rank == 0:
+        nndescent = nndescent_sub(fam, torch, X, w, args.prec, quality)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(X_np, w.k)
@@ -773,7 +817,7 @@ def main():
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "quality": quality, "kernels": kernels,
             "l2_peak": l2, "precision_compare": precision, "batch_256": batch,
-            "connect_nearest": nearest, "fp8_tiles": fp8,
+            "connect_nearest": nearest, "fp8_tiles": fp8, "nndescent": nndescent,
             "stages_ms": {k2: last[k2] for k2 in ("ms_knn", "ms_components", "ms_connect",
                                                   "ms_refine", "ms_mst", "ms_total")},
             "build": {"t": last["t"], "m": last["m"], "refine_sweeps": last["refine_sweeps"],

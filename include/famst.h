@@ -104,7 +104,7 @@ typedef struct famst_build_info {
                                  1 FP32 grouped sums, 2 BF16 dot products on the tensor
                                  cores (mma.sync); survivors of a filter are decided on
                                  canonical distances, so the result is the same */
-    int32_t reserved0;
+    int32_t knn_iters;        /* NN-Descent iterations of Phase 1 (0: exact tiles) */
     /* CUDA-event milliseconds of single kernels (0 when the kernel did not
      * run): the tcgen05 distance tiles of Phase 1's main pass, the
      * canonical re-rank with its certificate, Algorithm 3's kernel and
@@ -172,6 +172,49 @@ size_t famst_workspace_bytes(const famst_ctx *ctx);
  * INVALID_ARG, NONFINITE, UNSUPPORTED (tensor precisions need d <= 512). */
 famst_status famst_knn_graph(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
                              int32_t k, int32_t prec, int32_t *nbr, float *dist);
+
+/* --------------------------------------- Phase 1 alternative: NN-Descent
+ * GetANNs of Algorithm 1 as the paper runs it: an approximate kNN graph by
+ * NN-Descent (Dong, Charikar and Li, WWW 2011; the paper's Phase 1 library
+ * implements it, Sec. 2 and 3). Each step is a set operation, so the
+ * result is deterministic for a seed:
+ *   start  B[v] = the first k distinct ids among the draws
+ *          u = (r0 (n-1)) >> 32 (u += 1 if u >= v), r0 the first word of
+ *          Philox4x32-10(counter (v, r, 0, 1), key (seed_lo, seed_hi)),
+ *          r = 0 .. 8k-1, then the smallest unused ids; or init_nbr's row
+ *          (device, n x k distinct ids != v; NULL = draw); all entries new;
+ *   each iteration it = 0, 1, ...:
+ *     new[v] / old[v] = the S candidates smallest in (pr, u), pr = r0 of
+ *          Philox(counter (v, u, it, 2)), among the ids of B[v] flagged
+ *          new / old and the ids u whose B[u] holds v flagged new / old;
+ *          the new entries of B[v] that made new[v] become old;
+ *     every pair {a, b} of new[v] x new[v] and new[v] x old[v] (a != b)
+ *          proposes b to B[a] and a to B[b] with the canonical w(a, b);
+ *     B[a] = the k smallest distinct (w, id) of B[a] and its proposals,
+ *          added entries new; c = the number of entries added;
+ *   stop after an iteration with c = 0 or c < delta n k, or max_iters.
+ * nbr / dist (device, n x k) receive the lists, (w, id) ascending;
+ * *iters_out (HOST, may be NULL) = iterations run; updates and pairs (HOST
+ * arrays of max_iters, may be NULL) = c and the pairs the joins evaluated
+ * (C(|new[v]|, 2) + |new[v] x old[v]| over v, less pairs a = b) per
+ * iteration. Requires 1 <= k <= 32,
+ * k <= n-1, 1 <= S <= 32, max_iters >= 0, delta >= 0. Errors: INVALID_ARG
+ * (also a bad init_nbr row), NONFINITE, UNSUPPORTED (2 S rows of d floats
+ * beyond 200 KB of shared memory). Synchronises once per iteration. */
+famst_status famst_knn_nndescent(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                                 int32_t k, int32_t S, int32_t max_iters, double delta,
+                                 uint64_t seed, const int32_t *init_nbr, int32_t *nbr,
+                                 float *dist, int32_t *iters_out, int64_t *updates,
+                                 int64_t *pairs);
+
+/* Phase 1 of famst_build / famst_build_host: FAMST_KNN_EXACT (the exact
+ * tiles at the build's precision, the default) or FAMST_KNN_NNDESCENT
+ * (famst_knn_nndescent with the build's seed and these S (0: min(k, 32)),
+ * max_iters and delta; the build's prec is then unused). */
+#define FAMST_KNN_EXACT      0
+#define FAMST_KNN_NNDESCENT  1
+famst_status famst_set_knn_method(famst_ctx *ctx, int32_t method, int32_t S, int32_t max_iters,
+                                  double delta);
 
 /* ------------------------------------------------ Phase 2a: Algorithm 2
  * Connected components of the undirected graph G built from nbr (n x k):

@@ -56,11 +56,15 @@ struct famst_ctx {
     cudaStream_t bstream = nullptr;  // private stream of batched builds (graph capture)
     BatchCache batch;
     int *dstatus = nullptr;       // device status word
-    int32_t *pinned = nullptr;    // 64 bytes of pinned host memory, slots PIN_*
+    int32_t *pinned = nullptr;    // 128 bytes of pinned host memory, slots PIN_*
     double *dW = nullptr;         // device: W, W64
     int prune = 1;                // Phase 1 tile pruning
     int loop_limit = 0;           // bounded loops: 0 = defaults (famst_set_loop_limit)
     int connect_mode = FAMST_CONNECT_RANDOM;
+    // Phase 1 of builds: exact tiles or NN-Descent (famst_set_knn_method)
+    int knn_method = FAMST_KNN_EXACT, nnd_S = 0, nnd_iters = 10;
+    double nnd_delta = 0.001;
+    int32_t knn_iters = 0;        // NN-Descent iterations of the last build
     KernelTimers timers;          // per-kernel events of a build with info
     bool timers_made = false, timing = false;
     double tile_fraction = 1.0;   // of the last Phase 1
@@ -70,7 +74,7 @@ struct famst_ctx {
 namespace {
 
 // slots of the pinned host words: status word, component count, MST counter
-constexpr int PIN_STATUS = 0, PIN_T = 4, PIN_MST = 8, PIN_KNN = 12, PIN_REF = 14;
+constexpr int PIN_STATUS = 0, PIN_T = 4, PIN_MST = 8, PIN_KNN = 12, PIN_REF = 14, PIN_NND = 16;
 
 // Record the first error of a call (the innermost, most specific one).
 famst_status fail(famst_ctx *c, famst_status s, const char *msg) {
@@ -166,7 +170,6 @@ __global__ void check_finite_kernel(const float *__restrict__ X, int64_t count, 
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_status(dstatus, STATUS_NONFINITE);
 }
 
-constexpr int STATUS_BAD_ID = 16;
 
 // ids in [0, n); for the kNN lists also != own row
 __global__ void check_ids_kernel(const int32_t *__restrict__ ids, int64_t count, int64_t n, int k,
@@ -233,6 +236,7 @@ famst_status sync_status(famst_ctx *ctx) {
     if (s & STATUS_LOOP_LIMIT) return fail(ctx, FAMST_ERR_TIMEOUT, "a bounded device loop reached its limit");
     if (s & STATUS_REFINE_CAP) return fail(ctx, FAMST_ERR_NO_CONVERGENCE, "refinement reached max_iters");
     if (s & STATUS_DISCONNECTED) return fail(ctx, FAMST_ERR_DISCONNECTED, "graph is not connected");
+    if (s & STATUS_INTERNAL) return fail(ctx, FAMST_ERR_CUDA, "internal buffer bound exceeded");
     return FAMST_OK;
 }
 
@@ -441,8 +445,10 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     }
     int64_t got = 0;
     int rounds = 0;
+    // an NN-Descent graph is not the exact kNN: a vertex's lightest edge may
+    // come from another vertex's list
     ST(boruvka(ex, ar, n, nbr, dist, k, eu, evv, ew, m, MstOut{out.tu, out.tv, out.tw}, &got,
-               &rounds, ctx->pinned + PIN_MST, true, true));
+               &rounds, ctx->pinned + PIN_MST, ctx->knn_method != FAMST_KNN_NNDESCENT, true));
     if (got != n - 1) return fail(ctx, FAMST_ERR_DISCONNECTED, "candidate graph is not connected");
     ST(tree_weight(ex, ar, X, d, v4, out.tu, out.tv, out.tw, n - 1, ctx->dW));
     ev.mark(ctx->stream, 5);
@@ -487,12 +493,28 @@ famst_status build_impl(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     ST(check_points(ctx, X, n, d));
     ST(sync_status(ctx));
     Arena ar;
-    ST(ensure_ws(ctx, 0, build_knn_ws(ctx, n, d, k, prec), ar));
+    const bool nnd = ctx->knn_method == FAMST_KNN_NNDESCENT;
+    const int S = ctx->nnd_S > 0 ? ctx->nnd_S : (k < 32 ? k : 32);
+    if (nnd && !nndescent_supported(n, d, k, S))
+        return fail(ctx, FAMST_ERR_UNSUPPORTED, "NN-Descent needs k <= 32, S <= 32, 2 S d floats in shared memory");
+    ST(ensure_ws(ctx, 0, nnd ? align256(size_t(n) * k * 8) + align256(size_t(n) * 4) +
+                                   nndescent_workspace(n, d, k, S) + 4096
+                             : build_knn_ws(ctx, n, d, k, prec), ar));
     int32_t *nbr = ar.take<int32_t>(size_t(n) * k);
     float *dist = ar.take<float>(size_t(n) * k);
     int32_t *comp = ar.take<int32_t>(size_t(n));
     int64_t uncert = 0;
-    ST(knn_stage(ctx, ar, X, n, d, k, prec, nbr, dist, &uncert));
+    ctx->knn_iters = 0;
+    if (nnd) {
+        // the build's seed; the draws' counters (tags 1, 2) differ from Alg. 3's (0)
+        const size_t mark = ar.off;
+        ST(nndescent(exec_of(ctx), ar, X, n, d, k, S, ctx->nnd_iters, ctx->nnd_delta, seed,
+                     nullptr, nbr, dist, ctx->pinned + PIN_NND, &ctx->knn_iters, nullptr,
+                     nullptr));
+        ar.off = mark;
+    } else {
+        ST(knn_stage(ctx, ar, X, n, d, k, prec, nbr, dist, &uncert));
+    }
     ev.mark(ctx->stream, 1);
     famst_status s = build_rest(ctx, X, n, d, k, lambda, seed, max_iters, nbr, dist, comp, out,
                                 W_out, info, ev);
@@ -500,7 +522,8 @@ famst_status build_impl(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     if (info) {
         CK(cudaStreamSynchronize(ctx->stream));
         info->uncertified_rows = uncert;
-        info->knn_tile_fraction = prec == FAMST_PREC_FP32 ? 1.0 : ctx->tile_fraction;
+        info->knn_tile_fraction = prec == FAMST_PREC_FP32 || nnd ? 1.0 : ctx->tile_fraction;
+        info->knn_iters = ctx->knn_iters;
         info->ms_knn = ev.ms(0, 1);
         info->ms_components = ev.ms(1, 2);
         info->ms_connect = ev.ms(2, 3);
@@ -531,7 +554,7 @@ famst_status famst_create(famst_ctx **out, int device) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->dstatus, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->dW, 2 * sizeof(double));
-    if (e == cudaSuccess) e = cudaMallocHost(&ctx->pinned, 64);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->pinned, 128);
     if (e == cudaSuccess) e = cudaMemset(ctx->dstatus, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->bstream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -653,6 +676,48 @@ famst_status famst_knn_graph(famst_ctx *ctx, const float *X, int64_t n, int32_t 
     int64_t uncert = 0;
     ST(knn_stage(ctx, ar, X, n, d, k, prec, nbr, dist, &uncert));
     return sync_status(ctx);
+}
+
+famst_status famst_knn_nndescent(famst_ctx *ctx, const float *X, int64_t n, int32_t d,
+                                 int32_t k, int32_t S, int32_t max_iters, double delta,
+                                 uint64_t seed, const int32_t *init_nbr, int32_t *nbr,
+                                 float *dist, int32_t *iters_out, int64_t *updates,
+                                 int64_t *pairs) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (!nbr || !dist) return fail(ctx, FAMST_ERR_INVALID_ARG, "nbr/dist NULL");
+    if (n < 2) return fail(ctx, FAMST_ERR_INVALID_ARG, "need n >= 2");
+    if (max_iters < 0 || !(delta >= 0.0)) return fail(ctx, FAMST_ERR_INVALID_ARG, "need max_iters >= 0, delta >= 0");
+    if (S < 1 || S > 32) return fail(ctx, FAMST_ERR_INVALID_ARG, "need 1 <= S <= 32");
+    ST(check_knn_args(ctx, n, k));
+    if (!nndescent_supported(n, d, k, S))
+        return fail(ctx, FAMST_ERR_UNSUPPORTED, "NN-Descent needs k <= 32 and 2 S d floats in shared memory");
+    CK(cudaSetDevice(ctx->device));
+    ST(reset_status(ctx));
+    ST(check_points(ctx, X, n, d));
+    ST(sync_status(ctx));
+    Arena ar;
+    ST(ensure_ws(ctx, 0, nndescent_workspace(n, d, k, S), ar));
+    int32_t it = 0;
+    ST(nndescent(exec_of(ctx), ar, X, n, d, k, S, max_iters, delta, seed, init_nbr, nbr, dist,
+                 ctx->pinned + PIN_NND, &it, updates, pairs));
+    if (iters_out) *iters_out = it;
+    return sync_status(ctx);
+}
+
+famst_status famst_set_knn_method(famst_ctx *ctx, int32_t method, int32_t S, int32_t max_iters,
+                                  double delta) {
+    if (!ctx) return FAMST_ERR_INVALID_ARG;
+    ctx->err[0] = 0;
+    if (method != FAMST_KNN_EXACT && method != FAMST_KNN_NNDESCENT)
+        return fail(ctx, FAMST_ERR_INVALID_ARG, "unknown kNN method");
+    if (S < 0 || S > 32 || max_iters < 0 || !(delta >= 0.0))
+        return fail(ctx, FAMST_ERR_INVALID_ARG, "need 0 <= S <= 32, max_iters >= 0, delta >= 0");
+    ctx->knn_method = method;
+    ctx->nnd_S = S;
+    ctx->nnd_iters = max_iters;
+    ctx->nnd_delta = delta;
+    return FAMST_OK;
 }
 
 famst_status famst_components(famst_ctx *ctx, const int32_t *nbr, int64_t n, int32_t k,

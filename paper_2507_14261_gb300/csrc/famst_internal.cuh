@@ -45,6 +45,8 @@ enum : int {
     STATUS_REFINE_CAP = 2,      // an edge still changed in sweep max_iters
     STATUS_LOOP_LIMIT = 4,      // a bounded device loop reached its limit
     STATUS_DISCONNECTED = 8,    // Boruvka found no outgoing edge with >1 component left
+    STATUS_BAD_ID = 16,         // a vertex id out of range or inconsistent
+    STATUS_INTERNAL = 64,       // an internal buffer bound was exceeded (a bug)
 };
 
 #define FAMST_LAUNCH(ex, kern, grid, block, smem, ...)                         \
@@ -543,6 +545,14 @@ famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, i
                             const CUtensorMap *mA, const CUtensorMap *mB);
 bool knn_tc_batched_maps(const void *H, int64_t NP, int D, bool x3, CUtensorMap *mA,
                          CUtensorMap *mB);
+
+// nndescent.cu: Phase 1 by NN-Descent (k <= 32, S <= 32)
+bool nndescent_supported(int64_t n, int d, int k, int S);
+size_t nndescent_workspace(int64_t n, int d, int k, int S);
+famst_status nndescent(const Exec &ex, Arena &ar, const float *X, int64_t n, int d, int k, int S,
+                       int max_iters, double delta, uint64_t seed, const int32_t *init,
+                       int32_t *nbr, float *dist, int32_t *pinned_host, int32_t *iters_out,
+                       int64_t *updates, int64_t *pairs);
 
 // graph.cu
 famst_status exclusive_scan_i32(const Exec &ex, Arena &ar, const int32_t *in,

@@ -41,7 +41,7 @@ class BuildInfo(ctypes.Structure):
         ("ms_mst", ctypes.c_double), ("ms_total", ctypes.c_double),
         ("knn_tile_fraction", ctypes.c_double), ("refine_distance_evals", ctypes.c_int64),
         ("refine_canonical_evals", ctypes.c_int64), ("refine_filter", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32), ("ms_knn_tiles", ctypes.c_double),
+        ("knn_iters", ctypes.c_int32), ("ms_knn_tiles", ctypes.c_double),
         ("ms_rerank", ctypes.c_double), ("ms_connect_kernel", ctypes.c_double),
         ("ms_refine_kernel", ctypes.c_double), ("refine_rows_staged", ctypes.c_int64),
         ("refine_fixed_rows", ctypes.c_int64),
@@ -89,6 +89,9 @@ _SIGS = {
     "famst_launch_count": (ctypes.c_uint64, [_P]),
     "famst_workspace_bytes": (ctypes.c_size_t, [_P]),
     "famst_knn_graph": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _P, _P]),
+    "famst_knn_nndescent": (_I32, [_P, _P, _I64, _I32, _I32, _I32, _I32, ctypes.c_double, _U64,
+                                   _P, _P, _P, _PI32, _P, _P]),
+    "famst_set_knn_method": (_I32, [_P, _I32, _I32, _I32, ctypes.c_double]),
     "famst_components": (_I32, [_P, _P, _I64, _I32, _P, _PI64]),
     "famst_connect": (_I32, [_P, _P, _I64, _I32, _P, _I64, _I32, _U64, _P, _P, _P, _P, _P,
                              _I64, _PI64]),
@@ -214,6 +217,37 @@ class Context:
         st = lib().famst_knn_graph(self._h, _ptr(X), n, d, k, PREC[prec], _ptr(nbr), _ptr(dist))
         self._check(st, "famst_knn_graph")
         return nbr, dist
+
+    def knn_nndescent(self, X: torch.Tensor, k: int, S: int | None = None, max_iters: int = 10,
+                      delta: float = 0.001, seed: int = 0, init=None):
+        """famst_knn_nndescent: approximate kNN graph by NN-Descent. Returns
+        (nbr, dist, iterations, updates per iteration, join pairs per
+        iteration)."""
+        import numpy as np
+        _need(X, torch.float32, "X")
+        n, d = X.shape
+        S = min(k, 32) if S is None else S
+        if init is not None:
+            _need(init, torch.int32, "init")
+        nbr = torch.empty((n, k), dtype=torch.int32, device=X.device)
+        dist = torch.empty((n, k), dtype=torch.float32, device=X.device)
+        it = ctypes.c_int32(0)
+        upd = np.zeros(max(max_iters, 1), np.int64)
+        prs = np.zeros(max(max_iters, 1), np.int64)
+        self._stream()
+        st = lib().famst_knn_nndescent(self._h, _ptr(X), n, d, k, S, max_iters, float(delta),
+                                       seed & (2**64 - 1), _ptr(init) if init is not None else None,
+                                       _ptr(nbr), _ptr(dist), ctypes.byref(it),
+                                       upd.ctypes.data_as(ctypes.c_void_p),
+                                       prs.ctypes.data_as(ctypes.c_void_p))
+        self._check(st, "famst_knn_nndescent")
+        return nbr, dist, int(it.value), upd[:it.value].copy(), prs[:it.value].copy()
+
+    def set_knn_method(self, method: str, S: int = 0, max_iters: int = 10, delta: float = 0.001):
+        """Phase 1 of builds: "exact" (tiles) or "nndescent"."""
+        code = {"exact": 0, "nndescent": 1}[method]
+        self._check(lib().famst_set_knn_method(self._h, code, S, max_iters, float(delta)),
+                    "famst_set_knn_method")
 
     def components(self, nbr: torch.Tensor):
         _need(nbr, torch.int32, "nbr")
