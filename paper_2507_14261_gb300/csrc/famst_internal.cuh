@@ -509,6 +509,7 @@ struct PruneOut {
     TcTile *tab = nullptr;          // per query tile: its range of klist
     float *skipQ = nullptr;         // per query tile
     float *Xs = nullptr;            // the points in sorted order (FP32, n x d)
+    float *tau_row = nullptr;       // per sorted row: upper bound on its k-th neighbour distance
     int32_t *visited = nullptr;     // device: number of visited (query, key) tile pairs
     int64_t nq = 0, nk = 0;
 };

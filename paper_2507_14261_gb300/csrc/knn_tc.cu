@@ -191,6 +191,8 @@ struct TcArgs {
                              // of the columns) or 4 (0 reads as 4)
     const float *rscale;     // FP8 operands: per-row scale s (x' ~ s q), query and key rows
                              // alike (keys padded with 1 to nk_tiles * BN entries)
+    const float *thr0;       // non-null: per query row, a score every one of its k nearest
+                             // keys stays below (the lists start there; s+ is capped by it)
 };
 
 template <int KC>
@@ -383,7 +385,9 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             ls[p] = __int_as_float(0x7f800000);
             lj[p] = -1;
         }
-        float thr = __int_as_float(0x7f800000);
+        const float thr0v = (args.thr0 && i < args.n) ? __ldg(args.thr0 + i)
+                                                      : __int_as_float(0x7f800000);
+        float thr = thr0v;
         int cnt = 0;
         float *my_s = stg_s + half * CAPB * BM + row;
         int *my_j = stg_j + half * CAPB * BM + row;
@@ -407,7 +411,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
             cnt = 0;
             if (NH == 2) thr_sh[half * BM + row] = ls[KC - 1];
-            thr = fminf(ls[KC - 1], pt);
+            thr = fminf(fminf(ls[KC - 1], pt), thr0v);
         };
         bool ok = true;
         int my_comp = 0;
@@ -536,7 +540,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
 #pragma unroll
                 for (int p = 0; p < KC - 1; ++p) out[p] = lj[p] >= 0 ? lj[p] - shift : -1;
             }
-            args.splus[i - shift] = ls[KC - 1];
+            // keys that never entered the list scored at least min(KC-th, thr0)
+            args.splus[i - shift] = fminf(ls[KC - 1], thr0v);
         }
     }
     tc_fence_before();
@@ -707,6 +712,27 @@ __global__ void fill_inf_kernel(float *p, int64_t from, int64_t to) {
     if (i < to) p[i] = __int_as_float(0x7f800000);
 }
 
+// Start threshold of the pruned tiles' lists: every key y within tau_r of
+// row r (tau_r bounds r's k-th neighbour distance from above) has a tile
+// score s~(y) = ||y'||^2 - 2 x'.y' (rounded) with s~ <= ||x' - y'||^2 -
+// ||x'||^2 + E <= (tau_r + c)^2 - xn2 (1 - (d+1) u) + E, where c bounds the
+// centring rounding and E the tile's score error (the certificate's terms).
+// Written over tau_row in place.
+__global__ void thr0_kernel(float *__restrict__ tau_row, const float *__restrict__ xn2s,
+                            int64_t n, int d, const unsigned *__restrict__ ymax_bits,
+                            double eps_dot) {
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const double u24 = 1.0 / 16777216.0;
+    const double xn2 = double(xn2s[r]), xn = sqrt(xn2);
+    const double ym = double(__uint_as_float(*ymax_bits));
+    const double E = 2.0 * eps_dot * xn * ym * 1.01 + (d + 1) * u24 * 1.02 * ym * ym +
+                     2.0 * u24 * (ym * ym + 2.0 * xn * ym) * 1.01 + 1e-30;
+    const double t = (double(tau_row[r]) + 1.02 * u24 * (xn + ym)) * (1.0 + 0x1p-20);
+    const double thr = t * t - xn2 * (1.0 - (d + 1) * u24 * 1.02) + E;
+    tau_row[r] = __double2float_ru(thr + (thr >= 0.0 ? thr : -thr) * 0x1p-20 + 1e-30);
+}
+
 // ------------------------------------------------------------- rerank
 
 struct CertConst {
@@ -720,7 +746,11 @@ struct CertConst {
 // and leave the canonical distance unchanged). d is the true dimension used in
 // the error bounds. Returns whether the row was certified (then the k
 // results are written).
-template <int VEC, int KC>
+// XR > 0 (dc <= 32 XR): the warp computes one candidate's distance at a time,
+// lane l taking coordinates l, l + 32, ... (its canonical partial) from
+// coalesced row reads, the query row held in registers, G candidates in
+// flight; XR = 0: one candidate per lane, its 32 partials in registers.
+template <int VEC, int KC, int XR = 0>
 __device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, int dc, int d,
                                            const float *__restrict__ xi, int k,
                                            const int32_t *__restrict__ cand_row, float sp,
@@ -731,15 +761,69 @@ __device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, 
                                            const int32_t *__restrict__ idmap = nullptr) {
     constexpr int KP = KC - 1;
     uint64_t key[2];
+    if constexpr (XR > 0) {
+        constexpr int G = XR <= 8 ? 4 : (XR <= 16 ? 2 : 1);
+        float xr[XR];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        int c = h * 32 + lane;
-        key[h] = KEY_NONE;
-        if (c < KP) {
-            int j = cand_row[c];
-            if (j >= 0)
-                key[h] = nb_key(canon_dist<VEC>(xi, X + int64_t(j) * ld, dc),
-                                uint32_t(idmap ? idmap[j] : j));
+        for (int q = 0; q < XR; ++q) {
+            const int t = lane + 32 * q;
+            xr[q] = t < dc ? __ldg(xi + t) : 0.0f;
+        }
+        int jc[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = h * 32 + lane;
+            jc[h] = c < KP ? cand_row[c] : -1;
+        }
+        key[0] = key[1] = KEY_NONE;
+        for (int c0 = 0; c0 < KP; c0 += G) {
+            int j[G];
+            float y[G][XR];
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                const int c = c0 + g;
+                const int ja = __shfl_sync(0xffffffffu, jc[0], c & 31);
+                const int jb = __shfl_sync(0xffffffffu, jc[1], c & 31);
+                j[g] = c < KP ? (c < 32 ? ja : jb) : -1;
+#pragma unroll
+                for (int q = 0; q < XR; ++q) {
+                    const int t = lane + 32 * q;
+                    y[g][q] = (j[g] >= 0 && t < dc) ? __ldg(X + int64_t(j[g]) * ld + t) : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                float p = 0.0f;
+#pragma unroll
+                for (int q = 0; q < XR; ++q) {
+                    const float dl = __fsub_rn(xr[q], y[g][q]);
+                    p = __fmaf_rn(dl, dl, p);
+                }
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1)
+                    p = __fadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
+                const int c = c0 + g;
+                if (j[g] >= 0) {
+                    const uint64_t kg = nb_key(__fsqrt_rn(p), uint32_t(idmap ? idmap[j[g]] : j[g]));
+                    if (c < 32) {
+                        if (lane == c) key[0] = kg;
+                    } else if (lane == c - 32) {
+                        key[1] = kg;
+                    }
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int c = h * 32 + lane;
+            key[h] = KEY_NONE;
+            if (c < KP) {
+                int j = cand_row[c];
+                if (j >= 0)
+                    key[h] = nb_key(canon_dist<VEC>(xi, X + int64_t(j) * ld, dc),
+                                    uint32_t(idmap ? idmap[j] : j));
+            }
         }
     }
     // bitonic sort of 64 keys, element index = h*32 + lane
@@ -811,7 +895,7 @@ __device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, 
     return cert;
 }
 
-template <int VEC, int KC>
+template <int VEC, int KC, int XR>
 __global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int k,
                               const int32_t *__restrict__ cand, const float *__restrict__ splus,
                               const float *__restrict__ skip,
@@ -822,7 +906,7 @@ __global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int
     int lane = threadIdx.x & 31;
     if (i >= n) return;
     const float sk = skip ? skip[i] : __int_as_float(0x7f800000);
-    bool cert = rerank_row<VEC, KC>(X, d, d, d, X + i * d, k, cand + i * (KC - 1), splus[i], sk,
+    bool cert = rerank_row<VEC, KC, XR>(X, d, d, d, X + i * d, k, cand + i * (KC - 1), splus[i], sk,
                                     xnorm2[i], __uint_as_float(*ymax_bits), cc.eps_dot, lane,
                                     nbr + i * k, dist + i * k);
     if (!cert && lane == 0) fail_rows[atomicAdd(fail_count, 1)] = int32_t(i);
@@ -832,7 +916,7 @@ __global__ void rerank_kernel(const float *__restrict__ X, int64_t n, int d, int
 // candidate rows are read from the sorted copy Xs (a row's candidates are
 // mostly cell-mates, so they sit close together in memory), keyed and
 // written with their original ids.
-template <int VEC, int KC>
+template <int VEC, int KC, int XR>
 __global__ void __launch_bounds__(256, 5) rerank_sorted_kernel(const float *__restrict__ Xs, int64_t n, int d, int k,
                                      const int32_t *__restrict__ cand,
                                      const float *__restrict__ splus,
@@ -847,7 +931,7 @@ __global__ void __launch_bounds__(256, 5) rerank_sorted_kernel(const float *__re
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
     const int64_t i = perm[r];
-    const bool cert = rerank_row<VEC, KC>(Xs, d, d, d, Xs + r * d, k, cand + r * (KC - 1),
+    const bool cert = rerank_row<VEC, KC, XR>(Xs, d, d, d, Xs + r * d, k, cand + r * (KC - 1),
                                           splus[r], skipQ[r / BM], xnorm2[i],
                                           __uint_as_float(*ymax_bits), cc.eps_dot, lane,
                                           nbr + i * k, dist + i * k, perm);
@@ -1242,9 +1326,33 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
                 cudaSuccess)
             return FAMST_ERR_CUDA;
     }
+    // certificate constants (also the pruned lists' start thresholds)
+    const double u8 = 1.0 / 256.0;
+    const double kprod = double(x3 ? 3 * p.d_pad : p.d_pad);
+    CertConst cc;
+    cc.eps_dot = (x3 ? (3.0 * u8 * u8 + 3.0 * u8 * u8 * u8 + u8 * u8 * u8 * u8)
+                     : (2.0 * u8 + u8 * u8)) +
+                 kprod * std::ldexp(1.0, -22) * (1.0 + 4.0 * u8);
+    if (f8) {
+        // E4M3 with the row's scale: a normal element is within u = 2^-4 of
+        // x'_t (relative); an element below the normal range within 2^-10 s,
+        // and s <= 2 max|x'| / 448, so over the row those add at most
+        // sqrt(d) 2^-10 (2 / 448) ||x'|| per side. Products of E4M3 values
+        // are exact in FP32; the accumulation term is as for BF16.
+        // With |x^_t - x'_t| <= u|x'_t| + c ||x'|| (c = 2^-10 2/448) on both
+        // sides, |x^.y^ - x'.y'| <= ((2u + u^2) + 2 sqrt(d)(1 + u) c + d c^2)
+        // ||x'|| ||y'||.
+        const double u4 = 1.0 / 16.0, c8 = 2.0 / 448.0 / 1024.0, dp = double(p.d_pad);
+        cc.eps_dot = 2.0 * u4 + u4 * u4 + 2.0 * std::sqrt(dp) * (1.0 + u4) * c8 + dp * c8 * c8 +
+                     kprod * std::ldexp(1.0, -22) * (1.0 + 4.0 * u4);
+    }
+    cc.d_plus = double(d) + 4.0;
+    if (use_prune)
+        FAMST_LAUNCH(ex, thr0_kernel, unsigned((n + 255) / 256), 256, 0, P.tau_row, P.nys, n, d,
+                     ymax, cc.eps_dot);
     TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, use_prune ? P.nys : ny, cand_t,
              splus_t, ex.dstatus, use_prune ? P.tab : nullptr, cpad,
-             use_prune ? P.klist : nullptr, 0, p.epi, rscale};
+             use_prune ? P.klist : nullptr, 0, p.epi, rscale, use_prune ? P.tau_row : nullptr};
 #define TC_LAUNCH(KCV, M)                                                                        \
     do {                                                                                         \
         if (set_smem_attr(knn_tc_kernel<KCV, M>, int(p.smem), ex.stream) != cudaSuccess)         \
@@ -1277,48 +1385,35 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
 #undef TC_LAUNCH
 #undef TC_LAUNCH_F8
     if (cudaPeekAtLastError() != cudaSuccess) return FAMST_ERR_CUDA;
-    // rerank + certificate
-    const double u8 = 1.0 / 256.0;
-    const double kprod = double(x3 ? 3 * p.d_pad : p.d_pad);
-    CertConst cc;
-    cc.eps_dot = (x3 ? (3.0 * u8 * u8 + 3.0 * u8 * u8 * u8 + u8 * u8 * u8 * u8)
-                     : (2.0 * u8 + u8 * u8)) +
-                 kprod * std::ldexp(1.0, -22) * (1.0 + 4.0 * u8);
-    if (f8) {
-        // E4M3 with the row's scale: a normal element is within u = 2^-4 of
-        // x'_t (relative); an element below the normal range within 2^-10 s,
-        // and s <= 2 max|x'| / 448, so over the row those add at most
-        // sqrt(d) 2^-10 (2 / 448) ||x'|| per side. Products of E4M3 values
-        // are exact in FP32; the accumulation term is as for BF16.
-        // With |x^_t - x'_t| <= u|x'_t| + c ||x'|| (c = 2^-10 2/448) on both
-        // sides, |x^.y^ - x'.y'| <= ((2u + u^2) + 2 sqrt(d)(1 + u) c + d c^2)
-        // ||x'|| ||y'||.
-        const double u4 = 1.0 / 16.0, c8 = 2.0 / 448.0 / 1024.0, dp = double(p.d_pad);
-        cc.eps_dot = 2.0 * u4 + u4 * u4 + 2.0 * std::sqrt(dp) * (1.0 + u4) * c8 + dp * c8 * c8 +
-                     kprod * std::ldexp(1.0, -22) * (1.0 + 4.0 * u4);
-    }
-    cc.d_plus = double(d) + 4.0;
     const unsigned rgrid = unsigned((n * 32 + 255) / 256);
-#define RERANK(V, KCV)                                                                           \
+#define RERANK3(V, KCV, XRV)                                                                     \
     do {                                                                                         \
         if (use_prune)                                                                           \
-            FAMST_LAUNCH(ex, (rerank_sorted_kernel<V, KCV>), rgrid, 256, 0, P.Xs, n, d, k, cand_t, \
-                         splus_t, P.skipQ, P.perm, xn2, ymax, cc, nbr, dist, fail_rows,          \
+            FAMST_LAUNCH(ex, (rerank_sorted_kernel<V, KCV, XRV>), rgrid, 256, 0, P.Xs, n, d, k,  \
+                         cand_t, splus_t, P.skipQ, P.perm, xn2, ymax, cc, nbr, dist, fail_rows,  \
                          fail_count);                                                            \
         else                                                                                     \
-            FAMST_LAUNCH(ex, (rerank_kernel<V, KCV>), rgrid, 256, 0, X, n, d, k, cand, splus,    \
-                         nullptr, xn2, ymax, cc, nbr, dist, fail_rows, fail_count);              \
+            FAMST_LAUNCH(ex, (rerank_kernel<V, KCV, XRV>), rgrid, 256, 0, X, n, d, k, cand,      \
+                         splus, nullptr, xn2, ymax, cc, nbr, dist, fail_rows, fail_count);       \
+    } while (0)
+#define RERANK(V, KCV)                                                                           \
+    do {                                                                                         \
+        if (d <= 128) RERANK3(V, KCV, 4);                                                        \
+        else if (d <= 256) RERANK3(V, KCV, 8);                                                   \
+        else if (d <= 512) RERANK3(V, KCV, 16);                                                  \
+        else RERANK3(V, KCV, 0);                                                                 \
     } while (0)
     timer_mark(ex, TIMER_RERANK, false);
     if (p.kc == 32) {
-        if (vec4) RERANK(4, 32); else RERANK(1, 32);
+        RERANK(1, 32);
     } else if (p.kc == 48) {
-        if (vec4) RERANK(4, 48); else RERANK(1, 48);
+        RERANK(1, 48);
     } else {
-        if (vec4) RERANK(4, 64); else RERANK(1, 64);
+        RERANK(1, 64);
     }
     timer_mark(ex, TIMER_RERANK, true);
 #undef RERANK
+#undef RERANK3
     if (cudaMemcpyAsync(pinned_host, fail_count, 4, cudaMemcpyDeviceToHost, ex.stream) != cudaSuccess ||
         (use_prune && cudaMemcpyAsync(pinned_host + 1, P.visited, 4, cudaMemcpyDeviceToHost,
                                       ex.stream) != cudaSuccess) ||

@@ -195,7 +195,7 @@ __global__ void tau_kernel(const float *__restrict__ Xs, int d, int64_t n, int k
                            const uint32_t *__restrict__ skey,
                            const int32_t *__restrict__ cstart, const int32_t *__restrict__ gfirst,
                            const int32_t *__restrict__ glast, float rho,
-                           unsigned *__restrict__ tau_bits) {
+                           unsigned *__restrict__ tau_bits, float *__restrict__ tau_row) {
     const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= n) return;
@@ -228,7 +228,10 @@ __global__ void tau_kernel(const float *__restrict__ Xs, int d, int64_t n, int k
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
-    if (lane == 0) atomicMax(tau_bits + r / QT, __float_as_uint(t));
+    if (lane == 0) {
+        atomicMax(tau_bits + r / QT, __float_as_uint(t));
+        tau_row[r] = t;
+    }
 }
 
 // DP[a][b] <= |p_a - p_b| for b >= a (the upper triangle; dp_mirror_kernel
@@ -592,6 +595,7 @@ size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk)
     b += radix_sort_workspace(n) + scan_workspace(K + 1) + 256;
     b += align256(size_t(n) * kh * 2) + align256(size_t(nk) * KT * 4);         // sorted operand
     b += align256(size_t(K) * 4) + align256(size_t(nq) * 4);                   // R, tau
+    b += align256(size_t(n) * 4);                                              // tau per row
     b += align256(size_t(K) * K * 4) * 2;                                      // DP, DPr
     b += align256(size_t(4 * K) * 4) + align256(size_t(K) * 4) * 5;             // order, tree
     b += boruvka_workspace(K);                                                 // pivot tree
@@ -657,6 +661,7 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     float *nys = ar.take<float>(size_t(nk) * KT);
     float *R = ar.take<float>(size_t(K));
     float *tauQ = ar.take<float>(size_t(nq));
+    float *tau_row = ar.take<float>(size_t(n));
     float *DP = ar.take<float>(size_t(K) * K);
     float *DPr = ar.take<float>(size_t(K) * K);
     int32_t *ord = ar.take<int32_t>(size_t(4) * K);   // order, rank, gfirst, glast
@@ -678,7 +683,8 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     int32_t *total = ar.take<int32_t>(1);
     float *Xs = ar.take<float>(size_t(n) * d);
     if (!Xs) return FAMST_ERR_OOM;
-    if (!keys || !perm || !ccount || !cstart || !Hs || !nys || !R || !tauQ || !DP || !DPr || !ord ||
+    if (!keys || !perm || !ccount || !cstart || !Hs || !nys || !R || !tauQ || !tau_row || !DP ||
+        !DPr || !ord ||
         !tu || !tv || !tw || !nb || !nw || !qc || !kc || !qR || !kR || !cnt || !off || !klist ||
         !kkey || !skipQ || !tab ||
         !total)
@@ -772,7 +778,7 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
                      reinterpret_cast<unsigned *>(R));
 #define TAU(GG)                                                                                  \
     FAMST_LAUNCH(ex, tau_kernel<GG>, wgrid, 256, 0, Xs, d, n, k, keys, cstart, gfirst, glast,     \
-                 rho, reinterpret_cast<unsigned *>(tauQ))
+                 rho, reinterpret_cast<unsigned *>(tauQ), tau_row)
     switch (G) {
         case 2: TAU(2); break;
         case 4: TAU(4); break;
@@ -815,6 +821,7 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     out->tab = tab;
     out->skipQ = skipQ;
     out->Xs = Xs;
+    out->tau_row = tau_row;
     out->visited = total;
     out->nq = nq;
     out->nk = nk;
