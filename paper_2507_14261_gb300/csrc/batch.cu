@@ -177,12 +177,12 @@ inline int64_t up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
 
 // ------------------------------------------------------------- autotuner
 //
-// For each class of clouds (K extent of the tensor tiles, number of 32-wide
-// FP32 dim chunks, n rounded up to a power of two, k, precision) it times
+// For each class of clouds (K extent of the tensor tiles, d, n rounded up to
+// a power of two, k, precision) it times
 // the exact kNN of a synthetic cloud of that class on both paths and keeps
 // the faster one. Results are cached per process and, when the environment
 // variable FAMST_AUTOTUNE_CACHE names a file, appended to / read from it.
-using TuneKey = std::tuple<int, int, int, int, int, int>;  // device, d_pad, chunks, log2 n, k, x3
+using TuneKey = std::tuple<int, int, int, int, int, int>;  // device, d_pad, d, log2 n, k, x3
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tune;  // 1 = tensor tiles, 0 = FP32 tiles
 bool g_tune_loaded = false;
@@ -229,12 +229,12 @@ double time_ms(const Exec &ex, const std::function<famst_status()> &fn, famst_st
 }  // namespace
 
 int batch_autotune(const Exec &ex, int d, int64_t n, int k, bool x3) {
-    const int d_pad = int(up(d, 64)), chunks = int((d + 31) / 32);
+    const int d_pad = int(up(d, 64));
     int lg = 9;
     while ((int64_t(1) << lg) < n && lg < 15) ++lg;
     int dev = 0;
     cudaGetDevice(&dev);
-    const TuneKey key(dev, d_pad, chunks, lg, k, int(x3));
+    const TuneKey key(dev, d_pad, d, lg, k, int(x3));
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         tune_load();

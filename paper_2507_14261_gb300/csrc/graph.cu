@@ -190,11 +190,19 @@ __global__ void uf_init_kernel(int32_t *parent, int64_t n) {
     if (v < n) parent[v] = int32_t(v);
 }
 
-__global__ void uf_hook_kernel(const int32_t *__restrict__ nbr, int64_t nk, int k,
-                               int32_t *parent, int limit, int *dstatus) {
-    int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (e >= nk) return;
-    int a = int(e / k), b = nbr[e];
+// Vertices in a scrambled order: thread e takes edge j = e mod k of vertex
+// v = (e / k) * 0x9E3779B1 mod 2^m (odd multiplier: a bijection of
+// [0, 2^m), 2^m >= n; v >= n idle). When ids are contiguous in space (clouds
+// laid out one after another, sorted inputs), threads in flight together
+// would otherwise all hook onto the same few roots.
+__global__ void uf_hook_kernel(const int32_t *__restrict__ nbr, int64_t n, int k,
+                               uint32_t vmask, int32_t *parent, int limit, int *dstatus) {
+    const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t vl = e / k;
+    if (vl > int64_t(vmask)) return;
+    const uint32_t v = (uint32_t(vl) * 0x9E3779B1u) & vmask;
+    if (int64_t(v) >= n) return;
+    int a = int(v), b = nbr[int64_t(v) * k + (e - vl * k)];
     int ra = uf_find(parent, a, limit, dstatus), rb = uf_find(parent, b, limit, dstatus);
     for (int it = 0; it < limit; ++it) {
         if (ra == rb) return;
@@ -335,9 +343,12 @@ famst_status components_uf(const Exec &ex, Arena &ar, const int32_t *nbr, int64_
     const int lim = ex.loop_limit > 0 ? ex.loop_limit : UF_LIMIT;
     int64_t nk = n * k;
     FAMST_LAUNCH(ex, uf_init_kernel, blocks_for(n, th), th, 0, parent, n);
-    if (nk > 0)
-        FAMST_LAUNCH(ex, uf_hook_kernel, blocks_for(nk, th), th, 0, nbr, nk, k, parent, lim,
-                     ex.dstatus);
+    if (nk > 0) {
+        uint32_t vmask = 1;
+        while (int64_t(vmask) + 1 < n) vmask = (vmask << 1) | 1u;
+        FAMST_LAUNCH(ex, uf_hook_kernel, blocks_for((int64_t(vmask) + 1) * k, th), th, 0, nbr, n,
+                     k, vmask, parent, lim, ex.dstatus);
+    }
     FAMST_LAUNCH(ex, uf_flatten_kernel, blocks_for(n, th), th, 0, parent, n, root, flag, lim,
                  ex.dstatus);
     famst_status st = exclusive_scan_i32(ex, ar, flag, rank, n, t_dev);

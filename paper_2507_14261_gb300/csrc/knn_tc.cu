@@ -41,6 +41,7 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "famst_internal.cuh"
@@ -139,6 +140,17 @@ __device__ __forceinline__ void tmem_ld_wait16(uint32_t (&r)[16]) {
 __device__ __forceinline__ void epilogue_bar(int nthreads) {  // the epilogue warps only
     asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
+// The same barrier, returning whether any epilogue thread passed p = true.
+__device__ __forceinline__ bool epilogue_bar_any(int nthreads, bool p) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.s32 pi, %1, 0;\n\t"
+        "bar.red.or.pred po, 1, %2, pi;\n\tselp.s32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"(int(p)), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows
 // of 128 bytes, 8-row groups 1024 bytes apart (SBO), version 1.
@@ -193,6 +205,8 @@ struct TcArgs {
                              // alike (keys padded with 1 to nk_tiles * BN entries)
     const float *thr0;       // non-null: per query row, a score every one of its k nearest
                              // keys stays below (the lists start there; s+ is capped by it)
+    int nitems;              // > 0: work items (query tiles) handed to the CTAs round-robin
+                             // (persistent launch, grid <= nitems); 0: one per CTA
 };
 
 template <int KC>
@@ -221,20 +235,32 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // 1024-byte alignment for the swizzle atoms
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    int q0, kt0, kt1, nkb, row_end, shift;
-    if (args.tiles) {
-        const TcTile T = args.tiles[blockIdx.x];
-        q0 = T.q0; kt0 = T.kt0; kt1 = T.kt1; nkb = T.nkb; row_end = T.row_end; shift = T.shift;
-    } else {
-        q0 = blockIdx.x * BM; kt0 = 0; kt1 = args.nk_tiles; nkb = args.nkb; row_end = args.n;
-        shift = 0;
-    }
-    const int ntiles = kt1 - kt0;
-    // key tile of the t-th step of this CTA
-    auto ktile = [&](int t) { return args.klist ? __ldg(args.klist + kt0 + t) : kt0 + t; };
-    const int nA = (args.x3 ? 2 : 1) * nkb;           // resident A blocks
+    // Work items: query tile `item` with its key tiles. A CTA takes items
+    // blockIdx.x, blockIdx.x + gridDim.x, ...; TMEM, barriers and the
+    // pipeline state carry over from one item to the next.
+    const int nitems = args.nitems > 0 ? args.nitems : int(gridDim.x);
+    struct Item {
+        int q0, kt0, kt1, nkb, row_end, shift;
+    };
+    auto item_of = [&](int item) {
+        Item I;
+        if (args.tiles) {
+            const TcTile T = args.tiles[item];
+            I.q0 = T.q0; I.kt0 = T.kt0; I.kt1 = T.kt1; I.nkb = T.nkb; I.row_end = T.row_end;
+            I.shift = T.shift;
+        } else {
+            I.q0 = item * BM; I.kt0 = 0; I.kt1 = args.nk_tiles; I.nkb = args.nkb;
+            I.row_end = args.n; I.shift = 0;
+        }
+        return I;
+    };
+    // key tile of the t-th step of an item
+    auto ktile = [&](const Item &I, int t) {
+        return args.klist ? __ldg(args.klist + I.kt0 + t) : I.kt0 + t;
+    };
+    const int nA_max = (args.x3 ? 2 : 1) * args.nkb;  // resident A blocks (widest item)
     unsigned char *sA = base;
-    unsigned char *sB = sA + size_t(nA) * A_BLOCK;
+    unsigned char *sB = sA + size_t(nA_max) * A_BLOCK;
     const int EPI = args.epi == 8 ? 8 : 4;
     const int NH = EPI / 4;                           // column halves (1 or 2)
     // staging [NH][CAPB][BM] scores and ids; with two halves, the second
@@ -250,12 +276,11 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     uint64_t *tfull = a_full + 1;                // [2]
     uint64_t *tempty = tfull + 2;                // [2]
     uint64_t *mma_done = tempty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mma_done + 1);
+    uint64_t *a_empty = mma_done + 1;            // the A blocks may be overwritten
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(a_empty + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nkb_tile = args.x3 ? 2 * nkb : nkb;     // B blocks per key tile
-    const int total_blocks = ntiles * nkb_tile;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < args.stages; ++s) {
@@ -268,6 +293,7 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             mbar_init(&tempty[b], EPI);
         }
         mbar_init(mma_done, 1);
+        mbar_init(a_empty, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -288,30 +314,45 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                          : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB))
                          : "memory");
-            mbar_expect_tx(a_full, uint32_t(nA) * A_BLOCK);
-            // resident A blocks: hi blocks 0..nkb-1, then lo blocks (at column
-            // block args.nkb + kb of the operand rows)
-            for (int a = 0; a < nA; ++a) {
-                const int col = a < nkb ? a : args.nkb + (a - nkb);
-                tma_load_2d(sA + size_t(a) * A_BLOCK, &tmA, a_full, col * (F8 ? 2 * BK : BK), q0);
-            }
-            int it = 0;
+            int it = 0, a_issued = 0;   // B blocks and A batches issued
             bool ok = true;
-            for (; it < total_blocks && ok; ++it) {
-                const int s = it % args.stages, r = it / args.stages;
-                if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag, args.status)) {
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const Item I = item_of(item);
+                // the previous item's MMAs must be done with the A blocks
+                if (a_issued > 0 && !mbar_wait(a_empty, (a_issued - 1) & 1, abort_flag,
+                                               args.status)) {
                     ok = false;
                     break;
                 }
-                const int t = ktile(it / nkb_tile), blk = it % nkb_tile;
-                // x3 order per key tile: hi_0, lo_0, hi_1, lo_1, ...
-                const int col = args.x3 ? ((blk & 1) ? args.nkb + (blk >> 1) : (blk >> 1)) : blk;
-                mbar_expect_tx(&full[s], B_BLOCK);
-                tma_load_2d(sB + size_t(s) * B_BLOCK, &tmB, &full[s], col * (F8 ? 2 * BK : BK),
-                            t * BN);
+                const int nA = (args.x3 ? 2 : 1) * I.nkb;
+                mbar_expect_tx(a_full, uint32_t(nA) * A_BLOCK);
+                // resident A blocks: hi blocks 0..nkb-1, then lo blocks (at column
+                // block args.nkb + kb of the operand rows)
+                for (int a = 0; a < nA; ++a) {
+                    const int col = a < I.nkb ? a : args.nkb + (a - I.nkb);
+                    tma_load_2d(sA + size_t(a) * A_BLOCK, &tmA, a_full, col * (F8 ? 2 * BK : BK),
+                                I.q0);
+                }
+                ++a_issued;
+                const int nkb_tile = args.x3 ? 2 * I.nkb : I.nkb;   // B blocks per key tile
+                const int total = (I.kt1 - I.kt0) * nkb_tile;
+                for (int j = 0; j < total; ++j, ++it) {
+                    const int s = it % args.stages, r = it / args.stages;
+                    if (!mbar_wait(&empty[s], (r & 1) ^ 1, abort_flag, args.status)) {
+                        ok = false;
+                        break;
+                    }
+                    const int t = ktile(I, j / nkb_tile), blk = j % nkb_tile;
+                    // x3 order per key tile: hi_0, lo_0, hi_1, lo_1, ...
+                    const int col =
+                        args.x3 ? ((blk & 1) ? args.nkb + (blk >> 1) : (blk >> 1)) : blk;
+                    mbar_expect_tx(&full[s], B_BLOCK);
+                    tma_load_2d(sB + size_t(s) * B_BLOCK, &tmB, &full[s],
+                                col * (F8 ? 2 * BK : BK), t * BN);
+                }
             }
             // drain: every issued copy must land before the CTA leaves
-            mbar_drain(a_full, 0);
+            if (a_issued > 0) mbar_drain(a_full, (a_issued - 1) & 1);
             for (int s = 0; s < args.stages && s < it; ++s) {
                 int last = s + ((it - 1 - s) / args.stages) * args.stages;  // last use of stage s
                 mbar_drain(&full[s], (last / args.stages) & 1);
@@ -322,49 +363,60 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t IDESC = F8 ? idesc_e4m3(BM, BN) : idesc_bf16(BM, BN);
-            bool ok = mbar_wait(a_full, 0, abort_flag, args.status);
-            tc_fence_after();
-            int it = 0;
-            for (int t = 0; t < ntiles && ok; ++t) {
-                const int b = t & 1, use = t >> 1;
-                if (!mbar_wait(&tempty[b], (use & 1) ^ 1, abort_flag, args.status)) {
+            int it = 0, g = 0, na = 0;   // B blocks, key tiles and items consumed
+            bool ok = true;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x, ++na) {
+                const Item I = item_of(item);
+                if (!mbar_wait(a_full, na & 1, abort_flag, args.status)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + uint32_t(b * BN);
-                uint32_t acc = 0;
-                for (int blk = 0; blk < nkb_tile; ++blk, ++it) {
-                    const int s = it % args.stages, r = it / args.stages;
-                    if (!mbar_wait(&full[s], r & 1, abort_flag, args.status)) {
+                const int ntiles = I.kt1 - I.kt0;
+                const int nkb_tile = args.x3 ? 2 * I.nkb : I.nkb;
+                for (int t = 0; t < ntiles && ok; ++t, ++g) {
+                    const int b = g & 1, use = g >> 1;
+                    if (!mbar_wait(&tempty[b], (use & 1) ^ 1, abort_flag, args.status)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t bsm = smem_u32(sB + size_t(s) * B_BLOCK);
-                    const int kb = args.x3 ? (blk >> 1) : blk;
-                    const bool is_lo = args.x3 && (blk & 1);
-                    // which resident A blocks multiply this B block
-                    const int na = args.x3 ? (is_lo ? 1 : 2) : 1;
-                    for (int q = 0; q < na; ++q) {
-                        // hi B block: A_hi then A_lo; lo B block: A_hi
-                        const int ablk = (q == 0) ? kb : nkb + kb;
-                        const uint32_t asm_ = smem_u32(sA + size_t(ablk) * A_BLOCK);
-#pragma unroll
-                        for (int kk = 0; kk < BK / 16; ++kk) {
-                            if constexpr (F8)
-                                umma_f8(d_tmem, sdesc_sw128(asm_ + kk * 32),
-                                        sdesc_sw128(bsm + kk * 32), IDESC, acc);
-                            else
-                                umma_f16(d_tmem, sdesc_sw128(asm_ + kk * 32),
-                                         sdesc_sw128(bsm + kk * 32), IDESC, acc);
-                            acc = 1;
+                    const uint32_t d_tmem = tmem + uint32_t(b * BN);
+                    uint32_t acc = 0;
+                    for (int blk = 0; blk < nkb_tile; ++blk, ++it) {
+                        const int s = it % args.stages, r = it / args.stages;
+                        if (!mbar_wait(&full[s], r & 1, abort_flag, args.status)) {
+                            ok = false;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint32_t bsm = smem_u32(sB + size_t(s) * B_BLOCK);
+                        const int kb = args.x3 ? (blk >> 1) : blk;
+                        const bool is_lo = args.x3 && (blk & 1);
+                        // which resident A blocks multiply this B block
+                        const int nq = args.x3 ? (is_lo ? 1 : 2) : 1;
+                        for (int q = 0; q < nq; ++q) {
+                            // hi B block: A_hi then A_lo; lo B block: A_hi
+                            const int ablk = (q == 0) ? kb : I.nkb + kb;
+                            const uint32_t asm_ = smem_u32(sA + size_t(ablk) * A_BLOCK);
+#pragma unroll
+                            for (int kk = 0; kk < BK / 16; ++kk) {
+                                if constexpr (F8)
+                                    umma_f8(d_tmem, sdesc_sw128(asm_ + kk * 32),
+                                            sdesc_sw128(bsm + kk * 32), IDESC, acc);
+                                else
+                                    umma_f16(d_tmem, sdesc_sw128(asm_ + kk * 32),
+                                             sdesc_sw128(bsm + kk * 32), IDESC, acc);
+                                acc = 1;
+                            }
+                        }
+                        umma_commit(&empty[s]);  // stage s is free once these MMAs finish
                     }
-                    umma_commit(&empty[s]);  // stage s is free once these MMAs finish
+                    if (!ok) break;
+                    umma_commit(&tfull[b]);      // accumulator b is complete
                 }
                 if (!ok) break;
-                umma_commit(&tfull[b]);      // accumulator b is complete
+                umma_commit(a_empty);            // this item's A blocks are free once done
             }
             umma_commit(mma_done);
             mbar_drain(mma_done, 0);
@@ -377,7 +429,13 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         const int ncols = BN / NH;
         const int col0 = half * ncols;
         const int row = quarter * 32 + lane;
-        const int i = q0 + row;
+        float *my_s = stg_s + half * CAPB * BM + row;
+        int *my_j = stg_j + half * CAPB * BM + row;
+        int g = 0;   // key tiles consumed (accumulator buffer g & 1)
+        for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const Item I = item_of(item);
+        const int i = I.q0 + row;
+        const int ntiles = I.kt1 - I.kt0;
         float ls[KC];
         int lj[KC];
 #pragma unroll
@@ -389,8 +447,6 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                                                       : __int_as_float(0x7f800000);
         float thr = thr0v;
         int cnt = 0;
-        float *my_s = stg_s + half * CAPB * BM + row;
-        int *my_j = stg_j + half * CAPB * BM + row;
         // With two halves each list sees half the columns. A score at or above
         // the other list's KC-th is not in the row's KC smallest (that list
         // alone holds KC scores below it), so both filter with the smaller
@@ -419,8 +475,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         // FP8: acc = q_i . q_j, so x'_i . x'_j ~ s_i s_j acc
         float m2s = -2.0f;
         if constexpr (F8) m2s = -2.0f * (i < args.n ? __ldg(args.rscale + i) : 1.0f);
-        for (int t = 0; t < ntiles; ++t) {
-            const int b = t & 1, use = t >> 1;
+        for (int t = 0; t < ntiles; ++t, ++g) {
+            const int b = g & 1, use = g >> 1;
             // every lane waits; the warp proceeds only if all lanes saw the phase
             const bool got = mbar_wait(&tfull[b], use & 1, abort_flag, args.status);
             if (!__all_sync(0xffffffffu, got)) {
@@ -430,14 +486,14 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             tc_fence_after();
             const uint32_t tb =
                 tmem + (uint32_t(quarter * 32) << 16) + uint32_t(b * BN + col0);
-            const int kt_this = ktile(t);
+            const int kt_this = ktile(I, t);
             // key norms (and components) of this tile's columns straight from
             // global memory: every lane reads the same addresses (L1 broadcast);
             // the next tile's are prefetched into L1 meanwhile
             const float *nyt = args.ny + size_t(kt_this) * BN + col0;
             const int *cmt = MASK ? args.colcomp + size_t(kt_this) * BN + col0 : nullptr;
             if (t + 1 < ntiles && lane < ncols / 32) {
-                const size_t nxt = size_t(ktile(t + 1)) * BN + col0 + 32 * lane;
+                const size_t nxt = size_t(ktile(I, t + 1)) * BN + col0 + 32 * lane;
                 asm volatile("prefetch.global.L1 [%0];" ::"l"(args.ny + nxt));
                 if constexpr (MASK) asm volatile("prefetch.global.L1 [%0];" ::"l"(args.colcomp + nxt));
             }
@@ -532,16 +588,21 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                 }
             }
         }
-        if (ok && half == 0 && i < row_end) {
+        if (ok && half == 0 && i < I.row_end) {
             if constexpr (KC == 1) {   // top-1 mode: the best key and its score
-                args.cand[i - shift] = lj[0] >= 0 ? lj[0] - shift : -1;
+                args.cand[i - I.shift] = lj[0] >= 0 ? lj[0] - I.shift : -1;
             } else {
-                int32_t *out = args.cand + size_t(i - shift) * (KC - 1);
+                int32_t *out = args.cand + size_t(i - I.shift) * (KC - 1);
 #pragma unroll
-                for (int p = 0; p < KC - 1; ++p) out[p] = lj[p] >= 0 ? lj[p] - shift : -1;
+                for (int p = 0; p < KC - 1; ++p) out[p] = lj[p] >= 0 ? lj[p] - I.shift : -1;
             }
             // keys that never entered the list scored at least min(KC-th, thr0)
-            args.splus[i - shift] = fminf(ls[KC - 1], thr0v);
+            args.splus[i - I.shift] = fminf(ls[KC - 1], thr0v);
+        }
+        // next item: this row's published threshold starts over, and the
+        // staging area is free again; a failure anywhere stops every warp here
+        if (NH == 2) thr_sh[half * BM + row] = __int_as_float(0x7f800000);
+        if (epilogue_bar_any(32 * EPI, !ok)) break;
         }
     }
     tc_fence_before();
@@ -1244,6 +1305,8 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     if (npad > n)
         FAMST_LAUNCH(ex, fill_inf_kernel, unsigned((npad - n + 255) / 256), 256, 0, ny, n, npad);
     const bool use_prune = prune && !colcomp && prune_supported(n, d, k, vec4);
+    // persistent launches: one CTA per SM takes the query tiles round-robin
+    const unsigned pgrid = unsigned(std::min<int64_t>(p.nq_tiles, ex.num_sms));
     PruneOut P;
     if (use_prune) {
         // pivot cells: top-1 pivot of every point on the tensor tiles (BF16),
@@ -1277,8 +1340,9 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
                 FAMST_LAUNCH(ex, fill_inf_kernel, 1, 256, 0, nya, int64_t(kc), int64_t(nkt) * BN);
             TcArgs a1{int(n), nkt, p.nkb, 0, p1.stages, nya, c_out, s_out,
                       ex.dstatus, nullptr, nullptr, nullptr, 1, p1.epi};
-            FAMST_LAUNCH(ex, (knn_tc_kernel<1, false>), unsigned(p.nq_tiles), 64 + 32 * p1.epi, p1.smem,
-                         mA1, mB1, a1);
+            a1.nitems = int(p.nq_tiles);   // persistent: one CTA per SM walks the query tiles
+            FAMST_LAUNCH(ex, (knn_tc_kernel<1, false>), pgrid, 64 + 32 * p1.epi, p1.smem, mA1, mB1,
+                         a1);
             return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
         };
         int K = K0;
@@ -1353,6 +1417,8 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, use_prune ? P.nys : ny, cand_t,
              splus_t, ex.dstatus, use_prune ? P.tab : nullptr, cpad,
              use_prune ? P.klist : nullptr, 0, p.epi, rscale, use_prune ? P.tau_row : nullptr};
+    // one CTA per query tile: the pruned tiles' key lists differ in length,
+    // and a static round-robin over persistent CTAs measured slower here
 #define TC_LAUNCH(KCV, M)                                                                        \
     do {                                                                                         \
         if (set_smem_attr(knn_tc_kernel<KCV, M>, int(p.smem), ex.stream) != cudaSuccess)         \
@@ -1364,7 +1430,7 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     do {                                                                                            \
         if (set_smem_attr(knn_tc_kernel<KCV, false, true>, int(p.smem), ex.stream) != cudaSuccess)  \
             return FAMST_ERR_CUDA;                                                                  \
-        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false, true>), unsigned(p.nq_tiles), 64 + 32 * p.epi,  \
+        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false, true>), unsigned(p.nq_tiles), 64 + 32 * p.epi, \
                      p.smem, mA, mB, a);                                                            \
     } while (0)
     timer_mark(ex, TIMER_TILES, false);
@@ -1463,12 +1529,15 @@ famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, i
                  roff, voff, B, cl, D, int(x3), mean, H, ny, xn2, ymax);
     if (nctas > 0) {
         TcArgs a{0, 0, nkb, int(x3), stages, ny, cand, splus, ex.dstatus, tiles, nullptr, nullptr, 0, 4};
+        // persistent: one CTA per SM walks the (cloud, query tile) items round-robin
+        a.nitems = int(nctas);
+        const unsigned bgrid = unsigned(std::min<int64_t>(nctas, ex.num_sms));
 #define TCB_LAUNCH(KCV)                                                                          \
     do {                                                                                         \
         if (set_smem_attr(knn_tc_kernel<KCV, false>, \
                                  int(smem), ex.stream) != cudaSuccess)                                      \
             return FAMST_ERR_CUDA;                                                               \
-        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false>), unsigned(nctas), 64 + 32 * 4, smem, *mA, *mB, a); \
+        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false>), bgrid, 64 + 32 * 4, smem, *mA, *mB, a);   \
     } while (0)
         if (kc == 32) TCB_LAUNCH(32);
         else if (kc == 48) TCB_LAUNCH(48);
