@@ -431,6 +431,8 @@ def batch_sub(fam, torch, local: int, prec: str, steps: int = 5) -> dict:
             "clouds": len(clouds), "points": int(off[-1]), "steps": steps,
             "graph_replayed": info.graph_replayed, "graph_kernels": info.graph_kernels,
             "tensor_clouds": info.tensor_clouds, "uncertified_rows": info.uncertified_rows,
+            "tile_shape": {"epilogue_warps": info.tile_epilogue_warps,
+                           "ring_stages": info.tile_stages},
             "timing": "host wall clock around synchronised replays"}
 
 
@@ -545,7 +547,8 @@ def run_batch(args, world, rank, local):
                          "kernel": "whole batched build (distance FLOPs / step time; a lower bound "
                                    "on the distance kernel's own rate)"},
             "cpu_baseline": None, "e2e": None, "clocks": clocks, "gpu_launches": launches,
-            "build": {"tensor_clouds": info.tensor_clouds, "uncertified_rows": info.uncertified_rows,
+            "build": {"tile_epilogue_warps": info.tile_epilogue_warps, "tile_stages": info.tile_stages,
+                  "tensor_clouds": info.tensor_clouds, "uncertified_rows": info.uncertified_rows,
                       "m": info.m, "refine_sweeps": info.refine_sweeps,
                       "graph_kernels": info.graph_kernels, "graph_replayed": info.graph_replayed},
         }

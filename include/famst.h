@@ -335,6 +335,8 @@ typedef struct famst_batch_info {
     int32_t tensor_clouds;    /* clouds whose Phase 1 ran on the tensor tiles */
     int32_t graph_replayed;   /* 1 if this call replayed a captured graph */
     int64_t graph_kernels;    /* kernels in the captured sequence */
+    int32_t tile_epilogue_warps;  /* tile shape the autotuner chose for the tensor pass */
+    int32_t tile_stages;          /* (0 when no cloud used the tensor tiles) */
 } famst_batch_info;
 
 famst_status famst_build_batched(famst_ctx *ctx, const float *X, const int64_t *offsets,

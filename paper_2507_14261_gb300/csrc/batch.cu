@@ -282,6 +282,50 @@ int batch_autotune(const Exec &ex, int d, int64_t n, int k, bool x3) {
     return choice;
 }
 
+// Tile shapes of the batched tensor pass (epilogue warps and ring stages),
+// timed on the batch's own prepared operands; the pick is cached per
+// (device, operand width, k, precision, log2 of the work items).
+using ShapeKey = std::tuple<int, int, int, int, int>;
+std::map<ShapeKey, int> g_shape;   // guarded by g_tune_mu
+
+famst_status batch_tune_tiles(const Exec &ex, BatchPlan &P) {
+    if (!P.any_tc || P.n_shapes < 2) return FAMST_OK;
+    const int64_t items = int64_t(P.tct.size());
+    int lg = 0;
+    while ((int64_t(1) << lg) < items) ++lg;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const ShapeKey key(dev, P.D, P.k, int(P.x3), lg);
+    int pick = -1;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_shape.find(key);
+        if (it != g_shape.end()) pick = it->second;
+    }
+    if (pick < 0) {
+        double best = 0.0;
+        for (int sh = 0; sh < P.n_shapes; ++sh) {
+            famst_status st = FAMST_OK;
+            const double ms = time_ms(ex, [&]() {
+                return knn_tc_batched_tiles(ex, P.D, P.x3, P.shape_stages[sh], P.shape_smem[sh],
+                                            P.tc_kc, P.shape_epi[sh], P.dev.tct, items, P.dev.ny,
+                                            P.dev.cand, P.dev.splus, &P.mA, &P.mB);
+            }, &st);
+            if (st != FAMST_OK) return st;
+            if (pick < 0 || ms < best) {
+                best = ms;
+                pick = sh;
+            }
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_shape[key] = pick;
+    }
+    P.tc_epi = P.shape_epi[pick];
+    P.tc_stages = P.shape_stages[pick];
+    P.tc_smem = P.shape_smem[pick];
+    return FAMST_OK;
+}
+
 // ------------------------------------------------------------------ plan
 
 famst_status batch_plan(const Exec &ex, const int64_t *offsets, const int32_t *dims, int B, int k,
@@ -312,10 +356,26 @@ famst_status batch_plan(const Exec &ex, const int64_t *offsets, const int32_t *d
     P->tct.clear();
     P->f32t.clear();
     bool any_tc = false;
-    int tc_stages = 0, tc_kc = 32;
+    int tc_stages = 0, tc_kc = 32, tc_epi = 4;
     size_t tc_smem = 0;
     const bool tc_ok = prec != FAMST_PREC_FP32 &&
-                       knn_tc_batched_plan(P->D, k, P->x3, &tc_stages, &tc_smem, &tc_kc);
+                       knn_tc_batched_plan(P->D, k, P->x3, 4, &tc_stages, &tc_smem, &tc_kc, &tc_epi);
+    P->n_shapes = 0;
+    if (tc_ok) {
+        P->shape_epi[0] = tc_epi;
+        P->shape_stages[0] = tc_stages;
+        P->shape_smem[0] = tc_smem;
+        P->n_shapes = 1;
+        int s8 = 0, kc8 = 0, e8 = 0;
+        size_t m8 = 0;
+        if (knn_tc_batched_plan(P->D, k, P->x3, 8, &s8, &m8, &kc8, &e8) && e8 == 8 &&
+            kc8 == tc_kc) {
+            P->shape_epi[1] = 8;
+            P->shape_stages[1] = s8;
+            P->shape_smem[1] = m8;
+            P->n_shapes = 2;
+        }
+    }
     for (int b = 0; b < B; ++b) {
         const int nb = int(P->voff[b + 1] - P->voff[b]);
         CloudDev &c = P->cl[b];
@@ -341,6 +401,7 @@ famst_status batch_plan(const Exec &ex, const int64_t *offsets, const int32_t *d
     P->tc_stages = tc_stages;
     P->tc_smem = tc_smem;
     P->tc_kc = tc_kc;
+    P->tc_epi = tc_epi;
     int rounds = 2;
     while ((1 << (rounds - 2)) < nmax) ++rounds;
     P->max_rounds = rounds + 2;
@@ -498,7 +559,8 @@ famst_status batch_enqueue(const Exec &ex, BatchPlan &P, char *base, size_t cap,
     // Phase 1
     if (P.any_tc)
         ST_(knn_tc_batched(ex, V.Xc, int(D), N, P.NP, V.voff, V.roff, B, V.cl, V.tct,
-                           int64_t(P.tct.size()), k, P.x3, P.tc_stages, P.tc_smem, P.tc_kc, V.H,
+                           int64_t(P.tct.size()), k, P.x3, P.tc_stages, P.tc_smem, P.tc_kc,
+                           P.tc_epi, V.H,
                            V.ny, V.xn2, V.mean, V.ymax, V.cand, V.splus, V.fail_rows, V.fail_count,
                            V.nbr, V.dist, &P.mA, &P.mB));
     if (!P.f32t.empty())

@@ -68,8 +68,11 @@ struct BatchPlan {
     std::vector<TcTile> tct;
     std::vector<F32Tile> f32t;
     bool any_tc = false;
-    int tc_stages = 0, tc_kc = 32;
+    int tc_stages = 0, tc_kc = 32, tc_epi = 4;
     size_t tc_smem = 0;
+    // tile shapes the autotuner may pick from: epilogue warps, ring stages
+    int n_shapes = 0, shape_epi[2] = {4, 4}, shape_stages[2] = {0, 0};
+    size_t shape_smem[2] = {0, 0};
     CUtensorMap mA, mB;
     BatchDev dev;
     size_t scratch_off = 0;
@@ -87,5 +90,9 @@ famst_status batch_bind(BatchPlan &P, char *base, size_t cap, cudaStream_t s);
 famst_status batch_enqueue(const Exec &ex, BatchPlan &P, char *base, size_t cap, uint64_t seed,
                            BatchHost *host);
 int batch_status_capacity();
+// Times the batched tile pass once per tile shape on the plan's own data (the
+// eager run must have prepared it) and keeps the fastest in P (cached per
+// operand width, k, precision and work size).
+famst_status batch_tune_tiles(const Exec &ex, BatchPlan &P);
 
 }  // namespace famst

@@ -1067,6 +1067,8 @@ static famst_status batch_results(famst_ctx *ctx, const BatchCache &c, double *W
         info->tensor_clouds = 0;
         for (int b = 0; b < c.B; ++b) info->tensor_clouds += c.plan.cl[b].use_tc;
         info->graph_kernels = int64_t(c.graph_kernels);
+        info->tile_epilogue_warps = c.plan.any_tc ? c.plan.tc_epi : 0;
+        info->tile_stages = c.plan.any_tc ? c.plan.tc_stages : 0;
     }
     return FAMST_OK;
 }
@@ -1171,6 +1173,9 @@ famst_status famst_build_batched(famst_ctx *ctx, const float *X, const int64_t *
     }
     s = batch_results(ctx, c, W, t_out, info);
     if (s != FAMST_OK) return s;
+    // tile shape of the tensor pass, timed on this batch's prepared operands
+    s = batch_tune_tiles(ex, c.plan);
+    if (s != FAMST_OK) return fail(ctx, s, "batch tile tuning");
     // capture the same sequence once; later calls with this key replay it
     unsigned long long counted = 0;
     Exec cap_ex{ctx->bstream, &counted, ctx->num_sms, ctx->dstatus};
@@ -1199,7 +1204,11 @@ famst_status famst_build_batched(famst_ctx *ctx, const float *X, const int64_t *
     c.graph = g;
     c.graph_kernels = counted;
     c.valid = true;
-    if (info) info->graph_kernels = int64_t(counted);
+    if (info) {
+        info->graph_kernels = int64_t(counted);
+        info->tile_epilogue_warps = c.plan.any_tc ? c.plan.tc_epi : 0;
+        info->tile_stages = c.plan.any_tc ? c.plan.tc_stages : 0;
+    }
     return FAMST_OK;
 }
 

@@ -1501,14 +1501,42 @@ namespace famst {
 
 // Shared-memory plan of the batched tensor path for operand width D (the
 // largest cloud's K extent).
-bool knn_tc_batched_plan(int D, int k, bool x3, int *stages, size_t *smem, int *kc) {
+bool knn_tc_batched_plan(int D, int k, bool x3, int epi_req, int *stages, size_t *smem, int *kc,
+                         int *epi) {
     if (k + 1 > 64) return false;
-    TcPlan p = tc_plan(int64_t(1) << 20, D, k, x3, false);   // four epilogue warps
+    TcPlan p = tc_plan(int64_t(1) << 20, D, k, x3, epi_req == 8);
     if (p.stages < 2 || encode_fn() == nullptr) return false;
     *stages = p.stages;
     *smem = p.smem;
     *kc = p.kc;
+    *epi = p.epi;
     return true;
+}
+
+// The batched tile pass alone (one persistent launch over the (cloud, query
+// tile) items): the autotuner times it per shape on the batch's own data.
+famst_status knn_tc_batched_tiles(const Exec &ex, int D, bool x3, int stages, size_t smem, int kc,
+                                  int epi, const TcTile *tiles, int64_t nctas, const float *ny,
+                                  int32_t *cand, float *splus, const CUtensorMap *mA,
+                                  const CUtensorMap *mB) {
+    if (nctas <= 0) return FAMST_OK;
+    const int nkb = D / BK;
+    TcArgs a{0, 0, nkb, int(x3), stages, ny, cand, splus, ex.dstatus, tiles, nullptr, nullptr, 0,
+             epi};
+    // persistent: one CTA per SM walks the (cloud, query tile) items round-robin
+    a.nitems = int(nctas);
+    const unsigned bgrid = unsigned(std::min<int64_t>(nctas, ex.num_sms));
+#define TCB_LAUNCH(KCV)                                                                          \
+    do {                                                                                         \
+        if (set_smem_attr(knn_tc_kernel<KCV, false>, int(smem), ex.stream) != cudaSuccess)      \
+            return FAMST_ERR_CUDA;                                                               \
+        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false>), bgrid, 64 + 32 * epi, smem, *mA, *mB, a);  \
+    } while (0)
+    if (kc == 32) TCB_LAUNCH(32);
+    else if (kc == 48) TCB_LAUNCH(48);
+    else TCB_LAUNCH(64);
+#undef TCB_LAUNCH
+    return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
 // Everything of the batched tensor path that runs on the device; buffers
@@ -1516,10 +1544,10 @@ bool knn_tc_batched_plan(int D, int k, bool x3, int *stages, size_t *smem, int *
 famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, int64_t NP,
                             const long long *voff, const long long *roff, int B,
                             const CloudDev *cl, const TcTile *tiles, int64_t nctas, int k,
-                            bool x3, int stages, size_t smem, int kc, __nv_bfloat16 *H, float *ny,
-                            float *xn2, float *mean, unsigned *ymax, int32_t *cand, float *splus,
-                            int32_t *fail_rows, int32_t *fail_count, int32_t *nbr, float *dist,
-                            const CUtensorMap *mA, const CUtensorMap *mB) {
+                            bool x3, int stages, size_t smem, int kc, int epi, __nv_bfloat16 *H,
+                            float *ny, float *xn2, float *mean, unsigned *ymax, int32_t *cand,
+                            float *splus, int32_t *fail_rows, int32_t *fail_count, int32_t *nbr,
+                            float *dist, const CUtensorMap *mA, const CUtensorMap *mB) {
     FAMST_LAUNCH(ex, cloud_mean_kernel, B, 128, 0, Xc, D, cl, mean);
     if (cudaMemsetAsync(ymax, 0, size_t(B) * 4, ex.stream) != cudaSuccess ||
         cudaMemsetAsync(fail_count, 0, 4, ex.stream) != cudaSuccess)
@@ -1527,23 +1555,9 @@ famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, i
     const int nkb = D / BK;
     FAMST_LAUNCH(ex, tc_prep_batched_kernel, unsigned((NP * 32 + 255) / 256), 256, 0, Xc, D, NP,
                  roff, voff, B, cl, D, int(x3), mean, H, ny, xn2, ymax);
-    if (nctas > 0) {
-        TcArgs a{0, 0, nkb, int(x3), stages, ny, cand, splus, ex.dstatus, tiles, nullptr, nullptr, 0, 4};
-        // persistent: one CTA per SM walks the (cloud, query tile) items round-robin
-        a.nitems = int(nctas);
-        const unsigned bgrid = unsigned(std::min<int64_t>(nctas, ex.num_sms));
-#define TCB_LAUNCH(KCV)                                                                          \
-    do {                                                                                         \
-        if (set_smem_attr(knn_tc_kernel<KCV, false>, \
-                                 int(smem), ex.stream) != cudaSuccess)                                      \
-            return FAMST_ERR_CUDA;                                                               \
-        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false>), bgrid, 64 + 32 * 4, smem, *mA, *mB, a);   \
-    } while (0)
-        if (kc == 32) TCB_LAUNCH(32);
-        else if (kc == 48) TCB_LAUNCH(48);
-        else TCB_LAUNCH(64);
-#undef TCB_LAUNCH
-    }
+    famst_status st = knn_tc_batched_tiles(ex, D, x3, stages, smem, kc, epi, tiles, nctas, ny, cand,
+                                           splus, mA, mB);
+    if (st != FAMST_OK) return st;
     const unsigned rgrid = unsigned((N * 32 + 255) / 256);
     if (kc == 32)
         FAMST_LAUNCH(ex, rerank_batched_kernel<32>, rgrid, 256, 0, Xc, D, N, voff, B, cl, int(x3),

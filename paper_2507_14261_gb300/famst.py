@@ -56,7 +56,8 @@ class BatchInfo(ctypes.Structure):
         ("m", ctypes.c_int64), ("refine_sweeps", ctypes.c_int32),
         ("boruvka_rounds", ctypes.c_int32), ("uncertified_rows", ctypes.c_int64),
         ("tensor_clouds", ctypes.c_int32), ("graph_replayed", ctypes.c_int32),
-        ("graph_kernels", ctypes.c_int64),
+        ("graph_kernels", ctypes.c_int64), ("tile_epilogue_warps", ctypes.c_int32),
+        ("tile_stages", ctypes.c_int32),
     ]
 
     def as_dict(self):
