@@ -707,12 +707,23 @@ def main():
                     "bound (see profiles/), so the fraction is well below 1"}
     if ms_conk > 0:
         m_e = infos[-1]["m"]
-        cb = m_e / w.lam * (w.lam * w.lam) * 2.0 * w.d * 4.0
+        draws = m_e / w.lam * (w.lam * w.lam)
+        if infos[-1]["refine_filter"] == 2:
+            # builds holding the centred BF16 rows filter on those: per draw
+            # two rows of ld BF16 values plus their norm and error bound
+            ld = -(-w.d // 64) * 64
+            cb = draws * 2.0 * (2.0 * ld + 8.0)
+            kname = "connect_half_kernel"
+            note = ("lambda^2 draws x two BF16 rows (+ norm, error bound) per component pair; "
+                    "the canonical survivors' FP32 rows are not counted")
+        else:
+            cb = draws * 2.0 * w.d * 4.0
+            kname = "connect_filtered_kernel"
+            note = "lambda^2 draws x two FP32 rows per component pair"
         kernels["connect"] = {"bound": "l2", "ms": ms_conk,
                               "achieved": cb / (ms_conk / 1e3) / 1e9, "peak": l2["l2_gbs"],
                               "unit": "GB/s", "frac": cb / (ms_conk / 1e3) / 1e9 / l2["l2_gbs"],
-                              "kernel": "connect_filtered_kernel",
-                              "note": "lambda^2 draws x two FP32 rows per component pair"}
+                              "kernel": kname, "note": note}
     # dW/dX of the tree weight (the tree held fixed), after the timed builds:
     # per vertex its own row, its tree neighbours' rows and its gradient row
     # ((n - 1) d 4 B x 4 algorithmic bytes), timed on the library's stream

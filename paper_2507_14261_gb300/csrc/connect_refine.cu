@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "famst_internal.cuh"
+#include "staged_rows.cuh"
 
 namespace famst {
 namespace {
@@ -150,6 +151,156 @@ __global__ void __launch_bounds__(256, 4) connect_filtered_kernel(const float *_
             lo[q] = __fsub_rd(__fmul_rd(pf, 1.0f - rho), 1e-35f);
             const float hi = __fadd_ru(__fmul_ru(pf, 1.0f + rho), 1e-35f);
             hk[q] = s < L2 ? nb_key(hi, uint32_t(s)) : KEY_NONE;
+        }
+        // the lambda-th smallest upper bound
+        float H = 0.0f;
+        for (int r = 0; r < lambda; ++r) {
+            uint64_t mine = KEY_NONE;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) mine = hk[q] < mine ? hk[q] : mine;
+            const uint64_t best = warp_min_u64(mine);
+            H = key_w(best);
+#pragma unroll
+            for (int q = 0; q < PER; ++q)
+                if (hk[q] == best) hk[q] = KEY_NONE;
+        }
+        const float bound = __fmul_ru(H, widen);
+        uint64_t kk[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            kk[q] = KEY_NONE;
+            // survivors: canonical distance by the whole warp, kept by their lane
+            unsigned sv = __ballot_sync(0xffffffffu, lane + 32 * q < L2 && lo[q] <= bound);
+            while (sv) {
+                const int sl = __ffs(sv) - 1;
+                sv &= sv - 1;
+                const int a = __shfl_sync(0xffffffffu, uu[q], sl);
+                const int b = __shfl_sync(0xffffffffu, vv[q], sl);
+                const float w = __fsqrt_rn(
+                    canon_p_warp(X + int64_t(a) * d, X + int64_t(b) * d, d, lane));
+                if (lane == sl) kk[q] = nb_key(w, uint32_t(sl + 32 * q));
+            }
+        }
+        const int64_t ebase = pl * lambda;
+        for (int r = 0; r < lambda; ++r) {
+            uint64_t mine = KEY_NONE;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) mine = kk[q] < mine ? kk[q] : mine;
+            uint64_t best = warp_min_u64(mine);
+            int s = int(key_lo(best));
+            if ((s & 31) == lane) {
+                int qq = s >> 5;
+#pragma unroll
+                for (int q = 0; q < PER; ++q)
+                    if (q == qq) {
+                        kk[q] = KEY_NONE;
+                        eu[ebase + r] = uu[q];
+                        ev[ebase + r] = vv[q];
+                        ew[ebase + r] = key_w(best);
+                        eci[ebase + r] = int32_t(i);
+                        ecj[ebase + r] = int32_t(j);
+                    }
+            }
+        }
+    }
+}
+
+// 32 independent dot products of BF16 rows: lane l holds the pair (a[l],
+// b[l]) (a < 0: none, result 0) and receives h_a . h_b. Groups of G = 8
+// lanes read a row pair, lane g taking its 16-byte chunks g, g + 8, ...
+// (V = ld / 64 of them); each lane sums its 8 V exact products by fmaf,
+// then a transpose-sum inside the group (log2 G additions) gathers each
+// pair's total: at most 8 V + 3 roundings, each within 2^-24 of the
+// absolute sum of the products.
+template <int V>
+__device__ __forceinline__ float warp_pairdot32h(const __nv_bfloat16 *__restrict__ H, int ld,
+                                                 int a, int b, int lane) {
+    constexpr int G = 8, R = 32 / G;
+    const int g = lane % G, h = lane / G;
+    float acc[G];
+#pragma unroll
+    for (int s = 0; s < G; ++s) {
+        const int ia = __shfl_sync(0xffffffffu, a, s * R + h);
+        const int ib = __shfl_sync(0xffffffffu, b, s * R + h);
+        const uint4 *ra = reinterpret_cast<const uint4 *>(H + int64_t(ia >= 0 ? ia : 0) * ld);
+        const uint4 *rb = reinterpret_cast<const uint4 *>(H + int64_t(ia >= 0 ? ib : 0) * ld);
+        float sum = 0.0f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const uint4 x = __ldg(ra + g + G * v), y = __ldg(rb + g + G * v);
+            const uint32_t xs[4] = {x.x, x.y, x.z, x.w}, ys[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                sum = __fmaf_rn(__uint_as_float(xs[c] << 16), __uint_as_float(ys[c] << 16), sum);
+                sum = __fmaf_rn(__uint_as_float(xs[c] & 0xffff0000u),
+                                __uint_as_float(ys[c] & 0xffff0000u), sum);
+            }
+        }
+        acc[s] = sum;
+    }
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? acc[i] : acc[i + o];
+            const float keep = up ? acc[i + o] : acc[i];
+            acc[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
+        }
+    }
+    const float tot = __shfl_sync(0xffffffffu, acc[0], (lane % R) * G + lane / R);
+    return a >= 0 ? tot : 0.0f;
+}
+
+// Algorithm 3 with the filter on the centred BF16 rows of a build (half the
+// bytes of the FP32 rows): the same draws; for every draw the bounds [lo, hi]
+// on its canonical distance from the BF16 dot product, the rows' error
+// bounds and norms (staged::dist_bounds); the canonical distance for the
+// draws whose lo is within the lambda-th smallest hi, and the same selection
+// by (w, sample index) as the other variants, so the edges are identical.
+template <int PER, int V>
+__global__ void __launch_bounds__(256, 4) connect_half_kernel(
+    const float *__restrict__ X, int d, HalfRows hr, const int32_t *__restrict__ members,
+    const int32_t *__restrict__ comp_off, int64_t t, int lambda, uint64_t seed, float aerr,
+    float eps, int32_t *__restrict__ eu, int32_t *__restrict__ ev, float *__restrict__ ew,
+    int32_t *__restrict__ eci, int32_t *__restrict__ ecj) {
+    const int lane = threadIdx.x & 31;
+    const int64_t npairs = t * (t - 1) / 2;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int L2 = lambda * lambda;
+    const uint2 key = make_uint2(uint32_t(seed), uint32_t(seed >> 32));
+    const float widen = 1.0f + 0x1p-20f;
+    for (int64_t pl = warp0; pl < npairs; pl += nwarps) {
+        int64_t i, j;
+        pair_of(pl, t, i, j);
+        const uint64_t p = uint64_t(i) * uint64_t(t) + uint64_t(j);
+        const int32_t oi = comp_off[i], oj = comp_off[j];
+        const uint64_t si = uint64_t(comp_off[i + 1] - oi), sj = uint64_t(comp_off[j + 1] - oj);
+        int32_t uu[PER], vv[PER];
+        float lo[PER];
+        uint64_t hk[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int s = lane + 32 * q;
+            uu[q] = -1;
+            vv[q] = -1;
+            if (s < L2) {
+                uint4 r = philox4x32_10(make_uint4(uint32_t(s), uint32_t(p), uint32_t(p >> 32), 0u),
+                                        key);
+                uu[q] = members[oi + int64_t((uint64_t(r.x) * si) >> 32)];
+                vv[q] = members[oj + int64_t((uint64_t(r.y) * sj) >> 32)];
+            }
+            const float dt = warp_pairdot32h<V>(hr.h, hr.ld, uu[q], vv[q], lane);
+            lo[q] = __int_as_float(0x7f800000);
+            hk[q] = KEY_NONE;
+            if (s < L2) {
+                float l, h;
+                staged::dist_bounds(dt, __ldg(hr.n2 + uu[q]), __ldg(hr.n2 + vv[q]),
+                                    __ldg(hr.eb + uu[q]), __ldg(hr.eb + vv[q]), aerr, eps, l, h);
+                lo[q] = l;
+                hk[q] = nb_key(h, uint32_t(s));
+            }
         }
         // the lambda-th smallest upper bound
         float H = 0.0f;
@@ -584,10 +735,43 @@ __global__ void edge_tile_key_kernel(const int32_t *__restrict__ eci,
 famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
                            const int32_t *members, const int32_t *comp_off, int64_t t,
                            int lambda, uint64_t seed, int32_t *eu, int32_t *ev, float *ew,
-                           int32_t *eci, int32_t *ecj) {
+                           int32_t *eci, int32_t *ecj, const HalfRows *hr) {
     if (t < 2) return FAMST_OK;
     int64_t npairs = t * (t - 1) / 2;
     int per = (lambda * lambda + 31) / 32;
+    // BF16 rows of a build (ld = 64 .. 256): the filter reads those
+    if (hr && hr->h && hr->ld >= 64 && hr->ld <= 256 && per <= 4) {
+        const int th = 256;
+        const int64_t want = (npairs * 32 + th - 1) / th;
+        const int64_t cap = int64_t(ex.num_sms) * 16;
+        const unsigned grid = unsigned(want < cap ? want : cap);
+        // |p~ - ||h_a - h_b||^2| <= aerr (||h_a||^2 + ||h_b||^2): each norm
+        // within ld 2^-23 of its value, the dot within (8 V + 3) 2^-24 of the
+        // products' absolute sum (<= the half sum of the norms), the final
+        // rounding of p~; taken with a factor-two margin. eps: the canonical
+        // sum's own error, as for the refinement.
+        const float aerr = float(hr->ld * std::ldexp(1.0, -22) + std::ldexp(1.0, -18));
+        const float eps = float((d + 16) * std::ldexp(1.0, -24) * 1.1);
+        const int V = hr->ld / 64;
+#define CONNECT_H(P, VV)                                                                        \
+    FAMST_LAUNCH(ex, (connect_half_kernel<P, VV>), grid, th, 0, X, d, *hr, members, comp_off, t, \
+                 lambda, seed, aerr, eps, eu, ev, ew, eci, ecj)
+#define CONNECT_HV(P)                                                                          \
+    do {                                                                                       \
+        if (V == 1) CONNECT_H(P, 1);                                                           \
+        else if (V == 2) CONNECT_H(P, 2);                                                      \
+        else if (V == 3) CONNECT_H(P, 3);                                                      \
+        else CONNECT_H(P, 4);                                                                  \
+    } while (0)
+        timer_mark(ex, TIMER_CONNECT, false);
+        if (per <= 1) CONNECT_HV(1);
+        else if (per <= 2) CONNECT_HV(2);
+        else CONNECT_HV(4);
+        timer_mark(ex, TIMER_CONNECT, true);
+#undef CONNECT_HV
+#undef CONNECT_H
+        return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
+    }
     // filtered variant for the common shapes (lambda <= 11, 32 <= d <= 256)
     const int Gs = (vec4 && d >= 32) ? sq_group(d) : 0;
     const int G = (per <= 4 && (Gs == 4 || Gs == 8 || Gs == 16)) ? Gs : 0;

@@ -406,7 +406,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
             ar.off = mark;
         } else {
             ST(connect_edges(ex, X, d, v4, members, comp_off, t, lambda, seed, eu, evv, ew, eci,
-                             ecj));
+                             ecj, hr.h ? &hr : nullptr));
         }
         ev.mark(ctx->stream, 3);
         if (!(v4 && d >= 32 && d <= 256)) hr = HalfRows();   // the refinement filter needs them

@@ -626,10 +626,12 @@ famst_status connect_nearest(const Exec &ex, Arena &ar, const float *X, int d,
                              const int32_t *comp_off, const int32_t *comp_off_host, int64_t t,
                              int lambda, int32_t *eu, int32_t *ev, float *ew, int32_t *eci,
                              int32_t *ecj, unsigned long long *stats);
+// hr (optional): the build's centred BF16 rows; the filter then reads
+// those instead of the FP32 rows (same edges)
 famst_status connect_edges(const Exec &ex, const float *X, int d, bool vec4,
                            const int32_t *members, const int32_t *comp_off, int64_t t,
                            int lambda, uint64_t seed, int32_t *eu, int32_t *ev, float *ew,
-                           int32_t *eci, int32_t *ecj);
+                           int32_t *eci, int32_t *ecj, const HalfRows *hr = nullptr);
 famst_status connect_edges_batched(const Exec &ex, const float *X, int ld, int dc,
                                    const int32_t *members, const int32_t *comp_off,
                                    const long long *pp, const int32_t *cbase, int B, int lambda,
