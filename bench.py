@@ -251,6 +251,35 @@ def l2_copy_peak(device) -> dict:
     return {"l2_gbs": gbs, "how": "torch copy 16 MB -> 16 MB, 64 per graph replay, best of 10"}
 
 
+def fp32_simt_peak(device) -> dict:
+    """Measured FP32 throughput without tensor cores: a 4096^3 FP32 matrix
+    product with TF32 disabled (cuBLAS SGEMM on the FMA pipes), best of 5
+    after a warm-up. The denominator for the FP32 distance tiles."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        m = 4096
+        a = torch.randn(m, m, device=device)
+        b = torch.randn(m, m, device=device)
+        c = a @ b
+        torch.cuda.synchronize(device)
+        best = None
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize(device)
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return {"fp32_tflops": 2.0 * m ** 3 / (best / 1e3) / 1e12,
+            "how": "torch FP32 matmul 4096^3, TF32 off, best of 5"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -341,6 +370,12 @@ def precision_compare(fam, torch, bf16_peak=None) -> dict:
             out[prec]["issued_frac"] = out[prec]["tiles_frac"] * (3 if prec == "bf16x3" else 1)
             out[prec]["tiles_peak"] = ("measured bf16 x 2 (nominal fp8:bf16 ratio)"
                                        if prec == "fp8" else "measured bf16")
+    # FP32 SIMT tiles: 2 d FLOP per (query, key) pair over the whole stage
+    # (FP32 tiles, candidate re-rank), against a measured SGEMM rate
+    f32pk = fp32_simt_peak(X.device)
+    fl32 = 2.0 * w.n * w.n * w.d / (out["fp32"]["ms"] / 1e3) / 1e12
+    out["fp32"].update({"stage_tflops": fl32, "peak_fp32_tflops": f32pk["fp32_tflops"],
+                        "frac": fl32 / f32pk["fp32_tflops"], "peak_how": f32pk["how"]})
     ref = graphs["fp32"]
     out["identical_graphs"] = bool(all(torch.equal(g[0], ref[0]) and torch.equal(g[1], ref[1])
                                        for g in graphs.values()))

@@ -27,6 +27,10 @@ def lib_path() -> str:
     return os.path.join(out_dir(), "libfamst.so")
 
 
+def checked_lib_path() -> str:
+    return os.path.join(out_dir(), "libfamst_checked.so")
+
+
 def sources() -> list[str]:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
@@ -71,6 +75,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     lib = lib_path()
+    _link(nvcc, lib, objs, force)
+    return lib
+
+
+def _link(nvcc: str, lib: str, objs: list[str], force: bool) -> None:
     if force or _stale(lib, objs):
         tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
@@ -78,6 +87,31 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(tmp, lib)
+
+
+def build_checked(force: bool = False) -> str:
+    """The debug build: the C ABI compiled with FAMST_CHECK_BOUNDS (every
+    index array a build stage hands to the next is validated on the device
+    before use; a violation fails the call instead of faulting), linked with
+    the release kernels into libfamst_checked.so beside libfamst.so."""
+    build()
+    od = out_dir()
+    nvcc = _nvcc()
+    src = os.path.join(CSRC, "famst_api.cu")
+    obj = os.path.join(od, "famst_api_checked.o")
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    headers += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+    if force or _stale(obj, [src] + headers):
+        cmd = [nvcc, "-c", src, "-o", obj, "-DFAMST_CHECK_BOUNDS"] + ARCH + [
+            "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I",
+            CSRC, "--expt-relaxed-constexpr"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
+    objs = [os.path.join(od, os.path.basename(s)[:-3] + ".o") for s in sources()
+            if os.path.basename(s) != "famst_api.cu"] + [obj]
+    lib = checked_lib_path()
+    _link(nvcc, lib, objs, force)
     return lib
 
 

@@ -10,7 +10,10 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "batch.cuh"
+
 #include "famst_internal.cuh"
 
 using namespace famst;
@@ -271,18 +274,66 @@ famst_status check_nbr(famst_ctx *ctx, const int32_t *nbr, int64_t n, int32_t k)
 
 // ---------------------------------------------------------- stage helpers
 
+// Debug build (compiled with FAMST_CHECK_BOUNDS: libfamst_checked.so): every
+// index array that one build stage hands to the next is validated on the
+// device before the next stage gathers with it -- kNN ids in [0, n) and not
+// the row itself, component labels in [0, t), member lists and offsets,
+// inter-component edges in range and in the components they claim (after
+// Alg. 3 and after Alg. 4), tree edges in range. A violation fails the call
+// with FAMST_ERR_CUDA and names the stage; nothing traps. Release builds
+// compile all of this away.
+#ifdef FAMST_CHECK_BOUNDS
+famst_status debug_check(famst_ctx *ctx, const char *after) {
+    CK(cudaMemcpyAsync(ctx->pinned + PIN_STATUS, ctx->dstatus, sizeof(int),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->pinned[PIN_STATUS] & STATUS_BAD_ID) {
+        snprintf(ctx->err, sizeof(ctx->err), "bounds check failed after %s", after);
+        return FAMST_ERR_CUDA;
+    }
+    return FAMST_OK;
+}
+#define FAMST_DEBUG_IDS(ids, count, range, k, after)                                            \
+    do {                                                                                      \
+        FAMST_LAUNCH(ex, check_ids_kernel, grid_cap(ctx, (count), 256), 256, 0, (ids),        \
+                     int64_t(count), int64_t(range), (k), ctx->dstatus);                      \
+        ST(debug_check(ctx, after));                                                          \
+    } while (0)
+#define FAMST_DEBUG_EDGES(after)                                                              \
+    do {                                                                                      \
+        if (m > 0)                                                                            \
+            FAMST_LAUNCH(ex, check_edges_kernel, unsigned((m + 255) / 256), 256, 0, eu, evv,  \
+                         eci, ecj, comp, m, n, ctx->dstatus);                                 \
+        ST(debug_check(ctx, after));                                                          \
+    } while (0)
+#else
+#define FAMST_DEBUG_IDS(ids, count, range, k, after) do { } while (0)
+#define FAMST_DEBUG_EDGES(after) do { } while (0)
+#endif
+
+// Stage boundaries of a build: CUDA events (when statistics were asked
+// for) and NVTX ranges on the host thread, one range per stage, so that a
+// profiler can attribute kernels to the paper's phases (NVTX is header-only
+// and costs nothing when no tool listens).
 struct Events {
     cudaEvent_t e[8] = {};
     int used = 0;
     bool on = false;
+    bool range_open = false;
     void init(bool enable) {
         on = enable;
         if (on)
             for (auto &x : e) cudaEventCreate(&x);
     }
     void mark(cudaStream_t s, int i) {
+        static const char *const stage[5] = {
+            "famst: Phase 1 kNN graph", "famst: Alg. 2 components", "famst: Alg. 3 connect",
+            "famst: Alg. 4 refine", "famst: MST and tree weight"};
         if (on) cudaEventRecord(e[i], s);
         if (i + 1 > used) used = i + 1;
+        if (range_open) nvtxRangePop();
+        range_open = i < 5;
+        if (range_open) nvtxRangePushA(stage[i]);
     }
     double ms(int a, int b) {
         float f = 0.0f;
@@ -290,6 +341,7 @@ struct Events {
         return double(f);
     }
     ~Events() {
+        if (range_open) nvtxRangePop();
         if (on)
             for (auto &x : e) cudaEventDestroy(x);
     }
@@ -365,6 +417,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     CK(cudaMemcpyAsync(ctx->pinned + PIN_T, t_dev, 4, cudaMemcpyDeviceToHost, ctx->stream));
     ST(sync_status(ctx));
     const int64_t t = ctx->pinned[PIN_T];
+    FAMST_DEBUG_IDS(comp, n, t, 0, "Alg. 2 (component labels)");
     ev.mark(ctx->stream, 2);
     const int64_t m = int64_t(lambda) * t * (t - 1) / 2;
     if (m >= (int64_t(1) << 31)) return fail(ctx, FAMST_ERR_UNSUPPORTED, "lambda*t*(t-1)/2 >= 2^31");
@@ -388,6 +441,8 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     int64_t first_delta = 0;
     if (t > 1) {
         ST(member_lists(ex, ar, comp, n, t, members, comp_off));
+        FAMST_DEBUG_IDS(members, n, n, 0, "member lists");
+        FAMST_DEBUG_IDS(comp_off, t + 1, n + 1, 0, "member list offsets");
         // BF16 copies of the points for the Alg. 4 filter (half the bytes per
         // candidate; exactness comes from the canonical survivors) and for the
         // nearest-pair connect
@@ -408,6 +463,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
             ST(connect_edges(ex, X, d, v4, members, comp_off, t, lambda, seed, eu, evv, ew, eci,
                              ecj, hr.h ? &hr : nullptr));
         }
+        FAMST_DEBUG_EDGES("Alg. 3 (inter-component edges)");
         ev.mark(ctx->stream, 3);
         if (!(v4 && d >= 32 && d <= 256)) hr = HalfRows();   // the refinement filter needs them
         int32_t *rev_off = ar.take<int32_t>(size_t(n + 1));
@@ -426,6 +482,7 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
             ST(refine_edges(ex, ar, X, d, v4, nbr, k, rev_off, rev_src, comp, t, eu, evv, ew, eci,
                             ecj, m, max_iters, hist, evals, false, &filter));
         }
+        FAMST_DEBUG_EDGES("Alg. 4 (refined edges)");
         ev.mark(ctx->stream, 4);
         famst_status s = sync_status(ctx);
         if (s != FAMST_OK) return s;
@@ -450,6 +507,8 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     ST(boruvka(ex, ar, n, nbr, dist, k, eu, evv, ew, m, MstOut{out.tu, out.tv, out.tw}, &got,
                &rounds, ctx->pinned + PIN_MST, ctx->knn_method != FAMST_KNN_NNDESCENT, true));
     if (got != n - 1) return fail(ctx, FAMST_ERR_DISCONNECTED, "candidate graph is not connected");
+    FAMST_DEBUG_IDS(out.tu, n - 1, n, 0, "MST (tree edge ends)");
+    FAMST_DEBUG_IDS(out.tv, n - 1, n, 0, "MST (tree edge ends)");
     ST(tree_weight(ex, ar, X, d, v4, out.tu, out.tv, out.tw, n - 1, ctx->dW));
     ev.mark(ctx->stream, 5);
     double W[2];
@@ -514,6 +573,10 @@ famst_status build_impl(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         ar.off = mark;
     } else {
         ST(knn_stage(ctx, ar, X, n, d, k, prec, nbr, dist, &uncert));
+    }
+    {
+        Exec ex = exec_of(ctx);
+        FAMST_DEBUG_IDS(nbr, n * k, n, k, "Phase 1 (kNN ids)");
     }
     ev.mark(ctx->stream, 1);
     famst_status s = build_rest(ctx, X, n, d, k, lambda, seed, max_iters, nbr, dist, comp, out,
