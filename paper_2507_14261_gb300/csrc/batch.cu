@@ -161,6 +161,48 @@ __global__ void bt_check_forest_kernel(const long long *__restrict__ edges, int6
     if (*edges != want) set_status(dstatus, STATUS_DISCONNECTED);
 }
 
+// Spatial order of the tensor clouds' rows (their key tiles are then visited
+// outward from the query tile's own, so the candidate lists meet near keys
+// first): sort key of row v = its cloud in the top cb bits, then the top
+// bits of its projection on a fixed +-1 direction (order-preserving bits of
+// the FP32 value). Rows of FP32-tile clouds keep their order (projection
+// bits 0; the sort is stable).
+__global__ void bt_proj_key_kernel(const float *__restrict__ Xc, int D, int64_t N,
+                                   const long long *__restrict__ voff, int B,
+                                   const CloudDev *__restrict__ cl, int cb,
+                                   uint32_t *__restrict__ keys, int32_t *__restrict__ vals) {
+    const int64_t v = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (v >= N) return;
+    const int b = cloud_of_v(voff, B, v);
+    const bool tc = cl[b].use_tc != 0;
+    float p = 0.0f;
+    if (tc)
+        for (int t = lane; t < D; t += 32) {
+            const float x = Xc[v * D + t];
+            p += ((uint32_t(t) * 0x9E3779B1u) >> 31) ? x : -x;
+        }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+    if (lane == 0) {
+        uint32_t u = __float_as_uint(p);
+        u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+        const uint32_t hi = cb > 0 ? uint32_t(b) << (32 - cb) : 0u;
+        const uint32_t lo = tc ? (cb > 0 ? u >> cb : u) : 0u;
+        keys[v] = hi | lo;
+        vals[v] = int32_t(v);
+    }
+}
+
+__global__ void bt_gather_rows_kernel(const float *__restrict__ Xc, int D, int64_t N,
+                                      const int32_t *__restrict__ perm, float *__restrict__ Xs) {
+    const int64_t i = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= N) return;
+    const float *src = Xc + int64_t(perm[i]) * D;
+    for (int t = lane; t < D; t += 32) Xs[i * D + t] = src[t];
+}
+
 // deterministic pseudo-random fill (SplitMix-style hash), for timing runs
 __global__ void bt_fill_kernel(float *p, int64_t count, uint32_t salt) {
     int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -309,7 +351,7 @@ famst_status batch_tune_tiles(const Exec &ex, BatchPlan &P) {
             const double ms = time_ms(ex, [&]() {
                 return knn_tc_batched_tiles(ex, P.D, P.x3, P.shape_stages[sh], P.shape_smem[sh],
                                             P.tc_kc, P.shape_epi[sh], P.dev.tct, items, P.dev.ny,
-                                            P.dev.cand, P.dev.splus, &P.mA, &P.mB);
+                                            P.dev.cand, P.dev.splus, &P.mA, &P.mB, true);
             }, &st);
             if (st != FAMST_OK) return st;
             if (pick < 0 || ms < best) {
@@ -429,6 +471,8 @@ size_t batch_workspace(const BatchPlan &P) {
         add(size_t(B) * 4);                        // ymax
         add(size_t(N) * (P.tc_kc - 1) * 4);        // candidates
         add(size_t(N) * 4 * 2 + 256);              // splus, fail rows, count
+        add(size_t(N) * D * 4);                    // rows in spatial order
+        add(size_t(N) * 4);                        // their permutation
     }
     if (!P.f32t.empty())
         add(size_t(N) * (P.k + 8) * 8 + size_t(N) * 4 + 512);  // FP32 candidates, fails
@@ -474,8 +518,10 @@ famst_status batch_bind(BatchPlan &P, char *base, size_t cap, cudaStream_t s) {
         V.splus = ar.take<float>(size_t(N));
         V.fail_rows = ar.take<int32_t>(size_t(N));
         V.fail_count = ar.take<int32_t>(1);
+        V.Xs = ar.take<float>(size_t(N) * D);
+        V.perm = ar.take<int32_t>(size_t(N));
         if (!V.H || !V.ny || !V.xn2 || !V.mean || !V.ymax || !V.cand || !V.splus || !V.fail_rows ||
-            !V.fail_count)
+            !V.fail_count || !V.Xs || !V.perm)
             return FAMST_ERR_OOM;
         if (!knn_tc_batched_maps(V.H, NP, int(D), P.x3, &P.mA, &P.mB)) return FAMST_ERR_CUDA;
     }
@@ -557,12 +603,25 @@ famst_status batch_enqueue(const Exec &ex, BatchPlan &P, char *base, size_t cap,
     FAMST_LAUNCH(ex, bt_pack_kernel, blocks_for(N * 32, th), th, 0, X, V.xoff, V.voff, V.dims, B, N,
                  int(D), V.Xc, ex.dstatus);
     // Phase 1
-    if (P.any_tc)
-        ST_(knn_tc_batched(ex, V.Xc, int(D), N, P.NP, V.voff, V.roff, B, V.cl, V.tct,
+    if (P.any_tc) {
+        // the tensor clouds' rows in a spatial order (V.keys is free until Alg. 2)
+        int cb = 0;
+        while ((int64_t(1) << cb) < B) ++cb;
+        FAMST_LAUNCH(ex, bt_proj_key_kernel, blocks_for(N * 32, th), th, 0, V.Xc, int(D), N,
+                     V.voff, B, V.cl, cb, V.keys, V.perm);
+        {
+            size_t mark = ar.off;
+            ST_(radix_sort_pairs(ex, ar, V.keys, V.perm, N, 32));
+            ar.off = mark;
+        }
+        FAMST_LAUNCH(ex, bt_gather_rows_kernel, blocks_for(N * 32, th), th, 0, V.Xc, int(D), N,
+                     V.perm, V.Xs);
+        ST_(knn_tc_batched(ex, V.Xs, int(D), N, P.NP, V.voff, V.roff, B, V.cl, V.tct,
                            int64_t(P.tct.size()), k, P.x3, P.tc_stages, P.tc_smem, P.tc_kc,
                            P.tc_epi, V.H,
                            V.ny, V.xn2, V.mean, V.ymax, V.cand, V.splus, V.fail_rows, V.fail_count,
-                           V.nbr, V.dist, &P.mA, &P.mB));
+                           V.nbr, V.dist, &P.mA, &P.mB, V.Xc, V.perm));
+    }
     if (!P.f32t.empty())
         ST_(knn_fp32_batched(ex, V.Xc, int(D), V.voff, B, V.cl, k, k + 8, V.f32t,
                              int64_t(P.f32t.size()), V.f32c, V.f32w, V.f32fail, V.f32nfail, V.nbr,

@@ -20,6 +20,8 @@ struct BatchDev {
     TcTile *tct = nullptr;
     F32Tile *f32t = nullptr;
     float *Xc = nullptr;
+    float *Xs = nullptr;         // tensor clouds' rows in a spatial order (within each cloud)
+    int32_t *perm = nullptr;     // sorted row -> compact id
     int32_t *nbr = nullptr;
     float *dist = nullptr;
     __nv_bfloat16 *H = nullptr;

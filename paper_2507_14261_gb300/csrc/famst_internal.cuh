@@ -544,14 +544,15 @@ bool knn_tc_batched_plan(int D, int k, bool x3, int epi_req, int *stages, size_t
 famst_status knn_tc_batched_tiles(const Exec &ex, int D, bool x3, int stages, size_t smem, int kc,
                                   int epi, const TcTile *tiles, int64_t nctas, const float *ny,
                                   int32_t *cand, float *splus, const CUtensorMap *mA,
-                                  const CUtensorMap *mB);
+                                  const CUtensorMap *mB, bool spiral = false);
 famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, int64_t NP,
                             const long long *voff, const long long *roff, int B,
                             const CloudDev *cl, const TcTile *tiles, int64_t nctas, int k,
                             bool x3, int stages, size_t smem, int kc, int epi, __nv_bfloat16 *H,
                             float *ny, float *xn2, float *mean, unsigned *ymax, int32_t *cand,
                             float *splus, int32_t *fail_rows, int32_t *fail_count, int32_t *nbr,
-                            float *dist, const CUtensorMap *mA, const CUtensorMap *mB);
+                            float *dist, const CUtensorMap *mA, const CUtensorMap *mB,
+                            const float *Xorig = nullptr, const int32_t *perm = nullptr);
 bool knn_tc_batched_maps(const void *H, int64_t NP, int D, bool x3, CUtensorMap *mA,
                          CUtensorMap *mB);
 

@@ -207,6 +207,9 @@ struct TcArgs {
                              // keys stays below (the lists start there; s+ is capped by it)
     int nitems;              // > 0: work items (query tiles) handed to the CTAs round-robin
                              // (persistent launch, grid <= nitems); 0: one per CTA
+    int spiral;              // 1: an item's key tiles [kt0, kt1) are visited outward from the
+                             // query tile's own (q0 / BN, then +1, -1, +2, ...): on rows in
+                             // a spatial order the lists fill with near keys first
 };
 
 template <int KC>
@@ -256,7 +259,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     };
     // key tile of the t-th step of an item
     auto ktile = [&](const Item &I, int t) {
-        return args.klist ? __ldg(args.klist + I.kt0 + t) : I.kt0 + t;
+        if (args.klist) return __ldg(args.klist + I.kt0 + t);
+        if (!args.spiral) return I.kt0 + t;
+        const int c0 = min(max(I.q0 / BN, I.kt0), I.kt1 - 1);
+        const int L = c0 - I.kt0, R = I.kt1 - 1 - c0, m = min(L, R);
+        if (t <= 2 * m) return (t & 1) ? c0 + ((t + 1) >> 1) : c0 - (t >> 1);
+        return R > L ? c0 + (t - m) : c0 - (t - m);
     };
     const int nA_max = (args.x3 ? 2 : 1) * args.nkb;  // resident A blocks (widest item)
     unsigned char *sA = base;
@@ -1011,6 +1019,9 @@ __device__ __forceinline__ int cloud_of(const long long *__restrict__ off, int B
 // Batched re-rank: one warp per compact row of a cloud that used the tensor
 // tiles. Xc holds the clouds' rows back to back with row stride ld (zero
 // beyond each cloud's d).
+// perm (may be null): the rows are in a spatial order within each cloud and
+// perm[v] is the compact id of row v; candidate ids are mapped through it
+// and the results written at the original row.
 template <int KC>
 __global__ void rerank_batched_kernel(const float *__restrict__ Xc, int ld, int64_t N,
                                       const long long *__restrict__ voff, int B,
@@ -1019,6 +1030,7 @@ __global__ void rerank_batched_kernel(const float *__restrict__ Xc, int ld, int6
                                       const float *__restrict__ splus,
                                       const float *__restrict__ xnorm2,
                                       const unsigned *__restrict__ ymax_bits,
+                                      const int32_t *__restrict__ perm,
                                       int32_t *__restrict__ nbr, float *__restrict__ dist,
                                       int32_t *__restrict__ fail_rows,
                                       int32_t *__restrict__ fail_count) {
@@ -1034,11 +1046,12 @@ __global__ void rerank_batched_kernel(const float *__restrict__ Xc, int ld, int6
                            : (2.0 * u8 + u8 * u8)) +
                        kprod * (1.0 / 4194304.0) * (1.0 + 4.0 * u8);
     const int dc = (c.d + 3) & ~3;
+    const int64_t pv = perm ? int64_t(perm[v]) : v;
     bool cert = rerank_row<4, KC>(Xc, ld, dc, c.d, Xc + v * ld, k, cand + v * (KC - 1), splus[v],
                                   __int_as_float(0x7f800000),
-                                  xnorm2[v], __uint_as_float(ymax_bits[b]), eps, lane, nbr + v * k,
-                                  dist + v * k);
-    if (!cert && lane == 0) fail_rows[atomicAdd(fail_count, 1)] = int32_t(v);
+                                  xnorm2[v], __uint_as_float(ymax_bits[b]), eps, lane, nbr + pv * k,
+                                  dist + pv * k, perm);
+    if (!cert && lane == 0) fail_rows[atomicAdd(fail_count, 1)] = int32_t(pv);
 }
 
 // Exact kNN of single rows by brute force within their cloud: one warp per
@@ -1518,13 +1531,14 @@ bool knn_tc_batched_plan(int D, int k, bool x3, int epi_req, int *stages, size_t
 famst_status knn_tc_batched_tiles(const Exec &ex, int D, bool x3, int stages, size_t smem, int kc,
                                   int epi, const TcTile *tiles, int64_t nctas, const float *ny,
                                   int32_t *cand, float *splus, const CUtensorMap *mA,
-                                  const CUtensorMap *mB) {
+                                  const CUtensorMap *mB, bool spiral) {
     if (nctas <= 0) return FAMST_OK;
     const int nkb = D / BK;
     TcArgs a{0, 0, nkb, int(x3), stages, ny, cand, splus, ex.dstatus, tiles, nullptr, nullptr, 0,
              epi};
     // persistent: one CTA per SM walks the (cloud, query tile) items round-robin
     a.nitems = int(nctas);
+    a.spiral = spiral ? 1 : 0;
     const unsigned bgrid = unsigned(std::min<int64_t>(nctas, ex.num_sms));
 #define TCB_LAUNCH(KCV)                                                                          \
     do {                                                                                         \
@@ -1547,7 +1561,8 @@ famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, i
                             bool x3, int stages, size_t smem, int kc, int epi, __nv_bfloat16 *H,
                             float *ny, float *xn2, float *mean, unsigned *ymax, int32_t *cand,
                             float *splus, int32_t *fail_rows, int32_t *fail_count, int32_t *nbr,
-                            float *dist, const CUtensorMap *mA, const CUtensorMap *mB) {
+                            float *dist, const CUtensorMap *mA, const CUtensorMap *mB,
+                            const float *Xorig, const int32_t *perm) {
     FAMST_LAUNCH(ex, cloud_mean_kernel, B, 128, 0, Xc, D, cl, mean);
     if (cudaMemsetAsync(ymax, 0, size_t(B) * 4, ex.stream) != cudaSuccess ||
         cudaMemsetAsync(fail_count, 0, 4, ex.stream) != cudaSuccess)
@@ -1556,20 +1571,21 @@ famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, i
     FAMST_LAUNCH(ex, tc_prep_batched_kernel, unsigned((NP * 32 + 255) / 256), 256, 0, Xc, D, NP,
                  roff, voff, B, cl, D, int(x3), mean, H, ny, xn2, ymax);
     famst_status st = knn_tc_batched_tiles(ex, D, x3, stages, smem, kc, epi, tiles, nctas, ny, cand,
-                                           splus, mA, mB);
+                                           splus, mA, mB, perm != nullptr);
     if (st != FAMST_OK) return st;
     const unsigned rgrid = unsigned((N * 32 + 255) / 256);
     if (kc == 32)
         FAMST_LAUNCH(ex, rerank_batched_kernel<32>, rgrid, 256, 0, Xc, D, N, voff, B, cl, int(x3),
-                     k, cand, splus, xn2, ymax, nbr, dist, fail_rows, fail_count);
+                     k, cand, splus, xn2, ymax, perm, nbr, dist, fail_rows, fail_count);
     else if (kc == 48)
         FAMST_LAUNCH(ex, rerank_batched_kernel<48>, rgrid, 256, 0, Xc, D, N, voff, B, cl, int(x3),
-                     k, cand, splus, xn2, ymax, nbr, dist, fail_rows, fail_count);
+                     k, cand, splus, xn2, ymax, perm, nbr, dist, fail_rows, fail_count);
     else
         FAMST_LAUNCH(ex, rerank_batched_kernel<64>, rgrid, 256, 0, Xc, D, N, voff, B, cl, int(x3),
-                     k, cand, splus, xn2, ymax, nbr, dist, fail_rows, fail_count);
-    FAMST_LAUNCH(ex, fallback_rows_kernel, unsigned(ex.num_sms) * 16, FB_WARPS * 32, 0, Xc, D, voff,
-                 B, cl, k, fail_rows, fail_count, nbr, dist);
+                     k, cand, splus, xn2, ymax, perm, nbr, dist, fail_rows, fail_count);
+    // rows no certificate covers: exact within their cloud, original order and ids
+    FAMST_LAUNCH(ex, fallback_rows_kernel, unsigned(ex.num_sms) * 16, FB_WARPS * 32, 0,
+                 Xorig ? Xorig : Xc, D, voff, B, cl, k, fail_rows, fail_count, nbr, dist);
     return cudaPeekAtLastError() == cudaSuccess ? FAMST_OK : FAMST_ERR_CUDA;
 }
 
