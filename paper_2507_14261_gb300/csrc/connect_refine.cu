@@ -679,7 +679,15 @@ __global__ void half_mean_kernel(const float *__restrict__ X, int64_t n, int d,
     const int64_t S = n < 256 ? n : 256;
     for (int t = threadIdx.x; t < d; t += blockDim.x) {
         float s = 0.0f;
-        for (int64_t i = 0; i < S; ++i) s += __ldg(X + (i * n / S) * d + t);
+        int64_t i = 0;
+        for (; i + 8 <= S; i += 8) {   // eight independent loads in flight
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = __ldg(X + ((i + q) * n / S) * d + t);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s += v[q];
+        }
+        for (; i < S; ++i) s += __ldg(X + (i * n / S) * d + t);
         m[t] = s / float(S);
     }
 }

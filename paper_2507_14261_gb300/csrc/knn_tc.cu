@@ -629,18 +629,21 @@ __global__ void colsum_partial_kernel(const float *__restrict__ X, int64_t n, in
                                       double *__restrict__ part) {
     int64_t r0 = int64_t(blockIdx.x) * rows_per;
     int64_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
+    // FP32 sums within the block's rows (the FP64 pipe is slow on this GPU,
+    // and the centre only has to be some fixed point near the data: every
+    // bound downstream holds for any centre), FP64 across blocks
     for (int c = threadIdx.x; c < d; c += blockDim.x) {
-        double s = 0.0;
+        float s = 0.0f;
         int64_t r = r0;
         for (; r + 8 <= r1; r += 8) {
             float v[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) v[q] = __ldg(X + (r + q) * d + c);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) s += double(v[q]);
+            for (int q = 0; q < 8; ++q) s += v[q];
         }
-        for (; r < r1; ++r) s += double(__ldg(X + r * d + c));
-        part[int64_t(blockIdx.x) * d + c] = s;
+        for (; r < r1; ++r) s += __ldg(X + r * d + c);
+        part[int64_t(blockIdx.x) * d + c] = double(s);
     }
 }
 
