@@ -57,6 +57,10 @@ struct famst_ctx {
     char *ws[4] = {nullptr, nullptr, nullptr, nullptr};
     size_t ws_cap[4] = {0, 0, 0, 0};
     cudaStream_t bstream = nullptr;  // private stream of batched builds (graph capture)
+    // second stream of a build: the refinement's lists are built on it while
+    // Algorithm 3 runs on the build's stream (fork / join events)
+    cudaStream_t astream = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     BatchCache batch;
     int *dstatus = nullptr;       // device status word
     int32_t *pinned = nullptr;    // 128 bytes of pinned host memory, slots PIN_*
@@ -448,7 +452,19 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
         // nearest-pair connect
         HalfRows hr;
         const bool nearest = ctx->connect_mode == FAMST_CONNECT_NEAREST;
-        if ((v4 && d >= 32 && d <= 256) || nearest) ST(half_rows(ex, ar, X, n, d, &hr));
+        const bool use_half = v4 && d >= 32 && d <= 256;   // the refinement's BF16 filter
+        if (use_half || nearest) ST(half_rows(ex, ar, X, n, d, &hr));
+        int32_t *rev_off = ar.take<int32_t>(size_t(n + 1));
+        int32_t *rev_src = ar.take<int32_t>(size_t(n) * k);
+        if (!rev_off || !rev_src || !hist) return fail(ctx, FAMST_ERR_OOM, "workspace");
+        // work left on the second stream is waited for if this call fails
+        struct AuxGuard {
+            cudaStream_t s = nullptr;
+            ~AuxGuard() {
+                if (s) cudaStreamSynchronize(s);
+            }
+        } aux;
+        bool forked = false;
         if (nearest) {
             if (d > 256) return fail(ctx, FAMST_ERR_UNSUPPORTED, "the nearest-pair connect needs d <= 256");
             std::vector<int32_t> off_h(size_t(t + 1));
@@ -460,17 +476,34 @@ famst_status build_rest(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
                                evv, ew, eci, ecj, nullptr));
             ar.off = mark;
         } else {
+            if (use_half) {
+                // the refinement's lists (reverse kNN lists, deduplicated G
+                // lists) do not depend on Alg. 3: built on the second stream
+                // while Alg. 3 runs (Alg. 3 allocates no workspace)
+                CK(cudaEventRecord(ctx->fork_ev, ctx->stream));
+                CK(cudaStreamWaitEvent(ctx->astream, ctx->fork_ev, 0));
+                aux.s = ctx->astream;
+                Exec ax = ex;
+                ax.stream = ctx->astream;
+                ax.timers = nullptr;
+                ST(reverse_csr(ax, ar, nbr, n, k, rev_off, rev_src));
+                ST(refine_glists(ax, ar, nbr, n, k, rev_off, rev_src, &hr));
+                CK(cudaEventRecord(ctx->join_ev, ctx->astream));
+                forked = true;
+            }
             ST(connect_edges(ex, X, d, v4, members, comp_off, t, lambda, seed, eu, evv, ew, eci,
                              ecj, hr.h ? &hr : nullptr));
         }
         FAMST_DEBUG_EDGES("Alg. 3 (inter-component edges)");
         ev.mark(ctx->stream, 3);
-        if (!(v4 && d >= 32 && d <= 256)) hr = HalfRows();   // the refinement filter needs them
-        int32_t *rev_off = ar.take<int32_t>(size_t(n + 1));
-        int32_t *rev_src = ar.take<int32_t>(size_t(n) * k);
-        if (!rev_off || !rev_src || !hist) return fail(ctx, FAMST_ERR_OOM, "workspace");
-        ST(reverse_csr(ex, ar, nbr, n, k, rev_off, rev_src));
-        ST(refine_glists(ex, ar, nbr, n, k, rev_off, rev_src, &hr));
+        if (!use_half) hr = HalfRows();   // only the refinement filter uses them
+        if (forked) {
+            CK(cudaStreamWaitEvent(ctx->stream, ctx->join_ev, 0));
+            aux.s = nullptr;   // later work on the build's stream is ordered after it
+        } else {
+            ST(reverse_csr(ex, ar, nbr, n, k, rev_off, rev_src));
+            ST(refine_glists(ex, ar, nbr, n, k, rev_off, rev_src, &hr));
+        }
         CK(cudaMemsetAsync(hist, 0, size_t(max_iters + 1) * 4, ctx->stream));
         if (!evals) return fail(ctx, FAMST_ERR_OOM, "workspace");
         CK(cudaMemsetAsync(evals, 0, 32, ctx->stream));
@@ -620,6 +653,9 @@ famst_status famst_create(famst_ctx **out, int device) {
     if (e == cudaSuccess) e = cudaMallocHost(&ctx->pinned, 128);
     if (e == cudaSuccess) e = cudaMemset(ctx->dstatus, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->bstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->astream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();
         famst_destroy(ctx);
@@ -635,6 +671,12 @@ famst_status famst_destroy(famst_ctx *ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     ctx->batch.release();
     if (ctx->bstream) cudaStreamDestroy(ctx->bstream);
+    if (ctx->astream) {
+        cudaStreamSynchronize(ctx->astream);
+        cudaStreamDestroy(ctx->astream);
+    }
+    if (ctx->fork_ev) cudaEventDestroy(ctx->fork_ev);
+    if (ctx->join_ev) cudaEventDestroy(ctx->join_ev);
     for (int i = 0; i < 4; ++i)
         if (ctx->ws[i]) cudaFree(ctx->ws[i]);
     if (ctx->dstatus) cudaFree(ctx->dstatus);
