@@ -1025,7 +1025,7 @@ __device__ __forceinline__ int cloud_of(const long long *__restrict__ off, int B
 // perm (may be null): the rows are in a spatial order within each cloud and
 // perm[v] is the compact id of row v; candidate ids are mapped through it
 // and the results written at the original row.
-template <int KC>
+template <int KC, int XR>
 __global__ void rerank_batched_kernel(const float *__restrict__ Xc, int ld, int64_t N,
                                       const long long *__restrict__ voff, int B,
                                       const CloudDev *__restrict__ cl, int x3, int k,
@@ -1050,7 +1050,7 @@ __global__ void rerank_batched_kernel(const float *__restrict__ Xc, int ld, int6
                        kprod * (1.0 / 4194304.0) * (1.0 + 4.0 * u8);
     const int dc = (c.d + 3) & ~3;
     const int64_t pv = perm ? int64_t(perm[v]) : v;
-    bool cert = rerank_row<4, KC>(Xc, ld, dc, c.d, Xc + v * ld, k, cand + v * (KC - 1), splus[v],
+    bool cert = rerank_row<4, KC, XR>(Xc, ld, dc, c.d, Xc + v * ld, k, cand + v * (KC - 1), splus[v],
                                   __int_as_float(0x7f800000),
                                   xnorm2[v], __uint_as_float(ymax_bits[b]), eps, lane, nbr + pv * k,
                                   dist + pv * k, perm);
@@ -1145,20 +1145,34 @@ __global__ void tc_prep_batched_kernel(const float *__restrict__ Xc, int ld, int
     if (lane == 0) {
         ny[r] = acc;
         xnorm[v] = acc;
-        atomicMax(ymax_bits + b, __float_as_uint(sqrtf(acc)));
+        // the cloud's rows all raise one word: only a row above it does
+        const unsigned nb = __float_as_uint(sqrtf(acc));
+        if (nb > *reinterpret_cast<volatile unsigned *>(ymax_bits + b)) atomicMax(ymax_bits + b, nb);
     }
 }
 
-// column means of every cloud (one block per cloud, double sums)
+// centre of every cloud (one block per cloud): the FP32 mean of up to 1024
+// evenly spaced rows, eight loads in flight; the centre only has to be some
+// fixed point near the cloud (every bound downstream holds for any centre)
 __global__ void cloud_mean_kernel(const float *__restrict__ Xc, int ld,
                                   const CloudDev *__restrict__ cl, float *__restrict__ mean) {
     const int b = blockIdx.x;
     const CloudDev c = cl[b];
+    const long long S = c.n < 1024 ? c.n : 1024;
     for (int t = threadIdx.x; t < ld; t += blockDim.x) {
-        double s = 0.0;
-        if (t < c.d)
-            for (long long v = c.voff; v < c.voff + c.n; ++v) s += double(Xc[v * ld + t]);
-        mean[int64_t(b) * ld + t] = t < c.d ? float(s / double(c.n)) : 0.0f;
+        float s = 0.0f;
+        if (t < c.d) {
+            long long i = 0;
+            for (; i + 8 <= S; i += 8) {
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = __ldg(Xc + (c.voff + (i + q) * c.n / S) * ld + t);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) s += v[q];
+            }
+            for (; i < S; ++i) s += __ldg(Xc + (c.voff + i * c.n / S) * ld + t);
+        }
+        mean[int64_t(b) * ld + t] = t < c.d && S > 0 ? s / float(S) : 0.0f;
     }
 }
 
@@ -1570,22 +1584,29 @@ famst_status knn_tc_batched(const Exec &ex, const float *Xc, int D, int64_t N, i
     if (cudaMemsetAsync(ymax, 0, size_t(B) * 4, ex.stream) != cudaSuccess ||
         cudaMemsetAsync(fail_count, 0, 4, ex.stream) != cudaSuccess)
         return FAMST_ERR_CUDA;
-    const int nkb = D / BK;
     FAMST_LAUNCH(ex, tc_prep_batched_kernel, unsigned((NP * 32 + 255) / 256), 256, 0, Xc, D, NP,
                  roff, voff, B, cl, D, int(x3), mean, H, ny, xn2, ymax);
     famst_status st = knn_tc_batched_tiles(ex, D, x3, stages, smem, kc, epi, tiles, nctas, ny, cand,
                                            splus, mA, mB, perm != nullptr);
     if (st != FAMST_OK) return st;
     const unsigned rgrid = unsigned((N * 32 + 255) / 256);
-    if (kc == 32)
-        FAMST_LAUNCH(ex, rerank_batched_kernel<32>, rgrid, 256, 0, Xc, D, N, voff, B, cl, int(x3),
-                     k, cand, splus, xn2, ymax, perm, nbr, dist, fail_rows, fail_count);
-    else if (kc == 48)
-        FAMST_LAUNCH(ex, rerank_batched_kernel<48>, rgrid, 256, 0, Xc, D, N, voff, B, cl, int(x3),
-                     k, cand, splus, xn2, ymax, perm, nbr, dist, fail_rows, fail_count);
-    else
-        FAMST_LAUNCH(ex, rerank_batched_kernel<64>, rgrid, 256, 0, Xc, D, N, voff, B, cl, int(x3),
-                     k, cand, splus, xn2, ymax, perm, nbr, dist, fail_rows, fail_count);
+    // one candidate at a time per warp over coalesced row reads when the
+    // padded rows fit the register slices (D <= 512), else one per lane
+#define RRB(KCV, XRV)                                                                            \
+    FAMST_LAUNCH(ex, (rerank_batched_kernel<KCV, XRV>), rgrid, 256, 0, Xc, D, N, voff, B, cl,    \
+                 int(x3), k, cand, splus, xn2, ymax, perm, nbr, dist, fail_rows, fail_count)
+#define RRB_KC(KCV)                                                                              \
+    do {                                                                                         \
+        if (D <= 128) RRB(KCV, 4);                                                               \
+        else if (D <= 256) RRB(KCV, 8);                                                          \
+        else if (D <= 512) RRB(KCV, 16);                                                         \
+        else RRB(KCV, 0);                                                                        \
+    } while (0)
+    if (kc == 32) RRB_KC(32);
+    else if (kc == 48) RRB_KC(48);
+    else RRB_KC(64);
+#undef RRB_KC
+#undef RRB
     // rows no certificate covers: exact within their cloud, original order and ids
     FAMST_LAUNCH(ex, fallback_rows_kernel, unsigned(ex.num_sms) * 16, FB_WARPS * 32, 0,
                  Xorig ? Xorig : Xc, D, voff, B, cl, k, fail_rows, fail_count, nbr, dist);
