@@ -382,6 +382,9 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
             const int t1 = __shfl_sync(0xffffffffu, tl1, src);
             const int base = __shfl_sync(0xffffffffu, gl0, src);
             const int deg = __shfl_sync(0xffffffffu, gl1, src) - base;
+            // a vertex with at most eight scans loads its task block (records
+            // and best keys, in shared memory) once for all its rounds
+            const bool single = t1 - t0 <= 8;
             for (int r0 = 0; r0 < deg; r0 += 32) {
                 const int idx = r0 + lane;
                 const bool valid = idx < deg;
@@ -398,14 +401,16 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
                 staged += unsigned(nv);
                 for (int tb = t0; tb < t1; tb += 8) {
                     const int ntb = t1 - tb < 8 ? t1 - tb : 8;
-                    fixed_rows += unsigned(ntb);
-                    if (lane < ntb) {
-                        const int4 r = rec[tb + lane];
-                        s_task[lane] = make_float4(__int_as_float(r.y), __int_as_float(r.z),
-                                                   __int_as_float(r.w), 0.0f);
-                        s_best[lane] = best[tb + lane];
+                    if (!single || r0 == 0) {
+                        if (lane < ntb) {
+                            const int4 r = rec[tb + lane];
+                            s_task[lane] = make_float4(__int_as_float(r.y), __int_as_float(r.z),
+                                                       __int_as_float(r.w), 0.0f);
+                            s_best[lane] = best[tb + lane];
+                        }
+                        __syncwarp();
                     }
-                    __syncwarp();
+                    fixed_rows += unsigned(ntb);
                     // B column j = the fixed row of task slot j (lane 4 j + t
                     // carries k pairs (2t, 2t+1) and (8+2t, 9+2t) of each k step)
                     uint32_t b0[NKS], b1[NKS];
@@ -499,7 +504,7 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
                         if (nq == 0) break;
                         canon_batch<XR>(X, d, nq, qf, qc, qt, s_best, lane);
                     }
-                    if (lane < ntb) best[tb + lane] = s_best[lane];
+                    if ((!single || r0 + 32 >= deg) && lane < ntb) best[tb + lane] = s_best[lane];
                     __syncwarp();
                 }
                 __syncwarp();   // the rows stay until every task block is done
