@@ -607,10 +607,12 @@ famst_status build_impl(famst_ctx *ctx, const float *X, int64_t n, int32_t d, in
     } else {
         ST(knn_stage(ctx, ar, X, n, d, k, prec, nbr, dist, &uncert));
     }
+#ifdef FAMST_CHECK_BOUNDS
     {
         Exec ex = exec_of(ctx);
         FAMST_DEBUG_IDS(nbr, n * k, n, k, "Phase 1 (kNN ids)");
     }
+#endif
     ev.mark(ctx->stream, 1);
     famst_status s = build_rest(ctx, X, n, d, k, lambda, seed, max_iters, nbr, dist, comp, out,
                                 W_out, info, ev);
