@@ -264,7 +264,8 @@ nnd_join_kernel(const float *__restrict__ X, int d, int n, int k, int S, int v0,
                 const int32_t *__restrict__ samp, const int32_t *__restrict__ scnt,
                 const uint64_t *__restrict__ Bk, int32_t *__restrict__ pt,
                 uint64_t *__restrict__ pk, unsigned long long *__restrict__ pcount,
-                unsigned long long pcap, unsigned long long *__restrict__ npairs, int *dstatus) {
+                unsigned long long pcap, unsigned long long *__restrict__ npairs, int vec4,
+                int *dstatus) {
     extern __shared__ float4 srow[];
     __shared__ int sid[64];
     __shared__ unsigned long long sthr[64];
@@ -280,11 +281,20 @@ nnd_join_kernel(const float *__restrict__ X, int d, int n, int k, int S, int v0,
         sthr[i] = Bk[int64_t(id) * k + k - 1];
     }
     __syncthreads();
-    float *sf = reinterpret_cast<float *>(srow);
-    const int dp = rs4 * 4;
-    for (int e = threadIdx.x; e < m * dp; e += blockDim.x) {
-        const int r = e / dp, t = e - r * dp;
-        sf[e] = t < d ? __ldg(X + int64_t(sid[r]) * d + t) : 0.0f;   // zeros add nothing
+    if (vec4) {   // rows 16-byte aligned, d % 4 == 0: one float4 per load
+        const int d4v = d >> 2;
+        for (int e = threadIdx.x; e < m * rs4; e += blockDim.x) {
+            const int r = e / rs4, c4 = e - r * rs4;
+            srow[e] = c4 < d4v ? __ldg(reinterpret_cast<const float4 *>(X + int64_t(sid[r]) * d) + c4)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);   // zeros add nothing
+        }
+    } else {
+        float *sf = reinterpret_cast<float *>(srow);
+        const int dp = rs4 * 4;
+        for (int e = threadIdx.x; e < m * dp; e += blockDim.x) {
+            const int r = e / dp, t = e - r * dp;
+            sf[e] = t < d ? __ldg(X + int64_t(sid[r]) * d + t) : 0.0f;   // zeros add nothing
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -354,13 +364,18 @@ nnd_join_kernel(const float *__restrict__ X, int d, int n, int k, int S, int v0,
     if (threadIdx.x == 0 && spairs) atomicAdd(npairs, (unsigned long long)spairs);
 }
 
+// proposals per target; the targets that receive any are listed once each
+// (in no particular order: each target's merge is independent)
 __global__ void nnd_group_count_kernel(const int32_t *__restrict__ pt,
                                        const unsigned long long *__restrict__ pcount,
-                                       unsigned long long pcap, int32_t *__restrict__ gcnt) {
+                                       unsigned long long pcap, int32_t *__restrict__ gcnt,
+                                       int32_t *__restrict__ act, int32_t *__restrict__ nact) {
     const unsigned long long np = *pcount < pcap ? *pcount : pcap;
     for (unsigned long long q = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; q < np;
-         q += uint64_t(gridDim.x) * blockDim.x)
-        atomicAdd(gcnt + pt[q], 1);
+         q += uint64_t(gridDim.x) * blockDim.x) {
+        const int t = pt[q];
+        if (atomicAdd(gcnt + t, 1) == 0) act[atomicAdd(nact, 1)] = t;
+    }
 }
 
 __global__ void nnd_group_scatter_kernel(const int32_t *__restrict__ pt,
@@ -378,16 +393,19 @@ __global__ void nnd_group_scatter_kernel(const int32_t *__restrict__ pt,
     }
 }
 
-// B[a] <- the k smallest distinct keys of B[a] and a's grouped proposals.
-// One warp per a.
-__global__ void nnd_merge_kernel(int n, int k, const int32_t *__restrict__ goff,
+// B[a] <- the k smallest distinct keys of B[a] and a's grouped proposals,
+// for the listed targets a (one warp per target, the warps striding over the
+// list).
+__global__ void nnd_merge_kernel(int k, const int32_t *__restrict__ act,
+                                 const int32_t *__restrict__ nact, const int32_t *__restrict__ goff,
                                  const uint64_t *__restrict__ gk, uint64_t *__restrict__ Bk,
                                  uint8_t *__restrict__ Bf) {
     const int lane = threadIdx.x & 31;
-    const int a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (a >= n) return;
+    const int na = *nact;
+    const int nwarps = int(gridDim.x * (blockDim.x >> 5));
+    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < na; w += nwarps) {
+    const int a = act[w];
     const int g0 = goff[a], g1 = goff[a + 1];
-    if (g0 == g1) return;
     uint64_t L = lane < k ? Bk[int64_t(a) * k + lane] : KEY_NONE;
     uint32_t Lf = lane < k ? Bf[int64_t(a) * k + lane] : 0u;
     bool changed = false;
@@ -410,6 +428,7 @@ __global__ void nnd_merge_kernel(int n, int k, const int32_t *__restrict__ goff,
     if (changed && lane < k) {
         Bk[int64_t(a) * k + lane] = L;
         Bf[int64_t(a) * k + lane] = uint8_t(Lf);
+    }
     }
 }
 
@@ -450,7 +469,7 @@ NndPlan nnd_plan(int64_t n, int d, int S) {
     p.rs4 = ((d + 3) / 4) | 1;
     p.smem = size_t(2 * S) * p.rs4 * 16;
     const int64_t per_v = int64_t(S) * (3 * S - 1);   // 2 proposals per pair
-    p.pcap = std::min<int64_t>(std::max<int64_t>(per_v, int64_t(1) << 27), n * per_v);
+    p.pcap = std::min<int64_t>(std::max<int64_t>(per_v, int64_t(1) << 28), n * per_v);
     p.chunk = std::max<int64_t>(1, p.pcap / per_v);
     return p;
 }
@@ -470,6 +489,7 @@ size_t nndescent_workspace(int64_t n, int d, int k, int S) {
     b += align256(size_t(2) * n * S * 4) + align256(size_t(2) * n * 4);   // samples
     b += align256(size_t(2 * n + 1) * 4) * 2 + align256(size_t(n) * k * 4);   // reverse
     b += align256(size_t(n + 1) * 4) * 2;                            // group counts, offsets
+    b += align256(size_t(n) * 4) + 256;                              // active targets
     b += align256(size_t(p.pcap) * 4) + align256(size_t(p.pcap) * 8) * 2;
     b += 256 * 4;
     b += scan_workspace(2 * n + 1);
@@ -492,16 +512,19 @@ famst_status nndescent(const Exec &ex, Arena &ar, const float *X, int64_t n, int
     int32_t *rsrc = ar.take<int32_t>(size_t(nk));
     int32_t *gcnt = ar.take<int32_t>(size_t(n + 1));
     int32_t *goff = ar.take<int32_t>(size_t(n + 1));
+    int32_t *act = ar.take<int32_t>(size_t(n));     // targets with proposals in a chunk
+    int32_t *nact = ar.take<int32_t>(1);
     int32_t *pt = ar.take<int32_t>(size_t(P.pcap));
     uint64_t *pk = ar.take<uint64_t>(size_t(P.pcap));
     uint64_t *gk = ar.take<uint64_t>(size_t(P.pcap));
     unsigned long long *pcount = ar.take<unsigned long long>(1);
     unsigned long long *cdev = ar.take<unsigned long long>(2);   // c, pairs
     if (!Bk || !Bf || !samp || !scnt || !rcnt || !roff || !rsrc || !gcnt || !goff || !pt ||
-        !pk || !gk || !pcount || !cdev)
+        !pk || !gk || !pcount || !cdev || !act || !nact)
         return FAMST_ERR_OOM;
     const uint2 key = make_uint2(uint32_t(seed), uint32_t(seed >> 32));
     const int ni = int(n);
+    const bool vec4 = (d % 4 == 0) && (reinterpret_cast<uintptr_t>(X) % 16 == 0);
     const unsigned wgrid = unsigned((n + 7) / 8);   // 8 warps per block
     const unsigned egrid = unsigned((nk + 255) / 256);
     const unsigned sgrid = unsigned(ex.num_sms) * 8;
@@ -535,18 +558,20 @@ famst_status nndescent(const Exec &ex, Arena &ar, const float *X, int64_t n, int
         // steps 3 and 4, chunk by chunk
         for (int64_t v0 = 0; v0 < n; v0 += P.chunk) {
             const int64_t nv = std::min<int64_t>(P.chunk, n - v0);
-            if (cudaMemsetAsync(pcount, 0, 8, ex.stream) != cudaSuccess) return FAMST_ERR_CUDA;
+            if (cudaMemsetAsync(pcount, 0, 8, ex.stream) != cudaSuccess ||
+                cudaMemsetAsync(nact, 0, 4, ex.stream) != cudaSuccess)
+                return FAMST_ERR_CUDA;
             FAMST_LAUNCH(ex, nnd_join_kernel, unsigned(nv), NND_JOIN_THREADS, P.smem, X, d, ni, k,
                          S, int(v0), P.rs4, samp, scnt, Bk, pt, pk, pcount,
-                         (unsigned long long)P.pcap, cdev + 1, ex.dstatus);
+                         (unsigned long long)P.pcap, cdev + 1, int(vec4), ex.dstatus);
             FAMST_LAUNCH(ex, nnd_group_count_kernel, sgrid, 256, 0, pt, pcount,
-                         (unsigned long long)P.pcap, gcnt);
+                         (unsigned long long)P.pcap, gcnt, act, nact);
             st = exclusive_scan_i32(ex, ar, gcnt, goff, n + 1, nullptr);
             ar.off = mark;
             if (st != FAMST_OK) return st;
             FAMST_LAUNCH(ex, nnd_group_scatter_kernel, sgrid, 256, 0, pt, pk, pcount,
                          (unsigned long long)P.pcap, goff, gcnt, gk);
-            FAMST_LAUNCH(ex, nnd_merge_kernel, wgrid, 256, 0, ni, k, goff, gk, Bk, Bf);
+            FAMST_LAUNCH(ex, nnd_merge_kernel, sgrid, 256, 0, k, act, nact, goff, gk, Bk, Bf);
         }
         FAMST_LAUNCH(ex, nnd_count_inserted_kernel, sgrid, 256, 0, Bf, nk, cdev);
         if (cudaMemcpyAsync(pinned_host, cdev, 16, cudaMemcpyDeviceToHost, ex.stream) !=
