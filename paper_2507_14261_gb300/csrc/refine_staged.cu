@@ -356,7 +356,9 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
         reinterpret_cast<unsigned long long *>(wb + S::ROWS_BYTES + 512);    // 8 best keys
     const float inf = __int_as_float(0x7f800000);
     const int g4 = lane >> 2, t4 = lane & 3;   // mma fragment row group / column pair
-    unsigned long long evals = 0, canon = 0, staged = 0, fixed_rows = 0;
+    // counters, one per lane: pairs (lane 0), canonical evaluations (1),
+    // rows staged (2), fixed rows read (3)
+    unsigned long long ctr = 0;
     // warp w visits the members at w, w + W, w + 2W, ... (W warps in all),
     // so the warps work on neighbouring members, i.e. a few components at a
     // time; the next 32 of its vertices are looked up together
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
                 s_en[lane] = en;
                 s_id[lane] = cand;
                 stage_rows<NKS>(H, cand, sbuf, lane);
-                staged += unsigned(nv);
+                if (lane == 2) ctr += unsigned(nv);
                 for (int tb = t0; tb < t1; tb += 8) {
                     const int ntb = t1 - tb < 8 ? t1 - tb : 8;
                     if (!single || r0 == 0) {
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
                         }
                         __syncwarp();
                     }
-                    fixed_rows += unsigned(ntb);
+                    if (lane == 3) ctr += unsigned(ntb);
                     // B column j = the fixed row of task slot j (lane 4 j + t
                     // carries k pairs (2t, 2t+1) and (8+2t, 9+2t) of each k step)
                     uint32_t b0[NKS], b1[NKS];
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
                         2 * t4 + 1 < ntb
                             ? __fmul_ru(fminf(mh1, key_w(s_best[2 * t4 + 1])), 1.0f + 0x1p-22f)
                             : -inf;
-                    if (lane == 0) evals += (unsigned long long)(nv) * ntb;
+                    if (lane == 0) ctr += unsigned(nv * ntb);
                     __syncwarp();
                     // survivors, decided on canonical distances by the whole
                     // warp, up to four at a time; bit 4 T + e2 of `my` marks a
@@ -478,7 +480,7 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
                         int cnt = __popc(my);
 #pragma unroll
                         for (int o = 16; o >= 1; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-                        if (lane == 0) canon += unsigned(cnt);
+                        if (lane == 1) ctr += unsigned(cnt);
                     }
 #pragma unroll 1
                     while (true) {
@@ -511,12 +513,7 @@ __global__ void __launch_bounds__(Stage<NKS>::WARPS * 32, MINB)
             }
         }
     }
-    if (evals_out && lane == 0) {   // pairs, canonical evaluations, rows staged, fixed rows read
-        atomicAdd(evals_out, evals);
-        atomicAdd(evals_out + 1, canon);
-        atomicAdd(evals_out + 2, staged);
-        atomicAdd(evals_out + 3, fixed_rows);
-    }
+    if (evals_out && lane < 4) atomicAdd(evals_out + lane, ctr);
 }
 
 // After the u-scans: move u; an edge whose u stays and whose v did not move
