@@ -127,79 +127,95 @@ __global__ void __launch_bounds__(256, 4) connect_filtered_kernel(const float *_
     const int L2 = lambda * lambda;
     const uint2 key = make_uint2(uint32_t(seed), uint32_t(seed >> 32));
     const float widen = 1.0f + 0x1p-20f;
+    __shared__ uint64_t s_kb[8][32 * PER];   // per warp: the draws' keys (hi, then w)
+    __shared__ int32_t s_ub[8][32 * PER], s_vb[8][32 * PER];
+    __shared__ float s_lob[8][32 * PER];
+    const int wib = threadIdx.x >> 5;
+    uint64_t *s_k = s_kb[wib];
+    int32_t *s_u = s_ub[wib], *s_v = s_vb[wib];
+    float *s_lo = s_lob[wib];
     for (int64_t pl = warp0; pl < npairs; pl += nwarps) {
         int64_t i, j;
         pair_of(pl, t, i, j);
         const uint64_t p = uint64_t(i) * uint64_t(t) + uint64_t(j);
         const int32_t oi = comp_off[i], oj = comp_off[j];
         const uint64_t si = uint64_t(comp_off[i + 1] - oi), sj = uint64_t(comp_off[j + 1] - oj);
-        int32_t uu[PER], vv[PER];
-        float lo[PER];
-        uint64_t hk[PER];
-#pragma unroll
+        // one compiled copy of the draw body (unrolled copies stalled on
+        // instruction fetch); a draw's state lives in its lane's slots of
+        // shared memory (only that lane reads them back)
+#pragma unroll 1
         for (int q = 0; q < PER; ++q) {
             const int s = lane + 32 * q;
-            uu[q] = -1;
-            vv[q] = -1;
+            int32_t u = -1, v = -1;
             if (s < L2) {
                 uint4 r = philox4x32_10(make_uint4(uint32_t(s), uint32_t(p), uint32_t(p >> 32), 0u),
                                         key);
-                uu[q] = members[oi + int64_t((uint64_t(r.x) * si) >> 32)];
-                vv[q] = members[oj + int64_t((uint64_t(r.y) * sj) >> 32)];
+                u = members[oi + int64_t((uint64_t(r.x) * si) >> 32)];
+                v = members[oj + int64_t((uint64_t(r.y) * sj) >> 32)];
             }
-            const float pf = warp_pairsq32g<G, 4>(X, d, uu[q], vv[q], lane);
-            lo[q] = __fsub_rd(__fmul_rd(pf, 1.0f - rho), 1e-35f);
-            const float hi = __fadd_ru(__fmul_ru(pf, 1.0f + rho), 1e-35f);
-            hk[q] = s < L2 ? nb_key(hi, uint32_t(s)) : KEY_NONE;
+            const float pf = warp_pairsq32g<G, 4>(X, d, u, v, lane);
+            s_u[s] = u;
+            s_v[s] = v;
+            s_lo[s] = __fsub_rd(__fmul_rd(pf, 1.0f - rho), 1e-35f);
+            s_k[s] = s < L2 ? nb_key(__fadd_ru(__fmul_ru(pf, 1.0f + rho), 1e-35f), uint32_t(s))
+                            : KEY_NONE;
         }
         // the lambda-th smallest upper bound
         float H = 0.0f;
-        for (int r = 0; r < lambda; ++r) {
-            uint64_t mine = KEY_NONE;
+        {
+            uint64_t hk[PER];
 #pragma unroll
-            for (int q = 0; q < PER; ++q) mine = hk[q] < mine ? hk[q] : mine;
-            const uint64_t best = warp_min_u64(mine);
-            H = key_w(best);
+            for (int q = 0; q < PER; ++q) hk[q] = s_k[lane + 32 * q];
+            for (int r = 0; r < lambda; ++r) {
+                uint64_t mine = KEY_NONE;
 #pragma unroll
-            for (int q = 0; q < PER; ++q)
-                if (hk[q] == best) hk[q] = KEY_NONE;
+                for (int q = 0; q < PER; ++q) mine = hk[q] < mine ? hk[q] : mine;
+                const uint64_t best = warp_min_u64(mine);
+                H = key_w(best);
+#pragma unroll
+                for (int q = 0; q < PER; ++q)
+                    if (hk[q] == best) hk[q] = KEY_NONE;
+            }
         }
         const float bound = __fmul_ru(H, widen);
-        uint64_t kk[PER];
-#pragma unroll
+#pragma unroll 1
         for (int q = 0; q < PER; ++q) {
-            kk[q] = KEY_NONE;
+            const int s = lane + 32 * q;
+            const int32_t u = s_u[s], v = s_v[s];
+            uint64_t kq = KEY_NONE;
             // survivors: canonical distance by the whole warp, kept by their lane
-            unsigned sv = __ballot_sync(0xffffffffu, lane + 32 * q < L2 && lo[q] <= bound);
+            unsigned sv = __ballot_sync(0xffffffffu, s < L2 && s_lo[s] <= bound);
             while (sv) {
                 const int sl = __ffs(sv) - 1;
                 sv &= sv - 1;
-                const int a = __shfl_sync(0xffffffffu, uu[q], sl);
-                const int b = __shfl_sync(0xffffffffu, vv[q], sl);
+                const int a = __shfl_sync(0xffffffffu, u, sl);
+                const int b = __shfl_sync(0xffffffffu, v, sl);
                 const float w = __fsqrt_rn(
                     canon_p_warp(X + int64_t(a) * d, X + int64_t(b) * d, d, lane));
-                if (lane == sl) kk[q] = nb_key(w, uint32_t(sl + 32 * q));
+                if (lane == sl) kq = nb_key(w, uint32_t(sl + 32 * q));
             }
+            s_k[s] = kq;
         }
+        uint64_t kk[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) kk[q] = s_k[lane + 32 * q];
         const int64_t ebase = pl * lambda;
         for (int r = 0; r < lambda; ++r) {
             uint64_t mine = KEY_NONE;
 #pragma unroll
             for (int q = 0; q < PER; ++q) mine = kk[q] < mine ? kk[q] : mine;
             uint64_t best = warp_min_u64(mine);
-            int s = int(key_lo(best));
-            if ((s & 31) == lane) {
-                int qq = s >> 5;
+            const int s = int(key_lo(best));
+            if (best != KEY_NONE && (s & 31) == lane) {
+                const int qq = s >> 5;
 #pragma unroll
                 for (int q = 0; q < PER; ++q)
-                    if (q == qq) {
-                        kk[q] = KEY_NONE;
-                        eu[ebase + r] = uu[q];
-                        ev[ebase + r] = vv[q];
-                        ew[ebase + r] = key_w(best);
-                        eci[ebase + r] = int32_t(i);
-                        ecj[ebase + r] = int32_t(j);
-                    }
+                    if (q == qq) kk[q] = KEY_NONE;
+                eu[ebase + r] = s_u[s];
+                ev[ebase + r] = s_v[s];
+                ew[ebase + r] = key_w(best);
+                eci[ebase + r] = int32_t(i);
+                ecj[ebase + r] = int32_t(j);
             }
         }
     }
@@ -271,85 +287,98 @@ __global__ void __launch_bounds__(256, 4) connect_half_kernel(
     const int L2 = lambda * lambda;
     const uint2 key = make_uint2(uint32_t(seed), uint32_t(seed >> 32));
     const float widen = 1.0f + 0x1p-20f;
+    __shared__ uint64_t s_kb[8][32 * PER];   // per warp: the draws' keys (hi, then w)
+    __shared__ int32_t s_ub[8][32 * PER], s_vb[8][32 * PER];
+    __shared__ float s_lob[8][32 * PER];
+    const int wib = threadIdx.x >> 5;
+    uint64_t *s_k = s_kb[wib];
+    int32_t *s_u = s_ub[wib], *s_v = s_vb[wib];
+    float *s_lo = s_lob[wib];
     for (int64_t pl = warp0; pl < npairs; pl += nwarps) {
         int64_t i, j;
         pair_of(pl, t, i, j);
         const uint64_t p = uint64_t(i) * uint64_t(t) + uint64_t(j);
         const int32_t oi = comp_off[i], oj = comp_off[j];
         const uint64_t si = uint64_t(comp_off[i + 1] - oi), sj = uint64_t(comp_off[j + 1] - oj);
-        int32_t uu[PER], vv[PER];
-        float lo[PER];
-        uint64_t hk[PER];
-#pragma unroll
+        // one compiled copy of the draw body (unrolled copies stalled on
+        // instruction fetch); a draw's state lives in its lane's slots of
+        // shared memory (only that lane reads them back)
+#pragma unroll 1
         for (int q = 0; q < PER; ++q) {
             const int s = lane + 32 * q;
-            uu[q] = -1;
-            vv[q] = -1;
+            int32_t u = -1, v = -1;
             if (s < L2) {
                 uint4 r = philox4x32_10(make_uint4(uint32_t(s), uint32_t(p), uint32_t(p >> 32), 0u),
                                         key);
-                uu[q] = members[oi + int64_t((uint64_t(r.x) * si) >> 32)];
-                vv[q] = members[oj + int64_t((uint64_t(r.y) * sj) >> 32)];
+                u = members[oi + int64_t((uint64_t(r.x) * si) >> 32)];
+                v = members[oj + int64_t((uint64_t(r.y) * sj) >> 32)];
             }
-            const float dt = warp_pairdot32h<V>(hr.h, hr.ld, uu[q], vv[q], lane);
-            lo[q] = __int_as_float(0x7f800000);
-            hk[q] = KEY_NONE;
-            if (s < L2) {
-                float l, h;
-                staged::dist_bounds(dt, __ldg(hr.n2 + uu[q]), __ldg(hr.n2 + vv[q]),
-                                    __ldg(hr.eb + uu[q]), __ldg(hr.eb + vv[q]), aerr, eps, l, h);
-                lo[q] = l;
-                hk[q] = nb_key(h, uint32_t(s));
-            }
+            const float dt = warp_pairdot32h<V>(hr.h, hr.ld, u, v, lane);
+            float l = __int_as_float(0x7f800000), h = 0.0f;
+            if (s < L2)
+                staged::dist_bounds(dt, __ldg(hr.n2 + u), __ldg(hr.n2 + v), __ldg(hr.eb + u),
+                                    __ldg(hr.eb + v), aerr, eps, l, h);
+            s_u[s] = u;
+            s_v[s] = v;
+            s_lo[s] = l;
+            s_k[s] = s < L2 ? nb_key(h, uint32_t(s)) : KEY_NONE;
         }
         // the lambda-th smallest upper bound
         float H = 0.0f;
-        for (int r = 0; r < lambda; ++r) {
-            uint64_t mine = KEY_NONE;
+        {
+            uint64_t hk[PER];
 #pragma unroll
-            for (int q = 0; q < PER; ++q) mine = hk[q] < mine ? hk[q] : mine;
-            const uint64_t best = warp_min_u64(mine);
-            H = key_w(best);
+            for (int q = 0; q < PER; ++q) hk[q] = s_k[lane + 32 * q];
+            for (int r = 0; r < lambda; ++r) {
+                uint64_t mine = KEY_NONE;
 #pragma unroll
-            for (int q = 0; q < PER; ++q)
-                if (hk[q] == best) hk[q] = KEY_NONE;
+                for (int q = 0; q < PER; ++q) mine = hk[q] < mine ? hk[q] : mine;
+                const uint64_t best = warp_min_u64(mine);
+                H = key_w(best);
+#pragma unroll
+                for (int q = 0; q < PER; ++q)
+                    if (hk[q] == best) hk[q] = KEY_NONE;
+            }
         }
         const float bound = __fmul_ru(H, widen);
-        uint64_t kk[PER];
-#pragma unroll
+#pragma unroll 1
         for (int q = 0; q < PER; ++q) {
-            kk[q] = KEY_NONE;
+            const int s = lane + 32 * q;
+            const int32_t u = s_u[s], v = s_v[s];
+            uint64_t kq = KEY_NONE;
             // survivors: canonical distance by the whole warp, kept by their lane
-            unsigned sv = __ballot_sync(0xffffffffu, lane + 32 * q < L2 && lo[q] <= bound);
+            unsigned sv = __ballot_sync(0xffffffffu, s < L2 && s_lo[s] <= bound);
             while (sv) {
                 const int sl = __ffs(sv) - 1;
                 sv &= sv - 1;
-                const int a = __shfl_sync(0xffffffffu, uu[q], sl);
-                const int b = __shfl_sync(0xffffffffu, vv[q], sl);
+                const int a = __shfl_sync(0xffffffffu, u, sl);
+                const int b = __shfl_sync(0xffffffffu, v, sl);
                 const float w = __fsqrt_rn(
                     canon_p_warp(X + int64_t(a) * d, X + int64_t(b) * d, d, lane));
-                if (lane == sl) kk[q] = nb_key(w, uint32_t(sl + 32 * q));
+                if (lane == sl) kq = nb_key(w, uint32_t(sl + 32 * q));
             }
+            s_k[s] = kq;
         }
+        uint64_t kk[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) kk[q] = s_k[lane + 32 * q];
         const int64_t ebase = pl * lambda;
         for (int r = 0; r < lambda; ++r) {
             uint64_t mine = KEY_NONE;
 #pragma unroll
             for (int q = 0; q < PER; ++q) mine = kk[q] < mine ? kk[q] : mine;
             uint64_t best = warp_min_u64(mine);
-            int s = int(key_lo(best));
-            if ((s & 31) == lane) {
-                int qq = s >> 5;
+            const int s = int(key_lo(best));
+            if (best != KEY_NONE && (s & 31) == lane) {
+                const int qq = s >> 5;
 #pragma unroll
                 for (int q = 0; q < PER; ++q)
-                    if (q == qq) {
-                        kk[q] = KEY_NONE;
-                        eu[ebase + r] = uu[q];
-                        ev[ebase + r] = vv[q];
-                        ew[ebase + r] = key_w(best);
-                        eci[ebase + r] = int32_t(i);
-                        ecj[ebase + r] = int32_t(j);
-                    }
+                    if (q == qq) kk[q] = KEY_NONE;
+                eu[ebase + r] = s_u[s];
+                ev[ebase + r] = s_v[s];
+                ew[ebase + r] = key_w(best);
+                eci[ebase + r] = int32_t(i);
+                ecj[ebase + r] = int32_t(j);
             }
         }
     }
