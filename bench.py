@@ -614,6 +614,9 @@ def main():
     ap.add_argument("--sweep-workloads", default="blobs_small,blobs_100k")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the precision comparison and the batch_256 sub-object")
+    ap.add_argument("--knn", default="exact", choices=["exact", "nndescent"],
+                    help="Phase 1 of the timed builds: the exact tiles (default) or NN-Descent "
+                         "(S = min(k, 32), at most 10 iterations, delta 0.001)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -640,6 +643,8 @@ def main():
     X_np = rank_workload(w, rank).points()
     X = torch.from_numpy(X_np).cuda()
     ctx = fam.Context(local)
+    if args.knn == "nndescent":
+        ctx.set_knn_method("nndescent", min(w.k, 32), 10, 0.001)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -862,7 +867,8 @@ def main():
             "dtype": "f32" if args.prec == "fp32" else "bf16",
             "data": "synthetic (seeded; inputs larger than L2, no flush)",
             "config": {"workload": w.name, "n": w.n, "d": w.d, "k": w.k, "lambda": w.lam,
-                       "prec": args.prec, "parallelism": f"replicas x{world}",
+                       "prec": args.prec, "knn": args.knn,
+                       "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (X = %d MB)" % (X_np.nbytes >> 20)},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches, "quality": quality, "kernels": kernels,
@@ -876,7 +882,8 @@ def main():
                       "knn_tile_fraction": last["knn_tile_fraction"],
                       "refine_distance_evals": last["refine_distance_evals"],
                       "refine_canonical_evals": last["refine_canonical_evals"],
-                      "refine_filter": last["refine_filter"]},
+                      "refine_filter": last["refine_filter"],
+                      "knn_iters": last["knn_iters"]},
         }
         print(json.dumps(line), flush=True)
     if pg is not None:
