@@ -818,10 +818,11 @@ struct CertConst {
 // and leave the canonical distance unchanged). d is the true dimension used in
 // the error bounds. Returns whether the row was certified (then the k
 // results are written).
-// XR > 0 (dc <= 32 XR): the warp computes one candidate's distance at a time,
-// lane l taking coordinates l, l + 32, ... (its canonical partial) from
-// coalesced row reads, the query row held in registers, G candidates in
-// flight; XR = 0: one candidate per lane, its 32 partials in registers.
+// XR > 0 (dc <= 32 XR): lane l takes coordinates l, l + 32, ... (its
+// canonical partial) of every candidate from coalesced row reads, the query
+// row held in registers, and the warp sums the partials of a batch of
+// candidates at once (below); XR = 0: one candidate per lane, its 32
+// partials in registers.
 template <int VEC, int KC, int XR = 0>
 __device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, int dc, int d,
                                            const float *__restrict__ xi, int k,
@@ -834,7 +835,18 @@ __device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, 
     constexpr int KP = KC - 1;
     uint64_t key[2];
     if constexpr (XR > 0) {
-        constexpr int G = XR <= 8 ? 4 : (XR <= 16 ? 2 : 1);
+        // batches of NB candidates: lane l's partial of candidate c in
+        // acc[c mod NB]; the butterfly's steps xor 16 .. xor NB on all NB,
+        // then its later steps (xor NB/2 .. 1) transposed, each lane passing
+        // on the half it does not keep. The additions are the butterfly's
+        // own (same pairs, same order), so lane l ends with the canonical
+        // total of candidate NB b + (l mod NB), with 2 NB - 1 + NB log2(32/NB)
+        // shuffles per batch instead of 5 NB.
+        // (wider rows take smaller batches, within the sorted kernel's
+        // register budget; NB = 1 is the plain butterfly)
+        constexpr int NB = XR <= 4 ? 16 : (XR <= 8 ? 2 : 1);
+        constexpr int G = XR <= 8 ? 2 : 1;   // candidates with loads in flight
+        static_assert(NB % G == 0, "a batch is whole load groups");
         float xr[XR];
 #pragma unroll
         for (int q = 0; q < XR; ++q) {
@@ -848,41 +860,61 @@ __device__ __forceinline__ bool rerank_row(const float *__restrict__ X, int ld, 
             jc[h] = c < KP ? cand_row[c] : -1;
         }
         key[0] = key[1] = KEY_NONE;
-        for (int c0 = 0; c0 < KP; c0 += G) {
-            int j[G];
-            float y[G][XR];
+#pragma unroll 1
+        for (int b = 0; b < (KP + NB - 1) / NB; ++b) {
+            float acc[NB];
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                const int c = c0 + g;
-                const int ja = __shfl_sync(0xffffffffu, jc[0], c & 31);
-                const int jb = __shfl_sync(0xffffffffu, jc[1], c & 31);
-                j[g] = c < KP ? (c < 32 ? ja : jb) : -1;
+            for (int g0 = 0; g0 < NB; g0 += G) {
+                int j[G];
+                float y[G][XR];
 #pragma unroll
-                for (int q = 0; q < XR; ++q) {
-                    const int t = lane + 32 * q;
-                    y[g][q] = (j[g] >= 0 && t < dc) ? __ldg(X + int64_t(j[g]) * ld + t) : 0.0f;
+                for (int g = 0; g < G; ++g) {
+                    const int c = NB * b + g0 + g;
+                    const int ja = __shfl_sync(0xffffffffu, jc[0], c & 31);
+                    const int jb = __shfl_sync(0xffffffffu, jc[1], c & 31);
+                    j[g] = c < KP ? (c < 32 ? ja : jb) : -1;
+#pragma unroll
+                    for (int q = 0; q < XR; ++q) {
+                        const int t = lane + 32 * q;
+                        y[g][q] = (j[g] >= 0 && t < dc) ? __ldg(X + int64_t(j[g]) * ld + t) : 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    float p = 0.0f;
+#pragma unroll
+                    for (int q = 0; q < XR; ++q) {
+                        const float dl = __fsub_rn(xr[q], y[g][q]);
+                        p = __fmaf_rn(dl, dl, p);
+                    }
+                    acc[g0 + g] = p;
                 }
             }
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                float p = 0.0f;
+            for (int o = 16; o >= NB; o >>= 1)
 #pragma unroll
-                for (int q = 0; q < XR; ++q) {
-                    const float dl = __fsub_rn(xr[q], y[g][q]);
-                    p = __fmaf_rn(dl, dl, p);
-                }
+                for (int i = 0; i < NB; ++i)
+                    acc[i] = __fadd_rn(acc[i], __shfl_xor_sync(0xffffffffu, acc[i], o));
 #pragma unroll
-                for (int o = 16; o >= 1; o >>= 1)
-                    p = __fadd_rn(p, __shfl_xor_sync(0xffffffffu, p, o));
-                const int c = c0 + g;
-                if (j[g] >= 0) {
-                    const uint64_t kg = nb_key(__fsqrt_rn(p), uint32_t(idmap ? idmap[j[g]] : j[g]));
-                    if (c < 32) {
-                        if (lane == c) key[0] = kg;
-                    } else if (lane == c - 32) {
-                        key[1] = kg;
-                    }
+            for (int o = NB / 2; o >= 1; o >>= 1) {
+                const bool up = (lane & o) != 0;
+#pragma unroll
+                for (int i = 0; i < o; ++i) {
+                    const float send = up ? acc[i] : acc[i + o];
+                    const float keep = up ? acc[i + o] : acc[i];
+                    acc[i] = __fadd_rn(keep, __shfl_xor_sync(0xffffffffu, send, o));
                 }
+            }
+            // candidate c of this lane; sort element c (register c / 32 of
+            // lane c mod 32) takes it from the lane of the matching block
+            const int c = NB * b + (lane & (NB - 1));
+            const int ja = __shfl_sync(0xffffffffu, jc[0], c & 31);
+            const int jb = __shfl_sync(0xffffffffu, jc[1], c & 31);
+            const int jl = c < KP ? (c < 32 ? ja : jb) : -1;
+            if ((lane & ~(NB - 1)) == ((NB * b) & 31) && jl >= 0) {
+                const uint64_t kg = nb_key(__fsqrt_rn(acc[0]), uint32_t(idmap ? idmap[jl] : jl));
+                if (c < 32) key[0] = kg;
+                else key[1] = kg;
             }
         }
     } else {
