@@ -4,9 +4,10 @@
 // The union-find parent array, the root flags / ranks and the per-tile
 // sums of the rank scan live in one file-scope static device array of
 // FAMST_NOALLOC_MAX_N-sized regions. Host code cannot pass that array's
-// name to a kernel (on the host it is only a stand-in symbol), so the first
-// call on each device looks up its device address with
-// cudaGetSymbolAddress and caches it; every kernel receives that address.
+// name to a kernel (on the host it is only a stand-in symbol), so every
+// call looks up its device address in the current context with
+// cudaGetSymbolAddress (nothing is cached, so a context reset leaves no
+// stale address behind); every kernel receives that address.
 //
 // The array is shared by every call on a device and keeps the previous
 // call's contents; the kernels below initialise every word they read
