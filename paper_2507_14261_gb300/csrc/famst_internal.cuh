@@ -454,7 +454,16 @@ struct TcTile {
     int nkb;       // active 64-wide K blocks of the hi part
     int row_end;   // padded rows >= row_end are padding
     int shift;     // compact id = padded row - shift
+    int part;      // 0: the query tile's whole key list; s > 0: one part of a split
+                   // list, whose rows' sorted candidates go to side slot s - 1
 };
+// Long key lists of a pruned Phase 1 are split so that no work item holds
+// much more than a share of one SM's tiles: at most PRUNE_SPLIT_TILES query
+// tiles are split, into at most PRUNE_SPLIT_SLOTS parts in all; a list is
+// split when longer than max(PRUNE_SPLIT_MIN, visited / PRUNE_SPLIT_TILES).
+constexpr int PRUNE_SPLIT_TILES = 640;
+constexpr int PRUNE_SPLIT_SLOTS = 2 * PRUNE_SPLIT_TILES;
+constexpr int PRUNE_SPLIT_MIN = 16;
 struct F32Tile {
     int qbase;     // first query row of the block (64 rows)
     int nq;        // valid queries in the block
@@ -506,7 +515,10 @@ struct PruneOut {
     __nv_bfloat16 *Hs = nullptr;    // operand rows in sorted order
     float *nys = nullptr;           // key norms in sorted order (+inf padding)
     int32_t *klist = nullptr;       // key tiles per query tile
-    TcTile *tab = nullptr;          // per query tile: its range of klist
+    TcTile *tab = nullptr;          // work items: parts of split lists, then whole lists
+    int32_t *nitems = nullptr;      // device: work items in tab (<= nq + PRUNE_SPLIT_SLOTS)
+    int32_t *splitq = nullptr;      // device: per split query tile (q, first slot, parts)
+    int32_t *nsplit = nullptr;      // device: split query tiles
     float *skipQ = nullptr;         // per query tile
     float *Xs = nullptr;            // the points in sorted order (FP32, n x d)
     float *tau_row = nullptr;       // per sorted row: upper bound on its k-th neighbour distance

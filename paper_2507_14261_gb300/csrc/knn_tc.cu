@@ -46,6 +46,7 @@
 
 #include "famst_internal.cuh"
 #include "mbarrier.cuh"
+#include "topk_merge.cuh"
 
 namespace famst {
 namespace {
@@ -210,6 +211,10 @@ struct TcArgs {
     int spiral;              // 1: an item's key tiles [kt0, kt1) are visited outward from the
                              // query tile's own (q0 / BN, then +1, -1, +2, ...): on rows in
                              // a spatial order the lists fill with near keys first
+    const int32_t *nitems_dev;  // non-null (one item per CTA): CTAs from *nitems_dev on are idle
+    int32_t *side_j;         // items that are parts of a split list (TcTile::part = s + 1):
+    float *side_s;           //   per slot s and tile row, the KC - 1 smallest (id, score),
+    float *side_splus;       //   ascending, and the part's s+
 };
 
 template <int KC>
@@ -230,6 +235,20 @@ __device__ __forceinline__ void list_insert(float (&ls)[KC], int (&lj)[KC], floa
     lj[0] = here0 ? j : lj[0];
 }
 
+// Absorb a batch of eight (bs ascending, +inf where empty) of which at most
+// nq per lane are finite (nq warp-uniform): one or two insertions cost less
+// than the merging network, more take the network.
+template <int KC>
+__device__ __forceinline__ void list_absorb8(float (&ls)[KC], int (&lj)[KC], const float (&bs)[8],
+                                             const int (&bj)[8], int nq) {
+    if (nq <= 2) {
+        list_insert<KC>(ls, lj, bs[0], bj[0]);
+        if (nq == 2) list_insert<KC>(ls, lj, bs[1], bj[1]);
+    } else {
+        topk::merge8<KC>(ls, lj, bs, bj);
+    }
+}
+
 template <int KC, bool MASK, bool F8 = false>
 __global__ void __launch_bounds__(KC <= 2 * CAPB ? TC_THREADS_MAX : 64 + 32 * 4, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -241,9 +260,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
     // Work items: query tile `item` with its key tiles. A CTA takes items
     // blockIdx.x, blockIdx.x + gridDim.x, ...; TMEM, barriers and the
     // pipeline state carry over from one item to the next.
+    // a launch sized for the most items a table can hold: the CTAs beyond
+    // the table's count leave before touching barriers or TMEM
+    if (args.nitems_dev && int(blockIdx.x) >= __ldg(args.nitems_dev)) return;
     const int nitems = args.nitems > 0 ? args.nitems : int(gridDim.x);
     struct Item {
-        int q0, kt0, kt1, nkb, row_end, shift;
+        int q0, kt0, kt1, nkb, row_end, shift, part;
     };
     auto item_of = [&](int item) {
         Item I;
@@ -251,9 +273,10 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             const TcTile T = args.tiles[item];
             I.q0 = T.q0; I.kt0 = T.kt0; I.kt1 = T.kt1; I.nkb = T.nkb; I.row_end = T.row_end;
             I.shift = T.shift;
+            I.part = T.part;
         } else {
             I.q0 = item * BM; I.kt0 = 0; I.kt1 = args.nk_tiles; I.nkb = args.nkb;
-            I.row_end = args.n; I.shift = 0;
+            I.row_end = args.n; I.shift = 0; I.part = 0;
         }
         return I;
     };
@@ -465,12 +488,43 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         auto flush = [&]() {
             const int mx = __reduce_max_sync(0xffffffffu, cnt);
             const float pt = partner_thr();
-            for (int q = 0; q < mx; ++q) {
-                if (q < cnt) {
-                    float sv = my_s[q * BM];
-                    int jv = my_j[q * BM];
-                    if ((args.cross || jv != i) && sv < fminf(ls[KC - 1], pt))
-                        list_insert<KC>(ls, lj, sv, jv);
+            if constexpr (KC >= 32) {
+                // eight staged candidates at a time: those still below the
+                // list's KC-th score are sorted and merged into the list
+                for (int q0 = 0; q0 < mx; q0 += 8) {
+                    const float lim = fminf(ls[KC - 1], pt);
+                    float bs[8];
+                    int bj[8];
+                    int nq = 0;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        float sv = __int_as_float(0x7f800000);
+                        int jv = -1;
+                        if (q0 + c < cnt) {
+                            const float s = my_s[(q0 + c) * BM];
+                            const int j = my_j[(q0 + c) * BM];
+                            if ((args.cross || j != i) && s < lim) {
+                                sv = s;
+                                jv = j;
+                                ++nq;
+                            }
+                        }
+                        bs[c] = sv;
+                        bj[c] = jv;
+                    }
+                    nq = __reduce_max_sync(0xffffffffu, nq);
+                    if (nq == 0) continue;
+                    topk::sort8(bs, bj);
+                    list_absorb8<KC>(ls, lj, bs, bj, nq);
+                }
+            } else {
+                for (int q = 0; q < mx; ++q) {
+                    if (q < cnt) {
+                        float sv = my_s[q * BM];
+                        int jv = my_j[q * BM];
+                        if ((args.cross || jv != i) && sv < fminf(ls[KC - 1], pt))
+                            list_insert<KC>(ls, lj, sv, jv);
+                    }
                 }
             }
             cnt = 0;
@@ -589,23 +643,55 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
             }
             epilogue_bar(32 * EPI);
             if (half == 0) {
-                for (int p = 0; p < KC; ++p) {   // ascending: stop at the first that cannot enter
-                    const float sv = stg_s[p * BM + row];
-                    if (!(sv < ls[KC - 1])) break;
-                    list_insert<KC>(ls, lj, sv, stg_j[p * BM + row]);
+                if constexpr (KC >= 32) {
+                    // the other list is ascending: batches of eight, until no
+                    // lane has an entry below its KC-th score
+                    for (int p0 = 0; p0 < KC; p0 += 8) {
+                        const float lim = ls[KC - 1];
+                        float bs[8];
+                        int bj[8];
+                        int nq = 0;
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const float s = stg_s[(p0 + c) * BM + row];
+                            const bool in = s < lim;
+                            bs[c] = in ? s : __int_as_float(0x7f800000);
+                            bj[c] = in ? stg_j[(p0 + c) * BM + row] : -1;
+                            nq += in;
+                        }
+                        nq = __reduce_max_sync(0xffffffffu, nq);
+                        if (nq == 0) break;
+                        list_absorb8<KC>(ls, lj, bs, bj, nq);
+                    }
+                } else {
+                    for (int p = 0; p < KC; ++p) {   // ascending: stop at the first that cannot enter
+                        const float sv = stg_s[p * BM + row];
+                        if (!(sv < ls[KC - 1])) break;
+                        list_insert<KC>(ls, lj, sv, stg_j[p * BM + row]);
+                    }
                 }
             }
         }
         if (ok && half == 0 && i < I.row_end) {
             if constexpr (KC == 1) {   // top-1 mode: the best key and its score
                 args.cand[i - I.shift] = lj[0] >= 0 ? lj[0] - I.shift : -1;
+            } else if (I.part > 0) {   // one part of a split list: scores too, for the merge
+                const size_t at = size_t(I.part - 1) * BM + row;
+                int32_t *oj = args.side_j + at * (KC - 1);
+                float *os = args.side_s + at * (KC - 1);
+#pragma unroll
+                for (int p = 0; p < KC - 1; ++p) {
+                    oj[p] = lj[p] >= 0 ? lj[p] - I.shift : -1;
+                    os[p] = ls[p];
+                }
+                args.side_splus[at] = fminf(ls[KC - 1], thr0v);
             } else {
                 int32_t *out = args.cand + size_t(i - I.shift) * (KC - 1);
 #pragma unroll
                 for (int p = 0; p < KC - 1; ++p) out[p] = lj[p] >= 0 ? lj[p] - I.shift : -1;
             }
             // keys that never entered the list scored at least min(KC-th, thr0)
-            args.splus[i - I.shift] = fminf(ls[KC - 1], thr0v);
+            if (KC == 1 || I.part == 0) args.splus[i - I.shift] = fminf(ls[KC - 1], thr0v);
         }
         // next item: this row's published threshold starts over, and the
         // staging area is free again; a failure anywhere stops every warp here
@@ -619,6 +705,49 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
         tc_fence_after();
         tmem_dealloc(tmem, 512);
     }
+}
+
+// Rows of split query tiles (one block of BM threads per split tile): the
+// row's candidates are the KC - 1 smallest scores over its parts' lists and
+// s+ = min(the KC-th smallest of those lists, every part's s+). A key that
+// no part kept scored at least its part's s+; a kept key left out here
+// scored at least the KC-th. So the row gets the candidates and s+ the
+// unsplit list would have had (up to the order of equal scores).
+template <int KC>
+__global__ void __launch_bounds__(BM)
+split_merge_kernel(const int32_t *__restrict__ splitq, const int32_t *__restrict__ nsplit,
+                   const int32_t *__restrict__ side_j, const float *__restrict__ side_s,
+                   const float *__restrict__ side_splus, int64_t n, int32_t *__restrict__ cand,
+                   float *__restrict__ splus) {
+    if (int(blockIdx.x) >= __ldg(nsplit)) return;
+    const int q = splitq[3 * blockIdx.x], slot0 = splitq[3 * blockIdx.x + 1];
+    const int P = splitq[3 * blockIdx.x + 2];
+    const int row = threadIdx.x;
+    const int64_t i = int64_t(q) * BM + row;
+    if (i >= n) return;
+    float ls[KC];
+    int lj[KC];
+#pragma unroll
+    for (int p = 0; p < KC; ++p) {
+        ls[p] = __int_as_float(0x7f800000);
+        lj[p] = -1;
+    }
+    float sp = __int_as_float(0x7f800000);
+    for (int part = 0; part < P; ++part) {
+        const size_t at = size_t(slot0 + part) * BM + row;
+        sp = fminf(sp, side_splus[at]);
+        const float *ps = side_s + at * (KC - 1);
+        const int32_t *pj = side_j + at * (KC - 1);
+        for (int p = 0; p < KC - 1; ++p) {   // ascending: stop at the first that cannot enter
+            const float sv = ps[p];
+            if (!(sv < ls[KC - 1])) break;
+            list_insert<KC>(ls, lj, sv, pj[p]);
+        }
+    }
+    int32_t *out = cand + i * (KC - 1);
+#pragma unroll
+    for (int p = 0; p < KC - 1; ++p) out[p] = lj[p];
+    splus[i] = fminf(ls[KC - 1], sp);
 }
 
 // ------------------------------------------------------------- prep
@@ -1434,10 +1563,15 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     // in sorted order first
     int32_t *cand_t = cand;
     float *splus_t = splus;
+    int32_t *side_j = nullptr;   // candidates of the parts of split lists
+    float *side_s = nullptr, *side_sp = nullptr;
     if (use_prune) {
         cand_t = ar.take<int32_t>(size_t(n) * (p.kc - 1));
         splus_t = ar.take<float>(size_t(n));
-        if (!cand_t || !splus_t) return FAMST_ERR_OOM;
+        side_j = ar.take<int32_t>(size_t(PRUNE_SPLIT_SLOTS) * BM * (p.kc - 1));
+        side_s = ar.take<float>(size_t(PRUNE_SPLIT_SLOTS) * BM * (p.kc - 1));
+        side_sp = ar.take<float>(size_t(PRUNE_SPLIT_SLOTS) * BM);
+        if (!cand_t || !splus_t || !side_j || !side_s || !side_sp) return FAMST_ERR_OOM;
     }
     const void *Hop = f8 ? static_cast<const void *>(Q)
                          : static_cast<const void *>(use_prune ? P.Hs : H);
@@ -1479,20 +1613,30 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
     TcArgs a{int(n), int(p.nk_tiles), p.nkb, int(x3), p.stages, use_prune ? P.nys : ny, cand_t,
              splus_t, ex.dstatus, use_prune ? P.tab : nullptr, cpad,
              use_prune ? P.klist : nullptr, 0, p.epi, rscale, use_prune ? P.tau_row : nullptr};
-    // one CTA per query tile: the pruned tiles' key lists differ in length,
-    // and a static round-robin over persistent CTAs measured slower here
+    // one CTA per work item: the pruned tiles' key lists differ in length,
+    // and a static round-robin over persistent CTAs measured slower here.
+    // Pruned lists come as work items, long ones split into parts; the grid
+    // covers the most items the table can hold and the CTAs beyond its
+    // count leave at once.
+    unsigned tgrid = unsigned(p.nq_tiles);
+    if (use_prune) {
+        a.nitems_dev = P.nitems;
+        a.side_j = side_j;
+        a.side_s = side_s;
+        a.side_splus = side_sp;
+        tgrid = unsigned(p.nq_tiles + PRUNE_SPLIT_SLOTS);
+    }
 #define TC_LAUNCH(KCV, M)                                                                        \
     do {                                                                                         \
         if (set_smem_attr(knn_tc_kernel<KCV, M>, int(p.smem), ex.stream) != cudaSuccess)         \
             return FAMST_ERR_CUDA;                                                               \
-        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, M>), unsigned(p.nq_tiles), 64 + 32 * p.epi, p.smem, \
-                     mA, mB, a);                                                                 \
+        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, M>), tgrid, 64 + 32 * p.epi, p.smem, mA, mB, a);   \
     } while (0)
 #define TC_LAUNCH_F8(KCV)                                                                           \
     do {                                                                                            \
         if (set_smem_attr(knn_tc_kernel<KCV, false, true>, int(p.smem), ex.stream) != cudaSuccess)  \
             return FAMST_ERR_CUDA;                                                                  \
-        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false, true>), unsigned(p.nq_tiles), 64 + 32 * p.epi, \
+        FAMST_LAUNCH(ex, (knn_tc_kernel<KCV, false, true>), tgrid, 64 + 32 * p.epi,                \
                      p.smem, mA, mB, a);                                                            \
     } while (0)
     timer_mark(ex, TIMER_TILES, false);
@@ -1508,6 +1652,15 @@ famst_status knn_tc(const Exec &ex, Arena &ar, const float *X, int64_t n, int d,
         if (p.kc == 32) TC_LAUNCH(32, false);
         else if (p.kc == 48) TC_LAUNCH(48, false);
         else TC_LAUNCH(64, false);
+    }
+    if (use_prune) {   // rows of split lists: merge their parts
+#define SPLIT_MERGE(KCV)                                                                        \
+    FAMST_LAUNCH(ex, split_merge_kernel<KCV>, unsigned(PRUNE_SPLIT_TILES), BM, 0, P.splitq,     \
+                 P.nsplit, side_j, side_s, side_sp, n, cand_t, splus_t)
+        if (p.kc == 32) SPLIT_MERGE(32);
+        else if (p.kc == 48) SPLIT_MERGE(48);
+        else SPLIT_MERGE(64);
+#undef SPLIT_MERGE
     }
     timer_mark(ex, TIMER_TILES, true);
 #undef TC_LAUNCH

@@ -367,14 +367,15 @@ __global__ void tile_radius_kernel(const float *__restrict__ X, const float *__r
 // the smallest pivot distance between their cells, then tile index), so the
 // candidate lists of the tile kernel fill with near points early and its
 // thresholds reject most keys of the later tiles. The set of tiles is the
-// same; lists longer than 1024 keep their ascending order.
+// same; lists longer than KLIST_SORT_MAX keep their ascending order.
+constexpr int KLIST_SORT_MAX = 4096;   // 32 KB of keys in shared memory
 __global__ void __launch_bounds__(256) klist_sort_kernel(const int32_t *__restrict__ off,
                                                          const float *__restrict__ kkey,
                                                          int32_t *__restrict__ klist) {
-    __shared__ unsigned long long sk[1024];
+    __shared__ unsigned long long sk[KLIST_SORT_MAX];
     const int Q = blockIdx.x;
     const int s0 = off[Q], len = off[Q + 1] - s0;
-    if (len <= 1 || len > 1024) return;
+    if (len <= 1 || len > KLIST_SORT_MAX) return;
     int npow = 1;
     while (npow < len) npow <<= 1;
     // keys are distances >= 0: their bit patterns order like the values
@@ -493,18 +494,122 @@ tile_pairs_kernel(const int32_t *__restrict__ qc, const int32_t *__restrict__ kc
     }
 }
 
-__global__ void table_kernel(const int32_t *__restrict__ off, int64_t nq, int nkb, int64_t n,
-                             TcTile *__restrict__ tab) {
-    const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (q >= nq) return;
-    TcTile t;
-    t.q0 = int(q * QT);
-    t.kt0 = off[q];
-    t.kt1 = off[q + 1];
-    t.nkb = nkb;
-    t.row_end = int(n);
-    t.shift = 0;
-    tab[q] = t;
+// Exclusive scan of three counters over the block (blockDim.x a multiple of
+// 32): every thread's v becomes the sum of the lower threads' values.
+__device__ __forceinline__ void block_scan3(int3 &v) {
+    __shared__ int3 wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int3 inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, inc.x, o);
+        const int b = __shfl_up_sync(0xffffffffu, inc.y, o);
+        const int c = __shfl_up_sync(0xffffffffu, inc.z, o);
+        if (lane >= o) {
+            inc.x += a;
+            inc.y += b;
+            inc.z += c;
+        }
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int3 w = lane < nw ? wsum[lane] : make_int3(0, 0, 0);
+        int3 wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(0xffffffffu, wi.x, o);
+            const int b = __shfl_up_sync(0xffffffffu, wi.y, o);
+            const int c = __shfl_up_sync(0xffffffffu, wi.z, o);
+            if (lane >= o) {
+                wi.x += a;
+                wi.y += b;
+                wi.z += c;
+            }
+        }
+        if (lane < nw) wsum[lane] = make_int3(wi.x - w.x, wi.y - w.y, wi.z - w.z);
+    }
+    __syncthreads();
+    const int3 wb = wsum[warp];
+    v = make_int3(wb.x + inc.x - v.x, wb.y + inc.y - v.y, wb.z + inc.z - v.z);
+    __syncthreads();
+}
+
+// Work items of the pruned tile kernel (one block of 1024 threads). A query
+// tile whose key list is longer than L = max(PRUNE_SPLIT_MIN, ceil(visited /
+// PRUNE_SPLIT_TILES)) becomes ceil(len / L) parts of near-equal length, each
+// its own item with a side slot for its rows' candidates; the parts come
+// first (the longest work starts first), then the whole lists in tile
+// order. The counts are bounded: fewer than PRUNE_SPLIT_TILES lists are
+// longer than L, and their parts number fewer than visited / L plus that
+// count, i.e. fewer than PRUNE_SPLIT_SLOTS. Were the bound to fail, nothing
+// would be split.
+__global__ void __launch_bounds__(1024)
+split_table_kernel(const int32_t *__restrict__ off, int64_t nq, int nkb, int64_t n,
+                   const int32_t *__restrict__ visited, TcTile *__restrict__ tab,
+                   int32_t *__restrict__ nitems, int32_t *__restrict__ splitq,
+                   int32_t *__restrict__ nsplit) {
+    __shared__ int3 totals;
+    const int64_t per = (nq + blockDim.x - 1) / blockDim.x;
+    const int64_t q0 = min(nq, int64_t(threadIdx.x) * per), q1 = min(nq, q0 + per);
+    const int64_t vis = *visited;
+    int64_t L = (vis + PRUNE_SPLIT_TILES - 1) / PRUNE_SPLIT_TILES;
+    if (L < PRUNE_SPLIT_MIN) L = PRUNE_SPLIT_MIN;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        int3 c = make_int3(0, 0, 0);   // parts, whole lists, split lists
+        for (int64_t q = q0; q < q1; ++q) {
+            const int64_t len = off[q + 1] - off[q];
+            if (len > L) {
+                c.x += int((len + L - 1) / L);
+                c.z += 1;
+            } else {
+                c.y += 1;
+            }
+        }
+        int3 pre = c;
+        block_scan3(pre);
+        if (threadIdx.x == blockDim.x - 1) totals = make_int3(pre.x + c.x, pre.y + c.y, pre.z + c.z);
+        __syncthreads();
+        const int3 tot = totals;
+        __syncthreads();
+        if (tot.x > PRUNE_SPLIT_SLOTS || tot.z > PRUNE_SPLIT_TILES) {
+            L = int64_t(1) << 40;   // split nothing (uniform: every thread saw the same totals)
+            continue;
+        }
+        int pi = pre.x, wi = tot.x + pre.y, si = pre.z;
+        for (int64_t q = q0; q < q1; ++q) {
+            const int kt0 = off[q], kt1 = off[q + 1];
+            const int64_t len = kt1 - kt0;
+            TcTile t;
+            t.q0 = int(q * QT);
+            t.nkb = nkb;
+            t.row_end = int(n);
+            t.shift = 0;
+            if (len > L) {
+                const int P = int((len + L - 1) / L);
+                splitq[3 * si] = int(q);
+                splitq[3 * si + 1] = pi;
+                splitq[3 * si + 2] = P;
+                ++si;
+                for (int p = 0; p < P; ++p) {
+                    t.kt0 = kt0 + int(len * p / P);
+                    t.kt1 = kt0 + int(len * (p + 1) / P);
+                    t.part = pi + 1;
+                    tab[pi++] = t;
+                }
+            } else {
+                t.kt0 = kt0;
+                t.kt1 = kt1;
+                t.part = 0;
+                tab[wi++] = t;
+            }
+        }
+        if (threadIdx.x == 0) {
+            *nitems = tot.x + tot.y;
+            *nsplit = tot.z;
+        }
+        return;
+    }
 }
 
 // Order of the cells. The minimum spanning tree of the pivots is cut at
@@ -603,7 +708,11 @@ size_t prune_workspace(int64_t n, int d, int kh, int kp, int64_t nq, int64_t nk)
     b += align256(size_t(nq) * 4) + align256(size_t(nk) * 4);                  // tile balls
     b += align256(size_t(nq + 1) * 4) * 2 + scan_workspace(nq + 1) + 256;      // counts, offsets
     b += align256(size_t(nq) * nk * 4) * 2;                                    // lists, keys (worst case)
-    b += align256(size_t(nq) * 4) + align256(size_t(nq) * sizeof(TcTile));     // skip, table
+    b += align256(size_t(nq) * 4) +
+         align256(size_t(nq + PRUNE_SPLIT_SLOTS) * sizeof(TcTile));           // skip, work items
+    b += align256(4) * 2 + align256(size_t(3) * PRUNE_SPLIT_TILES * 4);        // item and split counts
+    b += align256(size_t(PRUNE_SPLIT_SLOTS) * QT * kp * 4) * 2 +
+         align256(size_t(PRUNE_SPLIT_SLOTS) * QT * 4);                         // parts' candidates
     b += align256(size_t(n) * kp * 4) + align256(size_t(n) * 4);               // sorted outputs
     b += align256(size_t(n) * d * 4);                                          // sorted points
     return b;
@@ -679,14 +788,17 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     int32_t *klist = ar.take<int32_t>(size_t(nq) * nk);
     float *kkey = ar.take<float>(size_t(nq) * nk);
     float *skipQ = ar.take<float>(size_t(nq));
-    TcTile *tab = ar.take<TcTile>(size_t(nq));
+    TcTile *tab = ar.take<TcTile>(size_t(nq + PRUNE_SPLIT_SLOTS));
+    int32_t *nitems = ar.take<int32_t>(1);
+    int32_t *nsplit = ar.take<int32_t>(1);
+    int32_t *splitq = ar.take<int32_t>(size_t(3) * PRUNE_SPLIT_TILES);
     int32_t *total = ar.take<int32_t>(1);
     float *Xs = ar.take<float>(size_t(n) * d);
     if (!Xs) return FAMST_ERR_OOM;
     if (!keys || !perm || !ccount || !cstart || !Hs || !nys || !R || !tauQ || !tau_row || !DP ||
         !DPr || !ord ||
         !tu || !tv || !tw || !nb || !nw || !qc || !kc || !qR || !kR || !cnt || !off || !klist ||
-        !kkey || !skipQ || !tab ||
+        !kkey || !skipQ || !tab || !nitems || !nsplit || !splitq ||
         !total)
         return FAMST_ERR_OOM;
     const float rho = fast_rho(d, 4);
@@ -813,12 +925,16 @@ famst_status prune_partition(const Exec &ex, Arena &ar, const float *X, int d, i
     FAMST_LAUNCH(ex, tile_pairs_kernel<true>, unsigned(nq), 256, 0, qc, kc, qR, kR, nk, K, DPr, R,
                  tauQ, margin, nullptr, off, klist, kkey, skipQ);
     FAMST_LAUNCH(ex, klist_sort_kernel, unsigned(nq), 256, 0, off, kkey, klist);
-    FAMST_LAUNCH(ex, table_kernel, nblk(nq, 256), 256, 0, off, nq, nkb, n, tab);
+    FAMST_LAUNCH(ex, split_table_kernel, 1, 1024, 0, off, nq, nkb, n, total, tab, nitems, splitq,
+                 nsplit);
     out->perm = perm;
     out->Hs = Hs;
     out->nys = nys;
     out->klist = klist;
     out->tab = tab;
+    out->nitems = nitems;
+    out->splitq = splitq;
+    out->nsplit = nsplit;
     out->skipQ = skipQ;
     out->Xs = Xs;
     out->tau_row = tau_row;
