@@ -235,20 +235,6 @@ __device__ __forceinline__ void list_insert(float (&ls)[KC], int (&lj)[KC], floa
     lj[0] = here0 ? j : lj[0];
 }
 
-// Absorb a batch of eight (bs ascending, +inf where empty) of which at most
-// nq per lane are finite (nq warp-uniform): one or two insertions cost less
-// than the merging network, more take the network.
-template <int KC>
-__device__ __forceinline__ void list_absorb8(float (&ls)[KC], int (&lj)[KC], const float (&bs)[8],
-                                             const int (&bj)[8], int nq) {
-    if (nq <= 2) {
-        list_insert<KC>(ls, lj, bs[0], bj[0]);
-        if (nq == 2) list_insert<KC>(ls, lj, bs[1], bj[1]);
-    } else {
-        topk::merge8<KC>(ls, lj, bs, bj);
-    }
-}
-
 template <int KC, bool MASK, bool F8 = false>
 __global__ void __launch_bounds__(KC <= 2 * CAPB ? TC_THREADS_MAX : 64 + 32 * 4, 1)
 knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -512,10 +498,12 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                         bs[c] = sv;
                         bj[c] = jv;
                     }
-                    nq = __reduce_max_sync(0xffffffffu, nq);
-                    if (nq == 0) continue;
+                    // one merging network for any number of entries: a
+                    // single-insertion shortcut beside it measured slower
+                    // (instruction-fetch stalls from the larger loop body)
+                    if (__reduce_max_sync(0xffffffffu, nq) == 0) continue;
                     topk::sort8(bs, bj);
-                    list_absorb8<KC>(ls, lj, bs, bj, nq);
+                    topk::merge8<KC>(ls, lj, bs, bj);
                 }
             } else {
                 for (int q = 0; q < mx; ++q) {
@@ -659,9 +647,8 @@ knn_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ C
                             bj[c] = in ? stg_j[(p0 + c) * BM + row] : -1;
                             nq += in;
                         }
-                        nq = __reduce_max_sync(0xffffffffu, nq);
-                        if (nq == 0) break;
-                        list_absorb8<KC>(ls, lj, bs, bj, nq);
+                        if (__reduce_max_sync(0xffffffffu, nq) == 0) break;
+                        topk::merge8<KC>(ls, lj, bs, bj);
                     }
                 } else {
                     for (int p = 0; p < KC; ++p) {   // ascending: stop at the first that cannot enter
