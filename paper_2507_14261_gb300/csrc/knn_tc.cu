@@ -21,10 +21,14 @@
 //              tcgen05.ld, forms s = ny_j - 2 acc (key norms read from L1),
 //              and stages the columns that beat its row's threshold in
 //              shared memory. When any lane's stage is nearly full the warp
-//              merges all stages into per-row sorted register lists of the
-//              KC smallest scores (lanes insert in parallel), then tightens
-//              the threshold to the KC-th score (the smaller of the two
-//              halves' when E = 8); the halves' lists merge at the end.
+//              merges the stages, eight candidates at a time (a sorting
+//              network, then a bitonic merge: topk_merge.cuh), into per-row
+//              sorted register lists of the KC smallest scores, then
+//              tightens the threshold to the KC-th score (the smaller of the
+//              two halves' when E = 8); the halves' lists merge at the end.
+// Work items: a query tile with its key tiles (all of them, or a pruned
+// list); a long pruned list is split into parts run by separate CTAs, whose
+// rows' lists split_merge_kernel combines.
 // Nothing of the n x n score matrix leaves the SM. Every mbarrier wait is
 // bounded in time; on expiry the CTA sets an error bit, drains its own
 // copies and MMAs, frees its TMEM and returns.
